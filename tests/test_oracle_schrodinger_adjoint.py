@@ -1,0 +1,168 @@
+"""Pins of the oracle's Schrodinger eigenpairs, capacitance and adjoint (no GPU).
+
+- Particle in a box: for Q1 elements with consistent mass on a uniform box
+  with psi = 0 walls the discrete spectrum is known in closed form,
+  lambda = sum_d (hbar^2/2m_d) (6/h_d^2) (1 - cos t_d)/(2 + cos t_d),
+  t_d = k_d pi h_d / L_d (the paper's 2D/3D infinite-well check, Sec. II.B).
+- Harmonic oscillator: E_0 = (3/2) hbar omega with O(h^2) convergence (the
+  paper's parabolic-well check, Sec. II.B).
+- Appendix B: the paper's triangular-well formula gives E_1 = 7.11 meV at
+  F = 8.256e6 V/m after the 25.003 meV shift (Sec. III).
+- Adjoint sensitivities against central finite differences of full solves.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import capacitance as C
+from oracle import fem, physics
+from oracle import schrodinger as S
+from oracle.mesh import Mesh
+from oracle.poisson import PoissonProblem
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _box(L, n):
+    dev = dict(Lx=L[0], Ly=L[1], nx=n[0], ny=n[1], layers=[dict(material=0, thickness=L[2], n=n[2])],
+               materials=[dict(W.SI)], gates=[], bottom_ohmic=0, dots=[],
+               subdomain=dict(i0=0, i1=n[0], j0=0, j1=n[1], k0=0, k1=n[2]), bias=dict(T=4.0, V_gate=[]))
+    return Mesh(dev)
+
+
+def test_box_spectrum_closed_form():
+    L, n, me = (20.0, 16.0, 12.0), (10, 8, 6), (0.19, 0.3, 0.98)
+    m = _box(L, n)
+    sel, inter = m.subdomain_elements(), m.subdomain_interior_nodes()
+    H, M, _ = S.operators(m, sel, inter, me, np.zeros((sel.sum(), 8)))
+    E, X = S.lowest_eigenpairs(H, M, 8, sigma=-1.0)
+    h2m = physics.hbar2_over_2m0()
+    ev = []
+    for ks in itertools.product(range(1, n[0]), range(1, n[1]), range(1, n[2])):
+        lam = 0.0
+        for k, Ld, nd, md in zip(ks, L, n, me):
+            h = Ld / nd
+            t = k * math.pi * h / Ld
+            lam += h2m / md * 6.0 / h ** 2 * (1 - math.cos(t)) / (2 + math.cos(t))
+        ev.append(lam)
+    ev = np.sort(ev)[:8]
+    assert np.max(np.abs(E - ev) / ev) < 1e-10
+    # M-orthonormal eigenvectors
+    G = X.T @ (M @ X)
+    assert np.max(np.abs(G - np.eye(8))) < 1e-10
+    # a constant potential shifts the whole spectrum
+    H2, M2, _ = S.operators(m, sel, inter, me, np.full((sel.sum(), 8), -0.2))
+    E2, _ = S.lowest_eigenpairs(H2, M2, 8, sigma=-1.0)
+    assert np.max(np.abs(E2 - (E - 0.2))) < 1e-12
+
+
+def _oscillator(n, hw=0.01, m_rel=0.19):
+    h2m = physics.hbar2_over_2m0() / m_rel
+    ell2 = 2.0 * h2m / hw  # hbar/(m omega) in nm^2
+    L = 10.0 * math.sqrt(ell2)
+    mesh = _box((L, L, L), (n, n, n))
+    sel, inter = mesh.subdomain_elements(), mesh.subdomain_interior_nodes()
+    xq = np.einsum("qa,eai->eqi", fem.NQ, mesh.elem_coords)
+    r2 = np.sum((xq - L / 2) ** 2, axis=2)
+    Vq = hw ** 2 * r2 / (4.0 * h2m)  # (1/2) m omega^2 r^2
+    H, M, _ = S.operators(mesh, sel, inter, (m_rel,) * 3, Vq)
+    E, _ = S.lowest_eigenpairs(H, M, 4, sigma=-0.01)
+    return E
+
+
+def test_harmonic_oscillator_convergence():
+    hw = 0.01
+    Es = [_oscillator(n, hw) for n in (12, 24)]
+    err = [abs(E[0] - 1.5 * hw) for E in Es]
+    rate = math.log2(err[0] / err[1])
+    assert abs(rate - 2.0) < 0.15, rate
+    assert err[1] < 0.02 * hw
+    # first excited level is threefold degenerate at 2.5 hbar omega
+    assert np.max(np.abs(Es[1][1:4] - 2.5 * hw)) < 0.05 * hw
+    assert np.max(Es[1][1:4]) - np.min(Es[1][1:4]) < 1e-9 * hw
+
+
+def test_appendix_b_triangular_well_e1():
+    # E_i = (hbar^2 q^2 F^2 / (2 m_l))^(1/3) [3 pi/2 (i - 1/4)]^(2/3), shifted down by 25.003 meV
+    F = GOLD["triangular_well_field_V_per_m"]["value"] * 1e-9  # V/nm
+    shift = GOLD["triangular_well_shift_eV"]["value"]
+    h2m_l = physics.hbar2_over_2m0() / W.SI["m_l"]
+    E1 = (h2m_l * F ** 2) ** (1.0 / 3.0) * (1.5 * math.pi * 0.75) ** (2.0 / 3.0) - shift
+    assert abs(E1 * 1e3 - GOLD["triangular_well_E1_meV"]["value"]) < 0.015
+    # the transverse mass would miss it by more than 2 meV: the constants are pinned
+    h2m_t = physics.hbar2_over_2m0() / W.SI["m_t"]
+    E1t = (h2m_t * F ** 2) ** (1.0 / 3.0) * (1.5 * math.pi * 0.75) ** (2.0 / 3.0) - shift
+    assert abs(E1t * 1e3 - 7.11) > 2.0
+
+
+@pytest.fixture(scope="module")
+def dqd():
+    dev = W.five_gate_device(n=(24, 24, 16), T=4.0)
+    P = PoissonProblem(dev)
+    phi, rep = P.solve()
+    assert rep["converged"]
+    return dev, P, phi
+
+
+def test_dots_hold_electrons(dqd):
+    dev, P, phi = dqd
+    N = C.electron_counts(P, phi)
+    assert np.all(N > 0.1) and np.all(N < 100.0)
+
+
+def test_adjoint_gate_sensitivity_vs_central_fd(dqd):
+    dev, P, phi = dqd
+    dN_dV, _ = C.adjoint(P, phi)
+    h = 1e-4
+    for g in range(len(dev["bias"]["V_gate"])):
+        Ns = []
+        for s in (+1, -1):
+            b = dict(dev["bias"])
+            b["V_gate"] = list(b["V_gate"])
+            b["V_gate"][g] += s * h
+            Pg = PoissonProblem(dev, bias=b)
+            pg, rep = Pg.solve(phi0=phi)
+            assert rep["converged"]
+            Ns.append(C.electron_counts(Pg, pg))
+        fd = (Ns[0] - Ns[1]) / (2 * h)
+        scale = np.max(np.abs(dN_dV))
+        assert np.max(np.abs(fd - dN_dV[:, g])) < 1e-5 * scale, (g, fd, dN_dV[:, g])
+    # plungers load their own dot most strongly
+    assert dN_dV[0, 1] > dN_dV[0, 3] and dN_dV[1, 3] > dN_dV[1, 1]
+
+
+def test_adjoint_fixed_charge_gradient_vs_fd(dqd):
+    dev, P, phi = dqd
+    theta = np.array(W.interface_fixed_charge(dev, seed=5))
+    P0 = PoissonProblem(dev, fixed_charge=theta)
+    ph0, rep = P0.solve(phi0=phi)
+    assert rep["converged"]
+    _, dN_dth = C.adjoint(P0, ph0)
+    rng = np.random.default_rng(1)
+    eps = 1e-4 * np.max(np.abs(theta))
+    for _ in range(2):
+        d = rng.standard_normal(theta.size) * (theta != 0)
+        Ns = []
+        for s in (+1, -1):
+            Ps = PoissonProblem(dev, fixed_charge=theta + s * eps * d)
+            ps, rep = Ps.solve(phi0=ph0)
+            assert rep["converged"]
+            Ns.append(C.electron_counts(Ps, ps))
+        fd = (Ns[0] - Ns[1]) / (2 * eps)
+        ad = dN_dth @ d
+        assert np.max(np.abs(fd - ad)) < 1e-5 * np.max(np.abs(ad)), (fd, ad)
+
+
+def test_fd_capacitance_agrees_with_adjoint(dqd):
+    dev, P, phi = dqd
+    dN_dV, _ = C.adjoint(P, phi)
+    Cf, N1, N2 = C.fd_capacitance(dev, gate=1, dV=GOLD["capacitance_dV_V"]["value"], phi0=phi)
+    # forward difference with dV = 0.01 V: first-order agreement with q dN/dV
+    Ca = C.Q_AF * dN_dV[:, 1]
+    assert np.all(Cf > 0)
+    assert np.max(np.abs(Cf - Ca) / np.abs(Ca)) < 0.1
