@@ -1,0 +1,254 @@
+/*
+ * qcad.h - C ABI of libqcad, a GB300 (sm_103a) finite-element solver for the
+ * semiclassical nonlinear Poisson equation and the effective-mass Schrodinger
+ * equation of silicon quantum-dot devices, after Gao et al., "QCAD Simulation
+ * and Optimization of Semiconductor Quantum Dots" (arXiv:1403.7561).
+ *
+ * Units everywhere: length nm, potential V, energy eV, density nm^-3,
+ * temperature K, permittivity relative to eps0, effective masses in m0.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Device pointers must be CUDA device memory of the device the mesh was
+ *   created on. Host pointers are ordinary host memory. The caller owns every
+ *   pointer it passes; the library owns everything inside a qcad_mesh_t.
+ * - All GPU work of a mesh runs on the stream given at creation. For NULL the
+ *   mesh creates its own blocking stream (ordered with the legacy default
+ *   stream, and capturable into CUDA graphs). Every call returns after that
+ *   stream has been synchronized, because several calls return host outputs.
+ * - Node index n = i + (nx+1)*(j + (ny+1)*k); element index
+ *   e = i + nx*(j + ny*k) (x fastest, k counts element layers upward from z=0).
+ * - On QCAD_ERR_INVALID_ARG no output is touched. On any error a message is
+ *   available from qcad_last_error() (thread-local, valid until the next call
+ *   on the same thread). No C++ exception crosses this boundary.
+ */
+#ifndef QCAD_H
+#define QCAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QCAD_OK = 0,
+  QCAD_ERR_INVALID_ARG = 1,   /* bad size, pointer or option; outputs untouched */
+  QCAD_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  QCAD_ERR_OOM = 3,           /* device allocation failed */
+  QCAD_ERR_NOT_CONVERGED = 4, /* iteration limit reached; outputs hold the last iterate */
+  QCAD_ERR_NONFINITE = 5,     /* a NaN/Inf appeared; outputs undefined */
+  QCAD_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} qcad_status;
+
+/* Material parameters (Sec. II.A: eps_s, chi, E_g of Eq. EcEv_phi; the DOS
+ * masses of Eq. EffectiveMass; dopants and ionization energies/degeneracies of
+ * Eq. FinalIonization). A device holds at most one semiconductor material. */
+typedef struct {
+  double eps_r;        /* relative static permittivity */
+  double chi;          /* electron affinity, eV */
+  double Eg;           /* band gap, eV */
+  int semiconductor;   /* 1: carries n, p and dopant charge; 0: insulator (rho = 0) */
+  double m_l, m_t;     /* electron longitudinal / transverse masses, m0 */
+  double m_hh, m_lh;   /* heavy / light hole masses, m0 */
+  double N_A, N_D;     /* acceptor / donor concentrations, nm^-3 */
+  double E_a, E_d;     /* acceptor / donor ionization energies, eV */
+  double g_A, g_D;     /* ground-state degeneracies (paper: 4 and 2) */
+} qcad_material;
+
+typedef struct { double x0, x1, y0, y1; } qcad_rect;          /* closed rectangle on the top face */
+typedef struct { double x0, x1, y0, y1, z0, z1; } qcad_box;   /* element-centroid box */
+
+/* Layered box device on a structured Q1 hexahedral mesh: uniform spacing in x
+ * and y, uniform within each z layer group (bottom to top). Gates are
+ * Dirichlet patches on the top face z = Lz; the bottom face is an Ohmic
+ * contact when bottom_ohmic is set; every other boundary is natural Neumann
+ * (Sec. II.A.4). Dots are the semiconductor elements whose centroid lies in a
+ * box (the paper's quantum region, Sec. III). The Schrodinger subdomain is the
+ * element block [sub[0],sub[1]) x [sub[2],sub[3]) x [sub[4],sub[5]) with
+ * psi = 0 on its boundary (Sec. II.B). All arrays are host memory, read only
+ * during qcad_mesh_create. */
+typedef struct {
+  double Lx, Ly;
+  int nx, ny;
+  int n_layers;
+  const int* layer_n;              /* [n_layers] element layers per group */
+  const double* layer_thickness;   /* [n_layers] nm */
+  const int* layer_material;       /* [n_layers] index into materials */
+  int n_materials;
+  const qcad_material* materials;  /* [n_materials] */
+  int n_gates;
+  const qcad_rect* gates;          /* [n_gates]; a node in several gates belongs to the first */
+  int gate_work_function_set;      /* 0: Phi_m = q phi_ref, so phi_ins = V_g (Eq. ContOnIns) */
+  double gate_work_function;       /* Phi_m in eV when gate_work_function_set */
+  int bottom_ohmic;
+  int n_dots;                      /* at most QCAD_MAX_DOTS */
+  const qcad_box* dots;
+  int has_subdomain;
+  int sub[6];
+} qcad_device;
+
+#define QCAD_MAX_DOTS 8
+#define QCAD_MAX_GATES 32
+
+typedef struct qcad_mesh_s* qcad_mesh_t;
+
+/* Bias point (Sec. II.A.2, II.A.4): E_F = -q V_sub in the semiconductor; gate
+ * Dirichlet values by Eq. ContOnIns; the Ohmic value by the contact formulas
+ * of Sec. II.A.4 for the chosen statistics (0 MB, Eq. MBstatistics; 1 FD,
+ * Eq. FDstatistics with Eq. FDIntApprox) and ionization model. */
+typedef struct {
+  double T;
+  int n_gates;
+  const double* V_gate;            /* host [n_gates], V */
+  double V_sub;
+  int statistics;                  /* 0 MB, 1 FD */
+  int incomplete_ionization;       /* 0 complete, 1 Eq. FinalIonization */
+} qcad_bias;
+
+typedef struct {
+  int precision;          /* 0: FP64 throughout; 1: mixed (FP32 Krylov operator, vectors and
+                             preconditioner; FP64 residual, reductions and Newton update) */
+  double newton_tol_R;    /* stop when max |R_i| over free nodes < this (V*nm) ... */
+  double newton_tol_dphi; /* ... and the last max |alpha delta| < this (V) */
+  int max_newton;
+  int max_krylov;         /* per linear solve */
+  int cheb_degree;        /* Chebyshev-Jacobi preconditioner degree; 1 = Jacobi; 0 = autotuned */
+  int warm_start;         /* 1: phi holds the initial guess; 0: Laplace solve with the contact values */
+  int linear;             /* 1: rho = 0 (dielectric-only solve) */
+} qcad_solver_opts;
+
+typedef struct {
+  int newton_iters;
+  int krylov_iters_total;
+  int applies_total;      /* operator applies issued (Krylov + preconditioner + power steps) */
+  double final_res_inf;
+  double final_dphi_inf;
+  double seconds;         /* host wall clock of the call */
+  int status_detail;
+} qcad_solve_report;
+
+/* Builds the mesh, its per-axis geometry tables, contact masks and region
+ * tables on the current CUDA device (Sec. I: FE mesh with material blocks).
+ * cuda_stream: cudaStream_t or NULL. On success *out owns device memory
+ * until qcad_mesh_destroy. Errors: INVALID_ARG (sizes, layers, pointers),
+ * OOM, CUDA. */
+qcad_status qcad_mesh_create(const qcad_device* dev, void* cuda_stream, qcad_mesh_t* out);
+void qcad_mesh_destroy(qcad_mesh_t m);
+qcad_status qcad_mesh_info(qcad_mesh_t m, int64_t* n_nodes, int64_t* n_elems, int* n_gates,
+                           int* n_dots, int64_t* n_sub_dof);
+
+/* Contact values (Sec. II.A.4): writes the Dirichlet value of every Dirichlet
+ * node into phi (device, n_nodes FP64) and leaves free nodes untouched.
+ * Returns the gate (Eq. ContOnIns) and Ohmic (Eqs. PotBC4MBCompIon,
+ * PotBC4MBIncompIon with Eq. Yval4MBIncompIon or Eq. ApproxLogTerms below
+ * 50 K, PotBC4FDCompIon with Eq. FDintInverse) values in host arrays
+ * phi_gate [n_gates] and *phi_ohmic (either may be NULL). */
+qcad_status qcad_contact_values(qcad_mesh_t m, const qcad_bias* b, double* phi,
+                                double* phi_gate, double* phi_ohmic);
+
+/* Nonlinear Poisson residual (Sec. II.A.3, Eq. PoissonWeakForm, scaled by
+ * 1/eps0): R_i = sum_e int eps_r grad phi.grad N_i - (q/eps0) int rho(phi) N_i
+ * on free nodes, 0 on Dirichlet nodes; rho = p - n + ND+ - NA- (+ fixed charge)
+ * at the 2x2x2 Gauss points. phi: device [n_nodes] (Dirichlet entries are used
+ * as given). R: device [n_nodes]. diag: device [n_nodes] diagonal of the
+ * Jacobian (1 on Dirichlet rows) or NULL. fixed_charge_elem: device [n_elems]
+ * nm^-3 or NULL. stats: host [2] = {max |R_i|, sum R_i^2} or NULL. */
+qcad_status qcad_poisson_residual(qcad_mesh_t m, const qcad_bias* b, const double* fixed_charge_elem,
+                                  const double* phi, double* R, double* diag, double* stats);
+
+/* Jacobian-vector product of the residual above (the Newton Jacobian of
+ * Sec. II.C.2, differentiated by hand): y = J(phi) v on free rows with J =
+ * K - (q/eps0) int rho'(phi) N_a N_b, and y_i = v_i on Dirichlet rows (v is
+ * read as zero at Dirichlet nodes). precision 0: FP64 apply; 1: the FP32
+ * apply used by the mixed solver (inputs and outputs still FP64 here).
+ * phi, v, y: device [n_nodes]. */
+qcad_status qcad_poisson_jv(qcad_mesh_t m, const qcad_bias* b, const double* phi, const double* v,
+                            double* y, int precision);
+
+/* Newton solve of the nonlinear Poisson equation (Sec. II.A; solved by a
+ * Newton solver in the paper, Sec. II.A.3) with a Chebyshev-Jacobi PCG linear
+ * solver, to the tolerances in o. phi: device [n_nodes]; input guess when
+ * o->warm_start, output solution (Dirichlet entries set to contact values).
+ * fixed_charge_elem: device [n_elems] or NULL. rep: host or NULL.
+ * Errors: NOT_CONVERGED (phi holds the last iterate, rep filled),
+ * NONFINITE, INVALID_ARG, CUDA. */
+qcad_status qcad_poisson_solve(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o,
+                               const double* fixed_charge_elem, double* phi, qcad_solve_report* rep);
+
+/* Integrated electron count N_d = int_dot n dOmega of every dot (Sec. III,
+ * capacitance equation), 2x2x2 Gauss quadrature. phi: device; N: host [n_dots]. */
+qcad_status qcad_electron_counts(qcad_mesh_t m, const qcad_bias* b, const double* fixed_charge_elem,
+                                 const double* phi, double* N);
+
+/* Dot-to-gate capacitances by the paper's finite difference (Sec. III):
+ * C_d = q (N_d(V_g + dV) - N_d(V_g)) / dV for gate `gate`, in aF. Two Newton
+ * solves; the second is warm-started from the first. phi: device [n_nodes]
+ * scratch/output (the solution at V_g + dV on return) or NULL (library
+ * scratch). C_aF: host [n_dots]. */
+qcad_status qcad_capacitance(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int gate,
+                             double dV, const double* fixed_charge_elem, double* phi, double* C_aF);
+
+/* Adjoint sensitivities of the dot electron counts at a converged phi:
+ * J lambda_d = dN_d/dphi on free rows (J symmetric), then
+ * dN_d/dV_g = dN_d/dphi_D . e_g - lambda_d . (J_fD e_g) and
+ * dN_d/dtheta_e = (q/eps0) sum_{a in e, free} lambda_{d,a} int_e N_a.
+ * q dN_d/dV_g is the capacitance of Sec. III in the limit dV -> 0.
+ * phi: device [n_nodes] converged solution. dN_dV: host [n_dots * n_gates]
+ * (row-major, 1/V). dN_dq: device [n_dots * n_elems] (electrons per nm^-3)
+ * or NULL. o->precision selects the linear solver precision. */
+qcad_status qcad_adjoint(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                         const double* fixed_charge_elem, double* dN_dV, double* dN_dq);
+
+/* Effective-mass Schrodinger operators on the subdomain (Sec. II.B, Eq.
+ * SchrodEqnWeakForm; diagonal mass tensor of Eq. Schrodinger3D; potential of
+ * Eq. SchrodPotEnergy without V_xc): for the nvec columns of X (device,
+ * n_sub_dof x nvec, column-major, interior subdomain nodes in node order),
+ * HX = H X and MX = M X (either may be NULL). phi: device [n_nodes].
+ * m_eff: host [3] (m_x, m_y, m_z) in m0. precision 0 FP64, 1 FP32 apply. */
+qcad_status qcad_schrodinger_apply(qcad_mesh_t m, const qcad_bias* b, const double* phi, const double* m_eff,
+                                   int nvec, const double* X, double* HX, double* MX, int precision);
+
+/* Lowest nev eigenpairs of H psi = E M psi on the subdomain by LOBPCG with a
+ * Jacobi preconditioner and FP64 Rayleigh-Ritz (the paper uses an Anasazi
+ * eigensolver, Sec. II.B). phi: device [n_nodes]. evals: host [nev], eV,
+ * ascending. evecs: device [n_sub_dof x nev] column-major, M-orthonormal, or
+ * NULL. tol: relative residual ||H x - E M x|| / (|E| ||M x||) per pair.
+ * Errors: NOT_CONVERGED (best pairs returned), INVALID_ARG (no subdomain,
+ * nev < 1 or nev > 16). */
+qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const double* phi, int nev,
+                                  const double* m_eff, double tol, double* evals, double* evecs,
+                                  qcad_solve_report* rep);
+
+/* Batched form: n independent meshes solved together (each with its own
+ * bias), the Krylov iterations of all instances advanced by one persistent
+ * kernel launch per step under a captured CUDA graph. ms, bs, phis: host
+ * arrays of n entries (phis[i] device pointers). reps: host [n] or NULL.
+ * o->precision must be 1 (mixed). */
+qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs,
+                                     const qcad_solver_opts* o, double* const* phis, qcad_solve_report* reps);
+
+/* Kernel timing: with profiling enabled, every launch of the timed kernel
+ * classes on the mesh stream (including those inside captured CUDA graphs) is
+ * bracketed by CUDA events and its duration accumulated. Classes: 0 FP32
+ * Jacobian apply (PCG), 1 FP64 Jacobian apply (PCG), 2 FP32 PCG update,
+ * 3 FP64 PCG update, 4 FP64 residual, 5 Schrodinger H/M apply.
+ * qcad_profile_read returns the launch count and total milliseconds of one
+ * class; qcad_profile_reset clears the counters. Profiling is off by default. */
+qcad_status qcad_profile_enable(qcad_mesh_t m, int enable);
+qcad_status qcad_profile_reset(qcad_mesh_t m);
+qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches, double* total_ms);
+
+/* Launch configuration of the z-marching kernels (tile rows 4, 8 or 16 and
+ * z-chunk length), per kernel family: 0 residual, 1 FP64 apply, 2 FP32 apply.
+ * The autotuner sets these; the defaults are 8 and 16. */
+qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk);
+qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk,
+                          float* best_ms);
+
+const char* qcad_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCAD_H */

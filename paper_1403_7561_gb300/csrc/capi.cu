@@ -1,0 +1,246 @@
+// C ABI of libqcad (include/qcad.h): argument checks, error translation and
+// the launch-configuration autotuner. No C++ exception crosses this boundary.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mesh.h"
+
+namespace qcad {
+void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out);
+Phys make_phys(const qcad_mesh_s* m, const qcad_bias* b);
+void set_contacts(qcad_mesh_s* m, const qcad_bias* b, const Phys& P, double* phi, double* gate_vals, double* ohm_val);
+qcad_status poisson_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* theta,
+                          double* phi, qcad_solve_report* rep);
+qcad_status poisson_residual(qcad_mesh_s* m, const qcad_bias* b, const double* theta, const double* phi, double* R,
+                             double* diag, double* stats);
+qcad_status poisson_jv(qcad_mesh_s* m, const qcad_bias* b, const double* phi, const double* v, double* y,
+                       int precision);
+qcad_status electron_counts(qcad_mesh_s* m, const qcad_bias* b, const double* theta, const double* phi, double* N);
+qcad_status capacitance(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, int gate, double dV,
+                        const double* theta, double* phi, double* C_aF);
+qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                    const double* theta, double* dN_dV, double* dN_dq);
+qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* phi, const double* m_eff, int nvec,
+                              const double* X, double* HX, double* MX, int precision);
+qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
+                             double tol, double* evals, double* evecs, qcad_solve_report* rep);
+qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                                double* const* phis, qcad_solve_report* reps);
+qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk, float* best);
+}  // namespace qcad
+
+static thread_local std::string g_last_error;
+
+template <class F>
+static qcad_status guarded(F&& f) {
+  g_last_error.clear();
+  try {
+    return f();
+  } catch (const qcad::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return QCAD_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return QCAD_ERR_CUDA;
+  } catch (...) {
+    g_last_error = "unknown error";
+    return QCAD_ERR_CUDA;
+  }
+}
+
+static void need_mesh(qcad_mesh_t m) {
+  if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+  int dev = -1;
+  qcad::check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != m->device) throw qcad::Error(QCAD_ERR_INVALID_ARG, "current CUDA device differs from the mesh's device");
+}
+
+extern "C" {
+
+qcad_status qcad_mesh_create(const qcad_device* dev, void* cuda_stream, qcad_mesh_t* out) {
+  return guarded([&] {
+    qcad::mesh_create(dev, cuda_stream, out);
+    return QCAD_OK;
+  });
+}
+
+void qcad_mesh_destroy(qcad_mesh_t m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  delete m;
+}
+
+qcad_status qcad_mesh_info(qcad_mesh_t m, int64_t* n_nodes, int64_t* n_elems, int* n_gates, int* n_dots,
+                           int64_t* n_sub_dof) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    if (n_nodes) *n_nodes = m->n_nodes;
+    if (n_elems) *n_elems = m->n_elems;
+    if (n_gates) *n_gates = m->n_gates;
+    if (n_dots) *n_dots = m->dots.n;
+    if (n_sub_dof)
+      *n_sub_dof = m->has_sub ? (int64_t)(m->sub[1] - m->sub[0] - 1) * (m->sub[3] - m->sub[2] - 1) *
+                                    (m->sub[5] - m->sub[4] - 1)
+                              : 0;
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_contact_values(qcad_mesh_t m, const qcad_bias* b, double* phi, double* phi_gate,
+                                double* phi_ohmic) {
+  return guarded([&] {
+    need_mesh(m);
+    if (!b || b->n_gates != m->n_gates) throw qcad::Error(QCAD_ERR_INVALID_ARG, "bias does not match the mesh");
+    const qcad::Phys P = qcad::make_phys(m, b);
+    qcad::set_contacts(m, b, P, phi, phi_gate, phi_ohmic);
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_poisson_residual(qcad_mesh_t m, const qcad_bias* b, const double* fixed_charge_elem,
+                                  const double* phi, double* R, double* diag, double* stats) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::poisson_residual(m, b, fixed_charge_elem, phi, R, diag, stats);
+  });
+}
+
+qcad_status qcad_poisson_jv(qcad_mesh_t m, const qcad_bias* b, const double* phi, const double* v, double* y,
+                            int precision) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::poisson_jv(m, b, phi, v, y, precision);
+  });
+}
+
+qcad_status qcad_poisson_solve(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o,
+                               const double* fixed_charge_elem, double* phi, qcad_solve_report* rep) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::poisson_solve(m, b, o, fixed_charge_elem, phi, rep);
+  });
+}
+
+qcad_status qcad_electron_counts(qcad_mesh_t m, const qcad_bias* b, const double* fixed_charge_elem,
+                                 const double* phi, double* N) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::electron_counts(m, b, fixed_charge_elem, phi, N);
+  });
+}
+
+qcad_status qcad_capacitance(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int gate, double dV,
+                             const double* fixed_charge_elem, double* phi, double* C_aF) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::capacitance(m, b, o, gate, dV, fixed_charge_elem, phi, C_aF);
+  });
+}
+
+qcad_status qcad_adjoint(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                         const double* fixed_charge_elem, double* dN_dV, double* dN_dq) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::adjoint(m, b, o, phi, fixed_charge_elem, dN_dV, dN_dq);
+  });
+}
+
+qcad_status qcad_schrodinger_apply(qcad_mesh_t m, const qcad_bias* b, const double* phi, const double* m_eff,
+                                   int nvec, const double* X, double* HX, double* MX, int precision) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::schrodinger_apply(m, b, phi, m_eff, nvec, X, HX, MX, precision);
+  });
+}
+
+qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const double* phi, int nev,
+                                  const double* m_eff, double tol, double* evals, double* evecs,
+                                  qcad_solve_report* rep) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::schrodinger_eigs(m, b, phi, nev, m_eff, tol, evals, evecs, rep);
+  });
+}
+
+qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                                     double* const* phis, qcad_solve_report* reps) {
+  return guarded([&] { return qcad::poisson_solve_batch(n, ms, bs, o, phis, reps); });
+}
+
+qcad_status qcad_profile_enable(qcad_mesh_t m, int enable) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    m->prof.on = enable != 0;
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_profile_reset(qcad_mesh_t m) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    for (int c = 0; c < qcad::PROF_NCLASS; ++c) {
+      m->prof.launches[c] = 0;
+      m->prof.ms[c] = 0.0;
+    }
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches, double* total_ms) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    if (kernel_class < 0 || kernel_class >= qcad::PROF_NCLASS)
+      throw qcad::Error(QCAD_ERR_INVALID_ARG, "kernel class out of range");
+    if (launches) *launches = m->prof.launches[kernel_class];
+    if (total_ms) *total_ms = m->prof.ms[kernel_class];
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16)
+      throw qcad::Error(QCAD_ERR_INVALID_ARG, "tile_rows must be 4, 8 or 16");
+    if (z_chunk < 1 || z_chunk > 4096) throw qcad::Error(QCAD_ERR_INVALID_ARG, "z_chunk out of range");
+    qcad::LaunchCfg c;
+    c.by = tile_rows;
+    c.kchunk = z_chunk;
+    if (family == 0)
+      m->cfg_res = c;
+    else if (family == 1)
+      m->cfg64 = c;
+    else if (family == 2)
+      m->cfg32 = c;
+    else
+      throw qcad::Error(QCAD_ERR_INVALID_ARG, "family must be 0, 1 or 2");
+    // graphs captured with the old configuration are rebuilt on next use
+    m->graph64.key = nullptr;
+    m->graph32.key = nullptr;
+    return QCAD_OK;
+  });
+}
+
+qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk,
+                          float* best_ms) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::autotune(m, b, precision, tile_rows, z_chunk, best_ms);
+  });
+}
+
+const char* qcad_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+namespace qcad {
+// Message for a non-OK status returned without an exception (kept until the next call).
+void set_message(const std::string& msg) { g_last_error = msg; }
+}  // namespace qcad

@@ -1,0 +1,567 @@
+// Poisson kernels: FP64 nonlinear residual with fused Jacobian linearization,
+// matrix-free Jacobian apply (FP32 / FP64), fused preconditioned-CG kernels
+// and the Newton update. Sec. II.A (Eqs. Poisson, PoissonWeakForm,
+// MBstatistics, FDstatistics, FDIntApprox, FinalIonization).
+#include <cuda_runtime.h>
+
+#include "physics.cuh"
+#include "qcad_host.h"
+#include "qcad_internal.cuh"
+
+namespace qcad {
+
+template <class T>
+__device__ __forceinline__ long long elem_index(const Grid<T>& g, int i, int j, int k) {
+  return (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+}
+
+// Diagonal of the assembled stiffness from the 1D operator rows.
+template <class T>
+__device__ __forceinline__ T stiff_diag(const Grid<T>& g, int i, int j, int k) {
+  const T mxc = g.mx[3 * i + 1], kxc = g.kx[3 * i + 1];
+  const T myc = g.my[3 * j + 1], kyc = g.ky[3 * j + 1];
+  return kxc * myc * g.mzx[3 * k + 1] + mxc * kyc * g.mzy[3 * k + 1] + mxc * myc * g.kzz[3 * k + 1];
+}
+
+__device__ __forceinline__ int dot_of_element(const ResidualArgs& a, int i, int j, int k) {
+  const double xc = 0.5 * (a.xn[i] + a.xn[i + 1]);
+  const double yc = 0.5 * (a.yn[j] + a.yn[j + 1]);
+  const double zc = 0.5 * (a.zn[k] + a.zn[k + 1]);
+  for (int d = 0; d < a.dots.n; ++d) {
+    const double* B = a.dots.b[d];
+    if (xc >= B[0] && xc <= B[1] && yc >= B[2] && yc <= B[3] && zc >= B[4] && zc <= B[5]) return d;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Residual R(phi), Jacobian quadrature coefficients c_q = -(q/eps0) w|J| rho'(phi_q),
+// the Jacobian diagonal, norms of R and dot electron counts in one z-march (FP64).
+struct ResidualOp {
+  static constexpr int NF = 2;
+  static constexpr bool STIFF = true;
+  ResidualArgs a;
+  double acc_dot[QCAD_MAX_DOTS_K];
+  double acc_r2;
+  double acc_rmax;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int) {}
+  __device__ double load(const Grid<double>&, long long n, bool in, int, int, int) const {
+    return in ? a.phi[n] : 0.0;
+  }
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, double (*out)[8], bool own) {
+    const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
+    const long long e = elem_index(g, i, j, k);
+    const double th = a.theta ? a.theta[e] : 0.0;
+    double f[8], c[8];
+    if (a.layer_semi[k] && !a.linear) {
+      double pq[8];
+      tp_apply(v, pq, GaussConst<double>::a(), GaussConst<double>::b());
+      double nsum = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const Charge ch = charge_at(a.P, pq[q]);
+        f[q] = -a.P.qe * wdet * (ch.rho + th);
+        c[q] = -a.P.qe * wdet * ch.drho;
+        nsum += ch.n;
+      }
+      if (a.counts != nullptr) {
+        const int d = dot_of_element(a, i, j, k);
+        if (d >= 0 && own) acc_dot[d] += wdet * nsum;  // each element counted once
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        f[q] = -a.P.qe * wdet * th;
+        c[q] = 0.0;
+      }
+    }
+    tp_apply(f, out[0], GaussConst<double>::a(), GaussConst<double>::b());
+    const double a2 = GaussConst<double>::a() * GaussConst<double>::a();
+    const double b2 = GaussConst<double>::b() * GaussConst<double>::b();
+    tp_apply(c, out[1], a2, b2);
+    if (a.c64) {
+      double2* p = reinterpret_cast<double2*>(a.c64 + 8 * e);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) p[s] = make_double2(c[2 * s], c[2 * s + 1]);
+    }
+    if (a.c32) {
+      float4* p = reinterpret_cast<float4*>(a.c32 + 8 * e);
+      p[0] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+      p[1] = make_float4((float)c[4], (float)c[5], (float)c[6], (float)c[7]);
+    }
+  }
+  __device__ void node(const Grid<double>& g, long long n, int i, int j, int k, double, double stiff,
+                       const double* mass) {
+    double R = stiff + mass[0];
+    double dg = stiff_diag(g, i, j, k) + mass[1];
+    if (grid_is_dir(g, i, j, k)) {
+      R = 0.0;
+      dg = 1.0;
+    }
+    a.R[n] = R;
+    if (a.diag) a.diag[n] = dg;
+    if (a.dinv64) a.dinv64[n] = 1.0 / dg;
+    if (a.dinv32) a.dinv32[n] = (float)(1.0 / dg);
+    if (a.b64) a.b64[n] = -R;
+    if (a.b32) a.b32[n] = (float)(-R);
+    acc_r2 += R * R;
+    acc_rmax = fmax(acc_rmax, fabs(R));
+  }
+  __device__ void finish() {
+    if (a.stats) {
+      double s[1] = {acc_r2};
+      block_sum_atomic<1>(s, a.stats + 1);
+      block_max_atomic(acc_rmax, a.stats);
+    }
+    if (a.counts) {
+      double s[QCAD_MAX_DOTS_K];
+#pragma unroll
+      for (int d = 0; d < QCAD_MAX_DOTS_K; ++d) s[d] = acc_dot[d];
+      block_sum_atomic<QCAD_MAX_DOTS_K>(s, a.counts);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// y = J v: separable stiffness stencil plus the element quadrature-point mass
+// term with stored coefficients c; identity on Dirichlet rows unless raw.
+template <class T>
+struct ApplyOp {
+  static constexpr int NF = 1;
+  static constexpr bool STIFF = true;
+  ApplyArgs<T> a;
+  double acc;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int) {}
+  __device__ T load(const Grid<T>&, long long n, bool in, int, int, int) const { return in ? a.v[n] : T(0); }
+  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* v, T (*out)[8], bool) const {
+    T c[8];
+    load_c8<T>(a.c, elem_index(g, i, j, k), c);
+    qp_mass<T>(v, c, out[0]);
+  }
+  __device__ void node(const Grid<T>& g, long long n, int i, int j, int k, T vin, T stiff, const T* mass) {
+    T y = stiff + mass[0];
+    if (!a.raw && grid_is_dir(g, i, j, k)) y = vin;
+    a.y[n] = y;
+    acc += (double)vin * (double)y;
+  }
+  __device__ void finish() {
+    if (a.dot) {
+      double s[1] = {acc};
+      block_sum_atomic<1>(s, a.dot);
+    }
+  }
+};
+
+template <class T, class Op>
+static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s, int nvec = 1) {
+  switch (cfg.by) {
+    case 4: {
+      dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 4, cfg.kchunk, nvec);
+      march_kernel<T, 4, Op><<<grid, dim3(QCAD_BX, 4), 0, s>>>(g, op, cfg.kchunk);
+      break;
+    }
+    case 16: {
+      dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 16, cfg.kchunk, nvec);
+      march_kernel<T, 16, Op><<<grid, dim3(QCAD_BX, 16), 0, s>>>(g, op, cfg.kchunk);
+      break;
+    }
+    default: {
+      dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 8, cfg.kchunk, nvec);
+      march_kernel<T, 8, Op><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
+      break;
+    }
+  }
+}
+
+void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg cfg, cudaStream_t s) {
+  ResidualOp op = {};
+  op.a = args;
+  run_march<double>(g, op, cfg, s);
+}
+
+template <class T>
+void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  ApplyOp<T> op = {};
+  op.a = args;
+  run_march<T>(g, op, cfg, s);
+}
+template void launch_apply<float>(const Grid<float>&, const ApplyArgs<float>&, LaunchCfg, cudaStream_t);
+template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// dN_d/dphi nodal vector of one dot.
+struct CountGradOp {
+  static constexpr int NF = 1;
+  static constexpr bool STIFF = false;
+  ResidualArgs a;  // phi, layer_semi, coordinates, P, dots
+  int d;
+  double* out;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int) {}
+  __device__ double load(const Grid<double>&, long long n, bool in, int, int, int) const {
+    return in ? a.phi[n] : 0.0;
+  }
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, double (*o)[8], bool) const {
+    double f[8];
+    if (a.layer_semi[k] && dot_of_element(a, i, j, k) == d) {
+      const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
+      double pq[8];
+      tp_apply(v, pq, GaussConst<double>::a(), GaussConst<double>::b());
+#pragma unroll
+      for (int q = 0; q < 8; ++q) f[q] = wdet * charge_at(a.P, pq[q]).dn;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) f[q] = 0.0;
+    }
+    tp_apply(f, o[0], GaussConst<double>::a(), GaussConst<double>::b());
+  }
+  __device__ void node(const Grid<double>&, long long n, int, int, int, double, double, const double* mass) {
+    out[n] = mass[0];
+  }
+  __device__ void finish() {}
+};
+
+void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
+                           const double* xn, const double* yn, const double* zn, const Phys& P,
+                           const DotBoxes& dots, int d, double* out, LaunchCfg cfg, cudaStream_t s) {
+  CountGradOp op = {};
+  op.a.phi = phi;
+  op.a.layer_semi = layer_semi;
+  op.a.xn = xn;
+  op.a.yn = yn;
+  op.a.zn = zn;
+  op.a.P = P;
+  op.a.dots = dots;
+  op.d = d;
+  op.out = out;
+  run_march<double>(g, op, cfg, s);
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioned CG with device-resident scalars.
+//
+// Iteration t: apply kernel forms p_t = z_t + beta_t p_{t-1} while loading
+// (beta_t = rz_t / rz_{t-1}), writes p_t and Ap_t and accumulates p.Ap into
+// pAp[t%4]; update kernel forms alpha_t = rz_t / pAp_t, updates x, r, the
+// Jacobi-preconditioned z = D^-1 r, accumulates r.z and r.r into slot
+// (t+1)%4, and its last block advances t, tests convergence and clears the
+// slots the next iteration accumulates into.
+template <class T>
+struct PcgApplyOp {
+  static constexpr int NF = 1;
+  static constexpr bool STIFF = true;
+  PcgVecs<T> v;
+  PcgScalars* sc;
+  int t;
+  double beta;
+  double acc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {
+    t = sc->t;
+    beta = t > 0 ? sc->rz[t & 3] / sc->rz[(t - 1) & 3] : 0.0;
+  }
+  __device__ T load(const Grid<T>&, long long n, bool in, int, int, int) const {
+    if (!in) return T(0);
+    // p_{t-1} lives in p[(t+1)&1]; p_t is written to p[t&1], so halo reads never see new values
+    return t > 0 ? v.z[n] + (T)beta * v.p[(t + 1) & 1][n] : v.z[n];
+  }
+  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* x, T (*out)[8], bool) const {
+    T c[8];
+    load_c8<T>(v.c, elem_index(g, i, j, k), c);
+    qp_mass<T>(x, c, out[0]);
+  }
+  __device__ void node(const Grid<T>& g, long long n, int i, int j, int k, T pin, T stiff, const T* mass) {
+    T y = stiff + mass[0];
+    if (grid_is_dir(g, i, j, k)) y = pin;
+    v.p[t & 1][n] = pin;
+    v.Ap[n] = y;
+    acc += (double)pin * (double)y;
+  }
+  __device__ void finish() {
+    double s[1] = {acc};
+    block_sum_atomic<1>(s, &sc->pAp[t & 3]);
+  }
+};
+
+template <class T>
+void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  PcgApplyOp<T> op = {};
+  op.v = vecs;
+  op.sc = sc;
+  run_march<T>(g, op, cfg, s);
+}
+template void launch_pcg_apply<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t);
+template void launch_pcg_apply<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t);
+
+// Last block of a grid: returns true in exactly one block after all blocks' prior writes are visible.
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const unsigned int total = gridDim.x * gridDim.y * gridDim.z;
+    am_last = atomicAdd(counter, 1u) == total - 1;
+  }
+  __syncthreads();
+  return am_last;
+}
+
+__device__ __forceinline__ double ld_volatile(const double* p) { return *(volatile const double*)p; }
+
+constexpr int VEC_THREADS = 256;
+
+static int vec_blocks(long long n) {
+  long long b = (n + VEC_THREADS - 1) / VEC_THREADS;
+  const long long cap = 152 * 8;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(long long n, PcgVecs<T> v, PcgScalars* sc) {
+  double rz = 0.0, rr = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const T r = v.b[idx];
+    const T z = v.dinv[idx] * r;
+    v.x[idx] = T(0);
+    v.r[idx] = r;
+    v.z[idx] = z;
+    rz += (double)r * (double)z;
+    rr += (double)r * (double)r;
+  }
+  double s[2] = {rz, rr};
+  __shared__ double red[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double w = warp_sum(s[q]);
+    if (lane == 0) red[q][warp] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      double w = lane < (VEC_THREADS / 32) ? red[q][lane] : 0.0;
+      w = warp_sum(w);
+      if (lane == 0) atomicAdd(q == 0 ? &sc->rz[0] : &sc->rr[0], w);
+    }
+  }
+  if (last_block(&sc->counter) && threadIdx.x == 0) {
+    const double rr0 = ld_volatile(&sc->rr[0]);
+    const double rz0 = ld_volatile(&sc->rz[0]);
+    sc->rr0 = rr0;
+    sc->t = 0;
+    sc->iters = 0;
+    sc->pAp[0] = 0.0;
+    sc->rz[1] = 0.0;
+    sc->rr[1] = 0.0;
+    if (!(rr0 == rr0) || !(rz0 == rz0) || rr0 > 1e300) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+    } else if (rr0 == 0.0) {
+      sc->done = 1;
+    }
+    sc->counter = 0;
+  }
+}
+
+template <class T>
+void launch_pcg_init(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
+  pcg_init_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+}
+template void launch_pcg_init<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
+template void launch_pcg_init<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
+
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(long long n, PcgVecs<T> v, PcgScalars* sc) {
+  if (sc->done) return;
+  const int t = sc->t;
+  const double alpha_d = sc->rz[t & 3] / sc->pAp[t & 3];
+  const T alpha = (T)alpha_d;
+  double rz = 0.0, rr = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const T p = v.p[t & 1][idx];
+    const T ap = v.Ap[idx];
+    v.x[idx] += alpha * p;
+    const T r = v.r[idx] - alpha * ap;
+    const T z = v.dinv[idx] * r;
+    v.r[idx] = r;
+    v.z[idx] = z;
+    rz += (double)r * (double)z;
+    rr += (double)r * (double)r;
+  }
+  __shared__ double red[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  {
+    const double w0 = warp_sum(rz), w1 = warp_sum(rr);
+    if (lane == 0) {
+      red[0][warp] = w0;
+      red[1][warp] = w1;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double w0 = lane < (VEC_THREADS / 32) ? red[0][lane] : 0.0;
+    double w1 = lane < (VEC_THREADS / 32) ? red[1][lane] : 0.0;
+    w0 = warp_sum(w0);
+    w1 = warp_sum(w1);
+    if (lane == 0) {
+      atomicAdd(&sc->rz[(t + 1) & 3], w0);
+      atomicAdd(&sc->rr[(t + 1) & 3], w1);
+    }
+  }
+  if (last_block(&sc->counter) && threadIdx.x == 0) {
+    const double rr_new = ld_volatile(&sc->rr[(t + 1) & 3]);
+    const double rz_new = ld_volatile(&sc->rz[(t + 1) & 3]);
+    const int tn = t + 1;
+    sc->t = tn;
+    sc->pAp[tn & 3] = 0.0;
+    sc->rz[(tn + 1) & 3] = 0.0;
+    sc->rr[(tn + 1) & 3] = 0.0;
+    const bool bad = !(alpha_d == alpha_d) || !(rr_new == rr_new) || !(rz_new == rz_new) ||
+                     fabs(alpha_d) > 1e300 || alpha_d <= 0.0;
+    if (bad) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+      sc->iters = tn;
+    } else if (rr_new <= sc->tol2 * sc->rr0 || tn >= sc->maxit) {
+      sc->done = 1;
+      sc->iters = tn;
+    }
+    sc->counter = 0;
+  }
+}
+
+template <class T>
+void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
+  pcg_update_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+}
+template void launch_pcg_update<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
+template void launch_pcg_update<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS)
+newton_trial_kernel(long long n, const double* phi, const T* delta, double alpha, double* out, double* stats) {
+  double m = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double d = alpha * (double)delta[idx];
+    out[idx] = phi[idx] + d;
+    m = fmax(m, fabs(d));
+  }
+  const double w = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && w > 0.0) atomic_max_nonneg(stats, w);
+}
+
+template <class T>
+void launch_newton_trial(long long n, const double* phi, const T* delta, double alpha, double* phi_out,
+                         double* stats, cudaStream_t s) {
+  newton_trial_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, phi, delta, alpha, phi_out, stats);
+}
+template void launch_newton_trial<float>(long long, const double*, const float*, double, double*, double*, cudaStream_t);
+template void launch_newton_trial<double>(long long, const double*, const double*, double, double*, double*, cudaStream_t);
+
+__global__ void set_dirichlet_kernel(long long nxn, long long nyn, long long nzn, int bottom, double vb,
+                                     const signed char* gate_top, const double* vg, double* phi) {
+  const long long plane = nxn * nyn;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < plane;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (bottom) phi[idx] = vb;
+    const int gid = gate_top ? gate_top[idx] : -1;
+    if (gid >= 0) phi[(nzn - 1) * plane + idx] = vg[gid];
+  }
+}
+
+void launch_set_dirichlet(long long nxn, long long nyn, long long nzn, int bottom, double v_bottom,
+                          const signed char* gate_top, const double* v_gate, double* phi, cudaStream_t s) {
+  set_dirichlet_kernel<<<vec_blocks(nxn * nyn), VEC_THREADS, 0, s>>>(nxn, nyn, nzn, bottom, v_bottom, gate_top,
+                                                                    v_gate, phi);
+}
+
+__global__ void d2f_kernel(long long n, const double* a, float* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f2d_kernel(long long n, const float* a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+void launch_d2f(long long n, const double* a, float* b, cudaStream_t s) {
+  d2f_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
+}
+void launch_f2d(long long n, const float* a, double* b, cudaStream_t s) {
+  f2d_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
+}
+
+// theta gradient: out[e] = qe * (|e|/8) * sum of lam over the corners of e.
+__global__ void theta_gradient_kernel(int nx, int ny, int nz, const double* hx, const double* hy, const double* hz,
+                                      const double* lam, double qe, double* out) {
+  const long long ne = (long long)nx * ny * nz;
+  const long long nxn = nx + 1, plane = (long long)(nx + 1) * (ny + 1);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nx);
+    const int j = (int)((e / nx) % ny);
+    const int k = (int)(e / ((long long)nx * ny));
+    const long long n0 = i + nxn * j + plane * k;
+    const double s = lam[n0] + lam[n0 + 1] + lam[n0 + nxn] + lam[n0 + nxn + 1] + lam[n0 + plane] +
+                     lam[n0 + plane + 1] + lam[n0 + plane + nxn] + lam[n0 + plane + nxn + 1];
+    out[e] = qe * (hx[i] * hy[j] * hz[k] * 0.125) * s;
+  }
+}
+
+void launch_theta_gradient(int nx, int ny, int nz, const double* hx, const double* hy, const double* hz,
+                           const double* lam, double qe, double* out, cudaStream_t s) {
+  const long long ne = (long long)nx * ny * nz;
+  theta_gradient_kernel<<<vec_blocks(ne), VEC_THREADS, 0, s>>>(nx, ny, nz, hx, hy, hz, lam, qe, out);
+}
+
+}  // namespace qcad
+
+namespace qcad {
+
+// out[0] += sum_i a_i b_i (FP64 accumulation).
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) dot_kernel(long long n, const T* a, const T* b, double* out) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+}
+template <class T>
+void launch_dot(long long n, const T* a, const T* b, double* out, cudaStream_t s) {
+  dot_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b, out);
+}
+template void launch_dot<float>(long long, const float*, const float*, double*, cudaStream_t);
+template void launch_dot<double>(long long, const double*, const double*, double*, cudaStream_t);
+
+// y = a x + y with mixed types (FP64 y, T x).
+template <class T>
+__global__ void axpy_kernel(long long n, double a, const T* x, double* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * (double)x[i];
+}
+template <class T>
+void launch_axpy(long long n, double a, const T* x, double* y, cudaStream_t s) {
+  axpy_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, x, y);
+}
+template void launch_axpy<float>(long long, double, const float*, double*, cudaStream_t);
+template void launch_axpy<double>(long long, double, const double*, double*, cudaStream_t);
+
+// r = g - y (FP64), also writes the FP32 copy; zero on Dirichlet rows is inherited from g and y.
+__global__ void sub_kernel(long long n, const double* g, const double* y, double* r, float* r32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = g[i] - y[i];
+    r[i] = v;
+    if (r32) r32[i] = (float)v;
+  }
+}
+void launch_sub(long long n, const double* g, const double* y, double* r, float* r32, cudaStream_t s) {
+  sub_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, g, y, r, r32);
+}
+
+}  // namespace qcad

@@ -1,0 +1,142 @@
+// Host-side mesh object of libqcad and its helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/qcad.h"
+#include "qcad_dense.h"
+#include "qcad_host.h"
+#include "qcad_internal.cuh"
+
+namespace qcad {
+
+struct Error : std::runtime_error {
+  qcad_status code;
+  Error(qcad_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void check_cuda(cudaError_t e, const char* what);
+#define CK(x) ::qcad::check_cuda((x), #x)
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t b) {
+    if (bytes >= b && p) return;
+    release();
+    cudaError_t e = cudaMalloc(&p, b ? b : 16);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error(e == cudaErrorMemoryAllocation ? QCAD_ERR_OOM : QCAD_ERR_CUDA,
+                  std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    bytes = b;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Host description of one structured grid's 1D operator tables.
+struct GridTables {
+  std::vector<double> mx, kx, my, ky, mzx, mzy, kzz;
+};
+
+// Per-precision device copy of a grid's tables.
+template <class T>
+struct GridDev {
+  DevBuf mx, kx, my, ky, mzx, mzy, kzz, hx, hy, hz;
+  Grid<T> g{};
+};
+
+// Kernel classes timed with CUDA events when profiling is enabled.
+enum ProfClass { PROF_APPLY32 = 0, PROF_APPLY64, PROF_UPDATE32, PROF_UPDATE64, PROF_RESIDUAL, PROF_HM, PROF_NCLASS };
+
+struct Profiler {
+  bool on = false;
+  long long launches[PROF_NCLASS] = {};
+  double ms[PROF_NCLASS] = {};
+  std::vector<std::pair<cudaEvent_t, int>> pending_start;  // (start event, class) awaiting stop
+  std::vector<cudaEvent_t> pool;
+  struct Pair {
+    cudaEvent_t a, b;
+    int cls;
+  };
+  std::vector<Pair> open;
+  cudaEvent_t get();
+  void begin(int cls, cudaStream_t s, Pair& out);
+  void end(Pair& p, cudaStream_t s);
+  void harvest();  // after a stream sync: accumulate elapsed times of recorded pairs
+  ~Profiler();
+};
+
+template <class T>
+struct PcgBufs {
+  DevBuf x, r, z, p, Ap, b, dinv, c;
+};
+
+struct PcgGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void* key = nullptr;  // vector buffer the graph was captured with
+  int chunk = 0;
+  std::vector<Profiler::Pair> events;  // fixed event pairs inside the graph (profiling only)
+  ~PcgGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+}  // namespace qcad
+
+struct qcad_mesh_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  // geometry
+  int nx = 0, ny = 0, nz = 0;
+  long long nxn = 0, nyn = 0, nzn = 0, n_nodes = 0, n_elems = 0;
+  std::vector<double> xc, yc, zc;          // node coordinates
+  std::vector<double> hxv, hyv, hzv;       // element sizes
+  std::vector<int> layer_mat;              // per element layer
+  std::vector<qcad_material> mats;
+  int semi = -1;                           // index of the semiconductor material
+  std::vector<unsigned char> layer_semi;
+  std::vector<signed char> gate_top;       // gate id of top-plane nodes, -1 none
+  int n_gates = 0;
+  int wf_set = 0;
+  double wf = 0.0;
+  int bottom_ohmic = 1;
+  qcad::DotBoxes dots{};
+  int has_sub = 0;
+  int sub[6] = {0, 0, 0, 0, 0, 0};
+  // device geometry
+  qcad::GridDev<double> g64;
+  qcad::GridDev<float> g32;
+  qcad::DevBuf d_xn, d_yn, d_zn, d_layer_semi, d_gate_top, d_dir_top, d_vgate;
+  // solver state
+  qcad::PcgBufs<double> k64;
+  qcad::PcgBufs<float> k32;
+  qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
+  qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror
+  double* h_small = nullptr;               // pinned host scratch (64 doubles)
+  qcad::PcgGraph graph64, graph32;
+  qcad::LaunchCfg cfg_res, cfg64, cfg32;
+  qcad::Profiler prof;
+  // Schrodinger workspace
+  qcad::DevBuf s_mx, s_kx, s_my, s_ky, s_mzx, s_mzy, s_kzz, s_cV, s_dinv, s_interior, s_blocks, s_gram;
+  ~qcad_mesh_s();
+};

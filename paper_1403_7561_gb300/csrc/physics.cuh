@@ -1,0 +1,95 @@
+// Semiclassical charge density at a quadrature point (FP64), Sec. II.A.
+//
+// n = N_C F(eta_n), p = N_V F(eta_p) with eta_n = (E_F - E_C)/kT,
+// eta_p = (E_V - E_F)/kT, E_C = -q(phi - phi_ref) - chi, E_V = E_C - E_g
+// (Eqs. EcEv_phi, MBstatistics, FDstatistics); F is exp (MB) or the
+// Bednarczyk approximation of F_1/2 (Eq. FDIntApprox) with the paper's
+// replacement F(x) = e^x for x < -50. Ionized dopants follow Eq.
+// FinalIonization. Derivatives are those of the implemented expressions, so
+// the Jacobian is exact for the residual the solver uses.
+#pragma once
+#include "qcad_internal.cuh"
+
+namespace qcad {
+
+// F_1/2 and its derivative.
+__device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
+  if (x < -50.0) {
+    // exp underflows to exactly zero below -746, so skipping the call is exact
+    F = (x < -746.0) ? 0.0 : exp(x);
+    dF = F;
+    return;
+  }
+  const double xp1 = x + 1.0;
+  const double g = exp(-0.17 * xp1 * xp1);
+  const double x2 = x * x;
+  const double v = x2 * x2 + 50.0 + 33.6 * x * (1.0 - 0.68 * g);
+  const double dv = 4.0 * x2 * x + 33.6 * (1.0 - 0.68 * g) + 33.6 * 0.68 * 0.34 * x * xp1 * g;
+  const double emx = exp(-x);
+  const double C = 1.32934038817913702047;  // 3 sqrt(pi) / 4
+  const double vp = pow(v, -0.375);
+  const double D = emx + C * vp;
+  F = 1.0 / D;
+  const double dD = -emx - 0.375 * C * vp / v * dv;
+  dF = -dD * F * F;
+}
+
+// s = 1/(1 + g e^z) and 1 - s without overflow.
+__device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms) {
+  if (z > 0.0) {
+    const double e = exp(-z);
+    s = e / (e + g);
+    oms = g / (e + g);
+  } else {
+    const double e = exp(z);
+    s = 1.0 / (1.0 + g * e);
+    oms = g * e / (1.0 + g * e);
+  }
+}
+
+struct Charge {
+  double rho, drho, n, dn;
+};
+
+__device__ __forceinline__ Charge charge_at(const Phys& P, double phi) {
+  Charge c;
+  const double eta_n = (P.EF + phi - P.phi_ref + P.chi) / P.kT;
+  const double eta_p = (-phi + P.phi_ref - P.chi - P.Eg - P.EF) / P.kT;
+  double n, dn, p, dp;
+  if (P.statistics == 1) {
+    double F, dF;
+    fd_half_d(eta_n, F, dF);
+    n = P.NC * F;
+    dn = P.NC * dF / P.kT;
+    fd_half_d(eta_p, F, dF);
+    p = P.NV * F;
+    dp = -P.NV * dF / P.kT;
+  } else {
+    n = P.NC * exp(eta_n);
+    dn = n / P.kT;
+    p = P.NV * exp(eta_p);
+    dp = -p / P.kT;
+  }
+  double NDp = P.ND, dND = 0.0, NAm = P.NA, dNA = 0.0;
+  if (P.incomplete) {
+    if (P.ND != 0.0) {
+      double s, oms;
+      sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) / P.kT, P.gD, s, oms);
+      NDp = P.ND * s;
+      dND = -P.ND * s * oms / P.kT;
+    }
+    if (P.NA != 0.0) {
+      double s, oms;
+      sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) / P.kT, P.gA, s, oms);
+      NAm = P.NA * s;
+      dNA = P.NA * s * oms / P.kT;
+    }
+  }
+  c.rho = p - n + NDp - NAm;
+  c.drho = dp - dn + dND - dNA;
+  c.n = n;
+  c.dn = dn;
+  return c;
+}
+
+}  // namespace qcad

@@ -1,0 +1,47 @@
+// Schrodinger subdomain map, dense block kernels of LOBPCG and the small
+// host-side dense linear algebra of its Rayleigh-Ritz step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define QCAD_DENSE_MAXP 128
+
+namespace qcad {
+
+// Element block [i0, i0+nxs) x [j0, j0+nys) x [k0, k0+nzs) of a mesh with
+// nxn x nyn nodes per plane.
+struct SubdomainMap {
+  int i0, j0, k0;
+  int nxs, nys, nzs;   // subdomain elements per axis
+  long long nxn, nyn;  // global mesh nodes per axis (x, y)
+};
+
+template <class T>
+void launch_potential(const SubdomainMap& sm, const double* phi, double V0, const double* hx, const double* hy,
+                      const double* hz, T* cV, double* vmin, cudaStream_t s);
+void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
+                 int unpack, cudaStream_t s);
+void launch_gram(long long n, int p, int q, const double* A, long long lda, const double* B, long long ldb,
+                 double* G, cudaStream_t s);
+void launch_combine(long long n, int p, int q, const double* A, long long lda, const double* C, double* Y,
+                    long long ldy, double beta, cudaStream_t s);
+void launch_residual_block(long long n, int m, const double* HX, const double* MX, long long ld, const double* lam,
+                           const double* dinv, double* W, double* norms, cudaStream_t s);
+void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, double* X,
+                         cudaStream_t s);
+
+// Host dense routines on column-major n x n matrices (n <= QCAD_DENSE_MAXP).
+// Cholesky A = L L^T in place (lower); returns false if A is not numerically SPD.
+bool dense_cholesky(int n, double* A);
+// Symmetric eigen-decomposition by cyclic Jacobi rotations: A is destroyed,
+// w ascending eigenvalues, V column eigenvectors.
+void dense_sym_eig(int n, double* A, double* w, double* V);
+// Generalized symmetric-definite problem A x = lam B x via Cholesky of B:
+// returns false if B is not SPD. X is B-orthonormal.
+bool dense_gen_eig(int n, const double* A, const double* B, double* w, double* X);
+// Inverse of the lower Cholesky factor's transpose applied from the right:
+// returns Rinv (n x n, column-major) with B = L L^T and Rinv = L^-T.
+void dense_inv_lt(int n, const double* L, double* Rinv);
+
+}  // namespace qcad

@@ -1,0 +1,134 @@
+// Host-side interfaces between the kernel translation units and the solver
+// driver of libqcad (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qcad_internal.cuh"
+
+namespace qcad {
+
+// Device-resident scalars of one preconditioned CG solve. Slots are indexed
+// by iteration modulo 4 so that a kernel can accumulate the next dot product
+// while the current one is still being read; t is advanced by the last block
+// of the update kernel, so a captured sequence of kernels needs no host input.
+struct PcgScalars {
+  double rz[4];
+  double pAp[4];
+  double rr[4];
+  double rr0;
+  double tol2;
+  int t;
+  int done;
+  int iters;
+  int maxit;
+  unsigned int counter;
+  int nonfinite;
+};
+
+template <class T>
+struct PcgVecs {
+  T* x;
+  T* r;
+  T* z;
+  T* p[2];     // search direction, ping-ponged by iteration parity
+  T* Ap;
+  const T* b;
+  const T* dinv;
+  const T* c;   // element quadrature coefficients of the operator (8 per element)
+};
+
+struct ResidualArgs {
+  const double* phi;
+  const double* theta;       // fixed charge per element or null
+  double* R;
+  double* diag;              // or null
+  double* c64;               // or null
+  float* c32;                // or null
+  double* dinv64;            // or null
+  float* dinv32;             // or null
+  double* b64;               // -R or null
+  float* b32;                // -R or null
+  const unsigned char* layer_semi;
+  const double* xn;          // node coordinates (for dot membership)
+  const double* yn;
+  const double* zn;
+  Phys P;
+  DotBoxes dots;
+  double* counts;            // [n_dots] accumulated electron counts or null
+  double* stats;             // [2] {max|R| (as ordered bits), sum R^2} or null
+  int linear;
+};
+
+template <class T>
+struct ApplyArgs {
+  const T* v;
+  T* y;
+  const T* c;
+  double* dot;   // accumulate v.y (writer nodes) or null
+  int raw;       // 1: no identity override on Dirichlet rows (adjoint column sums)
+};
+
+struct LaunchCfg {
+  int by = 8;
+  int kchunk = 16;
+};
+
+void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg, cudaStream_t s);
+
+template <class T>
+void launch_apply(const Grid<T>& g, const ApplyArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+
+template <class T>
+void launch_pcg_init(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
+template <class T>
+void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
+template <class T>
+void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
+
+// phi_out = phi + alpha * delta on every node; stats[0] accumulates max |alpha delta| (ordered bits).
+template <class T>
+void launch_newton_trial(long long n, const double* phi, const T* delta, double alpha, double* phi_out,
+                         double* stats, cudaStream_t s);
+
+// Dirichlet values: bottom plane (if set) gets v_bottom, top-plane nodes with gate id >= 0 get v_gate[id].
+void launch_set_dirichlet(long long nxn, long long nyn, long long nzn, int bottom, double v_bottom,
+                          const signed char* gate_top, const double* v_gate, double* phi, cudaStream_t s);
+
+// Elementwise conversions.
+void launch_d2f(long long n, const double* a, float* b, cudaStream_t s);
+void launch_f2d(long long n, const float* a, double* b, cudaStream_t s);
+
+// dN_d/dphi as a nodal vector for dot d: sum over dot elements of w|J| n'(phi_q) N_a(q).
+void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
+                           const double* xn, const double* yn, const double* zn, const Phys& P,
+                           const DotBoxes& dots, int d, double* out, LaunchCfg cfg, cudaStream_t s);
+
+// theta-gradient of N_d: out[e] = qe * (|e|/8) * sum of lam over the 8 corners of e (lam is
+// zero on Dirichlet nodes); |e|/8 = int_e N_a exactly on a box.
+void launch_theta_gradient(int nx, int ny, int nz, const double* hx, const double* hy, const double* hz,
+                           const double* lam, double qe, double* out, cudaStream_t s);
+
+// Schrodinger operators on the subdomain grid (field 0: H, field 1: M).
+template <class T>
+struct HmArgs {
+  const T* x;      // nvec full-subdomain vectors, stride ldx
+  T* hx;           // or null
+  T* mx;           // or null
+  const T* cV;     // V * w|J| at the qp of every subdomain element
+  long long ld;    // vector stride (n_sub_nodes)
+  int nvec;
+};
+template <class T>
+void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+
+}  // namespace qcad
+
+namespace qcad {
+template <class T>
+void launch_dot(long long n, const T* a, const T* b, double* out, cudaStream_t s);
+template <class T>
+void launch_axpy(long long n, double a, const T* x, double* y, cudaStream_t s);
+void launch_sub(long long n, const double* g, const double* y, double* r, float* r32, cudaStream_t s);
+}  // namespace qcad

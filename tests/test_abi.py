@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point its header declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qcad.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qcad_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("qcad_build", os.path.join(ROOT, "paper_1403_7561_gb300", "build.py"))
+    B = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(B)
+    path, _ = B.build()
+    return path
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("qcad_mesh_create", "qcad_poisson_solve", "qcad_schrodinger_eigs", "qcad_capacitance",
+              "qcad_adjoint", "qcad_poisson_solve_batch", "qcad_last_error"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol(lib_path):
+    import paper_1403_7561_gb300 as q
+    for s in declared_symbols():
+        assert s in q.EXPORTED, s
+
+
+def test_invalid_mesh_is_rejected_without_gpu_work(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.qcad_mesh_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.qcad_mesh_create.restype = ctypes.c_int
+    lib.qcad_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    assert lib.qcad_mesh_create(None, None, ctypes.byref(out)) == 1  # QCAD_ERR_INVALID_ARG
+    assert b"null" in lib.qcad_last_error()

@@ -1,0 +1,176 @@
+"""GPU parity of the Poisson path against the FP64 oracle (run on a GB300).
+
+Every test calls the CUDA library through its C ABI (via the ctypes binding)
+and compares with the oracle on the same seeded inputs, element by element.
+Tolerances: potentials 1e-9 V (FP64 and mixed at the final FP64 residual
+1e-10); residual and FP64 Jacobian applies to 1e-12 relative to the largest
+entry; FP32 applies to 2e-6 relative (single precision).
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import capacitance as OC
+from oracle.poisson import PoissonProblem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1403_7561_gb300 as qcad
+    return qcad
+
+
+def dev_tensor(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+CASES = {
+    "mos_cap_16x16x32": lambda: W.get("mos_cap_16x16x32"),
+    "dqd_24x24x16_4K": lambda: W.five_gate_device(n=(24, 24, 16), T=4.0),
+    "dqd_37x33x21_0p5K": lambda: W.five_gate_device(n=(37, 33, 21), T=0.5),     # ragged tiles
+    "dqd_3x1x7_4K": lambda: W.five_gate_device(n=(3, 1, 7), T=4.0, with_subdomain=False),
+    "tiny_1x1x2": lambda: W.mos_capacitor(nx=1, ny=1, nz=2, n_ox=1),
+    "dqd_61x62x40_4K": lambda: W.five_gate_device(n=(61, 62, 40), T=4.0),        # several tiles, ragged
+}
+
+
+def perturbed_phi(P, seed, amp=0.01):
+    phi = P.initial_guess()
+    rng = np.random.default_rng(seed)
+    phi[P.free] += amp * rng.standard_normal(P.free.sum())
+    return phi
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_contact_values(q, name):
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    gv, ov = q.qcad_contact_values(m, dev["bias"], phi)
+    assert abs(ov - P.phi_ohm) < 1e-13
+    g = host(phi)
+    assert np.max(np.abs(g[P.dir] - P.g[P.dir])) < 1e-13
+    assert np.all(g[P.free] == 0.0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_diagonal(q, name):
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    m = q.qcad_mesh_create(dev)
+    phi_np = perturbed_phi(P, 1)
+    phi = dev_tensor(phi_np)
+    R = torch.empty_like(phi)
+    D = torch.empty_like(phi)
+    rmax, r2 = q.qcad_poisson_residual(m, dev["bias"], phi, R, D)
+    Ro = P.residual(phi_np)
+    scale = max(np.max(np.abs(Ro)), np.max(np.abs(P.K @ phi_np)))
+    assert np.max(np.abs(host(R) - Ro)) <= 1e-12 * scale
+    assert abs(rmax - np.max(np.abs(Ro))) <= 1e-12 * scale
+    assert abs(r2 - np.sum(Ro * Ro)) <= 1e-10 * max(np.sum(Ro * Ro), 1e-300)
+    Jd = P.jacobian(phi_np).diagonal()
+    Jd[P.dir] = 1.0
+    assert np.max(np.abs(host(D) - Jd) / np.abs(Jd)) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_jacobian_apply(q, name, precision):
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    m = q.qcad_mesh_create(dev)
+    phi_np = perturbed_phi(P, 2)
+    rng = np.random.default_rng(3)
+    v_np = rng.standard_normal(P.mesh.n_nodes)
+    v_np[P.dir] = 0.0
+    y = torch.empty(P.mesh.n_nodes, dtype=torch.float64, device="cuda")
+    q.qcad_poisson_jv(m, dev["bias"], dev_tensor(phi_np), dev_tensor(v_np), y, precision)
+    yo = P.jacobian(phi_np) @ v_np
+    yo[P.dir] = 0.0
+    tol = 1e-12 if precision == 0 else 2e-6
+    assert np.max(np.abs(host(y) - yo)) <= tol * np.max(np.abs(yo))
+
+
+@pytest.mark.parametrize("name", ["mos_cap_16x16x32", "dqd_24x24x16_4K", "dqd_37x33x21_0p5K", "dqd_3x1x7_4K",
+                                  "tiny_1x1x2"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_solve_matches_oracle(q, name, precision):
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    phi_o, rep_o = P.solve()
+    assert rep_o["converged"]
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision), phi)
+    assert rep["status"] == "OK", rep
+    assert rep["final_res_inf"] < 1e-10 and rep["final_dphi_inf"] < 1e-10
+    assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
+    # the oracle's residual of the GPU solution
+    assert np.max(np.abs(P.residual(host(phi)))) < 1e-9
+
+
+def test_solve_is_independent_of_launch_configuration(q):
+    dev = CASES["dqd_37x33x21_0p5K"]()
+    m = q.qcad_mesh_create(dev)
+    ref = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), ref)
+    for fam in (0, 1, 2):
+        for rows, ch in ((4, 3), (16, 64), (8, 1)):
+            q.qcad_set_launch(m, fam, rows, ch)
+    phi = torch.zeros_like(ref)
+    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), phi)
+    assert torch.max(torch.abs(phi - ref)).item() <= 1e-9
+
+
+def test_electron_counts_and_fixed_charge(q):
+    dev = CASES["dqd_24x24x16_4K"]()
+    theta = np.array(W.interface_fixed_charge(dev, seed=5))
+    P = PoissonProblem(dev, fixed_charge=theta)
+    phi_o, _ = P.solve()
+    m = q.qcad_mesh_create(dev)
+    th = dev_tensor(theta)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(), phi, fixed_charge=th)
+    assert rep["status"] == "OK"
+    assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
+    N = q.qcad_electron_counts(m, dev["bias"], phi, fixed_charge=th)
+    No = OC.electron_counts(P, phi_o)
+    assert np.all(No > 0.1)
+    assert np.max(np.abs(np.array(N) - No) / No) < 1e-8
+
+
+def test_invalid_arguments_are_rejected(q):
+    dev = CASES["tiny_1x1x2"]()
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    bad = dict(dev["bias"], V_gate=[0.1, 0.2])
+    with pytest.raises(q.QcadError) as e:
+        q.qcad_poisson_solve(m, bad, q.make_opts(), phi)
+    assert e.value.code == 1
+    with pytest.raises(q.QcadError):
+        q.qcad_poisson_solve(m, dict(dev["bias"], T=-1.0), q.make_opts(), phi)
+    with pytest.raises(q.QcadError):
+        q.qcad_set_launch(m, 0, 5, 16)
+    bad_dev = dict(dev, nx=0)
+    with pytest.raises(q.QcadError):
+        q.qcad_mesh_create(bad_dev)
+
+
+def test_not_converged_is_reported(q):
+    dev = CASES["dqd_24x24x16_4K"]()
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(max_newton=1), phi, allow_not_converged=True)
+    assert rep["status"] == "NOT_CONVERGED"
+    assert rep["newton_iters"] == 1
+    assert torch.isfinite(phi).all()
