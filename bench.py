@@ -1,0 +1,369 @@
+"""Benchmark of the QCAD finite-element hot path on GB300.
+
+One step is one full pass of the path on the five-gate double-quantum-dot
+device, 128 x 128 x 96 Q1 elements (1,614,177 nodes) over 200 x 200 x 100 nm
+at 4 K:
+  Newton solve of the nonlinear Poisson equation from a cold start (Laplace
+  guess), mixed precision (FP32 Krylov, FP64 residual) to the FP64 residual
+  ||R||_inf < 1e-10 V*nm and ||dphi||_inf < 1e-10 V;
+  the two dot electron counts; the adjoint 2 x 5 dot-to-gate capacitance;
+  the 10 lowest Schrodinger eigenpairs on the 64 x 64 x 32 quantum subdomain.
+The metric is device solves per second (whole job over all ranks). The same
+line reports the Poisson-only solve rate in mixed and in FP64 precision at
+the same final FP64 residual, the roofline of the dominant kernel (timed with
+CUDA events inside the library during the timed steps) and the CPU oracle
+timed on a bounded sample of the same device.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU: launched by torch.distributed.run; ranks solve independent
+replicas of the device (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s & op-apply HBM GB/s; mixed vs FP64 at same residual"
+WORKLOAD = "dqd_128x128x96_4K"
+NEV = 10
+SAMPLE_N = (32, 32, 24)  # bounded CPU sample of the same device for the oracle timing
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (also exercised by the CPU gloo test)
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device="cpu"):
+    import torch
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank, world, t_max):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        peak = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * peak] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(cls, n_nodes, n_elems):
+    """Bytes each launch must move at minimum given its stored linearization (per class)."""
+    return {
+        # p = z + beta p_prev (read z, p_prev; write p), Ap written, 8 FP32 qp coefficients per element
+        "apply32": 16 * n_nodes + 32 * n_elems,
+        "apply64": 32 * n_nodes + 64 * n_elems,
+        # x, r, p, Ap, D^-1 read; x, r, z written
+        "update32": 32 * n_nodes,
+        "update64": 64 * n_nodes,
+        # phi read; R, D^-1 (FP32), -R (FP32) written; FP32 qp coefficients written (mixed linearization)
+        "residual": 24 * n_nodes + 32 * n_elems,
+    }.get(cls)
+
+
+def oracle_sample(seconds_budget=30.0):
+    """Times the oracle on the bounded sample device; returns (seconds per sample pass, nodes of sample)."""
+    import numpy as np
+    import workloads as W
+    from oracle import capacitance as OC
+    from oracle import schrodinger as OS
+    from oracle.poisson import PoissonProblem
+    dev = W.five_gate_device(n=SAMPLE_N, T=4.0)
+    t0 = time.perf_counter()
+    P = PoissonProblem(dev)
+    phi, rep = P.solve()
+    OC.electron_counts(P, phi)
+    OC.adjoint(P, phi)
+    OS.solve_device(P, phi, nev=NEV)
+    dt = time.perf_counter() - t0
+    return dt, P.mesh.n_nodes
+
+
+def reference_arm(args):
+    """The oracle (plain FP64 CPU implementation) as the reference arm, on a bounded sample per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    full = W.n_nodes(W.get(args.workload))
+    times = []
+    nodes = None
+    for s in range(args.warmup + args.steps):
+        dt, nodes = oracle_sample()
+        if s >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = (1.0 / t) * (nodes / full)
+    sample = "five-gate device %dx%dx%d elements (%d nodes), full pipeline per step; solves/s scaled by node ratio %d/%d" % (
+        SAMPLE_N + (nodes, nodes, full))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nodes": full, "sample": list(SAMPLE_N)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def native_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_1403_7561_gb300 as q
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = W.get(args.workload)
+    bias = dev["bias"]
+    m = q.qcad_mesh_create(dev)
+    n_nodes, n_elems = m.n_nodes, m.n_elems
+    mixed = q.make_opts(precision=1)
+    phi = torch.zeros(n_nodes, dtype=torch.float64, device="cuda")
+    evecs = torch.empty(NEV, m.n_sub_dof, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        rep = q.qcad_poisson_solve(m, bias, mixed, phi)
+        N = q.qcad_electron_counts(m, bias, phi)
+        dNdV = q.qcad_adjoint(m, bias, phi, mixed)
+        E, erep = q.qcad_schrodinger_eigs(m, bias, phi, nev=NEV, tol=1e-8, evecs=evecs)
+        return rep, N, dNdV, E, erep
+
+    # launch tuning for this mesh (the autotuner picks tile rows and z chunk per precision)
+    tune32 = q.qcad_autotune(m, bias, precision=1)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    q.qcad_profile_reset(m)
+    q.qcad_profile_enable(m, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = q.qcad_launch_count()
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    info = None
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the timed interval)
+        ev[s][0].record()
+        info = step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    launches = q.qcad_launch_count() - launches0
+    clk = clocks.stop()
+    q.qcad_profile_enable(m, False)
+    t_local = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    t_max = max_over_ranks(dist, t_local, device="cuda")
+    value = aggregate(args.steps, world, t_max)
+    rep, N, dNdV, E, erep = info
+
+    # dominant kernel and its roofline
+    peak, peak_kind = load_peaks()
+    prof = {}
+    for cls in q.PROF_CLASSES:
+        nl, ms = q.qcad_profile_read(m, cls)
+        prof[cls] = (nl, ms)
+    dom = max((c for c in prof if algorithmic_bytes(c, n_nodes, n_elems) is not None), key=lambda c: prof[c][1])
+    nl, ms = prof[dom]
+    achieved = algorithmic_bytes(dom, n_nodes, n_elems) / (ms / nl / 1000.0) / 1e9 if nl else None
+    total_ms = sum(v[1] for v in prof.values())
+
+    # end to end through the public API with host buffers: the gate voltages go in from the host
+    # (inside the library, pinned staging), phi comes back to pinned host memory every step
+    phi_host = torch.empty(n_nodes, dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        b = dict(bias, V_gate=list(bias["V_gate"]))
+        rep_e = q.qcad_poisson_solve(m, b, mixed, phi)
+        Ne = q.qcad_electron_counts(m, b, phi)
+        dNe = q.qcad_adjoint(m, b, phi, mixed)
+        Ee, _ = q.qcad_schrodinger_eigs(m, b, phi, nev=NEV, tol=1e-8)
+        phi_host.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0, device="cuda")
+    e2e = aggregate(args.steps, world, t_e2e)
+    h2d = 8 * len(bias["V_gate"]) + 8 * 4  # gate voltages and bias scalars
+    d2h = 8 * n_nodes + 8 * (len(N) + len(N) * len(bias["V_gate"]) + NEV)
+
+    # Poisson-only: mixed vs FP64 at the same final FP64 residual
+    def poisson_rate(opts, reps):
+        ts = []
+        r = None
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r = q.qcad_poisson_solve(m, bias, opts, phi)
+            b_.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b_) / 1000.0)
+        return 1.0 / (sum(ts) / len(ts)), r
+
+    mixed_rate, mixed_rep = poisson_rate(mixed, 3)
+    phi_mixed = phi.clone()
+    fp64 = None
+    if not args.no_fp64:
+        fp64_rate, fp64_rep = poisson_rate(q.make_opts(precision=0), 1)
+        fp64 = {"solves_per_s": fp64_rate, "newton_iters": fp64_rep["newton_iters"],
+                "krylov_iters": fp64_rep["krylov_iters_total"], "final_res_inf": fp64_rep["final_res_inf"],
+                "max_abs_dphi_vs_mixed_V": float(torch.max(torch.abs(phi - phi_mixed)).item())}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        dt, nodes = oracle_sample()
+        cpu_value = (1.0 / dt) * (nodes / n_nodes)
+        cpu = {"value": cpu_value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "five-gate device %dx%dx%d elements (%d nodes), full pipeline; scaled by node ratio" % (
+                   SAMPLE_N + (nodes,))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nodes": n_nodes, "elements": n_elems,
+                       "step": "mixed Newton Poisson (FP64 residual 1e-10) + dot counts + 2x5 adjoint capacitance + %d LOBPCG eigenpairs" % NEV,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas x%d" % world,
+                       "apply_launch": {"tile_rows": tune32[0], "z_chunk": tune32[1]}},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "peak_kind": peak_kind, "launches": nl, "avg_ms": ms / nl if nl else None,
+                         "share_of_profiled_time": ms / total_ms if total_ms else None},
+            "kernel_profile_ms": {c: round(v[1], 3) for c, v in prof.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "poisson_only": {"mixed": {"solves_per_s": mixed_rate, "newton_iters": mixed_rep["newton_iters"],
+                                       "krylov_iters": mixed_rep["krylov_iters_total"],
+                                       "final_res_inf": mixed_rep["final_res_inf"]},
+                             "fp64": fp64},
+            "results": {"newton_iters": rep["newton_iters"], "krylov_iters": rep["krylov_iters_total"],
+                        "final_res_inf": rep["final_res_inf"], "dot_electrons": N,
+                        "capacitance_aF": [[1.602176634e-1 * x for x in row] for row in dNdV],
+                        "E_meV": [1e3 * e for e in E], "lobpcg_iters": erep["krylov_iters_total"]},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        native_arm(args)
+
+
+if __name__ == "__main__":
+    main()

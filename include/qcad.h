@@ -246,6 +246,10 @@ qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chun
 qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk,
                           float* best_ms);
 
+/* Number of CUDA kernels this library has launched in the process (kernels
+ * inside replayed CUDA graphs included). Host output *count. */
+qcad_status qcad_launch_count(int64_t* count);
+
 const char* qcad_last_error(void);
 
 #ifdef __cplusplus

@@ -108,6 +108,7 @@ _sigs = {
     "qcad_profile_read": [_P, C.c_int, C.POINTER(C.c_int64), _D],
     "qcad_set_launch": [_P, C.c_int, C.c_int, C.c_int],
     "qcad_autotune": [_P, C.POINTER(Bias), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)],
+    "qcad_launch_count": [C.POINTER(C.c_int64)],
     "qcad_last_error": [],
 }
 for _name, _args in _sigs.items():
@@ -351,6 +352,12 @@ def qcad_profile_read(mesh: Mesh, kernel_class):
 
 def qcad_set_launch(mesh: Mesh, family: int, tile_rows: int, z_chunk: int):
     _check(_lib.qcad_set_launch(mesh.handle, int(family), int(tile_rows), int(z_chunk)))
+
+
+def qcad_launch_count():
+    n = C.c_int64()
+    _check(_lib.qcad_launch_count(C.byref(n)))
+    return n.value
 
 
 def qcad_autotune(mesh: Mesh, bias: dict, precision=1):

@@ -236,6 +236,14 @@ qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int*
   });
 }
 
+qcad_status qcad_launch_count(int64_t* count) {
+  return guarded([&] {
+    if (!count) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null output");
+    *count = qcad::launch_count();
+    return QCAD_OK;
+  });
+}
+
 const char* qcad_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

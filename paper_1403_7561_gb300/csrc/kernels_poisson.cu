@@ -159,17 +159,17 @@ static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_
   switch (cfg.by) {
     case 4: {
       dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 4, cfg.kchunk, nvec);
-      march_kernel<T, 4, Op><<<grid, dim3(QCAD_BX, 4), 0, s>>>(g, op, cfg.kchunk);
+      note_launch(), march_kernel<T, 4, Op><<<grid, dim3(QCAD_BX, 4), 0, s>>>(g, op, cfg.kchunk);
       break;
     }
     case 16: {
       dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 16, cfg.kchunk, nvec);
-      march_kernel<T, 16, Op><<<grid, dim3(QCAD_BX, 16), 0, s>>>(g, op, cfg.kchunk);
+      note_launch(), march_kernel<T, 16, Op><<<grid, dim3(QCAD_BX, 16), 0, s>>>(g, op, cfg.kchunk);
       break;
     }
     default: {
       dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 8, cfg.kchunk, nvec);
-      march_kernel<T, 8, Op><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
+      note_launch(), march_kernel<T, 8, Op><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
       break;
     }
   }
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(long long n, PcgV
 
 template <class T>
 void launch_pcg_init(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
-  pcg_init_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+  note_launch(), pcg_init_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
 }
 template void launch_pcg_init<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_init<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(long long n, Pc
 
 template <class T>
 void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
-  pcg_update_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+  note_launch(), pcg_update_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
 }
 template void launch_pcg_update<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_update<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
@@ -460,7 +460,7 @@ newton_trial_kernel(long long n, const double* phi, const T* delta, double alpha
 template <class T>
 void launch_newton_trial(long long n, const double* phi, const T* delta, double alpha, double* phi_out,
                          double* stats, cudaStream_t s) {
-  newton_trial_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, phi, delta, alpha, phi_out, stats);
+  note_launch(), newton_trial_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, phi, delta, alpha, phi_out, stats);
 }
 template void launch_newton_trial<float>(long long, const double*, const float*, double, double*, double*, cudaStream_t);
 template void launch_newton_trial<double>(long long, const double*, const double*, double, double*, double*, cudaStream_t);
@@ -478,7 +478,7 @@ __global__ void set_dirichlet_kernel(long long nxn, long long nyn, long long nzn
 
 void launch_set_dirichlet(long long nxn, long long nyn, long long nzn, int bottom, double v_bottom,
                           const signed char* gate_top, const double* v_gate, double* phi, cudaStream_t s) {
-  set_dirichlet_kernel<<<vec_blocks(nxn * nyn), VEC_THREADS, 0, s>>>(nxn, nyn, nzn, bottom, v_bottom, gate_top,
+  note_launch(), set_dirichlet_kernel<<<vec_blocks(nxn * nyn), VEC_THREADS, 0, s>>>(nxn, nyn, nzn, bottom, v_bottom, gate_top,
                                                                     v_gate, phi);
 }
 
@@ -491,10 +491,10 @@ __global__ void f2d_kernel(long long n, const float* a, double* b) {
     b[i] = (double)a[i];
 }
 void launch_d2f(long long n, const double* a, float* b, cudaStream_t s) {
-  d2f_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
+  note_launch(), d2f_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
 }
 void launch_f2d(long long n, const float* a, double* b, cudaStream_t s) {
-  f2d_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
+  note_launch(), f2d_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b);
 }
 
 // theta gradient: out[e] = qe * (|e|/8) * sum of lam over the corners of e.
@@ -516,7 +516,7 @@ __global__ void theta_gradient_kernel(int nx, int ny, int nz, const double* hx, 
 void launch_theta_gradient(int nx, int ny, int nz, const double* hx, const double* hy, const double* hz,
                            const double* lam, double qe, double* out, cudaStream_t s) {
   const long long ne = (long long)nx * ny * nz;
-  theta_gradient_kernel<<<vec_blocks(ne), VEC_THREADS, 0, s>>>(nx, ny, nz, hx, hy, hz, lam, qe, out);
+  note_launch(), theta_gradient_kernel<<<vec_blocks(ne), VEC_THREADS, 0, s>>>(nx, ny, nz, hx, hy, hz, lam, qe, out);
 }
 
 }  // namespace qcad
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(VEC_THREADS) dot_kernel(long long n, const T* 
 }
 template <class T>
 void launch_dot(long long n, const T* a, const T* b, double* out, cudaStream_t s) {
-  dot_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b, out);
+  note_launch(), dot_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, b, out);
 }
 template void launch_dot<float>(long long, const float*, const float*, double*, cudaStream_t);
 template void launch_dot<double>(long long, const double*, const double*, double*, cudaStream_t);
@@ -547,7 +547,7 @@ __global__ void axpy_kernel(long long n, double a, const T* x, double* y) {
 }
 template <class T>
 void launch_axpy(long long n, double a, const T* x, double* y, cudaStream_t s) {
-  axpy_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, x, y);
+  note_launch(), axpy_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, a, x, y);
 }
 template void launch_axpy<float>(long long, double, const float*, double*, cudaStream_t);
 template void launch_axpy<double>(long long, double, const double*, double*, cudaStream_t);
@@ -561,7 +561,14 @@ __global__ void sub_kernel(long long n, const double* g, const double* y, double
   }
 }
 void launch_sub(long long n, const double* g, const double* y, double* r, float* r32, cudaStream_t s) {
-  sub_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, g, y, r, r32);
+  note_launch(), sub_kernel<<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, g, y, r, r32);
 }
 
+}  // namespace qcad
+
+#include <atomic>
+namespace qcad {
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace qcad

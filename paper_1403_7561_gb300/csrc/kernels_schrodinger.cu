@@ -51,9 +51,9 @@ void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg, cud
   const int by = cfg.by == 4 ? 4 : 8;
   dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, by, cfg.kchunk, args.nvec);
   if (by == 4)
-    march_kernel<T, 4, HmOp<T>><<<grid, dim3(QCAD_BX, 4), 0, s>>>(g, op, cfg.kchunk);
+    note_launch(), march_kernel<T, 4, HmOp<T>><<<grid, dim3(QCAD_BX, 4), 0, s>>>(g, op, cfg.kchunk);
   else
-    march_kernel<T, 8, HmOp<T>><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
+    note_launch(), march_kernel<T, 8, HmOp<T>><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
 }
 template void launch_hm_apply<float>(const Grid<float>&, const HmArgs<float>&, LaunchCfg, cudaStream_t);
 template void launch_hm_apply<double>(const Grid<double>&, const HmArgs<double>&, LaunchCfg, cudaStream_t);
@@ -107,7 +107,7 @@ template <class T>
 void launch_potential(const SubdomainMap& sm, const double* phi, double V0, const double* hx, const double* hy,
                       const double* hz, T* cV, double* vmin, cudaStream_t s) {
   const long long ne = (long long)sm.nxs * sm.nys * sm.nzs;
-  potential_kernel<T><<<dblocks(ne), DT, 0, s>>>(sm, phi, V0, hx, hy, hz, cV, vmin);
+  note_launch(), potential_kernel<T><<<dblocks(ne), DT, 0, s>>>(sm, phi, V0, hx, hy, hz, cV, vmin);
 }
 template void launch_potential<float>(const SubdomainMap&, const double*, double, const double*, const double*,
                                       const double*, float*, double*, cudaStream_t);
@@ -137,7 +137,7 @@ __global__ void pack_kernel(SubdomainMap sm, int nvec, double* full, long long l
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s) {
   const long long total = (long long)(sm.nxs - 1) * (sm.nys - 1) * (sm.nzs - 1) * nvec;
-  pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
+  note_launch(), pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
 }
 
 // G[p x q] (+)= A^T B for column-major A (n x p, lda) and B (n x q, ldb); FP64 accumulation.
@@ -183,7 +183,7 @@ void launch_gram(long long n, int p, int q, const double* A, long long lda, cons
                  double* G, cudaStream_t s) {
   const int nb = dblocks((n + GR - 1) / GR * DT) ;
   const size_t shm = (size_t)(p + q) * GR * sizeof(double);
-  gram_kernel<<<nb, 256, shm, s>>>(n, p, q, A, lda, B, ldb, G);
+  note_launch(), gram_kernel<<<nb, 256, shm, s>>>(n, p, q, A, lda, B, ldb, G);
 }
 
 // Y = A C (+ beta Y): A column-major n x p (lda), C p x q column-major (ldc = p), Y n x q (ldy).
@@ -205,7 +205,7 @@ __global__ void combine_kernel(long long n, int p, int q, const double* A, long 
 
 void launch_combine(long long n, int p, int q, const double* A, long long lda, const double* C, double* Y,
                     long long ldy, double beta, cudaStream_t s) {
-  combine_kernel<<<dblocks(n), DT, (size_t)p * q * sizeof(double), s>>>(n, p, q, A, lda, C, Y, ldy, beta);
+  note_launch(), combine_kernel<<<dblocks(n), DT, (size_t)p * q * sizeof(double), s>>>(n, p, q, A, lda, C, Y, ldy, beta);
 }
 
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms2[j] += |R_j|^2, mnorm2[j] += |MX_j|^2.
@@ -233,7 +233,7 @@ __global__ void residual_block_kernel(long long n, int m, const double* HX, cons
 
 void launch_residual_block(long long n, int m, const double* HX, const double* MX, long long ld, const double* lam,
                            const double* dinv, double* W, double* norms, cudaStream_t s) {
-  residual_block_kernel<<<dblocks(n), DT, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
+  note_launch(), residual_block_kernel<<<dblocks(n), DT, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
 }
 
 // Counter-based pseudo-random start block (SplitMix64 finalizer of the index), interior nodes only.
@@ -254,7 +254,7 @@ __global__ void random_block_kernel(long long n, int m, long long ld, const unsi
 
 void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, double* X,
                          cudaStream_t s) {
-  random_block_kernel<<<dblocks(n * m), DT, 0, s>>>(n, m, ld, interior, seed, X);
+  note_launch(), random_block_kernel<<<dblocks(n * m), DT, 0, s>>>(n, m, ld, interior, seed, X);
 }
 
 }  // namespace qcad

@@ -105,17 +105,19 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v) {
   }
   PcgScalars* sc = m->scal.as<PcgScalars>();
   const long long n = m->n_nodes;
+  const long long launches_before = launch_count();
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; it < PCG_CHUNK; ++it) {
-    if (prof) cudaEventRecord(G.events[2 * it].a, s);
+    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it].a, s, cudaEventRecordExternal));
     launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s);
-    if (prof) cudaEventRecord(G.events[2 * it].b, s);
-    if (prof) cudaEventRecord(G.events[2 * it + 1].a, s);
+    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it].b, s, cudaEventRecordExternal));
+    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it + 1].a, s, cudaEventRecordExternal));
     launch_pcg_update<T>(n, v, sc, s);
-    if (prof) cudaEventRecord(G.events[2 * it + 1].b, s);
+    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it + 1].b, s, cudaEventRecordExternal));
   }
   cudaGraph_t graph;
   CK(cudaStreamEndCapture(s, &graph));
+  note_launch((int)(launches_before - launch_count()));  // captured kernels run only when replayed
   cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
   cudaGraphDestroy(graph);
   CK(e);
@@ -151,6 +153,7 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit) {
   int guard = 0;
   for (;;) {
     CK(cudaGraphLaunch(G.exec, s));
+    note_launch(2 * PCG_CHUNK);
     CK(cudaMemcpyAsync(h, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (m->prof.on) {

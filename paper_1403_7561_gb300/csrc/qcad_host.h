@@ -132,3 +132,9 @@ template <class T>
 void launch_axpy(long long n, double a, const T* x, double* y, cudaStream_t s);
 void launch_sub(long long n, const double* g, const double* y, double* r, float* r32, cudaStream_t s);
 }  // namespace qcad
+
+namespace qcad {
+// Kernel launches issued by the library (graph replays count their kernels).
+void note_launch(int n = 1);
+long long launch_count();
+}  // namespace qcad
