@@ -109,6 +109,7 @@ _sigs = {
     "qcad_set_launch": [_P, C.c_int, C.c_int, C.c_int],
     "qcad_autotune": [_P, C.POINTER(Bias), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)],
     "qcad_launch_count": [C.POINTER(C.c_int64)],
+    "qcad_poisson_residual_noalloc": [C.POINTER(Device), C.POINTER(Bias), _P, _P, _P, _P, _D],
     "qcad_last_error": [],
 }
 for _name, _args in _sigs.items():
@@ -352,6 +353,50 @@ def qcad_profile_read(mesh: Mesh, kernel_class):
 
 def qcad_set_launch(mesh: Mesh, family: int, tile_rows: int, z_chunk: int):
     _check(_lib.qcad_set_launch(mesh.handle, int(family), int(tile_rows), int(z_chunk)))
+
+
+def _device_struct(dev: dict):
+    """C device description of a workloads dictionary plus the arrays it points to (keep both alive)."""
+    L = dev["layers"]
+    mats = dev["materials"]
+    gates = dev.get("gates", [])
+    dots = dev.get("dots", [])
+    keep = [(C.c_int * len(L))(*[l["n"] for l in L]), (C.c_double * len(L))(*[l["thickness"] for l in L]),
+            (C.c_int * len(L))(*[l["material"] for l in L]),
+            (Material * len(mats))(*[Material(*[float(m[k]) if k != "semiconductor" else int(m[k])
+                                                for k, _ in Material._fields_]) for m in mats]),
+            (Rect * max(1, len(gates)))(*[Rect(g["x0"], g["x1"], g["y0"], g["y1"]) for g in gates]),
+            (Box * max(1, len(dots)))(*[Box(d["x0"], d["x1"], d["y0"], d["y1"], d["z0"], d["z1"]) for d in dots])]
+    d = Device()
+    d.Lx, d.Ly, d.nx, d.ny = dev["Lx"], dev["Ly"], dev["nx"], dev["ny"]
+    d.n_layers, d.layer_n, d.layer_thickness, d.layer_material = len(L), keep[0], keep[1], keep[2]
+    d.n_materials, d.materials = len(mats), keep[3]
+    d.n_gates, d.gates = len(gates), keep[4]
+    wf = dev.get("gate_work_function")
+    d.gate_work_function_set = 0 if wf is None else 1
+    d.gate_work_function = 0.0 if wf is None else float(wf)
+    d.bottom_ohmic = int(dev.get("bottom_ohmic", 1))
+    d.n_dots, d.dots = len(dots), keep[5]
+    S = dev.get("subdomain")
+    d.has_subdomain = 0 if S is None else 1
+    if S is not None:
+        for q, k in enumerate(("i0", "i1", "j0", "j1", "k0", "k1")):
+            d.sub[q] = int(S[k])
+    return d, keep
+
+
+def qcad_poisson_residual_noalloc(dev: dict, bias: dict, phi, R, fixed_charge=None, stream=None):
+    """Allocation-free residual (no mesh object, no device allocation); returns (max |R_i|, sum R_i^2)."""
+    d, keep = _device_struct(dev)
+    b = make_bias(bias)
+    n_nodes = (dev["nx"] + 1) * (dev["ny"] + 1) * (sum(l["n"] for l in dev["layers"]) + 1)
+    n_elems = dev["nx"] * dev["ny"] * sum(l["n"] for l in dev["layers"])
+    st = (C.c_double * 2)()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(_lib.qcad_poisson_residual_noalloc(C.byref(d), C.byref(b), s,
+                                              _dptr(fixed_charge, n_elems, name="fixed_charge", allow_none=True),
+                                              _dptr(phi, n_nodes, name="phi"), _dptr(R, n_nodes, name="R"), st))
+    return st[0], st[1]
 
 
 def qcad_launch_count():

@@ -31,6 +31,8 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
 qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                 double* const* phis, qcad_solve_report* reps);
 qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk, float* best);
+qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* stream, const double* theta,
+                             const double* phi, double* R, double* stats);
 }  // namespace qcad
 
 static thread_local std::string g_last_error;
@@ -234,6 +236,12 @@ qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int*
     need_mesh(m);
     return qcad::autotune(m, b, precision, tile_rows, z_chunk, best_ms);
   });
+}
+
+qcad_status qcad_poisson_residual_noalloc(const qcad_device* dev, const qcad_bias* b, void* cuda_stream,
+                                          const double* fixed_charge_elem, const double* phi, double* R,
+                                          double* stats) {
+  return guarded([&] { return qcad::noalloc_residual(dev, b, cuda_stream, fixed_charge_elem, phi, R, stats); });
 }
 
 qcad_status qcad_launch_count(int64_t* count) {
