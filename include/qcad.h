@@ -239,7 +239,7 @@ qcad_status qcad_profile_enable(qcad_mesh_t m, int enable);
 qcad_status qcad_profile_reset(qcad_mesh_t m);
 qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches, double* total_ms);
 
-/* Launch configuration of the z-marching kernels (tile rows 4, 8 or 16 and
+/* Launch configuration of the z-marching kernels (tile rows 4, 8, 16 or 32 and
  * z-chunk length), per kernel family: 0 residual, 1 FP64 apply, 2 FP32 apply.
  * The autotuner sets these; the defaults are 8 and 16. */
 qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk);

@@ -26,7 +26,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
   c.ensure((size_t)m->n_elems * 8 * es + 64);
   CK(cudaMemsetAsync(v.p, 0, n * es, s));
   CK(cudaMemsetAsync(c.p, 0, (size_t)m->n_elems * 8 * es, s));
-  const int rows[3] = {4, 8, 16};
+  const int rows[4] = {4, 8, 16, 32};
   const int chunks[5] = {8, 16, 32, 64, 128};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

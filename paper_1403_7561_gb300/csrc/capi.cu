@@ -209,8 +209,8 @@ qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches
 qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk) {
   return guarded([&] {
     if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
-    if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16)
-      throw qcad::Error(QCAD_ERR_INVALID_ARG, "tile_rows must be 4, 8 or 16");
+    if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16 && tile_rows != 32)
+      throw qcad::Error(QCAD_ERR_INVALID_ARG, "tile_rows must be 4, 8, 16 or 32");
     if (z_chunk < 1 || z_chunk > 4096) throw qcad::Error(QCAD_ERR_INVALID_ARG, "z_chunk out of range");
     qcad::LaunchCfg c;
     c.by = tile_rows;

@@ -11,8 +11,8 @@
 namespace qcad {
 
 template <class T>
-__device__ __forceinline__ long long elem_index(const Grid<T>& g, int i, int j, int k) {
-  return (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+__device__ __forceinline__ int elem_index(const Grid<T>& g, int i, int j, int k) {
+  return i + g.nx * (j + g.ny * k);
 }
 
 // Diagonal of the assembled stiffness from the 1D operator rows.
@@ -34,25 +34,34 @@ __device__ __forceinline__ int dot_of_element(const ResidualArgs& a, int i, int 
   return -1;
 }
 
+template <class T>
+__device__ __forceinline__ C8<T> load_coeffs(const T* c, int e) {
+  C8<T> r;
+  load_c8<T>(c, e, r.c);
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // Residual R(phi), Jacobian quadrature coefficients c_q = -(q/eps0) w|J| rho'(phi_q),
 // the Jacobian diagonal, norms of R and dot electron counts in one z-march (FP64).
 struct ResidualOp {
   static constexpr int NF = 2;
   static constexpr bool STIFF = true;
+  using ED = double;  // fixed charge of the element
   ResidualArgs a;
-  double acc_dot[QCAD_MAX_DOTS_K];
+  double acc_dot0, acc_dot1;  // the first two dots in registers; further dots add atomically
   double acc_r2;
   double acc_rmax;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int) {}
-  __device__ double load(const Grid<double>&, long long n, bool in, int, int, int) const {
-    return in ? a.phi[n] : 0.0;
+  __device__ double load(const Grid<double>&, int n, bool in, int, int, int) const { return in ? a.phi[n] : 0.0; }
+  __device__ double edata(const Grid<double>& g, int i, int j, int k) const {
+    return a.theta ? a.theta[elem_index(g, i, j, k)] : 0.0;
   }
-  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, double (*out)[8], bool own) {
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, double th, double (*out)[8],
+                       bool own) {
     const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
-    const long long e = elem_index(g, i, j, k);
-    const double th = a.theta ? a.theta[e] : 0.0;
+    const int e = elem_index(g, i, j, k);
     double f[8], c[8];
     if (a.layer_semi[k] && !a.linear) {
       double pq[8];
@@ -65,9 +74,14 @@ struct ResidualOp {
         c[q] = -a.P.qe * wdet * ch.drho;
         nsum += ch.n;
       }
-      if (a.counts != nullptr) {
+      if (a.counts != nullptr && own) {  // each element counted once
         const int d = dot_of_element(a, i, j, k);
-        if (d >= 0 && own) acc_dot[d] += wdet * nsum;  // each element counted once
+        if (d == 0)
+          acc_dot0 += wdet * nsum;
+        else if (d == 1)
+          acc_dot1 += wdet * nsum;
+        else if (d > 1)
+          atomicAdd(a.counts + d, wdet * nsum);
       }
     } else {
 #pragma unroll
@@ -81,18 +95,17 @@ struct ResidualOp {
     const double b2 = GaussConst<double>::b() * GaussConst<double>::b();
     tp_apply(c, out[1], a2, b2);
     if (a.c64) {
-      double2* p = reinterpret_cast<double2*>(a.c64 + 8 * e);
+      double2* p = reinterpret_cast<double2*>(a.c64 + 8 * (size_t)e);
 #pragma unroll
       for (int s = 0; s < 4; ++s) p[s] = make_double2(c[2 * s], c[2 * s + 1]);
     }
     if (a.c32) {
-      float4* p = reinterpret_cast<float4*>(a.c32 + 8 * e);
+      float4* p = reinterpret_cast<float4*>(a.c32 + 8 * (size_t)e);
       p[0] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
       p[1] = make_float4((float)c[4], (float)c[5], (float)c[6], (float)c[7]);
     }
   }
-  __device__ void node(const Grid<double>& g, long long n, int i, int j, int k, double, double stiff,
-                       const double* mass) {
+  __device__ void node(const Grid<double>& g, int n, int i, int j, int k, double, double stiff, const double* mass) {
     double R = stiff + mass[0];
     double dg = stiff_diag(g, i, j, k) + mass[1];
     if (grid_is_dir(g, i, j, k)) {
@@ -115,10 +128,8 @@ struct ResidualOp {
       block_max_atomic(acc_rmax, a.stats);
     }
     if (a.counts) {
-      double s[QCAD_MAX_DOTS_K];
-#pragma unroll
-      for (int d = 0; d < QCAD_MAX_DOTS_K; ++d) s[d] = acc_dot[d];
-      block_sum_atomic<QCAD_MAX_DOTS_K>(s, a.counts);
+      double s[2] = {acc_dot0, acc_dot1};
+      block_sum_atomic<2>(s, a.counts);
     }
   }
 };
@@ -126,29 +137,31 @@ struct ResidualOp {
 // ---------------------------------------------------------------------------
 // y = J v: separable stiffness stencil plus the element quadrature-point mass
 // term with stored coefficients c; identity on Dirichlet rows unless raw.
+// The optional v.y partial sums run in the storage precision per thread and
+// in FP64 across threads.
 template <class T>
 struct ApplyOp {
   static constexpr int NF = 1;
   static constexpr bool STIFF = true;
+  using ED = C8<T>;
   ApplyArgs<T> a;
-  double acc;
+  T acc;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int) {}
-  __device__ T load(const Grid<T>&, long long n, bool in, int, int, int) const { return in ? a.v[n] : T(0); }
-  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* v, T (*out)[8], bool) const {
-    T c[8];
-    load_c8<T>(a.c, elem_index(g, i, j, k), c);
-    qp_mass<T>(v, c, out[0]);
+  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const { return in ? a.v[n] : T(0); }
+  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(a.c, elem_index(g, i, j, k)); }
+  __device__ void elem(const Grid<T>&, int, int, int, const T* v, const ED& ed, T (*out)[8], bool) const {
+    qp_mass<T>(v, ed.c, out[0]);
   }
-  __device__ void node(const Grid<T>& g, long long n, int i, int j, int k, T vin, T stiff, const T* mass) {
+  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T vin, T stiff, const T* mass) {
     T y = stiff + mass[0];
     if (!a.raw && grid_is_dir(g, i, j, k)) y = vin;
     a.y[n] = y;
-    acc += (double)vin * (double)y;
+    acc += vin * y;
   }
   __device__ void finish() {
     if (a.dot) {
-      double s[1] = {acc};
+      double s[1] = {(double)acc};
       block_sum_atomic<1>(s, a.dot);
     }
   }
@@ -167,6 +180,11 @@ static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_
       note_launch(), march_kernel<T, 16, Op><<<grid, dim3(QCAD_BX, 16), 0, s>>>(g, op, cfg.kchunk);
       break;
     }
+    case 32: {
+      dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 32, cfg.kchunk, nvec);
+      note_launch(), march_kernel<T, 32, Op><<<grid, dim3(QCAD_BX, 32), 0, s>>>(g, op, cfg.kchunk);
+      break;
+    }
     default: {
       dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 8, cfg.kchunk, nvec);
       note_launch(), march_kernel<T, 8, Op><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk);
@@ -178,7 +196,9 @@ static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_
 void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg cfg, cudaStream_t s) {
   ResidualOp op = {};
   op.a = args;
-  run_march<double>(g, op, cfg, s);
+  LaunchCfg c = cfg;
+  if (c.by == 32) c.by = 16;  // FP64 residual: 1024-thread tiles exceed its register budget
+  run_march<double>(g, op, c, s);
 }
 
 template <class T>
@@ -195,15 +215,15 @@ template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&
 struct CountGradOp {
   static constexpr int NF = 1;
   static constexpr bool STIFF = false;
+  using ED = char;
   ResidualArgs a;  // phi, layer_semi, coordinates, P, dots
   int d;
   double* out;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int) {}
-  __device__ double load(const Grid<double>&, long long n, bool in, int, int, int) const {
-    return in ? a.phi[n] : 0.0;
-  }
-  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, double (*o)[8], bool) const {
+  __device__ double load(const Grid<double>&, int n, bool in, int, int, int) const { return in ? a.phi[n] : 0.0; }
+  __device__ char edata(const Grid<double>&, int, int, int) const { return 0; }
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, char, double (*o)[8], bool) const {
     double f[8];
     if (a.layer_semi[k] && dot_of_element(a, i, j, k) == d) {
       const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
@@ -217,7 +237,7 @@ struct CountGradOp {
     }
     tp_apply(f, o[0], GaussConst<double>::a(), GaussConst<double>::b());
   }
-  __device__ void node(const Grid<double>&, long long n, int, int, int, double, double, const double* mass) {
+  __device__ void node(const Grid<double>&, int n, int, int, int, double, double, const double* mass) {
     out[n] = mass[0];
   }
   __device__ void finish() {}
@@ -236,7 +256,9 @@ void launch_count_gradient(const Grid<double>& g, const double* phi, const unsig
   op.a.dots = dots;
   op.d = d;
   op.out = out;
-  run_march<double>(g, op, cfg, s);
+  LaunchCfg c = cfg;
+  if (c.by == 32) c.by = 16;
+  run_march<double>(g, op, c, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,35 +274,35 @@ template <class T>
 struct PcgApplyOp {
   static constexpr int NF = 1;
   static constexpr bool STIFF = true;
+  using ED = C8<T>;
   PcgVecs<T> v;
   PcgScalars* sc;
   int t;
-  double beta;
-  double acc;
+  T beta;
+  T acc;
   __device__ bool skip() const { return sc->done != 0; }
   __device__ void set_vec(int) {
     t = sc->t;
-    beta = t > 0 ? sc->rz[t & 3] / sc->rz[(t - 1) & 3] : 0.0;
+    beta = t > 0 ? (T)(sc->rz[t & 3] / sc->rz[(t - 1) & 3]) : T(0);
   }
-  __device__ T load(const Grid<T>&, long long n, bool in, int, int, int) const {
+  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const {
     if (!in) return T(0);
     // p_{t-1} lives in p[(t+1)&1]; p_t is written to p[t&1], so halo reads never see new values
-    return t > 0 ? v.z[n] + (T)beta * v.p[(t + 1) & 1][n] : v.z[n];
+    return t > 0 ? v.z[n] + beta * v.p[(t + 1) & 1][n] : v.z[n];
   }
-  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* x, T (*out)[8], bool) const {
-    T c[8];
-    load_c8<T>(v.c, elem_index(g, i, j, k), c);
-    qp_mass<T>(x, c, out[0]);
+  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(v.c, elem_index(g, i, j, k)); }
+  __device__ void elem(const Grid<T>&, int, int, int, const T* x, const ED& ed, T (*out)[8], bool) const {
+    qp_mass<T>(x, ed.c, out[0]);
   }
-  __device__ void node(const Grid<T>& g, long long n, int i, int j, int k, T pin, T stiff, const T* mass) {
+  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T pin, T stiff, const T* mass) {
     T y = stiff + mass[0];
     if (grid_is_dir(g, i, j, k)) y = pin;
     v.p[t & 1][n] = pin;
     v.Ap[n] = y;
-    acc += (double)pin * (double)y;
+    acc += pin * y;
   }
   __device__ void finish() {
-    double s[1] = {acc};
+    double s[1] = {(double)acc};
     block_sum_atomic<1>(s, &sc->pAp[t & 3]);
   }
 };
@@ -318,36 +340,42 @@ static int vec_blocks(long long n) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// Sums two per-thread partials over the block (FP64 across threads) and adds them to dst0, dst1.
+__device__ __forceinline__ void block_sum2_atomic(double v0, double v1, double* dst0, double* dst1) {
+  __shared__ double red[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  if (lane == 0) {
+    red[0][warp] = v0;
+    red[1][warp] = v1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double w0 = lane < (int)(blockDim.x >> 5) ? red[0][lane] : 0.0;
+    double w1 = lane < (int)(blockDim.x >> 5) ? red[1][lane] : 0.0;
+    w0 = warp_sum(w0);
+    w1 = warp_sum(w1);
+    if (lane == 0) {
+      atomicAdd(dst0, w0);
+      atomicAdd(dst1, w1);
+    }
+  }
+}
+
 template <class T>
-__global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(long long n, PcgVecs<T> v, PcgScalars* sc) {
-  double rz = 0.0, rr = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
+  T rz = T(0), rr = T(0);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const T r = v.b[idx];
     const T z = v.dinv[idx] * r;
     v.x[idx] = T(0);
     v.r[idx] = r;
     v.z[idx] = z;
-    rz += (double)r * (double)z;
-    rr += (double)r * (double)r;
+    rz += r * z;
+    rr += r * r;
   }
-  double s[2] = {rz, rr};
-  __shared__ double red[2][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const double w = warp_sum(s[q]);
-    if (lane == 0) red[q][warp] = w;
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      double w = lane < (VEC_THREADS / 32) ? red[q][lane] : 0.0;
-      w = warp_sum(w);
-      if (lane == 0) atomicAdd(q == 0 ? &sc->rz[0] : &sc->rr[0], w);
-    }
-  }
+  block_sum2_atomic((double)rz, (double)rr, &sc->rz[0], &sc->rr[0]);
   if (last_block(&sc->counter) && threadIdx.x == 0) {
     const double rr0 = ld_volatile(&sc->rr[0]);
     const double rz0 = ld_volatile(&sc->rz[0]);
@@ -369,50 +397,36 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(long long n, PcgV
 
 template <class T>
 void launch_pcg_init(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
-  note_launch(), pcg_init_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+  note_launch(), pcg_init_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, sc);
 }
 template void launch_pcg_init<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_init<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
 
+// x += alpha p, r -= alpha Ap, z = D^-1 r, partial r.z and r.r per thread in the storage
+// precision (a handful of terms each), FP64 across threads.
 template <class T>
-__global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(long long n, PcgVecs<T> v, PcgScalars* sc) {
+__global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
   if (sc->done) return;
   const int t = sc->t;
   const double alpha_d = sc->rz[t & 3] / sc->pAp[t & 3];
   const T alpha = (T)alpha_d;
-  double rz = 0.0, rr = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const T p = v.p[t & 1][idx];
+  const T* __restrict__ p = v.p[t & 1];
+  T rz = T(0), rr = T(0);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const T pp = p[idx];
     const T ap = v.Ap[idx];
-    v.x[idx] += alpha * p;
-    const T r = v.r[idx] - alpha * ap;
-    const T z = v.dinv[idx] * r;
+    const T xo = v.x[idx];
+    const T ro = v.r[idx];
+    const T di = v.dinv[idx];
+    v.x[idx] = xo + alpha * pp;
+    const T r = ro - alpha * ap;
+    const T z = di * r;
     v.r[idx] = r;
     v.z[idx] = z;
-    rz += (double)r * (double)z;
-    rr += (double)r * (double)r;
+    rz += r * z;
+    rr += r * r;
   }
-  __shared__ double red[2][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  {
-    const double w0 = warp_sum(rz), w1 = warp_sum(rr);
-    if (lane == 0) {
-      red[0][warp] = w0;
-      red[1][warp] = w1;
-    }
-  }
-  __syncthreads();
-  if (warp == 0) {
-    double w0 = lane < (VEC_THREADS / 32) ? red[0][lane] : 0.0;
-    double w1 = lane < (VEC_THREADS / 32) ? red[1][lane] : 0.0;
-    w0 = warp_sum(w0);
-    w1 = warp_sum(w1);
-    if (lane == 0) {
-      atomicAdd(&sc->rz[(t + 1) & 3], w0);
-      atomicAdd(&sc->rr[(t + 1) & 3], w1);
-    }
-  }
+  block_sum2_atomic((double)rz, (double)rr, &sc->rz[(t + 1) & 3], &sc->rr[(t + 1) & 3]);
   if (last_block(&sc->counter) && threadIdx.x == 0) {
     const double rr_new = ld_volatile(&sc->rr[(t + 1) & 3]);
     const double rz_new = ld_volatile(&sc->rz[(t + 1) & 3]);
@@ -437,7 +451,7 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(long long n, Pc
 
 template <class T>
 void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
-  note_launch(), pcg_update_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>(n, v, sc);
+  note_launch(), pcg_update_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, sc);
 }
 template void launch_pcg_update<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_update<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);

@@ -16,18 +16,21 @@ template <class T>
 struct HmOp {
   static constexpr int NF = 2;
   static constexpr bool STIFF = true;
+  using ED = C8<T>;
   HmArgs<T> a;
   int vec;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int v) { vec = v; }
-  __device__ T load(const Grid<T>&, long long n, bool in, int, int, int) const {
+  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const {
     return in ? a.x[(long long)vec * a.ld + n] : T(0);
   }
-  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* v, T (*out)[8], bool) const {
-    const long long e = (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
-    T c[8];
-    load_c8<T>(a.cV, e, c);
-    qp_mass<T>(v, c, out[0]);
+  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const {
+    ED r;
+    load_c8<T>(a.cV, i + g.nx * (j + g.ny * k), r.c);
+    return r;
+  }
+  __device__ void elem(const Grid<T>& g, int i, int j, int k, const T* v, const ED& ed, T (*out)[8], bool) const {
+    qp_mass<T>(v, ed.c, out[0]);
     const T wdet = g.hx[i] * g.hy[j] * g.hz[k] * T(0.125);
     T u[8];
     tp_apply(v, u, GaussConst<T>::a(), GaussConst<T>::b());
@@ -35,7 +38,7 @@ struct HmOp {
     for (int q = 0; q < 8; ++q) u[q] *= wdet;
     tp_apply(u, out[1], GaussConst<T>::a(), GaussConst<T>::b());
   }
-  __device__ void node(const Grid<T>& g, long long n, int i, int j, int k, T, T stiff, const T* mass) {
+  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T, T stiff, const T* mass) {
     const bool bd = grid_is_dir(g, i, j, k);
     const long long o = (long long)vec * a.ld + n;
     if (a.hx) a.hx[o] = bd ? T(0) : stiff + mass[0];
@@ -140,14 +143,17 @@ void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, 
   note_launch(), pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
 }
 
-// G[p x q] (+)= A^T B for column-major A (n x p, lda) and B (n x q, ldb); FP64 accumulation.
-// Blocks take row tiles of 32 and add their partial products atomically.
+// G[p x q] (+)= A^T B for column-major A (n x p, lda) and B (n x q, ldb). Each thread sums
+// a 32-row tile in the storage precision T and accumulates tiles in FP64; blocks add
+// their partials atomically. Output row-major (o = a*q + b); all uses are symmetric.
 constexpr int GR = 32;
-__global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, const double* A, long long lda,
-                                                   const double* B, long long ldb, double* G) {
-  extern __shared__ double sh[];
-  double* sA = sh;             // [p][GR]
-  double* sB = sh + p * GR;    // [q][GR]
+template <class T>
+__global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, const T* A, long long lda,
+                                                   const T* B, long long ldb, double* G) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
+  T* sA = sh;             // [p][GR]
+  T* sB = sh + p * GR;    // [q][GR]
   const int nout = p * q;
   const int per = (nout + blockDim.x - 1) / blockDim.x;
   double acc[16];
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, co
     for (int t = threadIdx.x; t < (p + q) * GR; t += blockDim.x) {
       const int col = t / GR, rr = t % GR;
       const long long row = r0 + rr;
-      double v = 0.0;
+      T v = T(0);
       if (row < n) v = col < p ? A[col * lda + row] : B[(col - p) * ldb + row];
       sh[col * GR + rr] = v;
     }
@@ -166,10 +172,10 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, co
       const int o = threadIdx.x + s * blockDim.x;
       if (o < nout) {
         const int a = o / q, b = o % q;
-        double sum = 0.0;
+        T sum = T(0);
 #pragma unroll 8
         for (int rr = 0; rr < GR; ++rr) sum += sA[a * GR + rr] * sB[b * GR + rr];
-        acc[s] += sum;
+        acc[s] += (double)sum;
       }
     }
   }
@@ -179,48 +185,67 @@ __global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, co
   }
 }
 
-void launch_gram(long long n, int p, int q, const double* A, long long lda, const double* B, long long ldb,
-                 double* G, cudaStream_t s) {
-  const int nb = dblocks((n + GR - 1) / GR * DT) ;
-  const size_t shm = (size_t)(p + q) * GR * sizeof(double);
-  note_launch(), gram_kernel<<<nb, 256, shm, s>>>(n, p, q, A, lda, B, ldb, G);
+template <class T>
+void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B, long long ldb, double* G,
+                 cudaStream_t s) {
+  const int nb = dblocks((n + GR - 1) / GR * DT);
+  const size_t shm = (size_t)(p + q) * GR * sizeof(T);
+  note_launch(), gram_kernel<T><<<nb, 256, shm, s>>>(n, p, q, A, lda, B, ldb, G);
 }
+template void launch_gram<float>(long long, int, int, const float*, long long, const float*, long long, double*,
+                                 cudaStream_t);
+template void launch_gram<double>(long long, int, int, const double*, long long, const double*, long long, double*,
+                                  cudaStream_t);
 
-// Y = A C (+ beta Y): A column-major n x p (lda), C p x q column-major (ldc = p), Y n x q (ldy).
-__global__ void combine_kernel(long long n, int p, int q, const double* A, long long lda, const double* C,
-                               double* Y, long long ldy, double beta) {
-  extern __shared__ double sC[];
+// Row-wise block combination, safe in place: each row is read completely by one thread
+// before it is written. Y = A C with A n x p (lda), C p x q column-major; output
+// columns j < q1 go to Y1 (ldy), columns j >= q1 to Y2 (ldy).
+template <class T>
+__global__ void combine_kernel(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1,
+                               T* Y2, long long ldy) {
+  extern __shared__ __align__(16) unsigned char sc_raw[];
+  T* sC = reinterpret_cast<T*>(sc_raw);
   for (int t = threadIdx.x; t < p * q; t += blockDim.x) sC[t] = C[t];
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double a[QCAD_DENSE_MAXP];
+    T a[QCAD_DENSE_MAXP];
     for (int i = 0; i < p; ++i) a[i] = A[i * lda + r];
     for (int j = 0; j < q; ++j) {
-      double s = 0.0;
+      T s = T(0);
       for (int i = 0; i < p; ++i) s += a[i] * sC[j * p + i];
-      Y[j * ldy + r] = beta == 0.0 ? s : s + beta * Y[j * ldy + r];
+      if (j < q1)
+        Y1[j * ldy + r] = s;
+      else
+        Y2[(j - q1) * ldy + r] = s;
     }
   }
 }
 
-void launch_combine(long long n, int p, int q, const double* A, long long lda, const double* C, double* Y,
-                    long long ldy, double beta, cudaStream_t s) {
-  note_launch(), combine_kernel<<<dblocks(n), DT, (size_t)p * q * sizeof(double), s>>>(n, p, q, A, lda, C, Y, ldy, beta);
+template <class T>
+void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
+                    long long ldy, cudaStream_t s) {
+  note_launch(), combine_kernel<T><<<dblocks(n), DT, (size_t)p * q * sizeof(T), s>>>(n, p, q, q1, A, lda, C, Y1, Y2,
+                                                                                   ldy);
 }
+template void launch_combine<float>(long long, int, int, int, const float*, long long, const float*, float*, float*,
+                                    long long, cudaStream_t);
+template void launch_combine<double>(long long, int, int, int, const double*, long long, const double*, double*,
+                                     double*, long long, cudaStream_t);
 
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms2[j] += |R_j|^2, mnorm2[j] += |MX_j|^2.
-__global__ void residual_block_kernel(long long n, int m, const double* HX, const double* MX, long long ld,
-                                      const double* lam, const double* dinv, double* W, double* norms) {
+template <class T>
+__global__ void residual_block_kernel(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
+                                      const T* dinv, T* W, double* norms) {
   for (int j = 0; j < m; ++j) {
     double r2 = 0.0, m2 = 0.0;
-    const double l = lam[j];
+    const T l = (T)lam[j];
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
          r += (long long)gridDim.x * blockDim.x) {
-      const double mx = MX[j * ld + r];
-      const double res = HX[j * ld + r] - l * mx;
+      const T mx = MX[j * ld + r];
+      const T res = HX[j * ld + r] - l * mx;
       W[j * ld + r] = dinv[r] * res;
-      r2 += res * res;
-      m2 += mx * mx;
+      r2 += (double)res * (double)res;
+      m2 += (double)mx * (double)mx;
     }
     r2 = warp_sum(r2);
     m2 = warp_sum(m2);
@@ -231,14 +256,20 @@ __global__ void residual_block_kernel(long long n, int m, const double* HX, cons
   }
 }
 
-void launch_residual_block(long long n, int m, const double* HX, const double* MX, long long ld, const double* lam,
-                           const double* dinv, double* W, double* norms, cudaStream_t s) {
-  note_launch(), residual_block_kernel<<<dblocks(n), DT, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
+template <class T>
+void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
+                           const T* dinv, T* W, double* norms, cudaStream_t s) {
+  note_launch(), residual_block_kernel<T><<<dblocks(n), DT, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
 }
+template void launch_residual_block<float>(long long, int, const float*, const float*, long long, const double*,
+                                           const float*, float*, double*, cudaStream_t);
+template void launch_residual_block<double>(long long, int, const double*, const double*, long long, const double*,
+                                            const double*, double*, double*, cudaStream_t);
 
 // Counter-based pseudo-random start block (SplitMix64 finalizer of the index), interior nodes only.
+template <class T>
 __global__ void random_block_kernel(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed,
-                                    double* X) {
+                                    T* X) {
   const long long total = n * (long long)m;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const long long r = t % n;
@@ -248,13 +279,18 @@ __global__ void random_block_kernel(long long n, int m, long long ld, const unsi
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-    X[j * ld + r] = interior[r] ? u : 0.0;
+    X[j * ld + r] = interior[r] ? (T)u : T(0);
   }
 }
 
-void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, double* X,
+template <class T>
+void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, T* X,
                          cudaStream_t s) {
-  note_launch(), random_block_kernel<<<dblocks(n * m), DT, 0, s>>>(n, m, ld, interior, seed, X);
+  note_launch(), random_block_kernel<T><<<dblocks(n * m), DT, 0, s>>>(n, m, ld, interior, seed, X);
 }
+template void launch_random_block<float>(long long, int, long long, const unsigned char*, uint64_t, float*,
+                                         cudaStream_t);
+template void launch_random_block<double>(long long, int, long long, const unsigned char*, uint64_t, double*,
+                                          cudaStream_t);
 
 }  // namespace qcad

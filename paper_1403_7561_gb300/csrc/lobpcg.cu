@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "mesh.h"
@@ -27,6 +28,7 @@ template <class T>
 void build_grid(GridDev<T>& gd, const GridTables& t, const std::vector<double>& hx, const std::vector<double>& hy,
                 const std::vector<double>& hz, cudaStream_t s);
 double host_h2m0();
+void set_message(const std::string& msg);
 
 struct SubSetup {
   SubdomainMap sm;
@@ -177,63 +179,183 @@ qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* 
 }
 
 // ---------------------------------------------------------------------------
-struct Lobpcg {
+// One LOBPCG run in storage/apply precision T (FP32 for the iteration phase,
+// FP64 to polish). The blocks S = [X | W | P], HS = H S, MS = M S are kept
+// together (column-major, ns x 3nb each) so that the Rayleigh-Ritz Gram
+// matrices are two kernel launches; all block updates are row-wise in place.
+template <class T>
+struct LobpcgRun {
   qcad_mesh_s* m;
   SubSetup* S;
-  int nb;           // block size
-  long long ns;
-  double *Sx, *HS, *MS;  // [X | W | P] blocks, each ns x 3nb
-  double* T;             // temporary ns x nb
-  double* G;             // device gram buffer
-  std::vector<double> hG;
-  DevBuf tmp32;
   cudaStream_t s;
+  int nb, nev;
+  long long ns;
+  T* Sx;
+  T* HS;
+  T* MS;
+  const T* dinv;
+  double* G;
+  T* Cd;  // device combination coefficients
+  std::vector<double> lam;
+  std::vector<double> rel;
+  int applies = 0;
+  int iters = 0;
+  DevBuf tmp32;
 
-  double* X() { return Sx; }
-  double* W() { return Sx + ns * nb; }
-  double* P() { return Sx + 2 * ns * nb; }
-  double* blk(double* base, int b) { return base + (long long)b * ns * nb; }
+  T* blk(T* base, int b) { return base + (long long)b * ns * nb; }
 
-  // G = A^T B (p x q) to host.
-  void gram(int p, int q, const double* A, const double* B, std::vector<double>& out) {
+  void apply(int b) {
+    HmArgs<T> a{};
+    a.x = blk(Sx, b);
+    a.hx = blk(HS, b);
+    a.mx = blk(MS, b);
+    a.cV = cv();
+    a.ld = ns;
+    a.nvec = nb;
+    Profiler::Pair pp;
+    if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
+    launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
+    if (m->prof.on) m->prof.end(pp, s);
+    applies += nb;
+  }
+  const T* cv();
+  const Grid<T>& grid();
+
+  void gram(int p, int q, const T* A, const T* B, std::vector<double>& out) {
     CK(cudaMemsetAsync(G, 0, (size_t)p * q * sizeof(double), s));
-    launch_gram(ns, p, q, A, ns, B, ns, G, s);
+    launch_gram<T>(ns, p, q, A, ns, B, ns, G, s);
     out.resize((size_t)p * q);
     CK(cudaMemcpyAsync(out.data(), G, (size_t)p * q * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (int j = 0; j < q && p == q; ++j)
+      for (int i = 0; i < j; ++i) {
+        const double v = 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
+        out[(size_t)j * p + i] = out[(size_t)i * p + j] = v;
+      }
   }
 
-  // In-place A[:, 0:q] = A[:, 0:p] C for the three aligned blocks (S, HS, MS) at offset off.
-  void combine3(int off_blk, int p, int q, const std::vector<double>& C, int dst_blk) {
-    double* bases[3] = {Sx, HS, MS};
-    DevBuf cbuf;
-    cbuf.ensure((size_t)p * q * sizeof(double) + 64);
-    CK(cudaMemcpyAsync(cbuf.p, C.data(), (size_t)p * q * sizeof(double), cudaMemcpyHostToDevice, s));
-    for (int t = 0; t < 3; ++t) {
-      launch_combine(ns, p, q, blk(bases[t], off_blk), ns, cbuf.as<double>(), T, ns, 0.0, s);
-      CK(cudaMemcpyAsync(blk(bases[t], dst_blk), T, (size_t)ns * q * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    }
-    CK(cudaStreamSynchronize(s));
+  // For S, HS and MS: columns [src, src+p) times C (p x q); output columns < q1 to block dst1,
+  // the rest to block dst2 (in place).
+  void combine(int src_blk, int p, const std::vector<double>& C, int q, int q1, int dst1, int dst2) {
+    std::vector<T> ct(C.begin(), C.end());
+    CK(cudaMemcpyAsync(Cd, ct.data(), ct.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    T* bases[3] = {Sx, HS, MS};
+    for (T* base : bases)
+      launch_combine<T>(ns, p, q, q1, blk(base, src_blk), ns, Cd, blk(base, dst1), blk(base, dst2), ns, s);
+    CK(cudaStreamSynchronize(s));  // ct must outlive the pageable copy
   }
 
-  // M-orthonormalize block b (nb columns) by Cholesky QR; false if rank deficient.
   bool orthonormalize(int b) {
     std::vector<double> g;
     gram(nb, nb, blk(Sx, b), blk(MS, b), g);
-    for (int j = 0; j < nb; ++j)
-      for (int i = 0; i < j; ++i) {
-        const double v = 0.5 * (g[(size_t)j * nb + i] + g[(size_t)i * nb + j]);
-        g[(size_t)j * nb + i] = g[(size_t)i * nb + j] = v;
-      }
     if (!dense_cholesky(nb, g.data())) return false;
     std::vector<double> R((size_t)nb * nb);
     dense_inv_lt(nb, g.data(), R.data());
     for (double v : R)
       if (!std::isfinite(v)) return false;
-    combine3(b, nb, nb, R, b);
+    combine(b, nb, R, nb, nb, b, b);
     return true;
   }
+
+  // Rayleigh-Ritz on block 0 alone.
+  void rr_x() {
+    std::vector<double> GH, GM, w(nb), C((size_t)nb * nb);
+    gram(nb, nb, blk(Sx, 0), blk(HS, 0), GH);
+    gram(nb, nb, blk(Sx, 0), blk(MS, 0), GM);
+    if (!dense_gen_eig(nb, GH.data(), GM.data(), w.data(), C.data()))
+      throw Error(QCAD_ERR_NONFINITE, "LOBPCG: Rayleigh-Ritz on X failed");
+    combine(0, nb, C, nb, nb, 0, 0);
+    lam.assign(w.begin(), w.end());
+  }
+
+  // Iterates until the first nev relative residuals are <= tol; returns true when converged.
+  bool run(double tol, int maxit, DevBuf& lam_d, DevBuf& norms_d) {
+    bool haveP = false;
+    std::vector<double> norms(2 * nb), GH, GM, w, C;
+    rel.assign(nb, 1.0);
+    for (int it = 1; it <= maxit; ++it) {
+      CK(cudaMemcpyAsync(lam_d.p, lam.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(norms_d.p, 0, 2 * nb * sizeof(double), s));
+      launch_residual_block<T>(ns, nb, blk(HS, 0), blk(MS, 0), ns, lam_d.as<double>(), dinv, blk(Sx, 1),
+                               norms_d.as<double>(), s);
+      CK(cudaMemcpyAsync(norms.data(), norms_d.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int j = 0; j < nb; ++j) {
+        const double scale = std::max(std::fabs(lam[j]), 1e-12) * std::sqrt(std::max(norms[2 * j + 1], 1e-300));
+        rel[j] = std::sqrt(norms[2 * j]) / scale;
+        if (j < nev && !(rel[j] <= tol)) all = false;
+      }
+      if (all) return true;
+      ++iters;
+      apply(1);
+      if (!orthonormalize(1)) {
+        launch_random_block<T>(ns, nb, ns, S->interior.as<unsigned char>(), 0xABCDEF00ull + iters, blk(Sx, 1), s);
+        apply(1);
+        if (!orthonormalize(1)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
+      }
+      if (haveP && !orthonormalize(2)) haveP = false;
+      int nuse = haveP ? 3 * nb : 2 * nb;
+      gram(nuse, nuse, Sx, HS, GH);
+      gram(nuse, nuse, Sx, MS, GM);
+      w.resize(nuse);
+      C.resize((size_t)nuse * nuse);
+      bool ok = dense_gen_eig(nuse, GH.data(), GM.data(), w.data(), C.data());
+      if (!ok && haveP) {
+        haveP = false;
+        const int n2 = 2 * nb;
+        std::vector<double> gh2((size_t)n2 * n2), gm2((size_t)n2 * n2);
+        for (int j = 0; j < n2; ++j)
+          for (int i = 0; i < n2; ++i) {
+            gh2[(size_t)j * n2 + i] = GH[(size_t)j * nuse + i];
+            gm2[(size_t)j * n2 + i] = GM[(size_t)j * nuse + i];
+          }
+        nuse = n2;
+        w.resize(nuse);
+        C.resize((size_t)nuse * nuse);
+        ok = dense_gen_eig(nuse, gh2.data(), gm2.data(), w.data(), C.data());
+      }
+      if (!ok) throw Error(QCAD_ERR_NONFINITE, "LOBPCG Rayleigh-Ritz failed");
+      // new X = [X W P] C[:, :nb];  new P = [W P] C[nb:, :nb] = [X W P] (C[:, :nb] with the X rows zeroed)
+      std::vector<double> Cxp((size_t)nuse * 2 * nb, 0.0);
+      for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nuse; ++i) {
+          Cxp[(size_t)j * nuse + i] = C[(size_t)j * nuse + i];
+          Cxp[(size_t)(nb + j) * nuse + i] = i < nb ? 0.0 : C[(size_t)j * nuse + i];
+        }
+      combine(0, nuse, Cxp, 2 * nb, nb, 0, 2);
+      haveP = true;
+      lam.assign(w.begin(), w.begin() + nb);
+      if (iters % 25 == 0) apply(0);  // refresh H X, M X against recurrence drift
+    }
+    return false;
+  }
 };
+
+template <> const double* LobpcgRun<double>::cv() { return S->cV64.as<double>(); }
+template <> const float* LobpcgRun<float>::cv() { return S->cV32.as<float>(); }
+template <> const Grid<double>& LobpcgRun<double>::grid() { return S->g64.g; }
+template <> const Grid<float>& LobpcgRun<float>::grid() { return S->g32.g; }
+
+template <class T>
+static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, SubSetup* S, int nb, int nev, DevBuf& work, const T* dinv) {
+  L.m = m;
+  L.S = S;
+  L.s = m->stream;
+  L.nb = nb;
+  L.nev = nev;
+  L.ns = S->ns;
+  const long long ns = S->ns;
+  work.ensure((size_t)9 * nb * ns * sizeof(T) + (size_t)9 * nb * nb * (sizeof(double) + 2 * sizeof(T)) + 1024);
+  L.Sx = work.as<T>();
+  L.HS = L.Sx + 3 * nb * ns;
+  L.MS = L.HS + 3 * nb * ns;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(L.MS + 3 * nb * ns);
+  tail = reinterpret_cast<unsigned char*>(((uintptr_t)tail + 255) & ~(uintptr_t)255);
+  L.G = reinterpret_cast<double*>(tail);
+  L.Cd = reinterpret_cast<T*>(tail + (size_t)9 * nb * nb * sizeof(double) + 256);
+  L.dinv = dinv;
+}
 
 qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
                              double tol, double* evals, double* evecs, qcad_solve_report* rep) {
@@ -242,158 +364,55 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
   if (nev < 1 || nev > 16) throw Error(QCAD_ERR_INVALID_ARG, "nev must be in [1, 16]");
   if (!(tol > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tol must be > 0");
   SubSetup S;
-  setup_sub(m, b, phi, m_eff, 0, S);
+  setup_sub(m, b, phi, m_eff, 1, S);
   if (S.ndof < 3 * (nev + 4)) throw Error(QCAD_ERR_INVALID_ARG, "subdomain too small for nev");
   cudaStream_t s = m->stream;
-  Lobpcg L;
-  L.m = m;
-  L.S = &S;
-  L.nb = std::min<long long>(nev + std::max(2, nev / 4), S.ndof / 3);
-  const int nb = L.nb;
-  L.ns = S.ns;
-  L.s = s;
+  const int nb = (int)std::min<long long>(nev + std::max(2, nev / 4), S.ndof / 3);
   const long long ns = S.ns;
-  DevBuf work;
-  work.ensure((size_t)(3 * 3 * nb + nb) * ns * sizeof(double) + (size_t)9 * nb * nb * sizeof(double) + 256);
-  L.Sx = work.as<double>();
-  L.HS = L.Sx + 3 * nb * ns;
-  L.MS = L.HS + 3 * nb * ns;
-  L.T = L.MS + 3 * nb * ns;
-  L.G = L.T + nb * ns;
-  // random start on interior nodes, H and M of it, Rayleigh-Ritz
-  launch_random_block(ns, nb, ns, S.interior.as<unsigned char>(), 0x51ED5EEDull, L.X(), s);
-  hm_apply(m, S, 0, nb, L.X(), L.blk(L.HS, 0), L.blk(L.MS, 0), &L.tmp32);
-  std::vector<double> GH, GM, w(3 * nb), C((size_t)9 * nb * nb);
-  L.gram(nb, nb, L.X(), L.blk(L.HS, 0), GH);
-  L.gram(nb, nb, L.X(), L.blk(L.MS, 0), GM);
-  if (!dense_gen_eig(nb, GH.data(), GM.data(), w.data(), C.data()))
-    throw Error(QCAD_ERR_NONFINITE, "initial Rayleigh-Ritz failed");
-  L.combine3(0, nb, nb, std::vector<double>(C.begin(), C.begin() + (size_t)nb * nb), 0);
-  std::vector<double> lam(w.begin(), w.begin() + nb);
-  DevBuf lam_d, norms_d;
+  DevBuf lam_d, norms_d, dinv32;
   lam_d.ensure(nb * sizeof(double) + 64);
   norms_d.ensure(2 * nb * sizeof(double) + 64);
-  std::vector<double> norms(2 * nb);
-  bool haveP = false;
-  int it = 0, applies = nb;
-  bool converged = false;
-  const int maxit = 2000;
-  std::vector<double> rel(nb, 1.0);
-  for (it = 1; it <= maxit; ++it) {
-    // residual block W = D^-1 (H X - M X Lambda) and its norms
-    CK(cudaMemcpyAsync(lam_d.p, lam.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(norms_d.p, 0, 2 * nb * sizeof(double), s));
-    launch_residual_block(ns, nb, L.blk(L.HS, 0), L.blk(L.MS, 0), ns, lam_d.as<double>(), S.dinv.as<double>(), L.W(),
-                          norms_d.as<double>(), s);
-    CK(cudaMemcpyAsync(norms.data(), norms_d.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    bool all = true;
-    for (int j = 0; j < nb; ++j) {
-      const double scale = std::max(std::fabs(lam[j]), 1e-12) * std::sqrt(std::max(norms[2 * j + 1], 1e-300));
-      rel[j] = std::sqrt(norms[2 * j]) / scale;
-      if (j < nev && !(rel[j] <= tol)) all = false;
-    }
-    if (all) {
-      converged = true;
-      break;
-    }
-    // H W, M W; orthonormalize W against itself in the M inner product
-    hm_apply(m, S, 0, nb, L.W(), L.blk(L.HS, 1), L.blk(L.MS, 1), &L.tmp32);
-    applies += nb;
-    if (!L.orthonormalize(1)) {
-      // W numerically rank deficient: perturb with fresh random directions
-      launch_random_block(ns, nb, ns, S.interior.as<unsigned char>(), 0xABCDEF00ull + it, L.W(), s);
-      hm_apply(m, S, 0, nb, L.W(), L.blk(L.HS, 1), L.blk(L.MS, 1), &L.tmp32);
-      applies += nb;
-      if (!L.orthonormalize(1)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
-    }
-    if (haveP && !L.orthonormalize(2)) haveP = false;
-    const int nbas = haveP ? 3 * nb : 2 * nb;
-    L.gram(nbas, nbas, L.Sx, L.HS, GH);
-    L.gram(nbas, nbas, L.Sx, L.MS, GM);
-    w.resize(nbas);
-    C.resize((size_t)nbas * nbas);
-    bool ok = dense_gen_eig(nbas, GH.data(), GM.data(), w.data(), C.data());
-    if (!ok && haveP) {
-      haveP = false;
-      const int n2 = 2 * nb;
-      std::vector<double> gh2((size_t)n2 * n2), gm2((size_t)n2 * n2);
-      for (int j = 0; j < n2; ++j)
-        for (int i = 0; i < n2; ++i) {
-          gh2[(size_t)j * n2 + i] = GH[(size_t)j * nbas + i];
-          gm2[(size_t)j * n2 + i] = GM[(size_t)j * nbas + i];
-        }
-      w.resize(n2);
-      C.resize((size_t)n2 * n2);
-      ok = dense_gen_eig(n2, gh2.data(), gm2.data(), w.data(), C.data());
-      if (!ok) throw Error(QCAD_ERR_NONFINITE, "LOBPCG Rayleigh-Ritz failed");
-    }
-    const int nuse = haveP ? 3 * nb : 2 * nb;
-    // new P = [W P] C[nb:, :nb]; new X = [X W P] C[:, :nb]
-    std::vector<double> Cx((size_t)nuse * nb), Cp((size_t)(nuse - nb) * nb);
-    for (int j = 0; j < nb; ++j) {
-      for (int i = 0; i < nuse; ++i) Cx[(size_t)j * nuse + i] = C[(size_t)j * nuse + i];
-      for (int i = nb; i < nuse; ++i) Cp[(size_t)j * (nuse - nb) + (i - nb)] = C[(size_t)j * nuse + i];
-    }
-    L.combine3(1, nuse - nb, nb, Cp, 2);  // reads W (and old P) blocks, writes P
-    // X update must read the old P: recombine it from the stored (unchanged) blocks before P was overwritten.
-    // combine3 wrote P after reading [W, P_old]; rebuild X from X, W and (P_new - W Cw) is avoided by
-    // computing X as X C_X + P_new, since P_new = [W P_old] C[nb:, :nb].
-    {
-      std::vector<double> Cxx((size_t)nb * nb);
-      for (int j = 0; j < nb; ++j)
-        for (int i = 0; i < nb; ++i) Cxx[(size_t)j * nb + i] = C[(size_t)j * nuse + i];
-      DevBuf cbuf;
-      cbuf.ensure((size_t)nb * nb * sizeof(double) + 64);
-      CK(cudaMemcpyAsync(cbuf.p, Cxx.data(), (size_t)nb * nb * sizeof(double), cudaMemcpyHostToDevice, s));
-      double* bases[3] = {L.Sx, L.HS, L.MS};
-      for (int t = 0; t < 3; ++t) {
-        // T = X C_X ; X = T + P_new
-        launch_combine(ns, nb, nb, L.blk(bases[t], 0), ns, cbuf.as<double>(), L.T, ns, 0.0, s);
-        CK(cudaMemcpyAsync(L.blk(bases[t], 0), L.T, (size_t)ns * nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        std::vector<double> I((size_t)nb * nb, 0.0);
-        for (int q = 0; q < nb; ++q) I[(size_t)q * nb + q] = 1.0;
-        DevBuf ibuf;
-        ibuf.ensure((size_t)nb * nb * sizeof(double) + 64);
-        CK(cudaMemcpyAsync(ibuf.p, I.data(), (size_t)nb * nb * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_combine(ns, nb, nb, L.blk(bases[t], 2), ns, ibuf.as<double>(), L.blk(bases[t], 0), ns, 1.0, s);
-        CK(cudaStreamSynchronize(s));
-      }
-    }
-    haveP = true;
-    lam.assign(w.begin(), w.begin() + nb);
-    // periodically refresh H X and M X to stop drift of the recurrences
-    if (it % 25 == 0) {
-      hm_apply(m, S, 0, nb, L.X(), L.blk(L.HS, 0), L.blk(L.MS, 0), &L.tmp32);
-      applies += nb;
-    }
-  }
-  // final Rayleigh-Ritz on X with fresh applies (FP64)
-  hm_apply(m, S, 0, nb, L.X(), L.blk(L.HS, 0), L.blk(L.MS, 0), &L.tmp32);
-  applies += nb;
-  L.gram(nb, nb, L.X(), L.blk(L.HS, 0), GH);
-  L.gram(nb, nb, L.X(), L.blk(L.MS, 0), GM);
-  w.resize(nb);
-  C.resize((size_t)nb * nb);
-  if (!dense_gen_eig(nb, GH.data(), GM.data(), w.data(), C.data()))
-    throw Error(QCAD_ERR_NONFINITE, "final Rayleigh-Ritz failed");
-  L.combine3(0, nb, nb, C, 0);
-  for (int j = 0; j < nev; ++j) evals[j] = w[j];
-  if (evecs) launch_pack(S.sm, nev, L.X(), ns, evecs, S.ndof, 0, s);
+  dinv32.ensure(ns * sizeof(float) + 64);
+  launch_d2f(ns, S.dinv.as<double>(), dinv32.as<float>(), s);
+
+  // Phase 1: FP32 storage, applies and block arithmetic (FP64 Gram accumulation and host
+  // Rayleigh-Ritz) until the residuals reach the single-precision level.
+  DevBuf w32, w64;
+  LobpcgRun<float> A;
+  init_run<float>(A, m, &S, nb, nev, w32, dinv32.as<float>());
+  launch_random_block<float>(ns, nb, ns, S.interior.as<unsigned char>(), 0x51ED5EEDull, A.Sx, s);
+  A.apply(0);
+  A.rr_x();
+  const double tol32 = std::max(tol, 1e-5);
+  A.run(tol32, 3000, lam_d, norms_d);
+
+  // Phase 2: FP64 from the FP32 Ritz vectors to the requested tolerance.
+  LobpcgRun<double> B;
+  init_run<double>(B, m, &S, nb, nev, w64, S.dinv.as<double>());
+  launch_f2d(ns * nb, A.Sx, B.Sx, s);
+  B.apply(0);
+  B.rr_x();
+  bool converged = B.run(tol, 500, lam_d, norms_d);
+  // final Rayleigh-Ritz with fresh FP64 applies
+  B.apply(0);
+  B.rr_x();
+  for (int j = 0; j < nev; ++j) evals[j] = B.lam[j];
+  if (evecs) launch_pack(S.sm, nev, B.Sx, ns, evecs, S.ndof, 0, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   if (m->prof.on) m->prof.harvest();
   if (rep) {
-    rep->newton_iters = 0;
-    rep->krylov_iters_total = it;
-    rep->applies_total = applies;
+    rep->newton_iters = A.iters;  // FP32-phase iterations
+    rep->krylov_iters_total = A.iters + B.iters;
+    rep->applies_total = A.applies + B.applies;
     double worst = 0;
-    for (int j = 0; j < nev; ++j) worst = std::max(worst, rel[j]);
+    for (int j = 0; j < nev; ++j) worst = std::max(worst, B.rel[j]);
     rep->final_res_inf = worst;
     rep->final_dphi_inf = 0;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    rep->status_detail = 0;
+    rep->status_detail = B.iters;  // FP64-phase iterations
   }
+  if (!converged) set_message("LOBPCG did not reach the requested tolerance");
   return converged ? QCAD_OK : QCAD_ERR_NOT_CONVERGED;
 }
 

@@ -288,6 +288,10 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
     }
     m->nz = (int)m->layer_mat.size();
     if (m->nz > 65535) throw Error(QCAD_ERR_INVALID_ARG, "too many element layers");
+    // kernels index nodes and element coefficient arrays with 32-bit integers
+    if ((long long)(m->nx + 1) * (m->ny + 1) * (m->nz + 1) >= (1LL << 31) ||
+        8LL * m->nx * m->ny * m->nz >= (1LL << 31))
+      throw Error(QCAD_ERR_INVALID_ARG, "mesh too large for 32-bit node and coefficient indices");
     m->nxn = m->nx + 1;
     m->nyn = m->ny + 1;
     m->nzn = m->nz + 1;

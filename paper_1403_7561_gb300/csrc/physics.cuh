@@ -7,6 +7,10 @@
 // replacement F(x) = e^x for x < -50. Ionized dopants follow Eq.
 // FinalIonization. Derivatives are those of the implemented expressions, so
 // the Jacobian is exact for the residual the solver uses.
+//
+// FP64 division is a long instruction sequence on this GPU (FP64 runs at
+// 1/57 of the FP32 rate), so 1/kT is applied as a multiplication and each
+// logistic factor takes one reciprocal.
 #pragma once
 #include "qcad_internal.cuh"
 
@@ -38,12 +42,14 @@ __device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
 __device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms) {
   if (z > 0.0) {
     const double e = exp(-z);
-    s = e / (e + g);
-    oms = g / (e + g);
+    const double r = 1.0 / (e + g);
+    s = e * r;
+    oms = g * r;
   } else {
-    const double e = exp(z);
-    s = 1.0 / (1.0 + g * e);
-    oms = g * e / (1.0 + g * e);
+    const double ge = g * exp(z);
+    const double r = 1.0 / (1.0 + ge);
+    s = r;
+    oms = ge * r;
   }
 }
 
@@ -53,36 +59,37 @@ struct Charge {
 
 __device__ __forceinline__ Charge charge_at(const Phys& P, double phi) {
   Charge c;
-  const double eta_n = (P.EF + phi - P.phi_ref + P.chi) / P.kT;
-  const double eta_p = (-phi + P.phi_ref - P.chi - P.Eg - P.EF) / P.kT;
+  const double ik = P.inv_kT;
+  const double eta_n = (P.EF + phi - P.phi_ref + P.chi) * ik;
+  const double eta_p = (-phi + P.phi_ref - P.chi - P.Eg - P.EF) * ik;
   double n, dn, p, dp;
   if (P.statistics == 1) {
     double F, dF;
     fd_half_d(eta_n, F, dF);
     n = P.NC * F;
-    dn = P.NC * dF / P.kT;
+    dn = P.NC * dF * ik;
     fd_half_d(eta_p, F, dF);
     p = P.NV * F;
-    dp = -P.NV * dF / P.kT;
+    dp = -P.NV * dF * ik;
   } else {
     n = P.NC * exp(eta_n);
-    dn = n / P.kT;
+    dn = n * ik;
     p = P.NV * exp(eta_p);
-    dp = -p / P.kT;
+    dp = -p * ik;
   }
   double NDp = P.ND, dND = 0.0, NAm = P.NA, dNA = 0.0;
   if (P.incomplete) {
     if (P.ND != 0.0) {
       double s, oms;
-      sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) / P.kT, P.gD, s, oms);
+      sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) * ik, P.gD, s, oms);
       NDp = P.ND * s;
-      dND = -P.ND * s * oms / P.kT;
+      dND = -P.ND * s * oms * ik;
     }
     if (P.NA != 0.0) {
       double s, oms;
-      sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) / P.kT, P.gA, s, oms);
+      sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) * ik, P.gA, s, oms);
       NAm = P.NA * s;
-      dNA = P.NA * s * oms / P.kT;
+      dNA = P.NA * s * oms * ik;
     }
   }
   c.rho = p - n + NDp - NAm;

@@ -22,13 +22,17 @@ void launch_potential(const SubdomainMap& sm, const double* phi, double V0, cons
                       const double* hz, T* cV, double* vmin, cudaStream_t s);
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s);
-void launch_gram(long long n, int p, int q, const double* A, long long lda, const double* B, long long ldb,
-                 double* G, cudaStream_t s);
-void launch_combine(long long n, int p, int q, const double* A, long long lda, const double* C, double* Y,
-                    long long ldy, double beta, cudaStream_t s);
-void launch_residual_block(long long n, int m, const double* HX, const double* MX, long long ld, const double* lam,
-                           const double* dinv, double* W, double* norms, cudaStream_t s);
-void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, double* X,
+template <class T>
+void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B, long long ldb, double* G,
+                 cudaStream_t s);
+template <class T>
+void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
+                    long long ldy, cudaStream_t s);
+template <class T>
+void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
+                           const T* dinv, T* W, double* norms, cudaStream_t s);
+template <class T>
+void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, T* X,
                          cudaStream_t s);
 
 // Host dense routines on column-major n x n matrices (n <= QCAD_DENSE_MAXP).

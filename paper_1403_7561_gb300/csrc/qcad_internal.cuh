@@ -214,27 +214,35 @@ __device__ __forceinline__ void block_max_atomic(double v, double* dst) {
 // element layer k (between planes k and k+1) once per element, and gathers
 // element corner outputs to nodes: along x with warp shuffles (a warp is one
 // tile row), along y through shared memory, along z by carrying the upper
-// corner sums of layer k to plane k+1 in registers. The stencil part
-// (stiffness) is applied in three separable stages: z from the ring, y through
-// shared memory, x by shuffles.
+// corner sums of layer k to plane k+1 in registers. The stiffness part is
+// applied in three separable stages: z from the ring, y through shared
+// memory, x by shuffles.
+//
+// The march is software-pipelined: the input of plane k+2 and the element
+// data of layer k+1 are loaded into registers while layer k is computed, so
+// global-load latency overlaps the arithmetic and the barriers.
 //
 // Op supplies:
 //   NF                      number of gathered fields (field 0 gets the stencil)
 //   STIFF                   whether field 0 includes the stiffness stencil
+//   ED                      per-element data loaded from memory (coefficients)
 //   T load(g, n, in, i, j, k)           input value at node n (0 when !in)
-//   void elem(g, i, j, k, v[8], out[NF][8], own)  element corner outputs; own is true in
-//                           exactly one thread per element (for per-element reductions)
+//   ED edata(g, i, j, k)                element data of element (i, j, k)
+//   void elem(g, i, j, k, v[8], ed, out[NF][8], own)  element corner outputs; own is
+//                           true in exactly one thread per element (per-element reductions)
 //   void node(g, n, i, j, k, vin, stiff, mass[NF])  writer epilogue
 //   void finish()                       block-level epilogue (all threads)
-// The Op is copied per thread, so its data members double as per-thread
-// accumulators (constructed zeroed on the host).
 //   bool skip()                         uniform early exit (all threads)
 //   void set_vec(int)                   vector index of this block (block applies)
+// The Op is copied per thread, so its data members double as per-thread
+// accumulators (constructed zeroed on the host). Node and element indices are
+// 32-bit; mesh creation rejects meshes whose 8*n_elems or n_nodes exceed 2^31.
 template <class T, int BY, class Op>
 __global__ void __launch_bounds__(QCAD_BX * BY)
 march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
   constexpr int BX = QCAD_BX;
   constexpr int NF = Op::NF;
+  using ED = typename Op::ED;
   if (op_in.skip()) return;
   // blockIdx.z enumerates (vector, z chunk) pairs
   const int nch = (g.nzn + kchunk - 1) / kchunk;
@@ -251,9 +259,11 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
   const int j = blockIdx.y * (BY - 2) - 1 + ty;
   const int k0 = (blockIdx.z % nch) * kchunk;
   const int k1 = min(k0 + kchunk, g.nzn);
+  const int plane = (int)g.plane;
   const bool nin = (i >= 0 && i < g.nxn && j >= 0 && j < g.nyn);
   const bool writer = nin && tx >= 1 && tx < BX - 1 && ty >= 1 && ty < BY - 1;
   const bool eij = (i >= 0 && i < g.nx && j >= 0 && j < g.ny) && tx < BX - 1 && ty < BY - 1;
+  const bool own_ij = tx >= 1 && ty >= 1;
   const int txp = min(tx + 1, BX - 1), typ = min(ty + 1, BY - 1), tym = max(ty - 1, 0);
   T cmx[3] = {0, 0, 0}, ckx[3] = {0, 0, 0}, cmy[3] = {0, 0, 0}, cky[3] = {0, 0, 0};
   if (nin) {
@@ -265,13 +275,17 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
       cky[s] = g.ky[3 * j + s];
     }
   }
-  const long long nij = nin ? (long long)i + (long long)g.nxn * j : 0;
+  const int nij = nin ? i + g.nxn * j : 0;
   T carry[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) carry[f] = T(0);
 
-  if (k0 > 0) ring[(k0 - 1) & 3][ty][tx] = op.load(g, nij + (long long)(k0 - 1) * g.plane, nin, i, j, k0 - 1);
-  ring[k0 & 3][ty][tx] = op.load(g, nij + (long long)k0 * g.plane, nin, i, j, k0);
+  if (k0 > 0) ring[(k0 - 1) & 3][ty][tx] = op.load(g, nij + (k0 - 1) * plane, nin, i, j, k0 - 1);
+  ring[k0 & 3][ty][tx] = op.load(g, nij + k0 * plane, nin, i, j, k0);
+  // first prefetch: input plane k0+1 and element data of layer k0
+  T vnext = (k0 + 1 < g.nzn) ? op.load(g, nij + (k0 + 1) * plane, nin, i, j, k0 + 1) : T(0);
+  ED ednext{};
+  if (eij && k0 < g.nz) ednext = op.edata(g, i, j, k0);
   __syncthreads();
   if (k0 > 0) {
     // upper corners of element layer k0-1 feed node plane k0
@@ -287,7 +301,8 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
       v[5] = ring[k0 & 3][ty][txp];
       v[6] = ring[k0 & 3][typ][tx];
       v[7] = ring[k0 & 3][typ][txp];
-      op.elem(g, i, j, k, v, out, false);
+      const ED ed = op.edata(g, i, j, k);
+      op.elem(g, i, j, k, v, ed, out, false);
     } else {
 #pragma unroll
       for (int f = 0; f < NF; ++f)
@@ -308,7 +323,13 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
 
   for (int k = k0; k < k1; ++k) {
     const int kp = k + 1;
-    ring[kp & 3][ty][tx] = (kp < g.nzn) ? op.load(g, nij + (long long)kp * g.plane, nin, i, j, kp) : T(0);
+    ring[kp & 3][ty][tx] = vnext;
+    const ED ed = ednext;
+    if (k + 1 < k1) {
+      // issue the next iteration's loads before this iteration's arithmetic
+      vnext = (k + 2 < g.nzn) ? op.load(g, nij + (k + 2) * plane, nin, i, j, k + 2) : T(0);
+      if (eij && k + 1 < g.nz) ednext = op.edata(g, i, j, k + 1);
+    }
     __syncthreads();
     T out[NF][8];
     if (eij && k < g.nz) {
@@ -321,7 +342,7 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
       v[5] = ring[kp & 3][ty][txp];
       v[6] = ring[kp & 3][typ][tx];
       v[7] = ring[kp & 3][typ][txp];
-      op.elem(g, i, j, k, v, out, tx >= 1 && ty >= 1);
+      op.elem(g, i, j, k, v, ed, out, own_ij);
     } else {
 #pragma unroll
       for (int f = 0; f < NF; ++f)
@@ -372,7 +393,7 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
       const T dp = __shfl_down_sync(FULL_MASK, d, 1);
       stiff = ckx[0] * c1m + ckx[1] * c1 + ckx[2] * c1p + cmx[0] * dm + cmx[1] * d + cmx[2] * dp;
     }
-    if (writer) op.node(g, nij + (long long)k * g.plane, i, j, k, vc, stiff, mass);
+    if (writer) op.node(g, nij + k * plane, i, j, k, vc, stiff, mass);
   }
   op.finish();
 }
@@ -382,5 +403,11 @@ inline dim3 march_grid(int nxn, int nyn, int nzn, int by, int kchunk, int nvec =
   return dim3((nxn + QCAD_BX - 3) / (QCAD_BX - 2), (nyn + by - 3) / (by - 2),
               ((nzn + kchunk - 1) / kchunk) * nvec);
 }
+
+// Eight quadrature coefficients of one element.
+template <class T>
+struct C8 {
+  T c[8];
+};
 
 }  // namespace qcad

@@ -1,0 +1,66 @@
+"""Workloads for kernel profiling (ncu) of the library.
+
+``step``: one warm-up pass of the full hot path on a device, then one more
+pass; prints the library's kernel-launch counts of both so that a profiler
+can skip the warm-up (``ncu -s <warmup launches> -c <step launches>``).
+
+``apply``: the Jacobian apply of one precision on a device's linearization
+at the Laplace initial guess, repeated; used for single-kernel captures.
+
+Usage:
+  python -m paper_1403_7561_gb300.profile_driver step  [--workload NAME]
+  python -m paper_1403_7561_gb300.profile_driver apply [--workload NAME] [--precision 0|1] [--reps N]
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("mode", choices=["step", "apply"])
+    ap.add_argument("--workload", default="dqd_128x128x96_4K")
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    import torch
+
+    import paper_1403_7561_gb300 as q
+    import workloads as W
+
+    dev = W.get(a.workload)
+    bias = dev["bias"]
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    if a.mode == "step":
+        opts = q.make_opts(precision=1)
+
+        def step():
+            q.qcad_poisson_solve(m, bias, opts, phi)
+            q.qcad_electron_counts(m, bias, phi)
+            q.qcad_adjoint(m, bias, phi, opts)
+            q.qcad_schrodinger_eigs(m, bias, phi, nev=10, tol=1e-8)
+
+        c0 = q.qcad_launch_count()
+        step()
+        c1 = q.qcad_launch_count()
+        step()
+        c2 = q.qcad_launch_count()
+        torch.cuda.synchronize()
+        print("launches warmup=%d step=%d" % (c1 - c0, c2 - c1))
+    else:
+        q.qcad_contact_values(m, bias, phi)
+        v = torch.randn(m.n_nodes, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(v)
+        for _ in range(a.reps):
+            q.qcad_poisson_jv(m, bias, phi, v, y, a.precision)
+        torch.cuda.synchronize()
+        print("apply done: %d nodes, precision %d, %d reps" % (m.n_nodes, a.precision, a.reps))
+
+
+if __name__ == "__main__":
+    main()
