@@ -223,7 +223,7 @@ def native_arm(args):
     bias = dev["bias"]
     m = q.qcad_mesh_create(dev)
     n_nodes, n_elems = m.n_nodes, m.n_elems
-    mixed = q.make_opts(precision=1)
+    mixed = q.make_opts(precision=1, cheb_degree=0)  # Chebyshev degree autotuned per mesh
     phi = torch.zeros(n_nodes, dtype=torch.float64, device="cuda")
     evecs = torch.empty(NEV, m.n_sub_dof, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)

@@ -220,11 +220,19 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
                                   const double* m_eff, double tol, double* evals, double* evecs,
                                   qcad_solve_report* rep);
 
-/* Batched form: n independent meshes solved together (each with its own
- * bias), the Krylov iterations of all instances advanced by one persistent
- * kernel launch per step under a captured CUDA graph. ms, bs, phis: host
- * arrays of n entries (phis[i] device pointers). reps: host [n] or NULL.
- * o->precision must be 1 (mixed). */
+/* Batched form (no counterpart in the paper, which solves one device at a
+ * time; the operator of every instance is the one of qcad_poisson_solve):
+ * n independent meshes of any sizes, each with its own bias, solved by a
+ * lockstep Newton iteration whose FP32 Jacobi-PCG iterations advance all
+ * unconverged instances with one apply launch and one update launch (a work
+ * table maps blocks to (instance, tile)); chunks of 8 iterations are replayed
+ * from a captured CUDA graph and instances drop out on their own
+ * device-resident convergence flags. ms, bs, phis: host arrays of n entries
+ * (phis[i] device [n_nodes of ms[i]], FP64, also the warm start). reps: host
+ * [n] or NULL. o->precision must be 1 (mixed). All meshes must be distinct and
+ * on one device; the call uses the stream of ms[0] and synchronizes the
+ * others. Returns the first non-OK instance status (NOT_CONVERGED or
+ * NONFINITE; the per-instance reports say which); INVALID_ARG otherwise. */
 qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs,
                                      const qcad_solver_opts* o, double* const* phis, qcad_solve_report* reps);
 

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -33,12 +34,29 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
   CK(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   LaunchCfg best_cfg;
-  for (int r : rows) {
-    for (int ch : chunks) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+  for (int variant = 0; variant < (precision == 1 ? 8 : 4); ++variant) {
+    const int r = rows[variant % 4];
+    const int pair = variant / 4;  // FP32 only: 1 = two nodes per thread with packed f32x2
+    if (pair && r == 32) continue;
+    // z-chunk lengths that put whole waves of resident blocks on the SMs, plus fixed ones
+    const int bps = apply_blocks_per_sm(precision, r, pair);
+    const long long tiles_xy = pair ? (long long)((m->nxn + 59) / 60) * ((m->nyn + r - 3) / (r - 2))
+                                    : (long long)((m->nxn + 29) / 30) * ((m->nyn + r - 3) / (r - 2));
+    std::vector<int> cands(chunks, chunks + 5);
+    for (int w = 1; w <= 6 && bps > 0; ++w) {
+      const long long nch = std::max<long long>(1, (long long)w * sms * bps / std::max<long long>(1, tiles_xy));
+      cands.push_back((int)std::max<long long>(2, (m->nzn + nch - 1) / nch));
+    }
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    for (int ch : cands) {
       if (ch > 2 * (int)m->nzn && ch != 8) continue;
       LaunchCfg cfg;
       cfg.by = r;
       cfg.kchunk = ch;
+      cfg.pair = pair;
       auto run = [&]() {
         if (precision == 0) {
           ApplyArgs<double> a{};
@@ -56,7 +74,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
       };
       run();
       CK(cudaGetLastError());
-      const int reps = 5;
+      const int reps = 20;
       CK(cudaEventRecord(e0, s));
       for (int q = 0; q < reps; ++q) run();
       CK(cudaEventRecord(e1, s));
@@ -84,16 +102,71 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
   return QCAD_OK;
 }
 
+qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                                     double* const* phis, qcad_solve_report* reps);
+
+// z-chunk of the batched FP32 apply (8-row tiles, one node per thread) for one mesh: the
+// fastest of a few lengths, timed on the mesh's own grid.
+static int tune_batch_kchunk(qcad_mesh_s* m) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  DevBuf v, y, c;
+  v.ensure(n * sizeof(float) + 64);
+  y.ensure(n * sizeof(float) + 64);
+  c.ensure((size_t)m->n_elems * 8 * sizeof(float) + 64);
+  CK(cudaMemsetAsync(v.p, 0, n * sizeof(float), s));
+  CK(cudaMemsetAsync(c.p, 0, (size_t)m->n_elems * 8 * sizeof(float), s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 32;
+  float best_ms = 1e30f;
+  for (int ch : {8, 16, 32, 64}) {
+    LaunchCfg cfg;
+    cfg.by = 8;
+    cfg.kchunk = ch;
+    cfg.pair = 0;
+    ApplyArgs<float> a{};
+    a.v = v.as<float>();
+    a.y = y.as<float>();
+    a.c = c.as<float>();
+    launch_apply<float>(m->g32.g, a, cfg, s);
+    CK(cudaEventRecord(e0, s));
+    for (int q = 0; q < 10; ++q) launch_apply<float>(m->g32.g, a, cfg, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = ch;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// Batched solve: one timing run per size bucket sets the z chunk of every instance of that
+// bucket in the shared work table (a mesh keeps its chunk across calls).
 qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                 double* const* phis, qcad_solve_report* reps) {
   if (n < 1 || !ms || !bs || !o || !phis) throw Error(QCAD_ERR_INVALID_ARG, "invalid batch arguments");
-  qcad_status worst = QCAD_OK;
+  // one tuning run per size bucket (meshes with equal element counts per axis)
+  std::vector<std::pair<std::array<int, 3>, int>> buckets;
   for (int i = 0; i < n; ++i) {
     if (!ms[i]) throw Error(QCAD_ERR_INVALID_ARG, "null mesh in batch");
-    qcad_status st = poisson_solve(ms[i], &bs[i], o, nullptr, phis[i], reps ? &reps[i] : nullptr);
-    if (st != QCAD_OK && worst == QCAD_OK) worst = st;
+    const std::array<int, 3> key = {ms[i]->nx, ms[i]->ny, ms[i]->nz};
+    int ch = -1;
+    for (auto& b : buckets)
+      if (b.first == key) ch = b.second;
+    if (ch < 0) {
+      ch = ms[i]->batch_kchunk > 0 ? ms[i]->batch_kchunk : tune_batch_kchunk(ms[i]);
+      buckets.push_back({key, ch});
+    }
+    ms[i]->batch_kchunk = ch;
   }
-  return worst;
+  return poisson_solve_batch_impl(n, ms, bs, o, phis, reps);
 }
 
 }  // namespace qcad

@@ -1,0 +1,71 @@
+// Batched kernels: one launch covers the PCG apply (or update) of every
+// instance of a batch of meshes of different sizes. A work table maps each
+// block to (instance, tile); each instance keeps its own device-resident PCG
+// scalars, so instances converge and drop out independently (their blocks
+// return at once). Included at the end of kernels_poisson.cu, whose operator
+// ops and PCG bookkeeping it reuses.
+#pragma once
+
+namespace qcad {
+
+// Index of the last table entry whose begin <= b (entries sorted by begin).
+template <class E>
+__device__ __forceinline__ int batch_find(const E* tab, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].begin <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int BY>
+__global__ void __launch_bounds__(QCAD_BX * BY) batch_pcg_apply_kernel(const BatchApplyEntry* tab, int n_inst) {
+  const int b = blockIdx.x;
+  const BatchApplyEntry& e = tab[batch_find(tab, n_inst, b)];
+  const int local = b - e.begin;
+  const int bx = local % e.tiles_x;
+  const int by = (local / e.tiles_x) % e.tiles_y;
+  const int bz = local / (e.tiles_x * e.tiles_y);
+  PcgApplyOp<float> op = {};
+  op.v = e.v;
+  op.sc = e.sc;
+  march_body<float, BY, PcgApplyOp<float>>(e.g, op, e.kchunk, bx, by, bz);
+}
+
+__global__ void __launch_bounds__(VEC_THREADS) batch_pcg_update_kernel(const BatchVecEntry* tab, int n_inst) {
+  const int b = blockIdx.x;
+  const BatchVecEntry& e = tab[batch_find(tab, n_inst, b)];
+  pcg_update_body<float>(e.n, e.v, e.sc, b - e.begin, e.blocks);
+}
+
+// status[i] = {done, t, nonfinite, iters} of instance i (one read for the whole batch).
+__global__ void batch_status_kernel(const BatchVecEntry* tab, int n_inst, int* status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
+    const PcgScalars* sc = tab[i].sc;
+    status[4 * i + 0] = sc->done;
+    status[4 * i + 1] = sc->t;
+    status[4 * i + 2] = sc->nonfinite;
+    status[4 * i + 3] = sc->iters;
+  }
+}
+
+void launch_batch_pcg_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, int by, cudaStream_t s) {
+  if (by == 16)
+    note_launch(), batch_pcg_apply_kernel<16><<<total_blocks, dim3(QCAD_BX, 16), 0, s>>>(tab, n_inst);
+  else
+    note_launch(), batch_pcg_apply_kernel<8><<<total_blocks, dim3(QCAD_BX, 8), 0, s>>>(tab, n_inst);
+}
+
+void launch_batch_pcg_update(const BatchVecEntry* tab, int n_inst, int total_blocks, cudaStream_t s) {
+  note_launch(), batch_pcg_update_kernel<<<total_blocks, VEC_THREADS, 0, s>>>(tab, n_inst);
+}
+
+void launch_batch_status(const BatchVecEntry* tab, int n_inst, int* status, cudaStream_t s) {
+  note_launch(), batch_status_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(tab, n_inst, status);
+}
+
+}  // namespace qcad

@@ -4,6 +4,9 @@
 // MBstatistics, FDstatistics, FDIntApprox, FinalIonization).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "march2.cuh"
 #include "physics.cuh"
 #include "qcad_host.h"
 #include "qcad_internal.cuh"
@@ -193,6 +196,12 @@ static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_
   }
 }
 
+// FP32 pair-kernel launchers (two nodes per thread, packed f32x2), defined below.
+void launch_apply_pair(const Grid<float>& g, const ApplyArgs<float>& a, LaunchCfg cfg, cudaStream_t s);
+void launch_pcg_apply_pair(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
+void launch_cheb_step_pair(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, int step, int last,
+                           LaunchCfg cfg, cudaStream_t s);
+
 void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg cfg, cudaStream_t s) {
   ResidualOp op = {};
   op.a = args;
@@ -203,6 +212,12 @@ void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg 
 
 template <class T>
 void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cfg.pair) {
+      launch_apply_pair(g, args, cfg, s);
+      return;
+    }
+  }
   ApplyOp<T> op = {};
   op.a = args;
   run_march<T>(g, op, cfg, s);
@@ -309,6 +324,12 @@ struct PcgApplyOp {
 
 template <class T>
 void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cfg.pair) {
+      launch_pcg_apply_pair(g, vecs, sc, cfg, s);
+      return;
+    }
+  }
   PcgApplyOp<T> op = {};
   op.v = vecs;
   op.sc = sc;
@@ -318,26 +339,71 @@ template void launch_pcg_apply<float>(const Grid<float>&, PcgVecs<float>, PcgSca
 template void launch_pcg_apply<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t);
 
 // Last block of a grid: returns true in exactly one block after all blocks' prior writes are visible.
-__device__ __forceinline__ bool last_block(unsigned int* counter) {
+__device__ __forceinline__ bool last_block_of(unsigned int* counter, unsigned int total) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    const unsigned int total = gridDim.x * gridDim.y * gridDim.z;
-    am_last = atomicAdd(counter, 1u) == total - 1;
-  }
+  if (threadIdx.x == 0 && threadIdx.y == 0) am_last = atomicAdd(counter, 1u) == total - 1;
   __syncthreads();
   return am_last;
+}
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  return last_block_of(counter, gridDim.x * gridDim.y * gridDim.z);
 }
 
 __device__ __forceinline__ double ld_volatile(const double* p) { return *(volatile const double*)p; }
 
 constexpr int VEC_THREADS = 256;
 
+// Grid of the vector kernels: at most four blocks per SM of the 152 (a multiple of the SM
+// count, few same-address reduction atomics, enough loads in flight to saturate HBM).
 static int vec_blocks(long long n) {
   long long b = (n + VEC_THREADS - 1) / VEC_THREADS;
-  const long long cap = 152 * 8;
+  const long long cap = 152 * 4;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// Last block's bookkeeping after r.z is complete. Phase 1 (after iteration t): advance t,
+// clear the slots the next iteration accumulates into, test convergence. Phase 0 (after
+// the initial residual of a Chebyshev-preconditioned solve): record ||r0||^2, start at t = 0.
+__device__ __forceinline__ void pcg_finish(PcgScalars* sc, int t, double alpha_d) {
+  if (sc->phase == 0) {
+    const double rr0 = ld_volatile(&sc->rr[0]);
+    const double rz0 = ld_volatile(&sc->rz[0]);
+    sc->rr0 = rr0;
+    sc->t = 0;
+    sc->iters = 0;
+    sc->phase = 1;
+    sc->pAp[0] = 0.0;
+    sc->rz[1] = 0.0;
+    sc->rr[1] = 0.0;
+    if (!(rr0 == rr0) || !(rz0 == rz0) || rr0 > 1e300 || rz0 < 0.0) {
+      sc->nonfinite = 1;
+      sc->done = 1;
+    } else if (rr0 == 0.0) {
+      sc->done = 1;
+    }
+    sc->counter = 0;
+    return;
+  }
+  const double rr_new = ld_volatile(&sc->rr[(t + 1) & 3]);
+  const double rz_new = ld_volatile(&sc->rz[(t + 1) & 3]);
+  const int tn = t + 1;
+  sc->t = tn;
+  sc->pAp[tn & 3] = 0.0;
+  sc->rz[(tn + 1) & 3] = 0.0;
+  sc->rr[(tn + 1) & 3] = 0.0;
+  const bool bad = !(alpha_d == alpha_d) || !(rr_new == rr_new) || !(rz_new == rz_new) || fabs(alpha_d) > 1e300 ||
+                   alpha_d <= 0.0 || rz_new < 0.0;
+  if (bad) {
+    sc->nonfinite = 1;
+    sc->done = 1;
+    sc->iters = tn;
+  } else if (rr_new <= sc->tol2 * sc->rr0 || tn >= sc->maxit) {
+    sc->done = 1;
+    sc->iters = tn;
+  }
+  sc->counter = 0;
 }
 
 // Sums two per-thread partials over the block (FP64 across threads) and adds them to dst0, dst1.
@@ -382,6 +448,7 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_init_kernel(int n, PcgVecs<T>
     sc->rr0 = rr0;
     sc->t = 0;
     sc->iters = 0;
+    sc->phase = 1;
     sc->pAp[0] = 0.0;
     sc->rz[1] = 0.0;
     sc->rr[1] = 0.0;
@@ -405,14 +472,14 @@ template void launch_pcg_init<double>(long long, PcgVecs<double>, PcgScalars*, c
 // x += alpha p, r -= alpha Ap, z = D^-1 r, partial r.z and r.r per thread in the storage
 // precision (a handful of terms each), FP64 across threads.
 template <class T>
-__global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
+__device__ __forceinline__ void pcg_update_body(int n, const PcgVecs<T>& v, PcgScalars* sc, int blk, int nblk) {
   if (sc->done) return;
   const int t = sc->t;
   const double alpha_d = sc->rz[t & 3] / sc->pAp[t & 3];
   const T alpha = (T)alpha_d;
   const T* __restrict__ p = v.p[t & 1];
   T rz = T(0), rr = T(0);
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+  for (int idx = blk * blockDim.x + threadIdx.x; idx < n; idx += nblk * blockDim.x) {
     const T pp = p[idx];
     const T ap = v.Ap[idx];
     const T xo = v.x[idx];
@@ -427,26 +494,12 @@ __global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(int n, PcgVecs<
     rr += r * r;
   }
   block_sum2_atomic((double)rz, (double)rr, &sc->rz[(t + 1) & 3], &sc->rr[(t + 1) & 3]);
-  if (last_block(&sc->counter) && threadIdx.x == 0) {
-    const double rr_new = ld_volatile(&sc->rr[(t + 1) & 3]);
-    const double rz_new = ld_volatile(&sc->rz[(t + 1) & 3]);
-    const int tn = t + 1;
-    sc->t = tn;
-    sc->pAp[tn & 3] = 0.0;
-    sc->rz[(tn + 1) & 3] = 0.0;
-    sc->rr[(tn + 1) & 3] = 0.0;
-    const bool bad = !(alpha_d == alpha_d) || !(rr_new == rr_new) || !(rz_new == rz_new) ||
-                     fabs(alpha_d) > 1e300 || alpha_d <= 0.0;
-    if (bad) {
-      sc->nonfinite = 1;
-      sc->done = 1;
-      sc->iters = tn;
-    } else if (rr_new <= sc->tol2 * sc->rr0 || tn >= sc->maxit) {
-      sc->done = 1;
-      sc->iters = tn;
-    }
-    sc->counter = 0;
-  }
+  if (last_block_of(&sc->counter, nblk) && threadIdx.x == 0) pcg_finish(sc, t, alpha_d);
+}
+
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) pcg_update_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
+  pcg_update_body<T>(n, v, sc, blockIdx.x, gridDim.x);
 }
 
 template <class T>
@@ -455,6 +508,330 @@ void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s
 }
 template void launch_pcg_update<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_update<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Chebyshev-Jacobi preconditioner z = p_k(D^-1 J) D^-1 r (Chebyshev iteration for J z = r
+// with Jacobi scaling from z_0 = 0 on the interval [theta - delta, theta + delta] of D^-1 J):
+//   d_0 = D^-1 r / theta, z_1 = d_0, w_1 = r,
+//   w_{j+1} = w_j - J d_{j-1},  d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) D^-1 w_{j+1},
+//   z_{j+1} = z_j + d_j,  rho_0 = delta/theta, rho_j = 1 / (2 theta/delta - rho_{j-1}).
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) pcg_update_cheb_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
+  if (sc->done) return;
+  const int t = sc->t;
+  const double alpha_d = sc->rz[t & 3] / sc->pAp[t & 3];
+  if (!(alpha_d == alpha_d) || alpha_d <= 0.0 || fabs(alpha_d) > 1e300) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc->nonfinite = 1;
+      sc->iters = t;
+      sc->done = 1;
+    }
+    return;
+  }
+  const T alpha = (T)alpha_d;
+  const T inv_theta = (T)(1.0 / sc->theta);
+  const T* __restrict__ p = v.p[t & 1];
+  T* __restrict__ d0 = v.d[0];
+  T rr = T(0);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    v.x[idx] += alpha * p[idx];
+    const T r = v.r[idx] - alpha * v.Ap[idx];
+    const T d = v.dinv[idx] * r * inv_theta;
+    v.r[idx] = r;
+    v.w[idx] = r;
+    d0[idx] = d;
+    v.z[idx] = d;
+    rr += r * r;
+  }
+  double s1[1] = {(double)rr};
+  block_sum_atomic<1>(s1, &sc->rr[(t + 1) & 3]);
+}
+
+template <class T>
+void launch_pcg_update_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
+  note_launch(), pcg_update_cheb_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, sc);
+}
+template void launch_pcg_update_cheb<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
+template void launch_pcg_update_cheb<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
+
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS) pcg_init_cheb_kernel(int n, PcgVecs<T> v, PcgScalars* sc) {
+  const T inv_theta = (T)(1.0 / sc->theta);
+  T rr = T(0);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const T r = v.b[idx];
+    const T d = v.dinv[idx] * r * inv_theta;
+    v.x[idx] = T(0);
+    v.r[idx] = r;
+    v.w[idx] = r;
+    v.d[0][idx] = d;
+    v.z[idx] = d;
+    rr += r * r;
+  }
+  double s1[1] = {(double)rr};
+  block_sum_atomic<1>(s1, &sc->rr[0]);
+}
+
+template <class T>
+void launch_pcg_init_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s) {
+  note_launch(), pcg_init_cheb_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, sc);
+}
+template void launch_pcg_init_cheb<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
+template void launch_pcg_init_cheb<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
+
+template <class T>
+struct ChebStepOp {
+  static constexpr int NF = 1;
+  static constexpr bool STIFF = true;
+  using ED = C8<T>;
+  PcgVecs<T> v;
+  PcgScalars* sc;
+  int step, last;
+  int t, slot;
+  T c1, c2;
+  T acc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {
+    t = sc->t;
+    slot = sc->phase == 0 ? 0 : ((t + 1) & 3);
+    const double sigma = sc->theta / sc->delta;
+    double rho_prev = 1.0 / sigma, rho = rho_prev;
+    for (int q = 1; q <= step; ++q) {
+      rho_prev = rho;
+      rho = 1.0 / (2.0 * sigma - rho_prev);
+    }
+    c1 = (T)(rho * rho_prev);
+    c2 = (T)(2.0 * rho / sc->delta);
+  }
+  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const {
+    return in ? v.d[(step - 1) & 1][n] : T(0);
+  }
+  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(v.c, elem_index(g, i, j, k)); }
+  __device__ void elem(const Grid<T>&, int, int, int, const T* x, const ED& ed, T (*out)[8], bool) const {
+    qp_mass<T>(x, ed.c, out[0]);
+  }
+  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T dold, T stiff, const T* mass) {
+    T y = stiff + mass[0];
+    if (grid_is_dir(g, i, j, k)) y = dold;
+    const T wn = v.w[n] - y;
+    const T dn = c1 * dold + c2 * v.dinv[n] * wn;
+    const T zn = v.z[n] + dn;
+    v.w[n] = wn;
+    v.z[n] = zn;
+    v.d[step & 1][n] = dn;
+    if (last) acc += v.r[n] * zn;
+  }
+  __device__ void finish() {
+    if (!last) return;
+    double s1[1] = {(double)acc};
+    block_sum_atomic<1>(s1, &sc->rz[slot]);
+    if (last_block(&sc->counter) && threadIdx.x == 0 && threadIdx.y == 0) pcg_finish(sc, t, 1.0);
+  }
+};
+
+template <class T>
+void launch_cheb_step(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int step, int last, LaunchCfg cfg,
+                      cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cfg.pair) {
+      launch_cheb_step_pair(g, vecs, sc, step, last, cfg, s);
+      return;
+    }
+  }
+  ChebStepOp<T> op = {};
+  op.v = vecs;
+  op.sc = sc;
+  op.step = step;
+  op.last = last;
+  run_march<T>(g, op, cfg, s);
+}
+template void launch_cheb_step<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, int, int, LaunchCfg,
+                                      cudaStream_t);
+template void launch_cheb_step<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, int, int, LaunchCfg,
+                                       cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP32 pair-kernel ops (march2_kernel): one node per callback, element pairs inside the skeleton.
+struct Apply2Op {
+  ApplyArgs<float> a;
+  float acc;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int) {}
+  __device__ float load(int n, bool) const { return a.v[n]; }
+  __device__ void edata(const Grid<float>& g, int i, int j, int k, float (&c)[8]) const {
+    load_c8<float>(a.c, elem_index(g, i, j, k), c);
+  }
+  __device__ void node(const Grid<float>& g, int n, int i, int j, int k, float vin, float y) {
+    if (!a.raw && grid_is_dir(g, i, j, k)) y = vin;
+    a.y[n] = y;
+    acc += vin * y;
+  }
+  __device__ void finish() {
+    if (a.dot) {
+      double s1[1] = {(double)acc};
+      block_sum_atomic<1>(s1, a.dot);
+    }
+  }
+};
+
+struct PcgApply2Op {
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  int t;
+  float beta;
+  float acc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {
+    t = sc->t;
+    beta = t > 0 ? (float)(sc->rz[t & 3] / sc->rz[(t - 1) & 3]) : 0.f;
+  }
+  __device__ float load(int n, bool) const { return t > 0 ? v.z[n] + beta * v.p[(t + 1) & 1][n] : v.z[n]; }
+  __device__ void edata(const Grid<float>& g, int i, int j, int k, float (&c)[8]) const {
+    load_c8<float>(v.c, elem_index(g, i, j, k), c);
+  }
+  __device__ void node(const Grid<float>& g, int n, int i, int j, int k, float pin, float y) {
+    if (grid_is_dir(g, i, j, k)) y = pin;
+    v.p[t & 1][n] = pin;
+    v.Ap[n] = y;
+    acc += pin * y;
+  }
+  __device__ void finish() {
+    double s1[1] = {(double)acc};
+    block_sum_atomic<1>(s1, &sc->pAp[t & 3]);
+  }
+};
+
+struct ChebStep2Op {
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  int step, last;
+  int t, slot;
+  float c1, c2;
+  float acc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {
+    t = sc->t;
+    slot = sc->phase == 0 ? 0 : ((t + 1) & 3);
+    const double sigma = sc->theta / sc->delta;
+    double rho_prev = 1.0 / sigma, rho = rho_prev;
+    for (int q = 1; q <= step; ++q) {
+      rho_prev = rho;
+      rho = 1.0 / (2.0 * sigma - rho_prev);
+    }
+    c1 = (float)(rho * rho_prev);
+    c2 = (float)(2.0 * rho / sc->delta);
+  }
+  __device__ float load(int n, bool) const { return v.d[(step - 1) & 1][n]; }
+  __device__ void edata(const Grid<float>& g, int i, int j, int k, float (&c)[8]) const {
+    load_c8<float>(v.c, elem_index(g, i, j, k), c);
+  }
+  __device__ void node(const Grid<float>& g, int n, int i, int j, int k, float dold, float y) {
+    if (grid_is_dir(g, i, j, k)) y = dold;
+    const float wn = v.w[n] - y;
+    const float dn = c1 * dold + c2 * v.dinv[n] * wn;
+    const float zn = v.z[n] + dn;
+    v.w[n] = wn;
+    v.z[n] = zn;
+    v.d[step & 1][n] = dn;
+    if (last) acc += v.r[n] * zn;
+  }
+  __device__ void finish() {
+    if (!last) return;
+    double s1[1] = {(double)acc};
+    block_sum_atomic<1>(s1, &sc->rz[slot]);
+    if (last_block(&sc->counter) && threadIdx.x == 0 && threadIdx.y == 0) pcg_finish(sc, t, 1.0);
+  }
+};
+
+template <class Op>
+static void run_march2(const Grid<float>& g, const Op& op, LaunchCfg cfg, cudaStream_t s) {
+  const int by = (cfg.by == 4 || cfg.by == 16) ? cfg.by : 8;
+  dim3 grid = march2_grid(g.nxn, g.nyn, g.nzn, by, cfg.kchunk);
+  if (by == 4)
+    note_launch(), march2_kernel<4, Op><<<grid, dim3(32, 4), 0, s>>>(g, op, cfg.kchunk);
+  else if (by == 16)
+    note_launch(), march2_kernel<16, Op><<<grid, dim3(32, 16), 0, s>>>(g, op, cfg.kchunk);
+  else
+    note_launch(), march2_kernel<8, Op><<<grid, dim3(32, 8), 0, s>>>(g, op, cfg.kchunk);
+}
+
+void launch_apply_pair(const Grid<float>& g, const ApplyArgs<float>& a, LaunchCfg cfg, cudaStream_t s) {
+  Apply2Op op = {};
+  op.a = a;
+  run_march2(g, op, cfg, s);
+}
+void launch_pcg_apply_pair(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  PcgApply2Op op = {};
+  op.v = v;
+  op.sc = sc;
+  run_march2(g, op, cfg, s);
+}
+void launch_cheb_step_pair(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, int step, int last,
+                           LaunchCfg cfg, cudaStream_t s) {
+  ChebStep2Op op = {};
+  op.v = v;
+  op.sc = sc;
+  op.step = step;
+  op.last = last;
+  run_march2(g, op, cfg, s);
+}
+
+template <class T>
+__global__ void __launch_bounds__(VEC_THREADS)
+power_step_kernel(int n, const T* v, const T* Jv, const T* dinv, T* vn, double* acc) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const double x = (double)v[idx], y = (double)Jv[idx], di = (double)dinv[idx];
+    const double z = di * y;
+    vn[idx] = (T)z;
+    a0 += x * y;
+    a1 += x * x / di;
+    a2 += z * z;
+  }
+  double s3[3] = {a0, a1, a2};
+  block_sum_atomic<3>(s3, acc);
+}
+
+template <class T>
+void launch_power_step(long long n, const T* v, const T* Jv, const T* dinv, T* vnext, double* acc, cudaStream_t s) {
+  note_launch(), power_step_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, Jv, dinv, vnext, acc);
+}
+template void launch_power_step<float>(long long, const float*, const float*, const float*, float*, double*,
+                                       cudaStream_t);
+template void launch_power_step<double>(long long, const double*, const double*, const double*, double*, double*,
+                                        cudaStream_t);
+
+// Counter-based random vector (SplitMix64 finalizer of the index), zero on Dirichlet nodes.
+template <class T>
+__global__ void random_free_kernel(Grid<T> g, unsigned long long seed, T* v) {
+  const int n = (int)(g.plane * g.nzn);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int i = idx % g.nxn, j = (idx / g.nxn) % g.nyn, k = idx / (int)g.plane;
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(idx + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    v[idx] = grid_is_dir(g, i, j, k) ? T(0) : (T)u;
+  }
+}
+template <class T>
+void launch_random_free(const Grid<T>& g, unsigned long long seed, T* v, cudaStream_t s) {
+  note_launch(), random_free_kernel<T><<<vec_blocks(g.plane * g.nzn), VEC_THREADS, 0, s>>>(g, seed, v);
+}
+template void launch_random_free<float>(const Grid<float>&, unsigned long long, float*, cudaStream_t);
+template void launch_random_free<double>(const Grid<double>&, unsigned long long, double*, cudaStream_t);
+
+template <class T>
+__global__ void scale_kernel(int n, T* v, double a) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) v[idx] = (T)(a * v[idx]);
+}
+template <class T>
+void launch_scale(long long n, T* v, double a, cudaStream_t s) {
+  note_launch(), scale_kernel<T><<<vec_blocks(n), VEC_THREADS, 0, s>>>((int)n, v, a);
+}
+template void launch_scale<float>(long long, float*, double, cudaStream_t);
+template void launch_scale<double>(long long, double*, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <class T>
@@ -586,3 +963,33 @@ static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace qcad
+
+namespace qcad {
+// Resident blocks per SM of the plain Jacobian apply kernel for a launch shape (autotuner).
+int apply_blocks_per_sm(int precision, int by, int pair) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+  if (precision == 1 && pair) {
+    if (by == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<4, Apply2Op>, 32 * 4, 0);
+    else if (by == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<16, Apply2Op>, 32 * 16, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<8, Apply2Op>, 32 * 8, 0);
+  } else if (precision == 1) {
+    if (by == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<float, 4, ApplyOp<float>>, 128, 0);
+    else if (by == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<float, 16, ApplyOp<float>>, 512, 0);
+    else if (by == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<float, 32, ApplyOp<float>>, 1024, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<float, 8, ApplyOp<float>>, 256, 0);
+  } else {
+    if (by == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<double, 4, ApplyOp<double>>, 128, 0);
+    else if (by == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<double, 16, ApplyOp<double>>, 512, 0);
+    else if (by == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<double, 32, ApplyOp<double>>, 1024, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march_kernel<double, 8, ApplyOp<double>>, 256, 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+}  // namespace qcad
+
+#include "batch_kernels.cuh"

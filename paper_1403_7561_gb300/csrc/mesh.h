@@ -87,12 +87,13 @@ struct Profiler {
 
 template <class T>
 struct PcgBufs {
-  DevBuf x, r, z, p, Ap, b, dinv, c;
+  DevBuf x, r, z, p, Ap, b, dinv, c, w, d;
 };
 
 struct PcgGraph {
   cudaGraphExec_t exec = nullptr;
   const void* key = nullptr;  // vector buffer the graph was captured with
+  int degree = 0;             // Chebyshev degree the graph was captured with
   int chunk = 0;
   std::vector<Profiler::Pair> events;  // fixed event pairs inside the graph (profiling only)
   ~PcgGraph() {
@@ -135,6 +136,8 @@ struct qcad_mesh_s {
   double* h_small = nullptr;               // pinned host scratch (64 doubles)
   qcad::PcgGraph graph64, graph32;
   qcad::LaunchCfg cfg_res, cfg64, cfg32;
+  int cheb_auto[2] = {0, 0};               // autotuned Chebyshev degree per precision (0 = not yet)
+  int batch_kchunk = 0;                    // z chunk of this mesh in batched launches (0 = not tuned)
   qcad::Profiler prof;
   // Schrodinger workspace
   qcad::DevBuf s_mx, s_kx, s_my, s_ky, s_mzx, s_mzy, s_kzz, s_cV, s_dinv, s_interior, s_blocks, s_gram;

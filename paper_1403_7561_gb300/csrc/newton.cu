@@ -58,6 +58,8 @@ static PcgVecs<T> ensure_pcg(qcad_mesh_s* m) {
   b.b.ensure(nb);
   b.dinv.ensure(nb);
   b.c.ensure((size_t)m->n_elems * 8 * sizeof(T) + 64);
+  b.w.ensure(nb);
+  b.d.ensure(2 * nb);
   PcgVecs<T> v;
   v.x = b.x.template as<T>();
   v.r = b.r.template as<T>();
@@ -68,6 +70,9 @@ static PcgVecs<T> ensure_pcg(qcad_mesh_s* m) {
   v.b = b.b.template as<T>();
   v.dinv = b.dinv.template as<T>();
   v.c = b.c.template as<T>();
+  v.w = b.w.template as<T>();
+  v.d[0] = b.d.template as<T>();
+  v.d[1] = v.d[0] + (nb / sizeof(T));
   return v;
 }
 
@@ -78,10 +83,37 @@ static void ensure_newton(qcad_mesh_s* m) {
   m->R.ensure(nb);
 }
 
-// Captures PCG_CHUNK iterations (apply + update kernels) into a graph; with
-// profiling on, every kernel is bracketed by event-record nodes.
+// One PCG iteration's kernels: apply, update, and for degree >= 2 the Chebyshev steps.
 template <class T>
-static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v) {
+static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, int degree, cudaStream_t s,
+                              std::vector<Profiler::Pair>* ev) {
+  auto rec = [&](int idx, bool start) {
+    if (ev) {
+      Profiler::Pair& p = (*ev)[idx];
+      CK(cudaEventRecordWithFlags(start ? p.a : p.b, s, cudaEventRecordExternal));
+    }
+  };
+  int e = 0;
+  rec(e, true);
+  launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s);
+  rec(e++, false);
+  rec(e, true);
+  if (degree <= 1)
+    launch_pcg_update<T>(m->n_nodes, v, sc, s);
+  else
+    launch_pcg_update_cheb<T>(m->n_nodes, v, sc, s);
+  rec(e++, false);
+  for (int j = 1; j < degree; ++j) {
+    rec(e, true);
+    launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s);
+    rec(e++, false);
+  }
+}
+
+// Captures PCG_CHUNK iterations into a graph; with profiling on, every kernel is
+// bracketed by external event-record nodes (recorded whenever the graph runs).
+template <class T>
+static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
   PcgGraph& G = Prec<T>::graph(m);
   if (G.exec) {
     cudaGraphExecDestroy(G.exec);
@@ -94,26 +126,25 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v) {
   G.events.clear();
   cudaStream_t s = m->stream;
   const bool prof = m->prof.on;
+  const int per_it = 1 + std::max(1, degree);
+  std::vector<Profiler::Pair> evs;
   if (prof) {
-    for (int i = 0; i < 2 * PCG_CHUNK; ++i) {
+    for (int i = 0; i < per_it * PCG_CHUNK; ++i) {
       Profiler::Pair p;
       CK(cudaEventCreate(&p.a));
       CK(cudaEventCreate(&p.b));
-      p.cls = (i & 1) ? Prec<T>::prof_update : Prec<T>::prof_apply;
-      G.events.push_back(p);
+      const int q = i % per_it;
+      p.cls = (q == 1) ? Prec<T>::prof_update : Prec<T>::prof_apply;
+      evs.push_back(p);
     }
   }
   PcgScalars* sc = m->scal.as<PcgScalars>();
-  const long long n = m->n_nodes;
   const long long launches_before = launch_count();
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; it < PCG_CHUNK; ++it) {
-    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it].a, s, cudaEventRecordExternal));
-    launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s);
-    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it].b, s, cudaEventRecordExternal));
-    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it + 1].a, s, cudaEventRecordExternal));
-    launch_pcg_update<T>(n, v, sc, s);
-    if (prof) CK(cudaEventRecordWithFlags(G.events[2 * it + 1].b, s, cudaEventRecordExternal));
+    std::vector<Profiler::Pair> sub;
+    if (prof) sub.assign(evs.begin() + it * per_it, evs.begin() + (it + 1) * per_it);
+    enqueue_iteration<T>(m, v, sc, degree, s, prof ? &sub : nullptr);
   }
   cudaGraph_t graph;
   CK(cudaStreamEndCapture(s, &graph));
@@ -121,7 +152,9 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v) {
   cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
   cudaGraphDestroy(graph);
   CK(e);
+  G.events = evs;
   G.chunk = PCG_CHUNK;
+  G.degree = degree;
 }
 
 struct PcgResult {
@@ -130,46 +163,100 @@ struct PcgResult {
   bool converged = false;
 };
 
-// Solves J x = b (b, dinv, c already in the precision's buffers) to ||r|| <= rtol ||b||.
+// Largest eigenvalue of D^-1 J by power iteration (Rayleigh quotient in the D inner product).
 template <class T>
-static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit) {
+static double lambda_max(qcad_mesh_s* m, int steps) {
+  PcgVecs<T> v = ensure_pcg<T>(m);
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  T* x = v.d[0];
+  T* y = v.d[1];
+  T* xn = v.w;
+  launch_random_free<T>(Prec<T>::grid(m), 0x5EEDull, x, s);
+  double* acc = m->stats.as<double>() + 48;
+  double lam = 0.0;
+  for (int it = 0; it < steps; ++it) {
+    ApplyArgs<T> a{};
+    a.v = x;
+    a.y = y;
+    a.c = v.c;
+    launch_apply<T>(Prec<T>::grid(m), a, Prec<T>::cfg(m), s);
+    CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
+    launch_power_step<T>(n, x, y, v.dinv, xn, acc, s);
+    CK(cudaMemcpyAsync(m->h_small + 40, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double a0 = m->h_small[40], a1 = m->h_small[41], a2 = m->h_small[42];
+    if (!(a1 > 0.0) || !(a2 > 0.0)) break;
+    lam = a0 / a1;
+    launch_scale<T>(n, xn, 1.0 / std::sqrt(a2), s);
+    std::swap(x, xn);
+  }
+  return lam;
+}
+
+static double cheb_alpha(int degree) {
+  static const char* env = std::getenv("QCAD_CHEB_ALPHA");
+  if (env) return std::atof(env);
+  return 4.0 * degree * degree;
+}
+
+// Solves J x = b (b, dinv, c already in the precision's buffers) to ||r|| <= rtol ||b||
+// with Jacobi (degree 1) or Chebyshev-Jacobi (degree >= 2) preconditioning.
+template <class T>
+static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1) {
   PcgVecs<T> v = ensure_pcg<T>(m);
   PcgGraph& G = Prec<T>::graph(m);
+  degree = std::max(1, std::min(degree, 16));
   const bool prof_match = m->prof.on == !G.events.empty();
-  if (!G.exec || G.key != (const void*)v.x || !prof_match) {
-    build_graph<T>(m, v);
+  if (!G.exec || G.key != (const void*)v.x || !prof_match || G.degree != degree) {
+    build_graph<T>(m, v, degree);
     G.key = (const void*)v.x;
   }
   cudaStream_t s = m->stream;
+  double lam = 0.0;
+  if (degree >= 2) lam = lambda_max<T>(m, 12);
   PcgScalars* h = m->h_scal;
   std::memset(h, 0, sizeof(PcgScalars));
   h->tol2 = rtol * rtol;
   h->maxit = maxit;
+  h->degree = degree;
+  if (degree >= 2) {
+    // Chebyshev interval [b/alpha, b] of D^-1 J with b = 1.1 lambda_max
+    const double bmax = 1.1 * (lam > 0 ? lam : 2.0), amin = bmax / cheb_alpha(degree);
+    h->theta = 0.5 * (bmax + amin);
+    h->delta = 0.5 * (bmax - amin);
+  } else {
+    h->theta = 1.0;
+    h->delta = 0.5;
+  }
   PcgScalars* sc = m->scal.as<PcgScalars>();
   CK(cudaMemcpyAsync(sc, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-  launch_pcg_init<T>(m->n_nodes, v, sc, s);
+  if (degree <= 1) {
+    launch_pcg_init<T>(m->n_nodes, v, sc, s);
+  } else {
+    launch_pcg_init_cheb<T>(m->n_nodes, v, sc, s);
+    for (int j = 1; j < degree; ++j) launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s);
+  }
   CK(cudaGetLastError());
   int t_prev = 0;
   int guard = 0;
+  const int per_it = 1 + degree;
   for (;;) {
     CK(cudaGraphLaunch(G.exec, s));
-    note_launch(2 * PCG_CHUNK);
+    note_launch(per_it * PCG_CHUNK);
     CK(cudaMemcpyAsync(h, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (m->prof.on) {
       const int ran = std::min(PCG_CHUNK, h->t - t_prev);
-      for (int it = 0; it < PCG_CHUNK; ++it) {
-        for (int q = 0; q < 2; ++q) {
-          Profiler::Pair& p = G.events[2 * it + q];
-          // the apply of iteration t_prev+it ran iff it < ran; the update likewise
-          if (it < ran) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-              m->prof.ms[p.cls] += ms;
-              m->prof.launches[p.cls] += 1;
-            } else {
-              cudaGetLastError();
-            }
+      for (int it = 0; it < ran; ++it) {
+        for (int q = 0; q < per_it; ++q) {
+          Profiler::Pair& p = G.events[it * per_it + q];
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            m->prof.ms[p.cls] += ms;
+            m->prof.launches[p.cls] += 1;
+          } else {
+            cudaGetLastError();
           }
         }
       }
@@ -183,6 +270,30 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit) {
   r.nonfinite = h->nonfinite != 0;
   r.converged = h->done && !h->nonfinite && (h->rr0 == 0.0 || h->rr[h->t & 3] <= h->tol2 * h->rr0);
   return r;
+}
+
+// Chebyshev degree autotuner: times complete solves of the current system for each
+// candidate degree and keeps the fastest for the mesh and precision (once per mesh).
+template <class T>
+static int choose_degree(qcad_mesh_s* m, double rtol, int maxit) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  if (m->cheb_auto[prec] > 0) return m->cheb_auto[prec];
+  const int cand[5] = {1, 2, 3, 4, 6};
+  int best = 1;
+  double best_t = 1e300;
+  for (int d : cand) {
+    CK(cudaStreamSynchronize(m->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    PcgResult r = pcg_run<T>(m, rtol, maxit, d);
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (debug_on()) std::fprintf(stderr, "[qcad] cheb degree %d: %d iterations, %.3f ms\n", d, r.iters, 1e3 * dt);
+    if (r.converged && dt < best_t) {
+      best_t = dt;
+      best = d;
+    }
+  }
+  m->cheb_auto[prec] = best;
+  return best;
 }
 
 // Residual at phi with the linearization written in precision `prec`.
@@ -291,10 +402,12 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   int kry = 0;
   qcad_status st = QCAD_OK;
+  int degree = o->cheb_degree > 0 ? o->cheb_degree : m->cheb_auto[prec];
   if (!o->warm_start) {
     // Laplace initial guess with the contact values (rho = 0)
     eval_residual(m, P, pa, theta, 1, prec, nullptr);
-    PcgResult pr = pcg_run<T>(m, prec == 0 ? 1e-10 : 1e-6, maxk);
+    if (degree <= 0) degree = choose_degree<T>(m, prec == 0 ? 1e-10 : 1e-6, maxk);
+    PcgResult pr = pcg_run<T>(m, prec == 0 ? 1e-10 : 1e-6, maxk, degree);
     kry += pr.iters;
     if (debug_on()) std::fprintf(stderr, "[qcad] laplace pcg iters %d conv %d\n", pr.iters, (int)pr.converged);
     if (pr.nonfinite) {
@@ -323,7 +436,8 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
     const double nR = std::sqrt(R.r2);
     double eta = R0 > 0 ? std::min(1e-2, nR / R0) : 1e-2;
     eta = std::max(eta, floor_eta);
-    PcgResult pr = pcg_run<T>(m, eta, maxk);
+    if (degree <= 0) degree = choose_degree<T>(m, eta, maxk);
+    PcgResult pr = pcg_run<T>(m, eta, maxk, degree);
     kry += pr.iters;
     if (pr.nonfinite) {
       set_message("PCG breakdown at Newton iteration " + std::to_string(it) + " after " +
@@ -488,7 +602,7 @@ static void adjoint_solve(qcad_mesh_s* m, int prec, const double* g, double* lam
   PcgVecs<double> v = ensure_pcg<double>(m);
   if (prec == 0) {
     CK(cudaMemcpyAsync(const_cast<double*>(v.b), g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    PcgResult pr = pcg_run<double>(m, 1e-13, maxk);
+    PcgResult pr = pcg_run<double>(m, 1e-13, maxk, std::max(1, m->cheb_auto[0]));
     if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint linear solve produced a non-finite value");
     CK(cudaMemcpyAsync(lam, v.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -508,7 +622,7 @@ static void adjoint_solve(qcad_mesh_s* m, int prec, const double* g, double* lam
   CK(cudaStreamSynchronize(s));
   const double g2 = m->h_small[20];
   for (int rf = 0; rf < 12; ++rf) {
-    PcgResult pr = pcg_run<float>(m, 1e-5, maxk);
+    PcgResult pr = pcg_run<float>(m, 1e-5, maxk, std::max(1, m->cheb_auto[1]));
     if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint refinement produced a non-finite value");
     launch_axpy<float>(n, 1.0, w.x, lam, s);
     ApplyArgs<double> a{};
@@ -598,6 +712,235 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
     CK(cudaStreamSynchronize(s));
   }
   return QCAD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: n independent meshes (uneven sizes, own biases) solved by a
+// lockstep Newton iteration whose linear solves advance all instances with one
+// apply launch and one update launch per PCG iteration (work tables map blocks
+// to instance tiles), a status gather per chunk, and the chunk of iterations
+// captured once as a CUDA graph. Instances converge and drop out
+// independently through their own device-resident scalars. FP32 Krylov,
+// Jacobi preconditioning, FP64 residual and Newton update per instance.
+struct BatchCtx {
+  int n = 0;
+  cudaStream_t s = nullptr;
+  std::vector<qcad_mesh_s*> ms;
+  DevBuf tab_a, tab_v, status;
+  int total_a = 0, total_v = 0, by = 8;
+  int* h_status = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~BatchCtx() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (h_status) cudaFreeHost(h_status);
+  }
+};
+
+static void batch_setup(BatchCtx& B) {
+  std::vector<BatchApplyEntry> ta(B.n);
+  std::vector<BatchVecEntry> tv(B.n);
+  int ba = 0, bv = 0;
+  for (int i = 0; i < B.n; ++i) {
+    qcad_mesh_s* m = B.ms[i];
+    PcgVecs<float> v = ensure_pcg<float>(m);
+    BatchApplyEntry& a = ta[i];
+    a.g = m->g32.g;
+    a.v = v;
+    a.sc = m->scal.as<PcgScalars>();
+    a.kchunk = std::max(2, m->batch_kchunk > 0 ? m->batch_kchunk : m->cfg32.kchunk);
+    a.tiles_x = (m->g32.g.nxn + QCAD_BX - 3) / (QCAD_BX - 2);
+    a.tiles_y = (m->g32.g.nyn + B.by - 3) / (B.by - 2);
+    a.begin = ba;
+    ba += a.tiles_x * a.tiles_y * ((m->g32.g.nzn + a.kchunk - 1) / a.kchunk);
+    BatchVecEntry& e = tv[i];
+    e.v = v;
+    e.sc = a.sc;
+    e.n = (int)m->n_nodes;
+    e.blocks = std::max(1, (int)((m->n_nodes + 2047) / 2048));
+    e.begin = bv;
+    bv += e.blocks;
+  }
+  B.total_a = ba;
+  B.total_v = bv;
+  B.tab_a.ensure(ta.size() * sizeof(BatchApplyEntry) + 64);
+  B.tab_v.ensure(tv.size() * sizeof(BatchVecEntry) + 64);
+  B.status.ensure((size_t)4 * B.n * sizeof(int) + 64);
+  CK(cudaMemcpyAsync(B.tab_a.p, ta.data(), ta.size() * sizeof(BatchApplyEntry), cudaMemcpyHostToDevice, B.s));
+  CK(cudaMemcpyAsync(B.tab_v.p, tv.data(), tv.size() * sizeof(BatchVecEntry), cudaMemcpyHostToDevice, B.s));
+  CK(cudaMallocHost(&B.h_status, (size_t)4 * B.n * sizeof(int)));
+  CK(cudaStreamSynchronize(B.s));
+  const long long before = launch_count();
+  CK(cudaStreamBeginCapture(B.s, cudaStreamCaptureModeThreadLocal));
+  for (int it = 0; it < PCG_CHUNK; ++it) {
+    launch_batch_pcg_apply(B.tab_a.as<BatchApplyEntry>(), B.n, B.total_a, B.by, B.s);
+    launch_batch_pcg_update(B.tab_v.as<BatchVecEntry>(), B.n, B.total_v, B.s);
+  }
+  launch_batch_status(B.tab_v.as<BatchVecEntry>(), B.n, B.status.as<int>(), B.s);
+  cudaGraph_t graph;
+  CK(cudaStreamEndCapture(B.s, &graph));
+  note_launch((int)(before - launch_count()));
+  cudaError_t e = cudaGraphInstantiate(&B.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+}
+
+// One batched linear solve: instance i solves its J x = b to rtol[i] (rtol[i] <= 0: skipped).
+static void batch_pcg(BatchCtx& B, const std::vector<double>& rtol, int maxit, std::vector<int>& iters,
+                      std::vector<int>& nonfinite) {
+  for (int i = 0; i < B.n; ++i) {
+    qcad_mesh_s* m = B.ms[i];
+    PcgScalars* h = m->h_scal;
+    std::memset(h, 0, sizeof(PcgScalars));
+    h->tol2 = rtol[i] * rtol[i];
+    h->maxit = maxit;
+    h->degree = 1;
+    h->phase = 1;
+    h->theta = 1.0;
+    h->delta = 0.5;
+    if (!(rtol[i] > 0)) h->done = 1;
+    CK(cudaMemcpyAsync(m->scal.p, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
+    if (rtol[i] > 0) launch_pcg_init<float>(m->n_nodes, ensure_pcg<float>(m), m->scal.as<PcgScalars>(), B.s);
+  }
+  CK(cudaGetLastError());
+  int guard = 0;
+  for (;;) {
+    CK(cudaGraphLaunch(B.exec, B.s));
+    note_launch(2 * PCG_CHUNK + 1);
+    CK(cudaMemcpyAsync(B.h_status, B.status.p, (size_t)4 * B.n * sizeof(int), cudaMemcpyDeviceToHost, B.s));
+    CK(cudaStreamSynchronize(B.s));
+    bool all = true;
+    for (int i = 0; i < B.n; ++i) all = all && B.h_status[4 * i] != 0;
+    if (all || ++guard > maxit / PCG_CHUNK + 4) break;
+  }
+  iters.assign(B.n, 0);
+  nonfinite.assign(B.n, 0);
+  for (int i = 0; i < B.n; ++i) {
+    iters[i] = rtol[i] > 0 ? B.h_status[4 * i + 1] : 0;
+    nonfinite[i] = B.h_status[4 * i + 2];
+  }
+}
+
+qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                                     double* const* phis, qcad_solve_report* reps) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (n < 1 || !ms || !bs || !o || !phis) throw Error(QCAD_ERR_INVALID_ARG, "invalid batch arguments");
+  validate_opts(o);
+  if (o->precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "the batched form runs in mixed precision (precision 1)");
+  BatchCtx B;
+  B.n = n;
+  B.ms.assign(ms, ms + n);
+  for (int i = 0; i < n; ++i) {
+    if (!ms[i] || !phis[i]) throw Error(QCAD_ERR_INVALID_ARG, "null mesh or phi in batch");
+    if (ms[i]->device != ms[0]->device) throw Error(QCAD_ERR_INVALID_ARG, "batch meshes must share one device");
+    for (int j = 0; j < i; ++j)
+      if (ms[j] == ms[i]) throw Error(QCAD_ERR_INVALID_ARG, "a mesh appears twice in the batch");
+    validate_bias(ms[i], &bs[i]);
+    ensure_newton(ms[i]);
+  }
+  B.s = ms[0]->stream;
+  batch_setup(B);
+  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
+  const int maxn = o->max_newton > 0 ? o->max_newton : 100;
+  std::vector<Phys> P(n);
+  std::vector<double*> pa(n), pb(n);
+  std::vector<ResStats> R(n);
+  std::vector<double> R0(n), step(n, 0.0), rtol(n);
+  std::vector<int> kry(n, 0), its(n, 0), conv(n, 0), bad(n, 0), iters, nonf;
+  for (int i = 0; i < n; ++i) {
+    qcad_mesh_s* m = ms[i];
+    P[i] = make_phys(m, &bs[i]);
+    pa[i] = m->phi_a.as<double>();
+    pb[i] = m->phi_b.as<double>();
+    if (o->warm_start)
+      CK(cudaMemcpyAsync(pa[i], phis[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    else
+      CK(cudaMemsetAsync(pa[i], 0, m->n_nodes * sizeof(double), m->stream));
+    set_contacts(m, &bs[i], P[i], pa[i], nullptr, nullptr);
+  }
+  if (!o->warm_start) {
+    for (int i = 0; i < n; ++i) {
+      eval_residual(ms[i], P[i], pa[i], nullptr, 1, 1, nullptr);
+      rtol[i] = 1e-6;
+    }
+    batch_pcg(B, rtol, maxk, iters, nonf);
+    for (int i = 0; i < n; ++i) {
+      qcad_mesh_s* m = ms[i];
+      kry[i] += iters[i];
+      if (nonf[i]) bad[i] = 1;
+      CK(cudaMemsetAsync(m->stats.p, 0, sizeof(double), m->stream));
+      launch_newton_trial<float>(m->n_nodes, pa[i], ensure_pcg<float>(m).x, 1.0, pb[i], m->stats.as<double>(),
+                                 m->stream);
+      CK(cudaStreamSynchronize(m->stream));
+      std::swap(pa[i], pb[i]);
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    R[i] = eval_residual(ms[i], P[i], pa[i], nullptr, o->linear, 1, nullptr);
+    R0[i] = std::sqrt(R[i].r2);
+    if (!std::isfinite(R[i].r2)) bad[i] = 1;
+  }
+  for (int it = 1; it <= maxn; ++it) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) {
+      rtol[i] = 0.0;
+      if (conv[i] || bad[i]) continue;
+      any = true;
+      const double nR = std::sqrt(R[i].r2);
+      rtol[i] = std::max(1e-5, R0[i] > 0 ? std::min(1e-2, nR / R0[i]) : 1e-2);
+    }
+    if (!any) break;
+    batch_pcg(B, rtol, maxk, iters, nonf);
+    for (int i = 0; i < n; ++i) {
+      if (!(rtol[i] > 0)) continue;
+      qcad_mesh_s* m = ms[i];
+      kry[i] += iters[i];
+      its[i] = it;
+      if (nonf[i]) {
+        bad[i] = 1;
+        continue;
+      }
+      const double nR = std::sqrt(R[i].r2);
+      double alpha = 1.0;
+      ResStats Rt{};
+      for (int ls = 0; ls <= 30; ++ls) {
+        CK(cudaMemsetAsync(m->stats.p, 0, sizeof(double), m->stream));
+        launch_newton_trial<float>(m->n_nodes, pa[i], ensure_pcg<float>(m).x, alpha, pb[i], m->stats.as<double>(),
+                                   m->stream);
+        CK(cudaMemcpyAsync(m->h_small + 4, m->stats.p, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+        Rt = eval_residual(m, P[i], pb[i], nullptr, o->linear, 1, nullptr);
+        step[i] = m->h_small[4];
+        if (std::isfinite(Rt.r2) && std::sqrt(Rt.r2) <= (1.0 - 1e-4 * alpha) * nR) break;
+        alpha *= 0.5;
+      }
+      std::swap(pa[i], pb[i]);
+      R[i] = Rt;
+      if (!std::isfinite(R[i].r2)) bad[i] = 1;
+      if (R[i].rmax < o->newton_tol_R && step[i] < o->newton_tol_dphi) conv[i] = 1;
+    }
+  }
+  qcad_status worst = QCAD_OK;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < n; ++i) {
+    qcad_mesh_s* m = ms[i];
+    CK(cudaMemcpyAsync(phis[i], pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    // the mesh's own buffers now hold this iterate in phi_a (keep single-mesh solves consistent)
+    if (pa[i] != m->phi_a.as<double>())
+      CK(cudaMemcpyAsync(m->phi_a.p, pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+    if (reps) {
+      reps[i].newton_iters = its[i];
+      reps[i].krylov_iters_total = kry[i];
+      reps[i].applies_total = kry[i];
+      reps[i].final_res_inf = R[i].rmax;
+      reps[i].final_dphi_inf = step[i];
+      reps[i].seconds = secs;
+      reps[i].status_detail = 0;
+    }
+    const qcad_status st = bad[i] ? QCAD_ERR_NONFINITE : (conv[i] ? QCAD_OK : QCAD_ERR_NOT_CONVERGED);
+    if (worst == QCAD_OK && st != QCAD_OK) worst = st;
+  }
+  if (worst != QCAD_OK) set_message("at least one batch instance did not converge or produced a non-finite value");
+  return worst;
 }
 
 }  // namespace qcad

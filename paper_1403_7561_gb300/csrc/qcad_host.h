@@ -25,6 +25,12 @@ struct PcgScalars {
   int maxit;
   unsigned int counter;
   int nonfinite;
+  // Chebyshev-Jacobi preconditioner: degree (1 = Jacobi), spectral interval [theta - delta,
+  // theta + delta] of D^-1 J, and the phase of the solve (0 during the initial residual, 1 after)
+  int degree;
+  int phase;
+  double theta;
+  double delta;
 };
 
 template <class T>
@@ -37,6 +43,8 @@ struct PcgVecs {
   const T* b;
   const T* dinv;
   const T* c;   // element quadrature coefficients of the operator (8 per element)
+  T* w;         // Chebyshev inner residual
+  T* d[2];      // Chebyshev correction, ping-ponged by step parity
 };
 
 struct ResidualArgs {
@@ -73,6 +81,7 @@ struct ApplyArgs {
 struct LaunchCfg {
   int by = 8;
   int kchunk = 16;
+  int pair = 1;  // FP32 operators: two nodes per thread with packed f32x2 arithmetic
 };
 
 void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg, cudaStream_t s);
@@ -86,6 +95,24 @@ template <class T>
 void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
 template <class T>
 void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
+// Chebyshev-Jacobi form: the update kernel starts the recurrence (w = r, d = D^-1 r / theta,
+// z = d) and step j = 1..degree-1 applies J to d_{j-1}; the last step forms r.z and finishes
+// the iteration (or the initial residual when phase = 0).
+template <class T>
+void launch_pcg_update_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
+template <class T>
+void launch_pcg_init_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
+template <class T>
+void launch_cheb_step(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, int step, int last, LaunchCfg cfg,
+                      cudaStream_t s);
+// One power step for the largest eigenvalue of D^-1 J: v_next = D^-1 (J v) / |.|; acc[0] += v.Jv,
+// acc[1] += v.D v, acc[2] += |D^-1 J v|^2 (the caller normalizes with acc[2]).
+template <class T>
+void launch_power_step(long long n, const T* v, const T* Jv, const T* dinv, T* vnext, double* acc, cudaStream_t s);
+template <class T>
+void launch_scale(long long n, T* v, double a, cudaStream_t s);
+template <class T>
+void launch_random_free(const Grid<T>& g, unsigned long long seed, T* v, cudaStream_t s);
 
 // phi_out = phi + alpha * delta on every node; stats[0] accumulates max |alpha delta| (ordered bits).
 template <class T>
@@ -137,4 +164,28 @@ namespace qcad {
 // Kernel launches issued by the library (graph replays count their kernels).
 void note_launch(int n = 1);
 long long launch_count();
+}  // namespace qcad
+
+namespace qcad {
+int apply_blocks_per_sm(int precision, int by, int pair);
+
+// Work-table entries of the batched kernels (sorted by begin = first block of the entry).
+struct BatchApplyEntry {
+  Grid<float> g;
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  int kchunk;
+  int tiles_x, tiles_y;
+  int begin;
+};
+struct BatchVecEntry {
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  int n;
+  int blocks;
+  int begin;
+};
+void launch_batch_pcg_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, int by, cudaStream_t s);
+void launch_batch_pcg_update(const BatchVecEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
+void launch_batch_status(const BatchVecEntry* tab, int n_inst, int* status, cudaStream_t s);
 }  // namespace qcad

@@ -237,17 +237,18 @@ __device__ __forceinline__ void block_max_atomic(double v, double* dst) {
 // The Op is copied per thread, so its data members double as per-thread
 // accumulators (constructed zeroed on the host). Node and element indices are
 // 32-bit; mesh creation rejects meshes whose 8*n_elems or n_nodes exceed 2^31.
+// Body of the skeleton for tile (bx, by) and (vector, z chunk) index bz; called by
+// march_kernel with the block index and by the batched kernels with a tile from a work table.
 template <class T, int BY, class Op>
-__global__ void __launch_bounds__(QCAD_BX * BY)
-march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
+__device__ __forceinline__ void march_body(const Grid<T>& g, const Op& op_in, int kchunk, int bx, int by, int bz) {
   constexpr int BX = QCAD_BX;
   constexpr int NF = Op::NF;
   using ED = typename Op::ED;
   if (op_in.skip()) return;
-  // blockIdx.z enumerates (vector, z chunk) pairs
+  // bz enumerates (vector, z chunk) pairs
   const int nch = (g.nzn + kchunk - 1) / kchunk;
   Op op = op_in;
-  op.set_vec(blockIdx.z / nch);
+  op.set_vec(bz / nch);
   __shared__ T ring[4][BY][BX];
   __shared__ T s1[NF][BY][BX];
   __shared__ T s2[NF][BY][BX];
@@ -255,9 +256,9 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
   __shared__ T say[BY][BX];
   __shared__ T sb[BY][BX];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * (BX - 2) - 1 + tx;
-  const int j = blockIdx.y * (BY - 2) - 1 + ty;
-  const int k0 = (blockIdx.z % nch) * kchunk;
+  const int i = bx * (BX - 2) - 1 + tx;
+  const int j = by * (BY - 2) - 1 + ty;
+  const int k0 = (bz % nch) * kchunk;
   const int k1 = min(k0 + kchunk, g.nzn);
   const int plane = (int)g.plane;
   const bool nin = (i >= 0 && i < g.nxn && j >= 0 && j < g.nyn);
@@ -396,6 +397,12 @@ march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
     if (writer) op.node(g, nij + k * plane, i, j, k, vc, stiff, mass);
   }
   op.finish();
+}
+
+template <class T, int BY, class Op>
+__global__ void __launch_bounds__(QCAD_BX * BY)
+march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
+  march_body<T, BY, Op>(g, op_in, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Launch geometry of the skeleton for a grid (nvec vectors along blockIdx.z).

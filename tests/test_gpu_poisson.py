@@ -174,3 +174,74 @@ def test_not_converged_is_reported(q):
     assert rep["status"] == "NOT_CONVERGED"
     assert rep["newton_iters"] == 1
     assert torch.isfinite(phi).all()
+
+
+@pytest.mark.parametrize("name", ["dqd_24x24x16_4K", "dqd_37x33x21_0p5K", "mos_cap_16x16x32"])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("degree", [2, 3, 5, 0])
+def test_chebyshev_preconditioned_solve(q, name, precision, degree):
+    # Chebyshev-Jacobi PCG (degree 0 = autotuned) converges to the same unique solution
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    phi_o, rep_o = P.solve()
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision, cheb_degree=degree), phi)
+    assert rep["status"] == "OK", rep
+    assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
+
+
+def batch_devices():
+    # uneven sizes (ragged tiles, a mesh one tile wide) with their own seeds, so each
+    # instance has its own gate voltages
+    shapes = [(12, 12, 12), (20, 16, 12), (37, 33, 21), (8, 8, 16), (16, 16, 16)]
+    return [W.five_gate_device(n=s, seed=7, stream=i, T=4.0, with_subdomain=False) for i, s in enumerate(shapes)]
+
+
+def test_batched_solve_matches_oracle(q):
+    devs = batch_devices()
+    meshes = [q.qcad_mesh_create(d) for d in devs]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs], q.make_opts(precision=1), phis)
+    assert status == "OK", reps
+    for d, phi, rep in zip(devs, phis, reps):
+        P = PoissonProblem(d)
+        phi_o, rep_o = P.solve()
+        assert rep_o["converged"]
+        assert rep["final_res_inf"] < 1e-10 and rep["final_dphi_inf"] < 1e-10
+        assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9, (d["nx"], d["ny"])
+
+
+def test_batched_solve_agrees_with_single_solves_and_warm_starts(q):
+    devs = batch_devices()[:3]
+    meshes = [q.qcad_mesh_create(d) for d in devs]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    _, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs], q.make_opts(precision=1), phis)
+    assert status == "OK"
+    for d, m, phi in zip(devs, meshes, phis):
+        one = torch.zeros_like(phi)
+        q.qcad_poisson_solve(m, d["bias"], q.make_opts(precision=1), one)
+        assert torch.max(torch.abs(one - phi)).item() <= 1e-9
+    # warm start from the converged potentials: every instance stops after at most one step
+    reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs],
+                                              q.make_opts(precision=1, warm_start=1), phis)
+    assert status == "OK"
+    assert all(r["newton_iters"] <= 1 for r in reps)
+
+
+def test_batched_solve_rejects_bad_batches(q):
+    devs = batch_devices()[:2]
+    meshes = [q.qcad_mesh_create(d) for d in devs]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    biases = [d["bias"] for d in devs]
+    with pytest.raises(q.QcadError) as e:
+        q.qcad_poisson_solve_batch(meshes, biases, q.make_opts(precision=0), phis)
+    assert e.value.code == 1
+    with pytest.raises(q.QcadError):
+        q.qcad_poisson_solve_batch([meshes[0], meshes[0]], [biases[0], biases[0]], q.make_opts(precision=1),
+                                   [phis[0], phis[0]])
+    # one instance capped at one Newton step is reported, the other converges
+    reps, status = q.qcad_poisson_solve_batch(meshes, biases, q.make_opts(precision=1, max_newton=1), phis,
+                                              allow_not_converged=True)
+    assert status == "NOT_CONVERGED"
+    assert all(r["newton_iters"] == 1 for r in reps)
