@@ -247,12 +247,23 @@ qcad_status qcad_profile_enable(qcad_mesh_t m, int enable);
 qcad_status qcad_profile_reset(qcad_mesh_t m);
 qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches, double* total_ms);
 
-/* Launch configuration of the z-marching kernels (tile rows 4, 8, 16 or 32 and
- * z-chunk length), per kernel family: 0 residual, 1 FP64 apply, 2 FP32 apply.
- * The autotuner sets these; the defaults are 8 and 16. */
-qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk);
-qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk,
-                          float* best_ms);
+/* Launch configuration of the z-marching kernels, per kernel family: 0 FP64
+ * residual, 1 FP64 linear operators (Jacobian apply, PCG apply, Chebyshev
+ * step), 2 FP32 linear operators. tile_rows: warps per block, 4, 8, 16 or 32;
+ * z_chunk: node planes per block, 1..4096. variant (families 1 and 2; ignored
+ * for 0): 0 element-gather kernel, 1 element-gather with two nodes per thread
+ * and packed f32x2 arithmetic (FP32 only; FP64 runs variant 0), 2
+ * plane-factorized kernel with one node row per thread, 3 plane-factorized
+ * with two node rows per thread. Shapes a variant does not support are
+ * clamped to the nearest supported one (FP64 plane-factorized: at most 16
+ * warps, 8 with two rows). Defaults: variant 3, 8 warps, z chunk 16.
+ * qcad_autotune times the Jacobian apply of the given precision (0 FP64,
+ * 1 FP32) over variants, tile rows and z chunks on the mesh, keeps the
+ * fastest for that family and returns it (outputs may be NULL); best_ms is
+ * its time per apply. */
+qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_rows, int z_chunk);
+qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* variant, int* tile_rows,
+                          int* z_chunk, float* best_ms);
 
 /* Allocation-free residual, for callers that cannot allocate device memory
  * (code inside another framework's allocator or memory pool, under CUDA

@@ -106,8 +106,9 @@ _sigs = {
     "qcad_profile_enable": [_P, C.c_int],
     "qcad_profile_reset": [_P],
     "qcad_profile_read": [_P, C.c_int, C.POINTER(C.c_int64), _D],
-    "qcad_set_launch": [_P, C.c_int, C.c_int, C.c_int],
-    "qcad_autotune": [_P, C.POINTER(Bias), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)],
+    "qcad_set_launch": [_P, C.c_int, C.c_int, C.c_int, C.c_int],
+    "qcad_autotune": [_P, C.POINTER(Bias), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                      C.POINTER(C.c_float)],
     "qcad_launch_count": [C.POINTER(C.c_int64)],
     "qcad_poisson_residual_noalloc": [C.POINTER(Device), C.POINTER(Bias), _P, _P, _P, _P, _D],
     "qcad_last_error": [],
@@ -351,8 +352,8 @@ def qcad_profile_read(mesh: Mesh, kernel_class):
     return n.value, ms.value
 
 
-def qcad_set_launch(mesh: Mesh, family: int, tile_rows: int, z_chunk: int):
-    _check(_lib.qcad_set_launch(mesh.handle, int(family), int(tile_rows), int(z_chunk)))
+def qcad_set_launch(mesh: Mesh, family: int, variant: int, tile_rows: int, z_chunk: int):
+    _check(_lib.qcad_set_launch(mesh.handle, int(family), int(variant), int(tile_rows), int(z_chunk)))
 
 
 def _device_struct(dev: dict):
@@ -406,7 +407,9 @@ def qcad_launch_count():
 
 
 def qcad_autotune(mesh: Mesh, bias: dict, precision=1):
+    """Returns (variant, tile_rows, z_chunk, ms per apply) of the fastest launch shape."""
     b = make_bias(bias)
-    r, z, t = C.c_int(), C.c_int(), C.c_float()
-    _check(_lib.qcad_autotune(mesh.handle, C.byref(b), int(precision), C.byref(r), C.byref(z), C.byref(t)))
-    return r.value, z.value, t.value
+    v, r, z, t = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+    _check(_lib.qcad_autotune(mesh.handle, C.byref(b), int(precision), C.byref(v), C.byref(r), C.byref(z),
+                              C.byref(t)))
+    return v.value, r.value, z.value, t.value

@@ -13,9 +13,11 @@ namespace qcad {
 qcad_status poisson_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* theta,
                           double* phi, qcad_solve_report* rep);
 
-// Times the Jacobian apply of the mesh's current linearization for every
-// (tile rows, z chunk) candidate and keeps the fastest for that precision.
-qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk, float* best) {
+// Times the Jacobian apply (zero input and coefficients: the time does not depend on the
+// values) for every (variant, tile rows, z chunk) candidate and keeps the fastest for that
+// precision.
+qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* variant_out, int* tile_rows,
+                     int* z_chunk, float* best) {
   (void)b;
   if (precision != 0 && precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "precision must be 0 or 1");
   cudaStream_t s = m->stream;
@@ -27,7 +29,6 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
   c.ensure((size_t)m->n_elems * 8 * es + 64);
   CK(cudaMemsetAsync(v.p, 0, n * es, s));
   CK(cudaMemsetAsync(c.p, 0, (size_t)m->n_elems * 8 * es, s));
-  const int rows[4] = {4, 8, 16, 32};
   const int chunks[5] = {8, 16, 32, 64, 128};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -36,14 +37,23 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
   LaunchCfg best_cfg;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
-  for (int variant = 0; variant < (precision == 1 ? 8 : 4); ++variant) {
-    const int r = rows[variant % 4];
-    const int pair = variant / 4;  // FP32 only: 1 = two nodes per thread with packed f32x2
-    if (pair && r == 32) continue;
+  // (variant, warps) shapes: element-gather 0, element-gather with two nodes per thread 1
+  // (FP32), plane-factorized with one 2 or two 3 node rows per thread
+  std::vector<std::pair<int, int>> shapes;
+  for (int r : {4, 8, 16, 32}) shapes.push_back({0, r});
+  if (precision == 1)
+    for (int r : {4, 8, 16}) shapes.push_back({1, r});
+  for (int r : {4, 8, 16, 32})
+    if (precision == 1 || r <= 16) shapes.push_back({2, r});
+  for (int r : {4, 8, 16})
+    if (precision == 1 || r <= 8) shapes.push_back({3, r});
+  for (const auto& sh : shapes) {
+    const int variant = sh.first, r = sh.second;
     // z-chunk lengths that put whole waves of resident blocks on the SMs, plus fixed ones
-    const int bps = apply_blocks_per_sm(precision, r, pair);
-    const long long tiles_xy = pair ? (long long)((m->nxn + 59) / 60) * ((m->nyn + r - 3) / (r - 2))
-                                    : (long long)((m->nxn + 29) / 30) * ((m->nyn + r - 3) / (r - 2));
+    const int bps = apply_blocks_per_sm(precision, r, variant);
+    const int cols = variant == 1 ? 60 : 30;
+    const int trows = (variant == 3 ? 2 * r : r) - 2;
+    const long long tiles_xy = (long long)((m->nxn + cols - 1) / cols) * ((m->nyn + trows - 1) / trows);
     std::vector<int> cands(chunks, chunks + 5);
     for (int w = 1; w <= 6 && bps > 0; ++w) {
       const long long nch = std::max<long long>(1, (long long)w * sms * bps / std::max<long long>(1, tiles_xy));
@@ -56,7 +66,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
       LaunchCfg cfg;
       cfg.by = r;
       cfg.kchunk = ch;
-      cfg.pair = pair;
+      cfg.variant = variant;
       auto run = [&]() {
         if (precision == 0) {
           ApplyArgs<double> a{};
@@ -96,6 +106,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* til
     m->cfg32 = best_cfg;
   m->graph64.key = nullptr;
   m->graph32.key = nullptr;
+  if (variant_out) *variant_out = best_cfg.variant;
   if (tile_rows) *tile_rows = best_cfg.by;
   if (z_chunk) *z_chunk = best_cfg.kchunk;
   if (best) *best = best_ms;
@@ -125,7 +136,7 @@ static int tune_batch_kchunk(qcad_mesh_s* m) {
     LaunchCfg cfg;
     cfg.by = 8;
     cfg.kchunk = ch;
-    cfg.pair = 0;
+    cfg.variant = 0;
     ApplyArgs<float> a{};
     a.v = v.as<float>();
     a.y = y.as<float>();

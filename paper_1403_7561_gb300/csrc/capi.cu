@@ -30,7 +30,8 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
                              double tol, double* evals, double* evecs, qcad_solve_report* rep);
 qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                 double* const* phis, qcad_solve_report* reps);
-qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk, float* best);
+qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* variant, int* tile_rows, int* z_chunk,
+                     float* best);
 qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* stream, const double* theta,
                              const double* phi, double* R, double* stats);
 }  // namespace qcad
@@ -206,15 +207,17 @@ qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches
   });
 }
 
-qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chunk) {
+qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_rows, int z_chunk) {
   return guarded([&] {
     if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
     if (tile_rows != 4 && tile_rows != 8 && tile_rows != 16 && tile_rows != 32)
       throw qcad::Error(QCAD_ERR_INVALID_ARG, "tile_rows must be 4, 8, 16 or 32");
     if (z_chunk < 1 || z_chunk > 4096) throw qcad::Error(QCAD_ERR_INVALID_ARG, "z_chunk out of range");
+    if (variant < 0 || variant > 3) throw qcad::Error(QCAD_ERR_INVALID_ARG, "variant must be 0..3");
     qcad::LaunchCfg c;
     c.by = tile_rows;
     c.kchunk = z_chunk;
+    c.variant = (family == 1 && variant == 1) ? 0 : variant;
     if (family == 0)
       m->cfg_res = c;
     else if (family == 1)
@@ -230,11 +233,11 @@ qcad_status qcad_set_launch(qcad_mesh_t m, int family, int tile_rows, int z_chun
   });
 }
 
-qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* tile_rows, int* z_chunk,
-                          float* best_ms) {
+qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* variant, int* tile_rows,
+                          int* z_chunk, float* best_ms) {
   return guarded([&] {
     need_mesh(m);
-    return qcad::autotune(m, b, precision, tile_rows, z_chunk, best_ms);
+    return qcad::autotune(m, b, precision, variant, tile_rows, z_chunk, best_ms);
   });
 }
 

@@ -1,0 +1,121 @@
+// Launches of the plane-factorized z-march (linmarch.cuh) for the linear ops:
+// Jacobian apply, PCG apply with the fused search-direction update, and the
+// Chebyshev preconditioner step, in FP32 and FP64.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "linmarch.cuh"
+#include "pcg_ops.cuh"
+
+namespace qcad {
+
+// The kernels take more than the default 48 KB of dynamic shared memory; the opt-in is
+// set once per kernel and device.
+template <class T, int BY, int R, class Op>
+static void lin_launch(const Grid<T>& g, const Op& op, int kchunk, cudaStream_t s) {
+  using S = LinShape<T, BY, R>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(lin_march_kernel<T, BY, R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::dyn_bytes) == cudaSuccess)
+      attr_set[dev] = true;
+  }
+  const dim3 grid = lin_grid(g.nxn, g.nyn, g.nzn, BY, R, kchunk);
+  note_launch(), lin_march_kernel<T, BY, R, Op><<<grid, dim3(32, BY), S::dyn_bytes, s>>>(g, op, kchunk);
+}
+
+// Supported (warps, rows per thread): FP32 4/8/16/32 x 1 and 4/8/16 x 2; FP64 4/8/16 x 1 and
+// 4/8 x 2 (shared memory). Other requests are clamped to the nearest supported shape.
+template <class T, class Op>
+static void run_lin(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s) {
+  const int kc = cfg.kchunk > 0 ? cfg.kchunk : 16;
+  const bool two = cfg.variant == 3;
+  if constexpr (std::is_same<T, float>::value) {
+    if (two) {
+      if (cfg.by == 4) lin_launch<T, 4, 2>(g, op, kc, s);
+      else if (cfg.by >= 16) lin_launch<T, 16, 2>(g, op, kc, s);
+      else lin_launch<T, 8, 2>(g, op, kc, s);
+    } else {
+      if (cfg.by == 4) lin_launch<T, 4, 1>(g, op, kc, s);
+      else if (cfg.by == 16) lin_launch<T, 16, 1>(g, op, kc, s);
+      else if (cfg.by >= 32) lin_launch<T, 32, 1>(g, op, kc, s);
+      else lin_launch<T, 8, 1>(g, op, kc, s);
+    }
+  } else {
+    if (two) {
+      if (cfg.by == 4) lin_launch<T, 4, 2>(g, op, kc, s);
+      else lin_launch<T, 8, 2>(g, op, kc, s);
+    } else {
+      if (cfg.by == 4) lin_launch<T, 4, 1>(g, op, kc, s);
+      else if (cfg.by >= 16) lin_launch<T, 16, 1>(g, op, kc, s);
+      else lin_launch<T, 8, 1>(g, op, kc, s);
+    }
+  }
+}
+
+template <class T>
+void launch_apply_lin(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  ApplyOp<T> op = {};
+  op.a = args;
+  run_lin<T>(g, op, cfg, s);
+}
+template void launch_apply_lin<float>(const Grid<float>&, const ApplyArgs<float>&, LaunchCfg, cudaStream_t);
+template void launch_apply_lin<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t);
+
+template <class T>
+void launch_pcg_apply_lin(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  PcgApplyOp<T> op = {};
+  op.v = vecs;
+  op.sc = sc;
+  run_lin<T>(g, op, cfg, s);
+}
+template void launch_pcg_apply_lin<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t);
+template void launch_pcg_apply_lin<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg,
+                                           cudaStream_t);
+
+template <class T>
+void launch_cheb_step_lin(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int step, int last, LaunchCfg cfg,
+                          cudaStream_t s) {
+  ChebStepOp<T> op = {};
+  op.v = vecs;
+  op.sc = sc;
+  op.step = step;
+  op.last = last;
+  run_lin<T>(g, op, cfg, s);
+}
+template void launch_cheb_step_lin<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, int, int, LaunchCfg,
+                                          cudaStream_t);
+template void launch_cheb_step_lin<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, int, int, LaunchCfg,
+                                           cudaStream_t);
+
+// Resident blocks per SM of the plane-factorized apply (0 if the query fails).
+template <class T, int BY, int R>
+static int lin_occupancy() {
+  using S = LinShape<T, BY, R>;
+  int n = 0;
+  cudaFuncSetAttribute(lin_march_kernel<T, BY, R, ApplyOp<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)S::dyn_bytes);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lin_march_kernel<T, BY, R, ApplyOp<T>>, 32 * BY,
+                                                    S::dyn_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int lin_blocks_per_sm(int precision, int by, int rows) {
+  if (precision == 1) {
+    if (rows == 2) return by == 4 ? lin_occupancy<float, 4, 2>() : by >= 16 ? lin_occupancy<float, 16, 2>()
+                                                                             : lin_occupancy<float, 8, 2>();
+    return by == 4 ? lin_occupancy<float, 4, 1>() : by == 16 ? lin_occupancy<float, 16, 1>()
+                                                  : by >= 32 ? lin_occupancy<float, 32, 1>()
+                                                             : lin_occupancy<float, 8, 1>();
+  }
+  if (rows == 2) return by == 4 ? lin_occupancy<double, 4, 2>() : lin_occupancy<double, 8, 2>();
+  return by == 4 ? lin_occupancy<double, 4, 1>() : by >= 16 ? lin_occupancy<double, 16, 1>()
+                                                            : lin_occupancy<double, 8, 1>();
+}
+
+}  // namespace qcad

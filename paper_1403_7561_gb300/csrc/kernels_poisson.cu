@@ -7,16 +7,13 @@
 #include <type_traits>
 
 #include "march2.cuh"
+#include "pcg_ops.cuh"
 #include "physics.cuh"
 #include "qcad_host.h"
 #include "qcad_internal.cuh"
 
 namespace qcad {
 
-template <class T>
-__device__ __forceinline__ int elem_index(const Grid<T>& g, int i, int j, int k) {
-  return i + g.nx * (j + g.ny * k);
-}
 
 // Diagonal of the assembled stiffness from the 1D operator rows.
 template <class T>
@@ -37,12 +34,6 @@ __device__ __forceinline__ int dot_of_element(const ResidualArgs& a, int i, int 
   return -1;
 }
 
-template <class T>
-__device__ __forceinline__ C8<T> load_coeffs(const T* c, int e) {
-  C8<T> r;
-  load_c8<T>(c, e, r.c);
-  return r;
-}
 
 // ---------------------------------------------------------------------------
 // Residual R(phi), Jacobian quadrature coefficients c_q = -(q/eps0) w|J| rho'(phi_q),
@@ -137,38 +128,6 @@ struct ResidualOp {
   }
 };
 
-// ---------------------------------------------------------------------------
-// y = J v: separable stiffness stencil plus the element quadrature-point mass
-// term with stored coefficients c; identity on Dirichlet rows unless raw.
-// The optional v.y partial sums run in the storage precision per thread and
-// in FP64 across threads.
-template <class T>
-struct ApplyOp {
-  static constexpr int NF = 1;
-  static constexpr bool STIFF = true;
-  using ED = C8<T>;
-  ApplyArgs<T> a;
-  T acc;
-  __device__ bool skip() const { return false; }
-  __device__ void set_vec(int) {}
-  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const { return in ? a.v[n] : T(0); }
-  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(a.c, elem_index(g, i, j, k)); }
-  __device__ void elem(const Grid<T>&, int, int, int, const T* v, const ED& ed, T (*out)[8], bool) const {
-    qp_mass<T>(v, ed.c, out[0]);
-  }
-  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T vin, T stiff, const T* mass) {
-    T y = stiff + mass[0];
-    if (!a.raw && grid_is_dir(g, i, j, k)) y = vin;
-    a.y[n] = y;
-    acc += vin * y;
-  }
-  __device__ void finish() {
-    if (a.dot) {
-      double s[1] = {(double)acc};
-      block_sum_atomic<1>(s, a.dot);
-    }
-  }
-};
 
 template <class T, class Op>
 static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s, int nvec = 1) {
@@ -212,8 +171,12 @@ void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg 
 
 template <class T>
 void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  if (cfg.variant >= 2) {
+    launch_apply_lin<T>(g, args, cfg, s);
+    return;
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (cfg.pair) {
+    if (cfg.variant == 1) {
       launch_apply_pair(g, args, cfg, s);
       return;
     }
@@ -276,56 +239,15 @@ void launch_count_gradient(const Grid<double>& g, const double* phi, const unsig
   run_march<double>(g, op, c, s);
 }
 
-// ---------------------------------------------------------------------------
-// Preconditioned CG with device-resident scalars.
-//
-// Iteration t: apply kernel forms p_t = z_t + beta_t p_{t-1} while loading
-// (beta_t = rz_t / rz_{t-1}), writes p_t and Ap_t and accumulates p.Ap into
-// pAp[t%4]; update kernel forms alpha_t = rz_t / pAp_t, updates x, r, the
-// Jacobi-preconditioned z = D^-1 r, accumulates r.z and r.r into slot
-// (t+1)%4, and its last block advances t, tests convergence and clears the
-// slots the next iteration accumulates into.
-template <class T>
-struct PcgApplyOp {
-  static constexpr int NF = 1;
-  static constexpr bool STIFF = true;
-  using ED = C8<T>;
-  PcgVecs<T> v;
-  PcgScalars* sc;
-  int t;
-  T beta;
-  T acc;
-  __device__ bool skip() const { return sc->done != 0; }
-  __device__ void set_vec(int) {
-    t = sc->t;
-    beta = t > 0 ? (T)(sc->rz[t & 3] / sc->rz[(t - 1) & 3]) : T(0);
-  }
-  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const {
-    if (!in) return T(0);
-    // p_{t-1} lives in p[(t+1)&1]; p_t is written to p[t&1], so halo reads never see new values
-    return t > 0 ? v.z[n] + beta * v.p[(t + 1) & 1][n] : v.z[n];
-  }
-  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(v.c, elem_index(g, i, j, k)); }
-  __device__ void elem(const Grid<T>&, int, int, int, const T* x, const ED& ed, T (*out)[8], bool) const {
-    qp_mass<T>(x, ed.c, out[0]);
-  }
-  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T pin, T stiff, const T* mass) {
-    T y = stiff + mass[0];
-    if (grid_is_dir(g, i, j, k)) y = pin;
-    v.p[t & 1][n] = pin;
-    v.Ap[n] = y;
-    acc += pin * y;
-  }
-  __device__ void finish() {
-    double s[1] = {(double)acc};
-    block_sum_atomic<1>(s, &sc->pAp[t & 3]);
-  }
-};
 
 template <class T>
 void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  if (cfg.variant >= 2) {
+    launch_pcg_apply_lin<T>(g, vecs, sc, cfg, s);
+    return;
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (cfg.pair) {
+    if (cfg.variant == 1) {
       launch_pcg_apply_pair(g, vecs, sc, cfg, s);
       return;
     }
@@ -338,20 +260,6 @@ void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchC
 template void launch_pcg_apply<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t);
 template void launch_pcg_apply<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t);
 
-// Last block of a grid: returns true in exactly one block after all blocks' prior writes are visible.
-__device__ __forceinline__ bool last_block_of(unsigned int* counter, unsigned int total) {
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) am_last = atomicAdd(counter, 1u) == total - 1;
-  __syncthreads();
-  return am_last;
-}
-__device__ __forceinline__ bool last_block(unsigned int* counter) {
-  return last_block_of(counter, gridDim.x * gridDim.y * gridDim.z);
-}
-
-__device__ __forceinline__ double ld_volatile(const double* p) { return *(volatile const double*)p; }
 
 constexpr int VEC_THREADS = 256;
 
@@ -363,48 +271,6 @@ static int vec_blocks(long long n) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// Last block's bookkeeping after r.z is complete. Phase 1 (after iteration t): advance t,
-// clear the slots the next iteration accumulates into, test convergence. Phase 0 (after
-// the initial residual of a Chebyshev-preconditioned solve): record ||r0||^2, start at t = 0.
-__device__ __forceinline__ void pcg_finish(PcgScalars* sc, int t, double alpha_d) {
-  if (sc->phase == 0) {
-    const double rr0 = ld_volatile(&sc->rr[0]);
-    const double rz0 = ld_volatile(&sc->rz[0]);
-    sc->rr0 = rr0;
-    sc->t = 0;
-    sc->iters = 0;
-    sc->phase = 1;
-    sc->pAp[0] = 0.0;
-    sc->rz[1] = 0.0;
-    sc->rr[1] = 0.0;
-    if (!(rr0 == rr0) || !(rz0 == rz0) || rr0 > 1e300 || rz0 < 0.0) {
-      sc->nonfinite = 1;
-      sc->done = 1;
-    } else if (rr0 == 0.0) {
-      sc->done = 1;
-    }
-    sc->counter = 0;
-    return;
-  }
-  const double rr_new = ld_volatile(&sc->rr[(t + 1) & 3]);
-  const double rz_new = ld_volatile(&sc->rz[(t + 1) & 3]);
-  const int tn = t + 1;
-  sc->t = tn;
-  sc->pAp[tn & 3] = 0.0;
-  sc->rz[(tn + 1) & 3] = 0.0;
-  sc->rr[(tn + 1) & 3] = 0.0;
-  const bool bad = !(alpha_d == alpha_d) || !(rr_new == rr_new) || !(rz_new == rz_new) || fabs(alpha_d) > 1e300 ||
-                   alpha_d <= 0.0 || rz_new < 0.0;
-  if (bad) {
-    sc->nonfinite = 1;
-    sc->done = 1;
-    sc->iters = tn;
-  } else if (rr_new <= sc->tol2 * sc->rr0 || tn >= sc->maxit) {
-    sc->done = 1;
-    sc->iters = tn;
-  }
-  sc->counter = 0;
-}
 
 // Sums two per-thread partials over the block (FP64 across threads) and adds them to dst0, dst1.
 __device__ __forceinline__ void block_sum2_atomic(double v0, double v1, double* dst0, double* dst1) {
@@ -579,61 +445,16 @@ void launch_pcg_init_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_
 template void launch_pcg_init_cheb<float>(long long, PcgVecs<float>, PcgScalars*, cudaStream_t);
 template void launch_pcg_init_cheb<double>(long long, PcgVecs<double>, PcgScalars*, cudaStream_t);
 
-template <class T>
-struct ChebStepOp {
-  static constexpr int NF = 1;
-  static constexpr bool STIFF = true;
-  using ED = C8<T>;
-  PcgVecs<T> v;
-  PcgScalars* sc;
-  int step, last;
-  int t, slot;
-  T c1, c2;
-  T acc;
-  __device__ bool skip() const { return sc->done != 0; }
-  __device__ void set_vec(int) {
-    t = sc->t;
-    slot = sc->phase == 0 ? 0 : ((t + 1) & 3);
-    const double sigma = sc->theta / sc->delta;
-    double rho_prev = 1.0 / sigma, rho = rho_prev;
-    for (int q = 1; q <= step; ++q) {
-      rho_prev = rho;
-      rho = 1.0 / (2.0 * sigma - rho_prev);
-    }
-    c1 = (T)(rho * rho_prev);
-    c2 = (T)(2.0 * rho / sc->delta);
-  }
-  __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const {
-    return in ? v.d[(step - 1) & 1][n] : T(0);
-  }
-  __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(v.c, elem_index(g, i, j, k)); }
-  __device__ void elem(const Grid<T>&, int, int, int, const T* x, const ED& ed, T (*out)[8], bool) const {
-    qp_mass<T>(x, ed.c, out[0]);
-  }
-  __device__ void node(const Grid<T>& g, int n, int i, int j, int k, T dold, T stiff, const T* mass) {
-    T y = stiff + mass[0];
-    if (grid_is_dir(g, i, j, k)) y = dold;
-    const T wn = v.w[n] - y;
-    const T dn = c1 * dold + c2 * v.dinv[n] * wn;
-    const T zn = v.z[n] + dn;
-    v.w[n] = wn;
-    v.z[n] = zn;
-    v.d[step & 1][n] = dn;
-    if (last) acc += v.r[n] * zn;
-  }
-  __device__ void finish() {
-    if (!last) return;
-    double s1[1] = {(double)acc};
-    block_sum_atomic<1>(s1, &sc->rz[slot]);
-    if (last_block(&sc->counter) && threadIdx.x == 0 && threadIdx.y == 0) pcg_finish(sc, t, 1.0);
-  }
-};
 
 template <class T>
 void launch_cheb_step(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int step, int last, LaunchCfg cfg,
                       cudaStream_t s) {
+  if (cfg.variant >= 2) {
+    launch_cheb_step_lin<T>(g, vecs, sc, step, last, cfg, s);
+    return;
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (cfg.pair) {
+    if (cfg.variant == 1) {
       launch_cheb_step_pair(g, vecs, sc, step, last, cfg, s);
       return;
     }
@@ -681,17 +502,21 @@ struct PcgApply2Op {
   float beta;
   float acc;
   __device__ bool skip() const { return sc->done != 0; }
+  const float* pprev;
+  float* pcur;
   __device__ void set_vec(int) {
     t = sc->t;
     beta = t > 0 ? (float)(sc->rz[t & 3] / sc->rz[(t - 1) & 3]) : 0.f;
+    pprev = (t & 1) ? v.p[0] : v.p[1];
+    pcur = (t & 1) ? v.p[1] : v.p[0];
   }
-  __device__ float load(int n, bool) const { return t > 0 ? v.z[n] + beta * v.p[(t + 1) & 1][n] : v.z[n]; }
+  __device__ float load(int n, bool) const { return t > 0 ? v.z[n] + beta * pprev[n] : v.z[n]; }
   __device__ void edata(const Grid<float>& g, int i, int j, int k, float (&c)[8]) const {
     load_c8<float>(v.c, elem_index(g, i, j, k), c);
   }
   __device__ void node(const Grid<float>& g, int n, int i, int j, int k, float pin, float y) {
     if (grid_is_dir(g, i, j, k)) y = pin;
-    v.p[t & 1][n] = pin;
+    pcur[n] = pin;
     v.Ap[n] = y;
     acc += pin * y;
   }
@@ -706,6 +531,8 @@ struct ChebStep2Op {
   PcgScalars* sc;
   int step, last;
   int t, slot;
+  const float* dprev;
+  float* dcur;
   float c1, c2;
   float acc;
   __device__ bool skip() const { return sc->done != 0; }
@@ -720,8 +547,10 @@ struct ChebStep2Op {
     }
     c1 = (float)(rho * rho_prev);
     c2 = (float)(2.0 * rho / sc->delta);
+    dprev = (step & 1) ? v.d[0] : v.d[1];
+    dcur = (step & 1) ? v.d[1] : v.d[0];
   }
-  __device__ float load(int n, bool) const { return v.d[(step - 1) & 1][n]; }
+  __device__ float load(int n, bool) const { return dprev[n]; }
   __device__ void edata(const Grid<float>& g, int i, int j, int k, float (&c)[8]) const {
     load_c8<float>(v.c, elem_index(g, i, j, k), c);
   }
@@ -732,7 +561,7 @@ struct ChebStep2Op {
     const float zn = v.z[n] + dn;
     v.w[n] = wn;
     v.z[n] = zn;
-    v.d[step & 1][n] = dn;
+    dcur[n] = dn;
     if (last) acc += v.r[n] * zn;
   }
   __device__ void finish() {
@@ -966,10 +795,11 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace qcad {
 // Resident blocks per SM of the plain Jacobian apply kernel for a launch shape (autotuner).
-int apply_blocks_per_sm(int precision, int by, int pair) {
+int apply_blocks_per_sm(int precision, int by, int variant) {
+  if (variant >= 2) return lin_blocks_per_sm(precision, by, variant == 3 ? 2 : 1);
   int n = 0;
   cudaError_t e = cudaSuccess;
-  if (precision == 1 && pair) {
+  if (precision == 1 && variant == 1) {
     if (by == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<4, Apply2Op>, 32 * 4, 0);
     else if (by == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<16, Apply2Op>, 32 * 16, 0);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, march2_kernel<8, Apply2Op>, 32 * 8, 0);

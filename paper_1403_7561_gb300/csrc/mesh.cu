@@ -209,6 +209,14 @@ void build_grid(GridDev<T>& gd, const GridTables& t, const std::vector<double>& 
   upload<T>(gd.mzx, t.mzx, s);
   upload<T>(gd.mzy, t.mzy, s);
   upload<T>(gd.kzz, t.kzz, s);
+  std::vector<double> zt(12 * (t.kzz.size() / 3), 0.0);
+  for (size_t k = 0; k < t.kzz.size() / 3; ++k)
+    for (int q = 0; q < 3; ++q) {
+      zt[12 * k + q] = t.mzx[3 * k + q];
+      zt[12 * k + 3 + q] = t.mzy[3 * k + q];
+      zt[12 * k + 6 + q] = t.kzz[3 * k + q];
+    }
+  upload<T>(gd.zt, zt, s);
   upload<T>(gd.hx, hx, s);
   upload<T>(gd.hy, hy, s);
   upload<T>(gd.hz, hz, s);
@@ -227,6 +235,7 @@ void build_grid(GridDev<T>& gd, const GridTables& t, const std::vector<double>& 
   g.mzx = gd.mzx.template as<T>();
   g.mzy = gd.mzy.template as<T>();
   g.kzz = gd.kzz.template as<T>();
+  g.zt = gd.zt.template as<T>();
   g.hx = gd.hx.template as<T>();
   g.hy = gd.hy.template as<T>();
   g.hz = gd.hz.template as<T>();

@@ -60,7 +60,7 @@ struct GridTables {
 // Per-precision device copy of a grid's tables.
 template <class T>
 struct GridDev {
-  DevBuf mx, kx, my, ky, mzx, mzy, kzz, hx, hy, hz;
+  DevBuf mx, kx, my, ky, mzx, mzy, kzz, zt, hx, hy, hz;
   Grid<T> g{};
 };
 

@@ -78,10 +78,14 @@ struct ApplyArgs {
   int raw;       // 1: no identity override on Dirichlet rows (adjoint column sums)
 };
 
+// Launch shape of the z-marching kernels: by warps (tile rows) per block, kchunk node planes
+// per block, and for the linear operators the kernel variant: 0 element-gather, 1 element-gather
+// with two nodes per thread and packed f32x2 arithmetic (FP32 only), 2 plane-factorized with one
+// node row per thread, 3 plane-factorized with two node rows per thread.
 struct LaunchCfg {
   int by = 8;
   int kchunk = 16;
-  int pair = 1;  // FP32 operators: two nodes per thread with packed f32x2 arithmetic
+  int variant = 3;
 };
 
 void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg, cudaStream_t s);
@@ -167,7 +171,18 @@ long long launch_count();
 }  // namespace qcad
 
 namespace qcad {
-int apply_blocks_per_sm(int precision, int by, int pair);
+// Plane-factorized launches of the linear ops (variants 2 and 3).
+template <class T>
+void launch_apply_lin(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s);
+template <class T>
+void launch_pcg_apply_lin(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
+template <class T>
+void launch_cheb_step_lin(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int step, int last, LaunchCfg cfg,
+                          cudaStream_t s);
+int lin_blocks_per_sm(int precision, int by, int rows);
+
+// Resident blocks per SM of the Jacobian apply of a precision (0 FP64, 1 FP32) and variant.
+int apply_blocks_per_sm(int precision, int by, int variant);
 
 // Work-table entries of the batched kernels (sorted by begin = first block of the entry).
 struct BatchApplyEntry {

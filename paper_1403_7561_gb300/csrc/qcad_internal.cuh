@@ -38,6 +38,7 @@ struct Grid {
   const T* mzx;          // [nzn*3] kappa_x-weighted 1D mass along z
   const T* mzy;          // [nzn*3] kappa_y-weighted 1D mass along z
   const T* kzz;          // [nzn*3] kappa_z-weighted 1D stiffness along z
+  const T* zt;           // [nzn*12] mzx, mzy, kzz rows of each plane packed (3 zeros pad), or null
   const T* hx;           // [nx] element sizes
   const T* hy;           // [ny]
   const T* hz;           // [nz]

@@ -1,14 +1,19 @@
 """Workloads for kernel profiling (ncu) of the library.
 
-``step``: one warm-up pass of the full hot path on a device, then one more
-pass; prints the library's kernel-launch counts of both so that a profiler
-can skip the warm-up (``ncu -s <warmup launches> -c <step launches>``).
+``step``: launch autotuning, then one warm-up pass of the full hot path on a
+device (mixed Newton with autotuned Chebyshev degree, dot counts, adjoint,
+eigenpairs), then one more pass; prints the library's kernel-launch counts.
+
+``solve``: launch autotuning, then one mixed-precision Poisson solve with the
+autotuned Chebyshev degree; used for captures of the PCG kernels
+(``ncu -k regex:PcgApply -s <n> -c <k>``).
 
 ``apply``: the Jacobian apply of one precision on a device's linearization
 at the Laplace initial guess, repeated; used for single-kernel captures.
 
 Usage:
   python -m paper_1403_7561_gb300.profile_driver step  [--workload NAME]
+  python -m paper_1403_7561_gb300.profile_driver solve [--workload NAME]
   python -m paper_1403_7561_gb300.profile_driver apply [--workload NAME] [--precision 0|1] [--reps N]
 """
 import argparse
@@ -22,7 +27,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["step", "apply"])
+    ap.add_argument("mode", choices=["step", "solve", "apply"])
     ap.add_argument("--workload", default="dqd_128x128x96_4K")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
@@ -36,8 +41,15 @@ def main():
     bias = dev["bias"]
     m = q.qcad_mesh_create(dev)
     phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    if a.mode == "step":
-        opts = q.make_opts(precision=1)
+    if a.mode in ("step", "solve"):
+        q.qcad_autotune(m, bias, precision=1)
+        opts = q.make_opts(precision=1, cheb_degree=0)
+    if a.mode == "solve":
+        rep = q.qcad_poisson_solve(m, bias, opts, phi)
+        torch.cuda.synchronize()
+        print("solve done: %d nodes, %d Newton, %d Krylov iterations" % (m.n_nodes, rep["newton_iters"],
+                                                                          rep["krylov_iters_total"]))
+    elif a.mode == "step":
 
         def step():
             q.qcad_poisson_solve(m, bias, opts, phi)

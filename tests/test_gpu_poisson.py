@@ -119,17 +119,43 @@ def test_newton_solve_matches_oracle(q, name, precision):
     assert np.max(np.abs(P.residual(host(phi)))) < 1e-9
 
 
-def test_solve_is_independent_of_launch_configuration(q):
+@pytest.mark.parametrize("name", ["dqd_37x33x21_0p5K", "dqd_61x62x40_4K", "dqd_3x1x7_4K"])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_jacobian_apply_every_launch_shape(q, name, precision, variant):
+    # every kernel variant and tile shape, z chunks from 1 plane to more than the mesh
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    m = q.qcad_mesh_create(dev)
+    phi_np = perturbed_phi(P, 4)
+    rng = np.random.default_rng(5)
+    v_np = rng.standard_normal(P.mesh.n_nodes)
+    v_np[P.dir] = 0.0
+    yo = P.jacobian(phi_np) @ v_np
+    yo[P.dir] = 0.0
+    tol = 1e-12 if precision == 0 else 2e-6
+    y = torch.empty(P.mesh.n_nodes, dtype=torch.float64, device="cuda")
+    for rows, ch in ((4, 3), (8, 16), (16, 1), (32, 64), (8, 2)):
+        q.qcad_set_launch(m, 2 if precision else 1, variant, rows, ch)
+        y.fill_(float("nan"))
+        q.qcad_poisson_jv(m, dev["bias"], dev_tensor(phi_np), dev_tensor(v_np), y, precision)
+        assert np.max(np.abs(host(y) - yo)) <= tol * np.max(np.abs(yo)), (rows, ch)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_is_independent_of_launch_configuration(q, precision):
     dev = CASES["dqd_37x33x21_0p5K"]()
     m = q.qcad_mesh_create(dev)
     ref = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), ref)
-    for fam in (0, 1, 2):
-        for rows, ch in ((4, 3), (16, 64), (8, 1)):
-            q.qcad_set_launch(m, fam, rows, ch)
-    phi = torch.zeros_like(ref)
-    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), phi)
-    assert torch.max(torch.abs(phi - ref)).item() <= 1e-9
+    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision), ref)
+    for variant in (0, 1, 2, 3):
+        for degree in (1, 3):
+            for rows, ch in ((4, 3), (16, 64), (8, 1)):
+                for fam in (0, 1, 2):
+                    q.qcad_set_launch(m, fam, variant, rows, ch)
+                phi = torch.zeros_like(ref)
+                q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision, cheb_degree=degree), phi)
+                assert torch.max(torch.abs(phi - ref)).item() <= 1e-9, (variant, degree, rows, ch)
 
 
 def test_electron_counts_and_fixed_charge(q):
@@ -160,7 +186,9 @@ def test_invalid_arguments_are_rejected(q):
     with pytest.raises(q.QcadError):
         q.qcad_poisson_solve(m, dict(dev["bias"], T=-1.0), q.make_opts(), phi)
     with pytest.raises(q.QcadError):
-        q.qcad_set_launch(m, 0, 5, 16)
+        q.qcad_set_launch(m, 0, 0, 5, 16)
+    with pytest.raises(q.QcadError):
+        q.qcad_set_launch(m, 2, 4, 8, 16)
     bad_dev = dict(dev, nx=0)
     with pytest.raises(q.QcadError):
         q.qcad_mesh_create(bad_dev)
