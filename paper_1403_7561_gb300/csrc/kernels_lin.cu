@@ -18,8 +18,11 @@ static void lin_launch(const Grid<T>& g, const Op& op, int kchunk, cudaStream_t 
   static bool attr_set[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    // the whole shared-memory carveout: blocks per SM are limited by shared memory otherwise
     if (cudaFuncSetAttribute(lin_march_kernel<T, BY, R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)S::dyn_bytes) == cudaSuccess)
+                             (int)S::dyn_bytes) == cudaSuccess &&
+        cudaFuncSetAttribute(lin_march_kernel<T, BY, R, Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100) == cudaSuccess)
       attr_set[dev] = true;
   }
   const dim3 grid = lin_grid(g.nxn, g.nyn, g.nzn, BY, R, kchunk);
@@ -30,7 +33,7 @@ static void lin_launch(const Grid<T>& g, const Op& op, int kchunk, cudaStream_t 
 // 4/8 x 2 (shared memory). Other requests are clamped to the nearest supported shape.
 template <class T, class Op>
 static void run_lin(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s) {
-  const int kc = cfg.kchunk > 0 ? cfg.kchunk : 16;
+  const int kc = cfg.kchunk > 0 ? (cfg.kchunk < 128 ? cfg.kchunk : 128) : 16;  // LinShape::ZMAX
   const bool two = cfg.variant == 3;
   if constexpr (std::is_same<T, float>::value) {
     if (two) {
@@ -97,6 +100,7 @@ static int lin_occupancy() {
   int n = 0;
   cudaFuncSetAttribute(lin_march_kernel<T, BY, R, ApplyOp<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)S::dyn_bytes);
+  cudaFuncSetAttribute(lin_march_kernel<T, BY, R, ApplyOp<T>>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lin_march_kernel<T, BY, R, ApplyOp<T>>, 32 * BY,
                                                     S::dyn_bytes) != cudaSuccess) {
     cudaGetLastError();

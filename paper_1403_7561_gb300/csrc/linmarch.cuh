@@ -39,6 +39,15 @@ __device__ __forceinline__ void lin_cp_async16(void* smem, const void* gmem, boo
   const int n = valid ? 16 : 0;
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
 }
+// One element (4 or 8 bytes) global -> shared, asynchronous.
+template <class T>
+__device__ __forceinline__ void lin_cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void lin_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void lin_cp_wait() {
@@ -73,38 +82,19 @@ struct LinShape {
   static constexpr int TR = BY * R;                  // node rows of a tile (incl. two halo rows)
   static constexpr int NCH = (8 * sizeof(T)) / 16;   // 16-byte chunks of one element's coefficients
   static constexpr int NST = 3;                      // coefficient stages in flight
+  static constexpr int ZMAX = 128;                   // longest z chunk (plane tables held in shared memory)
   static constexpr size_t xch_bytes = (size_t)2 * (2 + 2 + 6) * BY * 32 * sizeof(T);
-  static constexpr size_t dyn_bytes = xch_bytes + (size_t)NST * TR * NCH * 32 * 16;
+  static constexpr size_t zt_bytes = (size_t)(ZMAX + 1) * 12 * sizeof(T);
+  static constexpr size_t vst_bytes = (size_t)3 * 2 * TR * 32 * sizeof(T);  // 3 planes x 2 raw inputs
+  static constexpr size_t dyn_bytes = xch_bytes + zt_bytes + vst_bytes + (size_t)NST * TR * NCH * 32 * 16;
 };
 
-// Launch geometry: x tiles of 30 interior nodes, y tiles of BY*R - 2 interior rows,
+// Launch geometry (kchunk at most LinShape::ZMAX): x tiles of 30 interior nodes, y tiles of
+// BY*R - 2 interior rows,
 // (vector, z chunk) pairs along z.
 inline dim3 lin_grid(int nxn, int nyn, int nzn, int by, int r, int kchunk, int nvec = 1) {
   const int tr = by * r;
   return dim3((nxn + 29) / 30, (nyn + tr - 3) / (tr - 2), ((nzn + kchunk - 1) / kchunk) * nvec);
-}
-
-// Plane tables of the separable z stage: mzx, mzy, kzz rows of plane k (packed, 16-byte aligned).
-template <class T>
-__device__ __forceinline__ void lin_ztab(const T* p, T* z);
-template <>
-__device__ __forceinline__ void lin_ztab<float>(const float* p, float* z) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-  const float4 c = __ldg(reinterpret_cast<const float4*>(p) + 2);
-  z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
-  z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
-  z[8] = c.x;
-}
-template <>
-__device__ __forceinline__ void lin_ztab<double>(const double* p, double* z) {
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p) + h);
-    z[2 * h] = a.x;
-    z[2 * h + 1] = a.y;
-  }
-  z[8] = __ldg(p + 8);
 }
 
 // Op: the linear ops of pcg_ops.cuh (lin_in, lin_out, lin_dir, skip, set_vec, finish, coeffs).
@@ -126,7 +116,9 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
   T(*xch_x)[2][BY][32] = reinterpret_cast<T(*)[2][BY][32]>(dyn);
   T(*xch_y)[2][BY][32] = xch_x + 2;
   T(*xch_s)[6][BY][32] = reinterpret_cast<T(*)[6][BY][32]>(xch_y + 2);
-  uint4* cst = reinterpret_cast<uint4*>(dyn + S::xch_bytes);
+  T* zts = reinterpret_cast<T*>(dyn + S::xch_bytes);  // plane tables of planes k0 .. k1-1
+  T* vst = reinterpret_cast<T*>(dyn + S::xch_bytes + S::zt_bytes);  // [3 planes][2 inputs][TR][32]
+  uint4* cst = reinterpret_cast<uint4*>(dyn + S::xch_bytes + S::zt_bytes + S::vst_bytes);
 
   const int lane = threadIdx.x, ty = threadIdx.y;
   // neighbour warps, clamped: the tile's halo rows read their own warp (their results are unused)
@@ -173,10 +165,21 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
   }
   const int eplane = g.nx * g.ny;
 
-  // coefficients of element layer `layer` into its stage, zeros where the element does not
-  // exist (outside the mesh in x or y, or the layer above the top plane); an empty group for
-  // layers the chunk does not use
-  auto issue_c = [&](int layer) {
+  // one copy group: the raw inputs of node plane vplane (if >= 0; clamped into the chunk's
+  // planes) and the coefficients of element layer `layer`, zeros where the element does not
+  // exist (outside the mesh in x or y, or the layer above the top plane); layers the chunk
+  // does not use are skipped
+  auto issue = [&](int layer, int vplane) {
+    if (vplane >= 0) {
+      T* vs = vst + (size_t)(vplane % 3) * (2 * TR * 32);
+      const int off = min(vplane, kmax) * plane;
+#pragma unroll
+      for (int q = 0; q < Op::NIN; ++q) {
+        const T* src = op.lin_src(q);
+#pragma unroll
+        for (int r = 0; r < R; ++r) lin_cp_async_elem<T>(vs + (q * TR + ty * R + r) * 32 + lane, src + nrow[r] + off);
+      }
+    }
     if (layer >= 0 && layer < k1) {
       uint4* st = cst + (size_t)(layer % NST) * (TR * NCH * 32);
       const bool lok = layer < g.nz;
@@ -205,9 +208,9 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
   };
 
   // ---- prologue: planes k0-1 .. k0+2, interpolations of planes k0-1 .. k0+1, carry of layer k0-1
-  issue_c(k0 - 1);
-  issue_c(k0);
-  issue_c(k0 + 1);
+  issue(k0 - 1, -1);
+  issue(k0, k0 + 3);
+  issue(k0 + 1, k0 + 4);
   T vm[R], vc[R], vp[R], vq[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -225,6 +228,7 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       xinterp(vc[r], X1[r]);
       xinterp(vp[r], X2[r]);
     }
+    for (int q = ty * 32 + lane; q < 12 * (k1 - k0); q += 32 * BY) zts[q] = g.zt[12 * k0 + q];
     // the stiffness buffer of parity 1: the first march step writes parity 0
     T(*pro)[BY][32] = xch_s[1];
     pro[0][ty][lane] = X0[0][0];
@@ -268,10 +272,11 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
   // ---- one node plane k; P is the parity of k - k0 (selects the exchange buffers)
   auto step = [&](int k, auto Pc) {
     constexpr int P = decltype(Pc)::value;
-    issue_c(k + 2);
-    T vnew[R];
+    issue(k + 2, k + 5);
+    typename Op::Pre pre[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) vnew[r] = loadv(r, k + 3);
+    for (int r = 0; r < R; ++r)
+      if (wr[r]) pre[r] = op.lin_pre(nrow[r] + k * plane);
     // X of plane k+2; the first row's is published for the warp below
     T Xq[R][2];
 #pragma unroll
@@ -279,6 +284,7 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
     xch_x[P][0][ty][lane] = Xq[0][0];
     xch_x[P][1][ty][lane] = Xq[0][1];
     // element layer k: the lower corners feed plane k, the upper ones are carried to k+1
+    // (the wait also completes the raw inputs of plane k+3)
     lin_cp_wait<2>();
     const uint4* st = cst + (size_t)(k % NST) * (TR * NCH * 32);
     T Ylo[R][2], Yhi[R][2];
@@ -302,8 +308,7 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
     xch_y[P][0][ty][lane] = Yhi[R - 1][0];
     xch_y[P][1][ty][lane] = Yhi[R - 1][1];
     // stiffness, z stage
-    T z[9];
-    lin_ztab<T>(g.zt + 12 * k, z);
+    const T* z = zts + 12 * (k - k0);
     T ax[R], ay[R], az[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -350,11 +355,16 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       const T stiff = ckx[0] * c1m + ckx[1] * c1 + ckx[2] * c1p + cmx[0] * dm + cmx[1] * d + cmx[2] * dp;
       const bool isdir = pdir || bnd[r] || (ptop && top[r]);
       const T y = isdir ? vc[r] : stiff + mass;
-      if (wr[r]) op.lin_out(nrow[r] + k * plane, vc[r], y);
+      if (wr[r]) op.lin_out(nrow[r] + k * plane, pre[r], vc[r], y);
     }
-    // interpolation of plane k+2 for the next layer, then shift the plane window
+    // interpolation of plane k+2 for the next layer, then shift the plane window (plane k+3
+    // from its stage)
+    const T* vs = vst + (size_t)((k + 3) % 3) * (2 * TR * 32);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      const T x0 = vs[(ty * R + r) * 32 + lane];
+      const T x1 = Op::NIN > 1 ? vs[(TR + ty * R + r) * 32 + lane] : T(0);
+      const T vnew = op.lin_mix(x0, x1);
       T Uq[4];
       uinterp(Xq[r], r + 1 < R ? Xq[r + 1 < R ? r + 1 : r] : Xa, Uq);
 #pragma unroll
@@ -365,7 +375,7 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       vm[r] = vc[r];
       vc[r] = vp[r];
       vp[r] = vq[r];
-      vq[r] = vnew[r];
+      vq[r] = vnew;
     }
   };
 

@@ -39,9 +39,14 @@ struct ApplyOp {
   __device__ const T* coeffs() const { return a.c; }
   // plane-factorized kernels: unpredicated input (n always in range), Dirichlet override
   // flag (the kernel substitutes the input on Dirichlet rows) and the store
+  struct Pre {};
+  static constexpr int NIN = 1;
+  __device__ const T* lin_src(int) const { return a.v; }
+  __device__ T lin_mix(T x0, T) const { return x0; }
   __device__ T lin_in(int n) const { return a.v[n]; }
+  __device__ Pre lin_pre(int) const { return Pre{}; }
   __device__ bool lin_dir() const { return !a.raw; }
-  __device__ void lin_out(int n, T vin, T y) {
+  __device__ void lin_out(int n, const Pre&, T vin, T y) {
     a.y[n] = y;
     acc += vin * y;
   }
@@ -93,9 +98,14 @@ struct PcgApplyOp {
     pcur = (t & 1) ? v.p[1] : v.p[0];
     pin_src = t > 0 ? pprev : v.z;  // at t = 0 beta = 0 and p_{-1} is never read
   }
+  struct Pre {};
+  static constexpr int NIN = 2;
+  __device__ const T* lin_src(int q) const { return q == 0 ? v.z : pin_src; }
+  __device__ T lin_mix(T z, T p) const { return z + beta * p; }
   __device__ T lin_in(int n) const { return v.z[n] + beta * pin_src[n]; }
+  __device__ Pre lin_pre(int) const { return Pre{}; }
   __device__ bool lin_dir() const { return true; }
-  __device__ void lin_out(int n, T pin, T y) {
+  __device__ void lin_out(int n, const Pre&, T pin, T y) {
     pcur[n] = pin;
     v.Ap[n] = y;
     acc += pin * y;
@@ -208,16 +218,31 @@ struct ChebStepOp {
     dprev = (step & 1) ? v.d[0] : v.d[1];
     dcur = (step & 1) ? v.d[1] : v.d[0];
   }
+  // the node data of the epilogue, loaded at the start of the plane (latency off the critical path)
+  struct Pre {
+    T w, dinv, z, r;
+  };
+  static constexpr int NIN = 1;
+  __device__ const T* lin_src(int) const { return dprev; }
+  __device__ T lin_mix(T x0, T) const { return x0; }
   __device__ T lin_in(int n) const { return dprev[n]; }
+  __device__ Pre lin_pre(int n) const {
+    Pre p;
+    p.w = v.w[n];
+    p.dinv = v.dinv[n];
+    p.z = v.z[n];
+    p.r = last ? v.r[n] : T(0);
+    return p;
+  }
   __device__ bool lin_dir() const { return true; }
-  __device__ void lin_out(int n, T dold, T y) {
-    const T wn = v.w[n] - y;
-    const T dn = c1 * dold + c2 * v.dinv[n] * wn;
-    const T zn = v.z[n] + dn;
+  __device__ void lin_out(int n, const Pre& p, T dold, T y) {
+    const T wn = p.w - y;
+    const T dn = c1 * dold + c2 * p.dinv * wn;
+    const T zn = p.z + dn;
     v.w[n] = wn;
     v.z[n] = zn;
     dcur[n] = dn;
-    if (last) acc += v.r[n] * zn;
+    if (last) acc += p.r * zn;
   }
   __device__ T load(const Grid<T>&, int n, bool in, int, int, int) const { return in ? dprev[n] : T(0); }
   __device__ ED edata(const Grid<T>& g, int i, int j, int k) const { return load_coeffs<T>(v.c, elem_index(g, i, j, k)); }
