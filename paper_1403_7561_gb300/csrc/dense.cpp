@@ -1,6 +1,7 @@
 // Small dense symmetric linear algebra for the LOBPCG Rayleigh-Ritz step
-// (host, FP64): Cholesky factorization, cyclic Jacobi eigenvalue iteration,
-// and the generalized symmetric-definite eigenproblem by Cholesky reduction.
+// (host, FP64): Cholesky factorization, the symmetric eigenproblem
+// (Householder tridiagonalization and implicit shifted QR), and the
+// generalized symmetric-definite eigenproblem by Cholesky reduction.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -28,50 +29,106 @@ bool dense_cholesky(int n, double* A) {
   return true;
 }
 
+// Symmetric eigenproblem in two stages: Householder reduction to tridiagonal form
+// T = Q^T A Q (Q accumulated), then the implicit symmetric QR iteration with Wilkinson
+// shifts on T, each step a chase of the bulge by Givens rotations that are accumulated
+// into Q. O(n^3) with a small constant; eigenvalues ascending on return.
 void dense_sym_eig(int n, double* A, double* w, double* V) {
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) V[(size_t)j * n + i] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int j = 0; j < n; ++j) {
-      diag += A_(j, j) * A_(j, j);
-      for (int i = 0; i < j; ++i) off += A_(i, j) * A_(i, j);
+  std::vector<double> v(n), p(n), wv(n);
+  // Householder: column k below the subdiagonal is annihilated by H = I - 2 u u^T acting on
+  // rows/columns k+1..n-1 (A22 <- A22 - 2 u w^T - 2 w u^T, w = A22 u - (u^T A22 u) u).
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double xn2 = 0.0;
+    for (int i = 0; i < m; ++i) {
+      v[i] = A_(k + 1 + i, k);
+      xn2 += v[i] * v[i];
     }
-    if (off <= 1e-32 * diag || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p) {
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A_(p, q);
-        if (apq == 0.0) continue;
-        const double app = A_(p, p), aqq = A_(q, q);
-        // rotation angle that annihilates A(p,q)
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A_(k, p), akq = A_(k, q);
-          A_(k, p) = c * akp - s * akq;
-          A_(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A_(p, k), aqk = A_(q, k);
-          A_(p, k) = c * apk - s * aqk;
-          A_(q, k) = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)p * n + k], vkq = V[(size_t)q * n + k];
-          V[(size_t)p * n + k] = c * vkp - s * vkq;
-          V[(size_t)q * n + k] = s * vkp + c * vkq;
-        }
+    const double xn = std::sqrt(xn2);
+    if (xn == 0.0) continue;
+    const double alpha = v[0] > 0.0 ? -xn : xn;
+    v[0] -= alpha;
+    double vn2 = 0.0;
+    for (int i = 0; i < m; ++i) vn2 += v[i] * v[i];
+    if (vn2 == 0.0) continue;
+    const double inv = 1.0 / std::sqrt(vn2);
+    for (int i = 0; i < m; ++i) v[i] *= inv;
+    double up = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += A_(k + 1 + i, k + 1 + j) * v[j];
+      p[i] = s;
+      up += v[i] * s;
+    }
+    for (int i = 0; i < m; ++i) wv[i] = p[i] - up * v[i];
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i) A_(k + 1 + i, k + 1 + j) -= 2.0 * (v[i] * wv[j] + wv[i] * v[j]);
+    A_(k + 1, k) = alpha;
+    A_(k, k + 1) = alpha;
+    for (int i = 1; i < m; ++i) {
+      A_(k + 1 + i, k) = 0.0;
+      A_(k, k + 1 + i) = 0.0;
+    }
+    // V <- V H on columns k+1..n-1
+    for (int r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += V[(size_t)(k + 1 + i) * n + r] * v[i];
+      for (int i = 0; i < m; ++i) V[(size_t)(k + 1 + i) * n + r] -= 2.0 * s * v[i];
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A_(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = A_(i + 1, i);
+  // implicit QR on the tridiagonal (d, e): deflate from the bottom, chase one bulge per step
+  const double eps = 2.220446049250313e-16;
+  int m = n - 1, guard = 0;
+  while (m > 0 && guard < 60 * n) {
+    if (std::fabs(e[m - 1]) <= eps * (std::fabs(d[m - 1]) + std::fabs(d[m]))) {
+      e[m - 1] = 0.0;
+      --m;
+      continue;
+    }
+    int l = m - 1;
+    while (l > 0 && std::fabs(e[l - 1]) > eps * (std::fabs(d[l - 1]) + std::fabs(d[l]))) --l;
+    ++guard;
+    // Wilkinson shift: eigenvalue of the trailing 2x2 block nearer to d[m]
+    const double delta = 0.5 * (d[m - 1] - d[m]);
+    const double b2 = e[m - 1] * e[m - 1];
+    const double den = delta + (delta >= 0.0 ? 1.0 : -1.0) * std::sqrt(delta * delta + b2);
+    const double mu = den != 0.0 ? d[m] - b2 / den : d[m];
+    double x = d[l] - mu, y = e[l], bulge = 0.0;
+    for (int k = l; k < m; ++k) {
+      if (k > l) {
+        x = e[k - 1];
+        y = bulge;
+      }
+      const double r = std::hypot(x, y);
+      const double c = r != 0.0 ? x / r : 1.0, s = r != 0.0 ? y / r : 0.0;
+      if (k > l) e[k - 1] = r;
+      const double a = d[k], b = e[k], cc = d[k + 1];
+      d[k] = c * c * a + 2.0 * c * s * b + s * s * cc;
+      e[k] = c * s * (cc - a) + (c * c - s * s) * b;
+      d[k + 1] = s * s * a - 2.0 * c * s * b + c * c * cc;
+      if (k + 1 < m) {
+        bulge = s * e[k + 1];
+        e[k + 1] *= c;
+      }
+      for (int r2 = 0; r2 < n; ++r2) {
+        const double vk = V[(size_t)k * n + r2], vk1 = V[(size_t)(k + 1) * n + r2];
+        V[(size_t)k * n + r2] = c * vk + s * vk1;
+        V[(size_t)(k + 1) * n + r2] = -s * vk + c * vk1;
       }
     }
   }
   // sort ascending
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
-  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A_(a, a) < A_(b, b); });
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] < d[b]; });
   std::vector<double> Vs((size_t)n * n);
   for (int j = 0; j < n; ++j) {
-    w[j] = A_(idx[j], idx[j]);
+    w[j] = d[idx[j]];
     for (int i = 0; i < n; ++i) Vs[(size_t)j * n + i] = V[(size_t)idx[j] * n + i];
   }
   std::copy(Vs.begin(), Vs.end(), V);

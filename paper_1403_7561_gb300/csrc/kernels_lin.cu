@@ -93,6 +93,71 @@ template void launch_cheb_step_lin<float>(const Grid<float>&, PcgVecs<float>, Pc
 template void launch_cheb_step_lin<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, int, int, LaunchCfg,
                                            cudaStream_t);
 
+// Schrodinger operators for nvec vectors (blockIdx.z runs over (vector, z chunk)): H = kinetic
+// stencil (kappa_d = hbar^2/(2 m_d)) plus the V quadrature-point mass term, M = consistent mass,
+// both zero on the subdomain boundary (psi = 0 there).
+template <class T>
+struct HmLinOp {
+  static constexpr int NIN = 1;
+  static constexpr bool SEPM = true;
+  struct Pre {};
+  HmArgs<T> a;
+  T mscale;
+  const T* xv;
+  T* hv;
+  T* mv;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int vec) {
+    const long long o = (long long)vec * a.ld;
+    xv = a.x + o;
+    hv = a.hx ? a.hx + o : nullptr;
+    mv = a.mx ? a.mx + o : nullptr;
+  }
+  __device__ const T* coeffs() const { return a.cV; }
+  __device__ const T* lin_src(int) const { return xv; }
+  __device__ T lin_mix(T x0, T) const { return x0; }
+  __device__ T lin_in(int n) const { return xv[n]; }
+  __device__ Pre lin_pre(int) const { return Pre{}; }
+  __device__ bool lin_dir() const { return true; }
+  __device__ T m_scale() const { return mscale; }
+  __device__ void lin_out(int, const Pre&, T, T) {}
+  __device__ void lin_out2(int n, T yh, T ym) {
+    if (hv) hv[n] = yh;
+    if (mv) mv[n] = ym;
+  }
+  __device__ void finish() {}
+};
+
+template <class T, int BY, int R, class Op>
+static void lin_launch_vec(const Grid<T>& g, const Op& op, int kchunk, int nvec, cudaStream_t s) {
+  using S = LinShape<T, BY, R>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(lin_march_kernel<T, BY, R, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::dyn_bytes) == cudaSuccess &&
+        cudaFuncSetAttribute(lin_march_kernel<T, BY, R, Op>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100) == cudaSuccess)
+      attr_set[dev] = true;
+  }
+  const dim3 grid = lin_grid(g.nxn, g.nyn, g.nzn, BY, R, kchunk, nvec);
+  note_launch(), lin_march_kernel<T, BY, R, Op><<<grid, dim3(32, BY), S::dyn_bytes, s>>>(g, op, kchunk);
+}
+
+template <class T>
+void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  HmLinOp<T> op = {};
+  op.a = args;
+  op.mscale = (T)args.mscale;
+  const int kc = cfg.kchunk > 0 ? (cfg.kchunk < 128 ? cfg.kchunk : 128) : 16;
+  if (cfg.variant == 3)
+    lin_launch_vec<T, 8, 2>(g, op, kc, args.nvec, s);
+  else
+    lin_launch_vec<T, 8, 1>(g, op, kc, args.nvec, s);
+}
+template void launch_hm_apply_lin<float>(const Grid<float>&, const HmArgs<float>&, LaunchCfg, cudaStream_t);
+template void launch_hm_apply_lin<double>(const Grid<double>&, const HmArgs<double>&, LaunchCfg, cudaStream_t);
+
 // Resident blocks per SM of the plane-factorized apply (0 if the query fails).
 template <class T, int BY, int R>
 static int lin_occupancy() {

@@ -3,6 +3,8 @@
 // Schrodinger3D) with the potential energy of Eq. SchrodPotEnergy (no V_xc).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "qcad_host.h"
 #include "qcad_internal.cuh"
 #include "qcad_dense.h"
@@ -49,6 +51,10 @@ struct HmOp {
 
 template <class T>
 void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+  if (cfg.variant >= 2) {
+    launch_hm_apply_lin<T>(g, args, cfg, s);
+    return;
+  }
   HmOp<T> op = {};
   op.a = args;
   const int by = cfg.by == 4 ? 4 : 8;
@@ -143,76 +149,156 @@ void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, 
   note_launch(), pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
 }
 
-// G[p x q] (+)= A^T B for column-major A (n x p, lda) and B (n x q, ldb). Each thread sums
-// a 32-row tile in the storage precision T and accumulates tiles in FP64; blocks add
-// their partials atomically. Output row-major (o = a*q + b); all uses are symmetric.
+// G1 = A^T B1 and optionally G2 = A^T B2 (p x q each, row-major o = a*q + b) for column-major
+// A (n x p, lda) and B1, B2 (n x q, ldb): tall-skinny products of the LOBPCG blocks.
+// A block walks 32-row tiles of its share of the rows, staged transposed in shared memory
+// ([row][column]); each thread owns a 4 x 4 tile of outputs (registers), sums a row tile in
+// the storage precision and accumulates tiles in FP64. Every block writes its partial sums
+// to its own slot of `part` (no atomics); gram_reduce_kernel adds the slots in a fixed order,
+// so the result is deterministic.
 constexpr int GR = 32;
+constexpr int GRAM_MAX_BLOCKS = 2 * 152;
+
 template <class T>
-__global__ void __launch_bounds__(256) gram_kernel(long long n, int p, int q, const T* A, long long lda,
-                                                   const T* B, long long ldb, double* G) {
+__global__ void __launch_bounds__(1024) gram_kernel(long long n, int p, int q, int nb2, const T* A, long long lda,
+                                                    const T* B1, const T* B2, long long ldb, double* part) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   T* sh = reinterpret_cast<T*>(sh_raw);
-  T* sA = sh;             // [p][GR]
-  T* sB = sh + p * GR;    // [q][GR]
-  const int nout = p * q;
-  const int per = (nout + blockDim.x - 1) / blockDim.x;
+  const int qt = q * nb2;                    // output columns over [B1 | B2]
+  const int ta_n = (p + 3) / 4, tb_n = (qt + 3) / 4;
+  const int pp = 4 * ta_n, qp = 4 * tb_n;
+  const int W = pp + qp + 4;                 // shared row stride (multiple of 4)
+  const int tid = threadIdx.x, nth = blockDim.x;
+  // padding columns stay zero (tile loads write only the real columns)
+  for (int t = tid; t < GR * W; t += nth) sh[t] = T(0);
+  const bool active = tid < ta_n * tb_n;
+  const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
   double acc[16];
+#pragma unroll
   for (int s = 0; s < 16; ++s) acc[s] = 0.0;
-  for (long long r0 = (long long)blockIdx.x * GR; r0 < n; r0 += (long long)gridDim.x * GR) {
+  const long long ntiles = (n + GR - 1) / GR;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long r0 = tile * GR;
     __syncthreads();
-    for (int t = threadIdx.x; t < (p + q) * GR; t += blockDim.x) {
+    for (int t = tid; t < (p + qt) * GR; t += nth) {
       const int col = t / GR, rr = t % GR;
       const long long row = r0 + rr;
       T v = T(0);
-      if (row < n) v = col < p ? A[col * lda + row] : B[(col - p) * ldb + row];
-      sh[col * GR + rr] = v;
+      int sc;
+      if (col < p) {
+        if (row < n) v = A[col * lda + row];
+        sc = col;
+      } else {
+        const int bc = col - p;
+        if (row < n) v = bc < q ? B1[bc * ldb + row] : B2[(bc - q) * ldb + row];
+        sc = pp + bc;
+      }
+      sh[rr * W + sc] = v;
     }
     __syncthreads();
-    for (int s = 0; s < per && s < 16; ++s) {
-      const int o = threadIdx.x + s * blockDim.x;
-      if (o < nout) {
-        const int a = o / q, b = o % q;
-        T sum = T(0);
-#pragma unroll 8
-        for (int rr = 0; rr < GR; ++rr) sum += sA[a * GR + rr] * sB[b * GR + rr];
-        acc[s] += (double)sum;
+    if (active) {
+      T s16[16];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) s16[s] = T(0);
+#pragma unroll 4
+      for (int rr = 0; rr < GR; ++rr) {
+        const T* row = sh + rr * W;
+        T av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = row[4 * ta + u];
+          bv[u] = row[pp + 4 * tb + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) s16[4 * u + v] += av[u] * bv[v];
       }
+#pragma unroll
+      for (int s = 0; s < 16; ++s) acc[s] += (double)s16[s];
     }
   }
-  for (int s = 0; s < per && s < 16; ++s) {
-    const int o = threadIdx.x + s * blockDim.x;
-    if (o < nout && acc[s] != 0.0) atomicAdd(G + o, acc[s]);
+  if (!active) return;
+  // slot layout: G1 block (p*q) then G2 block (p*q)
+  double* out = part + (size_t)blockIdx.x * p * qt;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = 4 * ta + u;
+    if (a >= p) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int bc = 4 * tb + v;
+      if (bc >= qt) continue;
+      const int o = bc < q ? a * q + bc : p * q + a * q + (bc - q);
+      out[o] = acc[4 * u + v];
+    }
   }
 }
 
-template <class T>
-void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B, long long ldb, double* G,
-                 cudaStream_t s) {
-  const int nb = dblocks((n + GR - 1) / GR * DT);
-  const size_t shm = (size_t)(p + q) * GR * sizeof(T);
-  note_launch(), gram_kernel<T><<<nb, 256, shm, s>>>(n, p, q, A, lda, B, ldb, G);
+__global__ void gram_reduce_kernel(int nblk, int p, int q, int nb2, const double* part, double* G1, double* G2) {
+  const int tot = p * q * nb2;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < tot; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * tot + o];
+    if (o < p * q)
+      G1[o] = s;
+    else
+      G2[o - p * q] = s;
+  }
 }
-template void launch_gram<float>(long long, int, int, const float*, long long, const float*, long long, double*,
-                                 cudaStream_t);
-template void launch_gram<double>(long long, int, int, const double*, long long, const double*, long long, double*,
-                                  cudaStream_t);
 
-// Row-wise block combination, safe in place: each row is read completely by one thread
-// before it is written. Y = A C with A n x p (lda), C p x q column-major; output
-// columns j < q1 go to Y1 (ldy), columns j >= q1 to Y2 (ldy).
+size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 * q; }
+
 template <class T>
-__global__ void combine_kernel(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1,
-                               T* Y2, long long ldy) {
+void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
+                 double* G1, double* G2, double* part, cudaStream_t s) {
+  const int nb2 = B2 ? 2 : 1;
+  const int qt = q * nb2;
+  const int ta_n = (p + 3) / 4, tb_n = (qt + 3) / 4;
+  const int nth = std::max(32, ((ta_n * tb_n + 31) / 32) * 32);
+  const long long ntiles = (n + GR - 1) / GR;
+  const int nblk = (int)std::max<long long>(1, std::min<long long>(GRAM_MAX_BLOCKS, ntiles));
+  const size_t shm = (size_t)GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T);
+  static bool attr = false;
+  if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) ==
+                    cudaSuccess;
+  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, q, nb2, A, lda, B1, B2, ldb, part);
+  note_launch(), gram_reduce_kernel<<<(p * qt + 255) / 256, 256, 0, s>>>(nblk, p, q, nb2, part, G1, G2);
+}
+template void launch_gram<float>(long long, int, int, const float*, long long, const float*, const float*, long long,
+                                 double*, double*, double*, cudaStream_t);
+template void launch_gram<double>(long long, int, int, const double*, long long, const double*, const double*,
+                                  long long, double*, double*, double*, cudaStream_t);
+
+// Row-wise block combination, safe in place: each row of A is read completely into
+// registers by one thread before any output of the row is written. Y = A C with A n x p
+// (lda), C p x q column-major (staged in shared memory with rows padded to a multiple of 4);
+// output columns j < q1 go to Y1 (ldy), columns j >= q1 to Y2 (ldy). PMAX >= p.
+template <class T, int PMAX>
+__global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q, int q1, const T* A, long long lda,
+                                                      const T* C, T* Y1, T* Y2, long long ldy) {
   extern __shared__ __align__(16) unsigned char sc_raw[];
-  T* sC = reinterpret_cast<T*>(sc_raw);
-  for (int t = threadIdx.x; t < p * q; t += blockDim.x) sC[t] = C[t];
+  T* sC = reinterpret_cast<T*>(sc_raw);  // [q][pp]
+  const int pp = (p + 3) & ~3;
+  for (int t = threadIdx.x; t < pp * q; t += blockDim.x) {
+    const int j = t / pp, i = t % pp;
+    sC[t] = i < p ? C[j * p + i] : T(0);
+  }
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    T a[QCAD_DENSE_MAXP];
-    for (int i = 0; i < p; ++i) a[i] = A[i * lda + r];
+    T a[PMAX];
+#pragma unroll
+    for (int i = 0; i < PMAX; ++i) a[i] = i < p ? A[i * lda + r] : T(0);
     for (int j = 0; j < q; ++j) {
+      const T* cj = sC + j * pp;
       T s = T(0);
-      for (int i = 0; i < p; ++i) s += a[i] * sC[j * p + i];
+#pragma unroll
+      for (int i = 0; i < PMAX; i += 4) {
+        if (i < pp) {
+          s += a[i] * cj[i] + a[i + 1] * cj[i + 1];
+          s += a[i + 2] * cj[i + 2] + a[i + 3] * cj[i + 3];
+        }
+      }
       if (j < q1)
         Y1[j * ldy + r] = s;
       else
@@ -224,18 +310,28 @@ __global__ void combine_kernel(long long n, int p, int q, int q1, const T* A, lo
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
                     long long ldy, cudaStream_t s) {
-  note_launch(), combine_kernel<T><<<dblocks(n), DT, (size_t)p * q * sizeof(T), s>>>(n, p, q, q1, A, lda, C, Y1, Y2,
-                                                                                   ldy);
+  const size_t shm = (size_t)((p + 3) & ~3) * q * sizeof(T);
+  const int nb = dblocks(n);
+  if (p <= 16)
+    note_launch(), combine_kernel<T, 16><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+  else if (p <= 32)
+    note_launch(), combine_kernel<T, 32><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+  else
+    note_launch(), combine_kernel<T, 64><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
 }
 template void launch_combine<float>(long long, int, int, int, const float*, long long, const float*, float*, float*,
                                     long long, cudaStream_t);
 template void launch_combine<double>(long long, int, int, int, const double*, long long, const double*, double*,
                                      double*, long long, cudaStream_t);
 
-// R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms2[j] += |R_j|^2, mnorm2[j] += |MX_j|^2.
+// R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms[2j] += |R_j|^2,
+// norms[2j+1] += |MX_j|^2 (FP64 sums per thread, reduced per block, one atomic per block).
 template <class T>
-__global__ void residual_block_kernel(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
-                                      const T* dinv, T* W, double* norms) {
+__global__ void __launch_bounds__(256) residual_block_kernel(long long n, int m, const T* HX, const T* MX,
+                                                             long long ld, const double* lam, const T* dinv, T* W,
+                                                             double* norms) {
+  __shared__ double red[2][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = 0; j < m; ++j) {
     double r2 = 0.0, m2 = 0.0;
     const T l = (T)lam[j];
@@ -243,28 +339,118 @@ __global__ void residual_block_kernel(long long n, int m, const T* HX, const T* 
          r += (long long)gridDim.x * blockDim.x) {
       const T mx = MX[j * ld + r];
       const T res = HX[j * ld + r] - l * mx;
-      W[j * ld + r] = dinv[r] * res;
+      W[j * ld + r] = dinv ? dinv[r] * res : res;
       r2 += (double)res * (double)res;
       m2 += (double)mx * (double)mx;
     }
     r2 = warp_sum(r2);
     m2 = warp_sum(m2);
-    if ((threadIdx.x & 31) == 0) {
-      if (r2 != 0.0) atomicAdd(norms + 2 * j, r2);
-      if (m2 != 0.0) atomicAdd(norms + 2 * j + 1, m2);
+    if (lane == 0) {
+      red[0][warp] = r2;
+      red[1][warp] = m2;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      atomicAdd(norms + 2 * j, a);
+      atomicAdd(norms + 2 * j + 1, b);
+    }
+    __syncthreads();
   }
 }
 
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s) {
-  note_launch(), residual_block_kernel<T><<<dblocks(n), DT, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
+  const int nb = (int)std::min<long long>(2 * 152, (n + 255) / 256);
+  note_launch(), residual_block_kernel<T><<<std::max(nb, 1), 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
 }
 template void launch_residual_block<float>(long long, int, const float*, const float*, long long, const double*,
                                            const float*, float*, double*, cudaStream_t);
 template void launch_residual_block<double>(long long, int, const double*, const double*, long long, const double*,
                                             const double*, double*, double*, cudaStream_t);
+
+// Block Chebyshev-Jacobi preconditioner of LOBPCG, column by column the recurrence of the
+// PCG preconditioner: z = p(D^-1 H) D^-1 r on the interval [theta - delta, theta + delta]
+// of D^-1 H. Init: w = r, d = D^-1 r / theta, z = d; step: w -= H d,
+// d = c1 d + c2 D^-1 w, z += d. Elementwise, so z may alias r.
+template <class T>
+__global__ void cheb_block_init_kernel(long long n, int m, long long ld, const T* R, const T* dinv, T inv_theta,
+                                       T* Wb, T* Db, T* Zb) {
+  const long long tot = n * (long long)m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t % n, idx = (t / n) * ld + r;
+    const T rv = R[idx];
+    const T d = dinv[r] * rv * inv_theta;
+    Wb[idx] = rv;
+    Db[idx] = d;
+    Zb[idx] = d;
+  }
+}
+template <class T>
+__global__ void cheb_block_step_kernel(long long n, int m, long long ld, const T* HD, const T* dinv, T c1, T c2,
+                                       T* Wb, T* Db, T* Zb) {
+  const long long tot = n * (long long)m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t % n, idx = (t / n) * ld + r;
+    const T w = Wb[idx] - HD[idx];
+    const T d = c1 * Db[idx] + c2 * dinv[r] * w;
+    Wb[idx] = w;
+    Db[idx] = d;
+    Zb[idx] += d;
+  }
+}
+template <class T>
+void launch_cheb_block_init(long long n, int m, long long ld, const T* R, const T* dinv, double inv_theta, T* W,
+                            T* D, T* Z, cudaStream_t s) {
+  note_launch(), cheb_block_init_kernel<T><<<dblocks(n * m), DT, 0, s>>>(n, m, ld, R, dinv, (T)inv_theta, W, D, Z);
+}
+template <class T>
+void launch_cheb_block_step(long long n, int m, long long ld, const T* HD, const T* dinv, double c1, double c2,
+                            T* W, T* D, T* Z, cudaStream_t s) {
+  note_launch(), cheb_block_step_kernel<T><<<dblocks(n * m), DT, 0, s>>>(n, m, ld, HD, dinv, (T)c1, (T)c2, W, D, Z);
+}
+template void launch_cheb_block_init<float>(long long, int, long long, const float*, const float*, double, float*,
+                                            float*, float*, cudaStream_t);
+template void launch_cheb_block_step<float>(long long, int, long long, const float*, const float*, double, double,
+                                            float*, float*, float*, cudaStream_t);
+
+// One power step for the largest eigenvalue of D^-1 H on the interior nodes (dinv > 0):
+// vn = D^-1 H v, acc[0] += v.Hv, acc[1] += v.D v, acc[2] += |vn|^2.
+template <class T>
+__global__ void power_sub_kernel(long long n, const T* v, const T* Hv, const T* dinv, T* vn, double* acc) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    const double di = (double)dinv[r];
+    if (di > 0.0) {
+      const double x = (double)v[r], y = (double)Hv[r], z = di * y;
+      vn[r] = (T)z;
+      a0 += x * y;
+      a1 += x * x / di;
+      a2 += z * z;
+    } else {
+      vn[r] = T(0);
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, a0);
+    atomicAdd(acc + 1, a1);
+    atomicAdd(acc + 2, a2);
+  }
+}
+template <class T>
+void launch_power_sub(long long n, const T* v, const T* Hv, const T* dinv, T* vn, double* acc, cudaStream_t s) {
+  note_launch(), power_sub_kernel<T><<<std::min(dblocks(n), 2 * 152), DT, 0, s>>>(n, v, Hv, dinv, vn, acc);
+}
+template void launch_power_sub<float>(long long, const float*, const float*, const float*, float*, double*,
+                                      cudaStream_t);
 
 // Counter-based pseudo-random start block (SplitMix64 finalizer of the index), interior nodes only.
 template <class T>

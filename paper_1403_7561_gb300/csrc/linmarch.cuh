@@ -97,7 +97,9 @@ inline dim3 lin_grid(int nxn, int nyn, int nzn, int by, int r, int kchunk, int n
   return dim3((nxn + 29) / 30, (nyn + tr - 3) / (tr - 2), ((nzn + kchunk - 1) / kchunk) * nvec);
 }
 
-// Op: the linear ops of pcg_ops.cuh (lin_in, lin_out, lin_dir, skip, set_vec, finish, coeffs).
+// Op: the linear ops of pcg_ops.cuh (lin_in, lin_out, lin_dir, skip, set_vec, finish, coeffs),
+// or an op with SEPM = true (m_scale, lin_out2), which writes the operator with zero Dirichlet
+// rows and, as a second output, the separable consistent mass (Schrodinger H and M).
 // Loads are unpredicated: node indices are clamped into the mesh (and into the chunk's
 // planes), and every value read outside the operator's support meets a zero table entry or
 // a zero coefficient, so only finiteness of the input matters there.
@@ -354,8 +356,14 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       const T dp = __shfl_down_sync(FULL_MASK, d, 1);
       const T stiff = ckx[0] * c1m + ckx[1] * c1 + ckx[2] * c1p + cmx[0] * dm + cmx[1] * d + cmx[2] * dp;
       const bool isdir = pdir || bnd[r] || (ptop && top[r]);
-      const T y = isdir ? vc[r] : stiff + mass;
-      if (wr[r]) op.lin_out(nrow[r] + k * plane, pre[r], vc[r], y);
+      if constexpr (Op::SEPM) {
+        // second output: the separable consistent mass Mx My Mz v (the x stage of c1 rescaled)
+        const T mm = op.m_scale() * (cmx[0] * c1m + cmx[1] * c1 + cmx[2] * c1p);
+        if (wr[r]) op.lin_out2(nrow[r] + k * plane, isdir ? T(0) : stiff + mass, isdir ? T(0) : mm);
+      } else {
+        const T y = isdir ? vc[r] : stiff + mass;
+        if (wr[r]) op.lin_out(nrow[r] + k * plane, pre[r], vc[r], y);
+      }
     }
     // interpolation of plane k+2 for the next layer, then shift the plane window (plane k+3
     // from its stage)

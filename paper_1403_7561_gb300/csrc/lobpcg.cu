@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -38,6 +40,7 @@ struct SubSetup {
   GridDev<float> g32;
   DevBuf cV64, cV32, dinv, interior;
   double vmin;
+  double inv_kx;    // 1 / kappa_x = 2 m_x / hbar^2 (scale of the separable mass stencil)
 };
 
 static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, const double* m_eff, int need32,
@@ -64,6 +67,7 @@ static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, con
   std::vector<double> hy(m->hyv.begin() + sm.j0, m->hyv.begin() + sm.j0 + sm.nys);
   std::vector<double> hz(m->hzv.begin() + sm.k0, m->hzv.begin() + sm.k0 + sm.nzs);
   const double h2m = host_h2m0();
+  S.inv_kx = m_eff[0] / h2m;
   // kinetic coefficients hbar^2 / (2 m_d) for each direction (Eq. Schrodinger3D)
   std::vector<double> kx(sm.nzs, h2m / m_eff[0]), ky(sm.nzs, h2m / m_eff[1]), kz(sm.nzs, h2m / m_eff[2]);
   GridTables t = make_tables(xs, ys, zs, kx, ky, kz);
@@ -129,6 +133,7 @@ static void hm_apply(qcad_mesh_s* m, SubSetup& S, int prec, int nvec, const doub
     a.cV = S.cV64.as<double>();
     a.ld = S.ns;
     a.nvec = nvec;
+    a.mscale = S.inv_kx;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
     launch_hm_apply<double>(S.g64.g, a, LaunchCfg{8, 16}, s);
     if (m->prof.on) m->prof.end(pp, s);
@@ -146,6 +151,7 @@ static void hm_apply(qcad_mesh_s* m, SubSetup& S, int prec, int nvec, const doub
     a.cV = S.cV32.as<float>();
     a.ld = S.ns;
     a.nvec = nvec;
+    a.mscale = S.inv_kx;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
     launch_hm_apply<float>(S.g32.g, a, LaunchCfg{8, 16}, s);
     if (m->prof.on) m->prof.end(pp, s);
@@ -179,28 +185,130 @@ qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* 
 }
 
 // ---------------------------------------------------------------------------
+// Chebyshev-Jacobi preconditioner of the LOBPCG residual block, applied in FP32 in both
+// phases (a preconditioner needs no more precision than that): W = p_k(D^-1 H) D^-1 R with
+// the Chebyshev polynomial of the interval [b / (4k^2), b] of D^-1 H, b = 1.1 lambda_max
+// (power iteration). k <= 1 means plain Jacobi.
+struct ChebPre {
+  int k = 0;
+  double theta = 0.0, delta = 0.0;
+  qcad_mesh_s* m = nullptr;
+  SubSetup* S = nullptr;
+  int nb = 0;
+  long long ns = 0;
+  DevBuf buf;
+  float *R32 = nullptr, *W = nullptr, *D = nullptr, *HD = nullptr;
+  const float* dinv = nullptr;
+
+  void hmul(const float* X, float* HX, int nvec) {
+    HmArgs<float> a{};
+    a.x = X;
+    a.hx = HX;
+    a.mx = nullptr;
+    a.cV = S->cV32.as<float>();
+    a.ld = ns;
+    a.nvec = nvec;
+    a.mscale = S->inv_kx;
+    launch_hm_apply<float>(S->g32.g, a, LaunchCfg{8, 16}, m->stream);
+  }
+  void init(qcad_mesh_s* m_, SubSetup* S_, int nb_, int k_, const float* dinv32) {
+    m = m_;
+    S = S_;
+    nb = nb_;
+    ns = S->ns;
+    k = k_;
+    dinv = dinv32;
+    if (k < 2) return;
+    buf.ensure((size_t)4 * nb * ns * sizeof(float) + 256);
+    R32 = buf.as<float>();
+    W = R32 + nb * ns;
+    D = W + nb * ns;
+    HD = D + nb * ns;
+    cudaStream_t s = m->stream;
+    // largest eigenvalue of D^-1 H by power iteration on one vector (uses W and D as scratch)
+    launch_random_block<float>(ns, 1, ns, S->interior.as<unsigned char>(), 0xC4EB5EEDull, W, s);
+    double* acc = m->stats.as<double>() + 48;
+    double lam = 0.0;
+    for (int it = 0; it < 12; ++it) {
+      hmul(W, HD, 1);
+      CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
+      launch_power_sub<float>(ns, W, HD, dinv, D, acc, s);
+      CK(cudaMemcpyAsync(m->h_small + 40, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double a0 = m->h_small[40], a1 = m->h_small[41], a2 = m->h_small[42];
+      if (!(a1 > 0.0) || !(a2 > 0.0)) break;
+      lam = a0 / a1;
+      launch_scale<float>(ns, D, 1.0 / std::sqrt(a2), s);
+      std::swap(W, D);
+    }
+    if (!(lam > 0.0)) {
+      k = 0;
+      return;
+    }
+    const double b = 1.1 * lam, a = b / (4.0 * k * k);
+    theta = 0.5 * (a + b);
+    delta = 0.5 * (b - a);
+  }
+  // Z = p_k(D^-1 H) D^-1 R for nb columns (Z may alias R).
+  void apply(const float* R, float* Z) {
+    cudaStream_t s = m->stream;
+    launch_cheb_block_init<float>(ns, nb, ns, R, dinv, 1.0 / theta, W, D, Z, s);
+    const double sigma = theta / delta;
+    double rho_prev = 1.0 / sigma, rho = rho_prev;
+    for (int j = 1; j < k; ++j) {
+      rho_prev = rho;
+      rho = 1.0 / (2.0 * sigma - rho_prev);
+      hmul(D, HD, nb);
+      launch_cheb_block_step<float>(ns, nb, ns, HD, dinv, rho * rho_prev, 2.0 * rho / delta, W, D, Z, s);
+    }
+  }
+};
+
+// FP32 preconditioning of a residual block stored in precision T.
+static void precondition_block(ChebPre& P, float* Rb, long long) { P.apply(Rb, Rb); }
+static void precondition_block(ChebPre& P, double* Rb, long long tot) {
+  launch_d2f(tot, Rb, P.R32, P.m->stream);
+  P.apply(P.R32, P.R32);
+  launch_f2d(tot, P.R32, Rb, P.m->stream);
+}
+
 // One LOBPCG run in storage/apply precision T (FP32 for the iteration phase,
 // FP64 to polish). The blocks S = [X | W | P], HS = H S, MS = M S are kept
 // together (column-major, ns x 3nb each) so that the Rayleigh-Ritz Gram
-// matrices are two kernel launches; all block updates are row-wise in place.
+// matrices of H and M are one kernel launch; all block updates are row-wise
+// in place. An iteration synchronizes with the host twice: after the Gram
+// matrix of [W P] (the residual norms of the previous Ritz pairs come back
+// with it) and after the Rayleigh-Ritz Gram matrices. Small matrices travel
+// through pinned host buffers, so the block combinations need no wait.
 template <class T>
 struct LobpcgRun {
-  qcad_mesh_s* m;
-  SubSetup* S;
-  cudaStream_t s;
-  int nb, nev;
-  long long ns;
-  T* Sx;
-  T* HS;
-  T* MS;
-  const T* dinv;
-  double* G;
-  T* Cd;  // device combination coefficients
+  qcad_mesh_s* m = nullptr;
+  SubSetup* S = nullptr;
+  cudaStream_t s = nullptr;
+  int nb = 0, nev = 0;
+  long long ns = 0;
+  T* Sx = nullptr;
+  T* HS = nullptr;
+  T* MS = nullptr;
+  const T* dinv = nullptr;
+  double* G = nullptr;     // device Gram outputs (two 3nb x 3nb)
+  double* part = nullptr;  // device Gram partial sums
+  T* Cd = nullptr;         // device combination coefficients
+  double* hG = nullptr;    // pinned: two 3nb x 3nb Gram matrices, then 2nb residual norms, nb eigenvalues
+  T* hC = nullptr;         // pinned: combination coefficients
   std::vector<double> lam;
   std::vector<double> rel;
   int applies = 0;
   int iters = 0;
-  DevBuf tmp32;
+  double t_sync = 0.0, t_host = 0.0;  // seconds waiting for the device, in host dense algebra
+  ChebPre* pre = nullptr;             // Chebyshev-Jacobi preconditioner (else Jacobi)
+
+  ~LobpcgRun() {
+    if (hG) cudaFreeHost(hG);
+    if (hC) cudaFreeHost(hC);
+  }
+  double* h_norms() { return hG + 2 * 9 * nb * nb; }
+  double* h_lam() { return h_norms() + 2 * nb; }
 
   T* blk(T* base, int b) { return base + (long long)b * ns * nb; }
 
@@ -212,6 +320,7 @@ struct LobpcgRun {
     a.cV = cv();
     a.ld = ns;
     a.nvec = nb;
+    a.mscale = S->inv_kx;
     Profiler::Pair pp;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
     launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
@@ -221,85 +330,147 @@ struct LobpcgRun {
   const T* cv();
   const Grid<T>& grid();
 
-  void gram(int p, int q, const T* A, const T* B, std::vector<double>& out) {
-    CK(cudaMemsetAsync(G, 0, (size_t)p * q * sizeof(double), s));
-    launch_gram<T>(ns, p, q, A, ns, B, ns, G, s);
-    out.resize((size_t)p * q);
-    CK(cudaMemcpyAsync(out.data(), G, (size_t)p * q * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int j = 0; j < q && p == q; ++j)
+  // Enqueues G1 = A^T B1 (and G2 = A^T B2) for p columns of A and q of B, with the copy of
+  // both to hG (G1 at hG, G2 at hG + p*q); the caller synchronizes.
+  void gram_async(int p, int q, const T* A, const T* B1, const T* B2) {
+    launch_gram<T>(ns, p, q, A, ns, B1, B2, ns, G, B2 ? G + (size_t)p * q : nullptr, part, s);
+    CK(cudaMemcpyAsync(hG, G, (size_t)p * q * (B2 ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  // Symmetrized copy of the p x p Gram matrix at hG + off.
+  std::vector<double> gram_sym(int p, size_t off) const {
+    std::vector<double> out(hG + off, hG + off + (size_t)p * p);
+    for (int j = 0; j < p; ++j)
       for (int i = 0; i < j; ++i) {
         const double v = 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
         out[(size_t)j * p + i] = out[(size_t)i * p + j] = v;
       }
+    return out;
+  }
+  void sync() {
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(cudaStreamSynchronize(s));
+    t_sync += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
 
   // For S, HS and MS: columns [src, src+p) times C (p x q); output columns < q1 to block dst1,
-  // the rest to block dst2 (in place).
+  // the rest to block dst2 (in place). hC is reused only after a later synchronization.
   void combine(int src_blk, int p, const std::vector<double>& C, int q, int q1, int dst1, int dst2) {
-    std::vector<T> ct(C.begin(), C.end());
-    CK(cudaMemcpyAsync(Cd, ct.data(), ct.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    for (size_t t = 0; t < (size_t)p * q; ++t) hC[t] = (T)C[t];
+    CK(cudaMemcpyAsync(Cd, hC, (size_t)p * q * sizeof(T), cudaMemcpyHostToDevice, s));
     T* bases[3] = {Sx, HS, MS};
     for (T* base : bases)
       launch_combine<T>(ns, p, q, q1, blk(base, src_blk), ns, Cd, blk(base, dst1), blk(base, dst2), ns, s);
-    CK(cudaStreamSynchronize(s));  // ct must outlive the pageable copy
-  }
-
-  bool orthonormalize(int b) {
-    std::vector<double> g;
-    gram(nb, nb, blk(Sx, b), blk(MS, b), g);
-    if (!dense_cholesky(nb, g.data())) return false;
-    std::vector<double> R((size_t)nb * nb);
-    dense_inv_lt(nb, g.data(), R.data());
-    for (double v : R)
-      if (!std::isfinite(v)) return false;
-    combine(b, nb, R, nb, nb, b, b);
-    return true;
   }
 
   // Rayleigh-Ritz on block 0 alone.
   void rr_x() {
-    std::vector<double> GH, GM, w(nb), C((size_t)nb * nb);
-    gram(nb, nb, blk(Sx, 0), blk(HS, 0), GH);
-    gram(nb, nb, blk(Sx, 0), blk(MS, 0), GM);
+    gram_async(nb, nb, blk(Sx, 0), blk(HS, 0), blk(MS, 0));
+    sync();
+    std::vector<double> GH = gram_sym(nb, 0), GM = gram_sym(nb, (size_t)nb * nb), w(nb), C((size_t)nb * nb);
     if (!dense_gen_eig(nb, GH.data(), GM.data(), w.data(), C.data()))
       throw Error(QCAD_ERR_NONFINITE, "LOBPCG: Rayleigh-Ritz on X failed");
     combine(0, nb, C, nb, nb, 0, 0);
     lam.assign(w.begin(), w.end());
   }
 
+  // W = D^-1 (H X - M X diag(lam)) (or its Chebyshev-Jacobi preconditioning) into block 1 and
+  // the residual norms of the Ritz pairs,
+  // copied to the pinned buffer (read after the next synchronization).
+  void residual(DevBuf& lam_d, DevBuf& norms_d) {
+    std::copy(lam.begin(), lam.end(), h_lam());
+    CK(cudaMemcpyAsync(lam_d.p, h_lam(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(norms_d.p, 0, 2 * nb * sizeof(double), s));
+    const bool cheb = pre && pre->k >= 2;
+    launch_residual_block<T>(ns, nb, blk(HS, 0), blk(MS, 0), ns, lam_d.as<double>(), cheb ? nullptr : dinv,
+                             blk(Sx, 1), norms_d.as<double>(), s);
+    CK(cudaMemcpyAsync(h_norms(), norms_d.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (cheb) precondition_block(*pre, blk(Sx, 1), ns * nb);
+  }
+  // Relative residuals ||H x - lam M x|| / (|lam| ||M x||) from the copied norms; true when the
+  // first nev are <= tol.
+  bool converged(double tol) {
+    const double* nr = h_norms();
+    bool all = true;
+    for (int j = 0; j < nb; ++j) {
+      const double scale = std::max(std::fabs(lam[j]), 1e-12) * std::sqrt(std::max(nr[2 * j + 1], 1e-300));
+      rel[j] = std::sqrt(nr[2 * j]) / scale;
+      if (j < nev && !(rel[j] <= tol)) all = false;
+    }
+    return all;
+  }
+  // R = L^-T for the Cholesky factor of the k x k diagonal block at `off` of the n x n matrix
+  // G; false if the block is not numerically SPD.
+  static bool chol_inv(const std::vector<double>& Gm, int n, int off, int k, std::vector<double>& R) {
+    std::vector<double> sub((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) sub[(size_t)j * k + i] = Gm[(size_t)(off + j) * n + off + i];
+    if (!dense_cholesky(k, sub.data())) return false;
+    R.assign((size_t)k * k, 0.0);
+    dense_inv_lt(k, sub.data(), R.data());
+    for (double v : R)
+      if (!std::isfinite(v)) return false;
+    return true;
+  }
+
   // Iterates until the first nev relative residuals are <= tol; returns true when converged.
-  bool run(double tol, int maxit, DevBuf& lam_d, DevBuf& norms_d) {
+  // With stall > 0 it also stops (returning false) once the largest of those residuals has
+  // not dropped below 0.9 of its best value for `stall` iterations (the storage precision's
+  // floor is reached).
+  bool run(double tol, int maxit, DevBuf& lam_d, DevBuf& norms_d, int stall = 0) {
     bool haveP = false;
-    std::vector<double> norms(2 * nb), GH, GM, w, C;
     rel.assign(nb, 1.0);
-    for (int it = 1; it <= maxit; ++it) {
-      CK(cudaMemcpyAsync(lam_d.p, lam.data(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(cudaMemsetAsync(norms_d.p, 0, 2 * nb * sizeof(double), s));
-      launch_residual_block<T>(ns, nb, blk(HS, 0), blk(MS, 0), ns, lam_d.as<double>(), dinv, blk(Sx, 1),
-                               norms_d.as<double>(), s);
-      CK(cudaMemcpyAsync(norms.data(), norms_d.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      bool all = true;
-      for (int j = 0; j < nb; ++j) {
-        const double scale = std::max(std::fabs(lam[j]), 1e-12) * std::sqrt(std::max(norms[2 * j + 1], 1e-300));
-        rel[j] = std::sqrt(norms[2 * j]) / scale;
-        if (j < nev && !(rel[j] <= tol)) all = false;
-      }
-      if (all) return true;
-      ++iters;
+    double best = 1e300;
+    int since = 0;
+    for (int it = 1; it <= maxit + 1; ++it) {
+      residual(lam_d, norms_d);
       apply(1);
-      if (!orthonormalize(1)) {
+      // one Gram matrix of [W P] in the M inner product serves both Cholesky QRs
+      int nwp = haveP ? 2 * nb : nb;
+      gram_async(nwp, nwp, blk(Sx, 1), blk(MS, 1), nullptr);
+      sync();
+      if (converged(tol)) return true;
+      if (it > maxit) break;
+      if (stall > 0) {
+        const double worst = *std::max_element(rel.begin(), rel.begin() + nev);
+        if (worst < 0.9 * best) {
+          best = worst;
+          since = 0;
+        } else if (++since >= stall) {
+          return false;
+        }
+      }
+      ++iters;
+      std::vector<double> Gwp = gram_sym(nwp, 0), RW, RP;
+      if (!chol_inv(Gwp, nwp, 0, nb, RW)) {
+        // W lost rank: restart it from a random block (and drop P)
+        haveP = false;
+        nwp = nb;
         launch_random_block<T>(ns, nb, ns, S->interior.as<unsigned char>(), 0xABCDEF00ull + iters, blk(Sx, 1), s);
         apply(1);
-        if (!orthonormalize(1)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
+        gram_async(nb, nb, blk(Sx, 1), blk(MS, 1), nullptr);
+        sync();
+        Gwp = gram_sym(nb, 0);
+        if (!chol_inv(Gwp, nb, 0, nb, RW)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
       }
-      if (haveP && !orthonormalize(2)) haveP = false;
+      if (haveP && !chol_inv(Gwp, nwp, nb, nb, RP)) haveP = false;
+      if (haveP) {
+        std::vector<double> C((size_t)4 * nb * nb, 0.0);  // diag(RW, RP), 2nb x 2nb
+        for (int j = 0; j < nb; ++j)
+          for (int i = 0; i < nb; ++i) {
+            C[(size_t)j * 2 * nb + i] = RW[(size_t)j * nb + i];
+            C[(size_t)(nb + j) * 2 * nb + nb + i] = RP[(size_t)j * nb + i];
+          }
+        combine(1, 2 * nb, C, 2 * nb, 2 * nb, 1, 1);
+      } else {
+        combine(1, nb, RW, nb, nb, 1, 1);
+      }
+      // Rayleigh-Ritz on [X W P]
       int nuse = haveP ? 3 * nb : 2 * nb;
-      gram(nuse, nuse, Sx, HS, GH);
-      gram(nuse, nuse, Sx, MS, GM);
-      w.resize(nuse);
-      C.resize((size_t)nuse * nuse);
+      gram_async(nuse, nuse, Sx, HS, MS);
+      sync();
+      const auto th = std::chrono::steady_clock::now();
+      std::vector<double> GH = gram_sym(nuse, 0), GM = gram_sym(nuse, (size_t)nuse * nuse), w(nuse),
+                          C((size_t)nuse * nuse);
       bool ok = dense_gen_eig(nuse, GH.data(), GM.data(), w.data(), C.data());
       if (!ok && haveP) {
         haveP = false;
@@ -323,6 +494,7 @@ struct LobpcgRun {
           Cxp[(size_t)j * nuse + i] = C[(size_t)j * nuse + i];
           Cxp[(size_t)(nb + j) * nuse + i] = i < nb ? 0.0 : C[(size_t)j * nuse + i];
         }
+      t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - th).count();
       combine(0, nuse, Cxp, 2 * nb, nb, 0, 2);
       haveP = true;
       lam.assign(w.begin(), w.begin() + nb);
@@ -346,15 +518,20 @@ static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, SubSetup* S, int nb, int n
   L.nev = nev;
   L.ns = S->ns;
   const long long ns = S->ns;
-  work.ensure((size_t)9 * nb * ns * sizeof(T) + (size_t)9 * nb * nb * (sizeof(double) + 2 * sizeof(T)) + 1024);
+  const size_t gram_d = (size_t)2 * 9 * nb * nb, part_d = gram_part_doubles(3 * nb, 3 * nb);
+  work.ensure((size_t)9 * nb * ns * sizeof(T) + (gram_d + part_d) * sizeof(double) +
+              (size_t)9 * nb * nb * 2 * sizeof(T) + 2048);
   L.Sx = work.as<T>();
   L.HS = L.Sx + 3 * nb * ns;
   L.MS = L.HS + 3 * nb * ns;
   unsigned char* tail = reinterpret_cast<unsigned char*>(L.MS + 3 * nb * ns);
   tail = reinterpret_cast<unsigned char*>(((uintptr_t)tail + 255) & ~(uintptr_t)255);
   L.G = reinterpret_cast<double*>(tail);
-  L.Cd = reinterpret_cast<T*>(tail + (size_t)9 * nb * nb * sizeof(double) + 256);
+  L.part = L.G + gram_d;
+  L.Cd = reinterpret_cast<T*>(L.part + part_d);
   L.dinv = dinv;
+  CK(cudaMallocHost(&L.hG, (gram_d + 3 * nb + 16) * sizeof(double)));
+  CK(cudaMallocHost(&L.hC, (size_t)9 * nb * nb * 2 * sizeof(T) + 64));
 }
 
 qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
@@ -365,6 +542,7 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
   if (!(tol > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tol must be > 0");
   SubSetup S;
   setup_sub(m, b, phi, m_eff, 1, S);
+  const double t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (S.ndof < 3 * (nev + 4)) throw Error(QCAD_ERR_INVALID_ARG, "subdomain too small for nev");
   cudaStream_t s = m->stream;
   const int nb = (int)std::min<long long>(nev + std::max(2, nev / 4), S.ndof / 3);
@@ -378,17 +556,24 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
   // Phase 1: FP32 storage, applies and block arithmetic (FP64 Gram accumulation and host
   // Rayleigh-Ritz) until the residuals reach the single-precision level.
   DevBuf w32, w64;
+  ChebPre pre;
+  static const char* kenv = std::getenv("QCAD_LOBPCG_CHEB");
+  pre.init(m, &S, nb, kenv ? std::atoi(kenv) : 6, dinv32.as<float>());
   LobpcgRun<float> A;
   init_run<float>(A, m, &S, nb, nev, w32, dinv32.as<float>());
+  A.pre = &pre;
   launch_random_block<float>(ns, nb, ns, S.interior.as<unsigned char>(), 0x51ED5EEDull, A.Sx, s);
   A.apply(0);
   A.rr_x();
-  const double tol32 = std::max(tol, 1e-5);
-  A.run(tol32, 3000, lam_d, norms_d);
+  // the FP32 phase runs until its residuals stop improving (about 1e-6) or reach tol
+  const double tol32 = std::max(tol, 2e-7);
+  A.run(tol32, 3000, lam_d, norms_d, 15);
+  const double t_a = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 
   // Phase 2: FP64 from the FP32 Ritz vectors to the requested tolerance.
   LobpcgRun<double> B;
   init_run<double>(B, m, &S, nb, nev, w64, S.dinv.as<double>());
+  B.pre = &pre;
   launch_f2d(ns * nb, A.Sx, B.Sx, s);
   B.apply(0);
   B.rr_x();
@@ -411,6 +596,14 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
     rep->final_dphi_inf = 0;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     rep->status_detail = B.iters;  // FP64-phase iterations
+  }
+  if (std::getenv("QCAD_DEBUG")) {
+    const double t_all = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::fprintf(stderr,
+                 "[qcad] lobpcg setup %.1f ms, fp32 %.1f ms (%d it, sync %.1f, host %.1f), fp64 %.1f ms "
+                 "(%d it, sync %.1f, host %.1f)\n",
+                 1e3 * t_setup, 1e3 * (t_a - t_setup), A.iters, 1e3 * A.t_sync, 1e3 * A.t_host,
+                 1e3 * (t_all - t_a), B.iters, 1e3 * B.t_sync, 1e3 * B.t_host);
   }
   if (!converged) set_message("LOBPCG did not reach the requested tolerance");
   return converged ? QCAD_OK : QCAD_ERR_NOT_CONVERGED;

@@ -138,6 +138,11 @@ struct qcad_mesh_s {
   qcad::LaunchCfg cfg_res, cfg64, cfg32;
   int cheb_auto[2] = {0, 0};               // autotuned Chebyshev degree per precision (0 = not yet)
   int batch_kchunk = 0;                    // z chunk of this mesh in batched launches (0 = not tuned)
+  // largest eigenvalue of D^-1 J of the stored linearization per precision, valid while
+  // lam_ver matches lin_ver (lin_ver counts the residual evaluations that rewrote it)
+  long long lin_ver[2] = {0, 0};
+  long long lam_ver[2] = {-1, -1};
+  double lam_cache[2] = {0.0, 0.0};
   qcad::Profiler prof;
   // Schrodinger workspace
   qcad::DevBuf s_mx, s_kx, s_my, s_ky, s_mzx, s_mzy, s_kzz, s_cV, s_dinv, s_interior, s_blocks, s_gram;

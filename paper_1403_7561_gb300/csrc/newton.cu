@@ -214,7 +214,16 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
   }
   cudaStream_t s = m->stream;
   double lam = 0.0;
-  if (degree >= 2) lam = lambda_max<T>(m, 12);
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  if (degree >= 2) {
+    if (m->lam_ver[pi] == m->lin_ver[pi]) {
+      lam = m->lam_cache[pi];
+    } else {
+      lam = lambda_max<T>(m, 12);
+      m->lam_cache[pi] = lam;
+      m->lam_ver[pi] = m->lin_ver[pi];
+    }
+  }
   PcgScalars* h = m->h_scal;
   std::memset(h, 0, sizeof(PcgScalars));
   h->tol2 = rtol * rtol;
@@ -336,6 +345,7 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   Profiler::Pair pp;
   if (m->prof.on) m->prof.begin(PROF_RESIDUAL, s, pp);
   launch_residual(m->g64.g, a, m->cfg_res, s);
+  m->lin_ver[prec == 0 ? 0 : 1] += 1;  // the stored linearization changed
   if (m->prof.on) m->prof.end(pp, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_small, a.stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

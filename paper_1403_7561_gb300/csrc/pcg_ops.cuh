@@ -41,6 +41,7 @@ struct ApplyOp {
   // flag (the kernel substitutes the input on Dirichlet rows) and the store
   struct Pre {};
   static constexpr int NIN = 1;
+  static constexpr bool SEPM = false;  // no separable-mass second output
   __device__ const T* lin_src(int) const { return a.v; }
   __device__ T lin_mix(T x0, T) const { return x0; }
   __device__ T lin_in(int n) const { return a.v[n]; }
@@ -100,6 +101,7 @@ struct PcgApplyOp {
   }
   struct Pre {};
   static constexpr int NIN = 2;
+  static constexpr bool SEPM = false;
   __device__ const T* lin_src(int q) const { return q == 0 ? v.z : pin_src; }
   __device__ T lin_mix(T z, T p) const { return z + beta * p; }
   __device__ T lin_in(int n) const { return v.z[n] + beta * pin_src[n]; }
@@ -223,6 +225,7 @@ struct ChebStepOp {
     T w, dinv, z, r;
   };
   static constexpr int NIN = 1;
+  static constexpr bool SEPM = false;  // no separable-mass second output
   __device__ const T* lin_src(int) const { return dprev; }
   __device__ T lin_mix(T x0, T) const { return x0; }
   __device__ T lin_in(int n) const { return dprev[n]; }

@@ -22,15 +22,27 @@ void launch_potential(const SubdomainMap& sm, const double* phi, double V0, cons
                       const double* hz, T* cV, double* vmin, cudaStream_t s);
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s);
+// G1 = A^T B1 and, if B2 is not null, G2 = A^T B2 (p x q each, row-major, FP64, overwritten).
+// part: device scratch of gram_part_doubles(p, q) doubles. p <= 64, q <= 64.
 template <class T>
-void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B, long long ldb, double* G,
-                 cudaStream_t s);
+void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
+                 double* G1, double* G2, double* part, cudaStream_t s);
+size_t gram_part_doubles(int p, int q);
+// p <= 64.
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
                     long long ldy, cudaStream_t s);
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s);
+template <class T>
+void launch_cheb_block_init(long long n, int m, long long ld, const T* R, const T* dinv, double inv_theta, T* W,
+                            T* D, T* Z, cudaStream_t s);
+template <class T>
+void launch_cheb_block_step(long long n, int m, long long ld, const T* HD, const T* dinv, double c1, double c2,
+                            T* W, T* D, T* Z, cudaStream_t s);
+template <class T>
+void launch_power_sub(long long n, const T* v, const T* Hv, const T* dinv, T* vn, double* acc, cudaStream_t s);
 template <class T>
 void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, T* X,
                          cudaStream_t s);

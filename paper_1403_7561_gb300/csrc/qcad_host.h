@@ -150,9 +150,14 @@ struct HmArgs {
   const T* cV;     // V * w|J| at the qp of every subdomain element
   long long ld;    // vector stride (n_sub_nodes)
   int nvec;
+  double mscale;   // 1 / kappa_x: the consistent mass is the kappa_x-weighted z mass stencil times this
 };
+// variant >= 2: plane-factorized kernel (M applied as the separable mass stencil), else
+// element-gather.
 template <class T>
 void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+template <class T>
+void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
 
 }  // namespace qcad
 
