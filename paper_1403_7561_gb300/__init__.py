@@ -413,3 +413,42 @@ def qcad_autotune(mesh: Mesh, bias: dict, precision=1):
     _check(_lib.qcad_autotune(mesh.handle, C.byref(b), int(precision), C.byref(v), C.byref(r), C.byref(z),
                               C.byref(t)))
     return v.value, r.value, z.value, t.value
+
+
+class QcadDotCharge(torch.autograd.Function):
+    """Dot electron counts as a differentiable function of the gate voltages and the fixed charge.
+
+    ``N = QcadDotCharge.apply(V_gate, fixed_charge, mesh, bias, opts)``: V_gate a 1-D tensor of
+    the gate voltages (V), fixed_charge a CUDA FP64 tensor of n_elems volume charges (nm^-3) or
+    None. Forward: Newton solve of the nonlinear Poisson problem (qcad_poisson_solve) and the
+    dot counts (qcad_electron_counts, Sec. III). Backward: one adjoint solve per dot
+    (qcad_adjoint) gives dN/dV (n_dots x n_gates) and dN/dtheta (n_dots x n_elems); the
+    incoming gradient is contracted with them. The converged potential of the last forward
+    call is kept on ctx for the backward pass.
+    """
+
+    @staticmethod
+    def forward(ctx, V_gate, fixed_charge, mesh, bias, opts=None):
+        o = opts if opts is not None else make_opts(precision=1)
+        b = dict(bias, V_gate=[float(v) for v in V_gate.detach().double().cpu().tolist()])
+        phi = torch.zeros(mesh.n_nodes, dtype=torch.float64, device="cuda")
+        fc = fixed_charge.detach() if fixed_charge is not None else None
+        qcad_poisson_solve(mesh, b, o, phi, fixed_charge=fc)
+        N = qcad_electron_counts(mesh, b, phi, fixed_charge=fc)
+        ctx.mesh, ctx.bias, ctx.opts, ctx.phi, ctx.fc = mesh, b, o, phi, fc
+        ctx.has_fc = fixed_charge is not None
+        return torch.tensor(N, dtype=torch.float64, device=V_gate.device)
+
+    @staticmethod
+    def backward(ctx, gN):
+        mesh = ctx.mesh
+        want_q = ctx.has_fc and ctx.needs_input_grad[1]
+        dq = torch.empty(mesh.n_dots * mesh.n_elems, dtype=torch.float64, device="cuda") if want_q else None
+        dNdV = qcad_adjoint(mesh, ctx.bias, ctx.phi, ctx.opts, fixed_charge=ctx.fc, dN_dq=dq)
+        g = gN.detach().double()
+        JV = torch.tensor(dNdV, dtype=torch.float64, device=g.device)
+        gV = g @ JV if ctx.needs_input_grad[0] else None
+        gq = None
+        if want_q:
+            gq = g.to(dq.device) @ dq.view(mesh.n_dots, mesh.n_elems)
+        return gV, gq, None, None, None

@@ -1,0 +1,179 @@
+"""Parity at the benchmark sizes (run on a GB300).
+
+The assembled oracle cannot solve these meshes in seconds, so the CUDA results
+are checked against oracle quantities computed one by one (the residual of
+Eq. PoissonWeakForm at sampled nodes, from the oracle's element routines, see
+sampled_oracle.py), against properties that hold at any size (the unique
+solution has zero residual; eigenpairs have small residuals in the oracle's
+assembled H and M and are M-orthonormal), and against central differences of
+the solution map (adjoint gradients).
+
+Sizes: dqd_128x128x96_4K (1.6M nodes), dqd_256x256x128_0p5K (8.5M nodes), a
+12-instance subset of the 96-instance batch covering all nine size buckets
+(N^3 elements, N = 48..112), and the 128x128x96 adjoint with the interface
+fixed-charge field.
+"""
+import types
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import physics
+from oracle import schrodinger as OS
+from oracle.mesh import Mesh
+from oracle.poisson import semiconductor_material
+from sampled_oracle import SampledPoisson
+
+pytestmark = pytest.mark.gpu
+
+R_TOL = 1e-9  # V*nm: oracle residual of a converged CUDA solution (Newton stops at 1e-10)
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1403_7561_gb300 as qcad
+    return qcad
+
+
+def solve(q, dev, precision=1, fixed_charge=None, phi=None, warm=False):
+    m = q.qcad_mesh_create(dev)
+    if phi is None:
+        phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision, cheb_degree=0,
+                                                           warm_start=int(warm)), phi, fixed_charge=fixed_charge)
+    assert rep["status"] == "OK", rep
+    return m, phi, rep
+
+
+@pytest.fixture(scope="module")
+def c2(q):
+    dev = W.get("dqd_128x128x96_4K")
+    m, phi, rep = solve(q, dev)
+    return dev, m, phi
+
+
+def test_c2_residual_kernel_and_solution(q, c2):
+    dev, m, phi = c2
+    S = SampledPoisson(dev)
+    ijk = S.sample_nodes(400, seed=21)
+    # the converged potential zeroes the oracle's residual at every sampled node
+    R = S.residual_at(phi.cpu().numpy(), ijk)
+    assert np.max(np.abs(R)) < R_TOL
+    # the residual kernel at a perturbed potential, node by node
+    rng = np.random.default_rng(5)
+    pp = phi.cpu().numpy() + 0.01 * rng.standard_normal(m.n_nodes)
+    pg = torch.tensor(pp, device="cuda")
+    Rg = torch.empty_like(pg)
+    q.qcad_poisson_residual(m, dev["bias"], pg, Rg)
+    Ro = S.residual_at(pp, ijk)
+    nodes = S.node(ijk[:, 0], ijk[:, 1], ijk[:, 2])
+    assert np.max(np.abs(Rg.cpu().numpy()[nodes] - Ro)) <= 1e-12 * np.max(np.abs(Ro))
+
+
+def test_c3_mixed_solution_and_fp64_agree(q):
+    dev = W.get("dqd_256x256x128_0p5K")
+    m, phi, rep = solve(q, dev, precision=1)
+    S = SampledPoisson(dev)
+    ijk = S.sample_nodes(300, seed=22)
+    assert np.max(np.abs(S.residual_at(phi.cpu().numpy(), ijk))) < R_TOL
+    phi64 = torch.zeros_like(phi)
+    rep64 = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=0), phi64)
+    assert rep64["status"] == "OK"
+    assert torch.max(torch.abs(phi64 - phi)).item() <= 1e-9
+
+
+def batch_subset():
+    inst = W.batch_instances()
+    picked, seen = [], set()
+    for d in inst:  # the first instance of each of the nine buckets
+        if d["nx"] not in seen:
+            seen.add(d["nx"])
+            picked.append(d)
+    for d in inst:  # then three more, in order
+        if len(picked) >= 12:
+            break
+        if d not in picked:
+            picked.append(d)
+    return picked
+
+
+def test_c4_batch_subset_all_buckets(q):
+    devs = batch_subset()
+    assert len(devs) == 12 and len({d["nx"] for d in devs}) == 9
+    meshes = [q.qcad_mesh_create(d) for d in devs]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs], q.make_opts(precision=1), phis)
+    assert status == "OK"
+    for d, phi, rep in zip(devs, phis, reps):
+        assert rep["final_res_inf"] < 1e-10 and rep["final_dphi_inf"] < 1e-10
+        S = SampledPoisson(d)
+        ijk = S.sample_nodes(80, seed=23)
+        assert np.max(np.abs(S.residual_at(phi.cpu().numpy(), ijk))) < R_TOL, d["name"]
+
+
+def test_c5_adjoint_against_central_differences(q):
+    dev = W.get("dqd_128x128x96_4K_adjoint")
+    theta = np.array(W.interface_fixed_charge(dev, seed=5))
+    th = torch.tensor(theta, device="cuda")
+    m, phi, _ = solve(q, dev, fixed_charge=th)
+    dq = torch.empty(m.n_dots * m.n_elems, dtype=torch.float64, device="cuda")
+    dNdV = np.array(q.qcad_adjoint(m, dev["bias"], phi, q.make_opts(precision=1), fixed_charge=th, dN_dq=dq))
+    G = dq.view(m.n_dots, m.n_elems).cpu().numpy()
+
+    def counts(bias, fc):
+        p = phi.clone()
+        q.qcad_poisson_solve(m, bias, q.make_opts(precision=1, warm_start=1), p, fixed_charge=fc)
+        return np.array(q.qcad_electron_counts(m, bias, p, fixed_charge=fc))
+
+    h = 1e-4  # V
+    for gi in range(m.n_gates):
+        bp = dict(dev["bias"], V_gate=list(dev["bias"]["V_gate"]))
+        bm = dict(dev["bias"], V_gate=list(dev["bias"]["V_gate"]))
+        bp["V_gate"][gi] += h
+        bm["V_gate"][gi] -= h
+        fd = (counts(bp, th) - counts(bm, th)) / (2 * h)
+        assert np.max(np.abs(fd - dNdV[:, gi])) <= 1e-5 * np.max(np.abs(dNdV)), gi
+    # theta: three random directions and the ten largest entries of each dot's gradient
+    rng = np.random.default_rng(9)
+    scale = np.max(np.abs(theta))
+    for _ in range(3):
+        d = rng.standard_normal(m.n_elems) * scale
+        ht = 1e-2
+        dt = torch.tensor(ht * d, device="cuda")
+        fd = (counts(dev["bias"], th + dt) - counts(dev["bias"], th - dt)) / (2 * ht)
+        ad = G @ d
+        assert np.max(np.abs(fd - ad)) <= 1e-5 * np.max(np.abs(ad))
+    for dot in range(m.n_dots):
+        for e in np.argsort(-np.abs(G[dot]))[:10]:
+            he = 1e-2 * scale
+            dt = torch.zeros(m.n_elems, dtype=torch.float64, device="cuda")
+            dt[int(e)] = he
+            fd = (counts(dev["bias"], th + dt) - counts(dev["bias"], th - dt)) / (2 * he)
+            assert abs(fd[dot] - G[dot, e]) <= 1e-4 * np.max(np.abs(G[dot])), (dot, e)
+
+
+def test_c2_eigenpairs_against_assembled_operators(q, c2):
+    dev, m, phi = c2
+    nev = 10
+    evecs = torch.empty(nev, m.n_sub_dof, dtype=torch.float64, device="cuda")
+    E, rep = q.qcad_schrodinger_eigs(m, dev["bias"], phi, nev=nev, tol=1e-8, evecs=evecs)
+    assert rep["status"] == "OK"
+    assert np.all(np.diff(E) >= 0)
+    mesh = Mesh(dev)
+    si = semiconductor_material(dev)
+    prob = types.SimpleNamespace(mesh=mesh, phi_r=physics.phi_ref(si, dev["bias"]["T"]), si=si)
+    sel = mesh.subdomain_elements()
+    Vq = OS.device_potential(prob, phi.cpu().numpy(), sel)
+    H, M, idx = OS.operators(mesh, sel, mesh.subdomain_interior_nodes(), (0.19, 0.19, 0.19), Vq)
+    X = evecs.cpu().numpy().T  # n_sub_dof x nev, interior nodes in node order
+    assert X.shape[0] == len(idx)
+    HX, MX = H @ X, M @ X
+    assert np.max(np.abs(X.T @ MX - np.eye(nev))) <= 1e-9
+    rq = np.einsum("ij,ij->j", X, HX)
+    assert np.max(np.abs(rq - E) / np.abs(E)) <= 1e-10
+    res = np.linalg.norm(HX - MX * np.array(E), axis=0) / (np.abs(E) * np.linalg.norm(MX, axis=0))
+    assert np.max(res) <= 1e-7

@@ -145,3 +145,34 @@ def test_fd_capacitance_matches_oracle(q, dqd):
     Cg = q.qcad_capacitance(m, dev["bias"], gate=1, dV=0.01)
     assert np.all(np.array(Co) > 0)
     assert np.max(np.abs(np.array(Cg) - Co) / np.abs(Co)) < 1e-6
+
+
+def test_dot_charge_autograd(q, dqd):
+    # QcadDotCharge: forward = solve + counts; backward = adjoint, checked against central
+    # differences of the forward map (h = 1e-4 V, and a random direction in theta)
+    dev, P, phi = dqd
+    m = q.qcad_mesh_create(dev)
+    opts = q.make_opts(precision=0)
+    V = torch.tensor(dev["bias"]["V_gate"], dtype=torch.float64, requires_grad=True)
+    theta = torch.tensor(np.array(W.interface_fixed_charge(dev, seed=5)), device="cuda", requires_grad=True)
+    N = q.QcadDotCharge.apply(V, theta, m, dev["bias"], opts)
+    assert N.shape == (m.n_dots,)
+    w = torch.tensor([1.0, -0.5], dtype=torch.float64)
+    (N * w).sum().backward()
+
+    def f(v, th):
+        with torch.no_grad():
+            return (q.QcadDotCharge.apply(v, th, m, dev["bias"], opts) * w).sum().item()
+
+    h = 1e-4
+    for gi in range(len(V)):
+        e = torch.zeros_like(V)
+        e[gi] = h
+        fd = (f(V.detach() + e, theta.detach()) - f(V.detach() - e, theta.detach())) / (2 * h)
+        assert abs(V.grad[gi].item() - fd) <= 1e-5 * max(1.0, abs(fd)), gi
+    rng = np.random.default_rng(8)
+    d = torch.tensor(rng.standard_normal(m.n_elems), device="cuda") * theta.detach().abs().max()
+    ht = 1e-2
+    fd = (f(V.detach(), theta.detach() + ht * d) - f(V.detach(), theta.detach() - ht * d)) / (2 * ht)
+    ad = torch.dot(theta.grad, d).item()
+    assert abs(ad - fd) <= 1e-5 * max(abs(fd), abs(ad))
