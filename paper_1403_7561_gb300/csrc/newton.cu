@@ -1,6 +1,6 @@
 // Solver drivers (host): preconditioned CG with device-resident scalars and
 // CUDA-graph-captured iteration chunks, the Newton iteration of the nonlinear
-// Poisson problem (Sec. II.A.3: "solved by a nonlinear Newton solver"),
+// Poisson problem (Sec. II.A.3, which solves it by Newton's method),
 // electron counts, finite-difference capacitance (Sec. III) and the adjoint.
 #include <cuda_runtime.h>
 
