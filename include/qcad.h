@@ -220,6 +220,18 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
                                   const double* m_eff, double tol, double* evals, double* evecs,
                                   qcad_solve_report* rep);
 
+/* The adjoint capacitance (as qcad_adjoint) and the Schrodinger eigenpairs (as
+ * qcad_schrodinger_eigs) at one converged potential phi, computed concurrently:
+ * the eigensolve runs on a second stream of the mesh from a second host thread
+ * while the adjoint runs on the mesh stream (the paper computes the two one
+ * after the other; they share only read-only data). Arguments as in the two
+ * calls; eig_rep is the eigensolve's report (may be NULL). Returns the
+ * adjoint's status if it is not OK, else the eigensolve's. */
+qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                              const double* fixed_charge_elem, double* dN_dV, double* dN_dq, int nev,
+                              const double* m_eff, double tol, double* evals, double* evecs,
+                              qcad_solve_report* eig_rep);
+
 /* Batched form (no counterpart in the paper, which solves one device at a
  * time; the operator of every instance is the one of qcad_poisson_solve):
  * n independent meshes of any sizes, each with its own bias, solved by a

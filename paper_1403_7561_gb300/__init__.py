@@ -101,6 +101,8 @@ _sigs = {
     "qcad_adjoint": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), _P, _P, _D, _P],
     "qcad_schrodinger_apply": [_P, C.POINTER(Bias), _P, _D, C.c_int, _P, _P, _P, C.c_int],
     "qcad_schrodinger_eigs": [_P, C.POINTER(Bias), _P, C.c_int, _D, C.c_double, _D, _P, C.POINTER(SolveReport)],
+    "qcad_adjoint_eigs": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), _P, _P, _D, _P, C.c_int, _D, C.c_double, _D,
+                          _P, C.POINTER(SolveReport)],
     "qcad_poisson_solve_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P),
                                  C.POINTER(SolveReport)],
     "qcad_profile_enable": [_P, C.c_int],
@@ -324,6 +326,27 @@ def qcad_schrodinger_eigs(mesh: Mesh, bias: dict, phi, nev=10, m_eff=(0.19, 0.19
     d = rep.as_dict()
     d["status"] = STATUS[code]
     return list(ev), d
+
+
+def qcad_adjoint_eigs(mesh: Mesh, bias: dict, phi, opts=None, fixed_charge=None, dN_dq=None, nev=10,
+                      m_eff=(0.19, 0.19, 0.19), tol=1e-7, evecs=None, allow_not_converged=False):
+    """qcad_adjoint and qcad_schrodinger_eigs at phi, run concurrently; returns (dN_dV, evals, eig_report)."""
+    b = make_bias(bias)
+    o = opts if opts is not None else make_opts()
+    out = (C.c_double * max(1, mesh.n_dots * mesh.n_gates))()
+    me = (C.c_double * 3)(*m_eff)
+    ev = (C.c_double * nev)()
+    rep = SolveReport()
+    code = _check(_lib.qcad_adjoint_eigs(mesh.handle, C.byref(b), C.byref(o), _dptr(phi, mesh.n_nodes, name="phi"),
+                                         _dptr(fixed_charge, mesh.n_elems, name="fixed_charge", allow_none=True), out,
+                                         _dptr(dN_dq, mesh.n_dots * mesh.n_elems, name="dN_dq", allow_none=True),
+                                         int(nev), me, float(tol), ev,
+                                         _dptr(evecs, mesh.n_sub_dof * nev, name="evecs", allow_none=True),
+                                         C.byref(rep)), allow_not_converged)
+    flat = list(out)
+    d = rep.as_dict()
+    d["status"] = STATUS[code]
+    return [flat[k * mesh.n_gates:(k + 1) * mesh.n_gates] for k in range(mesh.n_dots)], list(ev), d
 
 
 def qcad_poisson_solve_batch(meshes, biases, opts, phis, allow_not_converged=False):

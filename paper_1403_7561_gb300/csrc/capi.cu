@@ -4,7 +4,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mesh.h"
@@ -28,6 +30,9 @@ qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* 
                               const double* X, double* HX, double* MX, int precision);
 qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
                              double tol, double* evals, double* evecs, qcad_solve_report* rep);
+qcad_status schrodinger_eigs_stream2(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev,
+                                     const double* m_eff, double tol, double* evals, double* evecs,
+                                     qcad_solve_report* rep);
 qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                 double* const* phis, qcad_solve_report* reps);
 qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* variant, int* tile_rows, int* z_chunk,
@@ -169,6 +174,40 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
   return guarded([&] {
     need_mesh(m);
     return qcad::schrodinger_eigs(m, b, phi, nev, m_eff, tol, evals, evecs, rep);
+  });
+}
+
+qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                              const double* fixed_charge_elem, double* dN_dV, double* dN_dq, int nev,
+                              const double* m_eff, double tol, double* evals, double* evecs,
+                              qcad_solve_report* eig_rep) {
+  return guarded([&] {
+    need_mesh(m);
+    // the eigensolve on the mesh's second stream from a second host thread, the adjoint here
+    qcad_status st_eig = QCAD_OK;
+    std::string eig_msg;
+    std::exception_ptr eig_exc;
+    std::thread th([&] {
+      try {
+        CK(cudaSetDevice(m->device));
+        st_eig = qcad::schrodinger_eigs_stream2(m, b, phi, nev, m_eff, tol, evals, evecs, eig_rep);
+        if (st_eig != QCAD_OK) eig_msg = g_last_error;
+      } catch (...) {
+        eig_exc = std::current_exception();
+      }
+    });
+    qcad_status st_adj = QCAD_OK;
+    try {
+      st_adj = qcad::adjoint(m, b, o, phi, fixed_charge_elem, dN_dV, dN_dq);
+    } catch (...) {
+      th.join();
+      throw;
+    }
+    th.join();
+    if (eig_exc) std::rethrow_exception(eig_exc);
+    if (st_adj != QCAD_OK) return st_adj;
+    if (st_eig != QCAD_OK) g_last_error = eig_msg;
+    return st_eig;
   });
 }
 

@@ -149,66 +149,98 @@ void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, 
   note_launch(), pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
 }
 
-// G1 = A^T B1 and optionally G2 = A^T B2 (p x q each, row-major o = a*q + b) for column-major
-// A (n x p, lda) and B1, B2 (n x q, ldb): tall-skinny products of the LOBPCG blocks.
-// A block walks 32-row tiles of its share of the rows, staged transposed in shared memory
-// ([row][column]); each thread owns a 4 x 4 tile of outputs (registers), sums a row tile in
-// the storage precision and accumulates tiles in FP64. Every block writes its partial sums
-// to its own slot of `part` (no atomics); gram_reduce_kernel adds the slots in a fixed order,
-// so the result is deterministic.
-constexpr int GR = 32;
+// G1 = A^T B1 and optionally G2 = A^T B2 (p x p each, row-major o = a*p + b) for column-major
+// A (n x p, lda) and B1, B2 (n x p, ldb): the Gram matrices of the LOBPCG blocks. A block walks
+// 32-row tiles of its share of the rows, copied asynchronously (double-buffered) into shared
+// memory transposed ([row][column]); each thread owns a 4 x 4 tile of outputs (registers), sums
+// a row tile in the storage precision and accumulates tiles in FP64. Every block writes its
+// partial sums to its own slot of `part` (no atomics); gram_reduce_kernel adds the slots in a
+// fixed order, so the result is deterministic.
+constexpr int GR = 32;                   // rows per shared-memory tile
 constexpr int GRAM_MAX_BLOCKS = 2 * 152;
 
+// 4 consecutive values of a shared row (16-byte aligned for float, two 16-byte loads for double).
+__device__ __forceinline__ void gram_ld4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void gram_ld4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// One element global -> shared, asynchronous; zero fill when !valid.
 template <class T>
-__global__ void __launch_bounds__(1024) gram_kernel(long long n, int p, int q, int nb2, const T* A, long long lda,
-                                                    const T* B1, const T* B2, long long ldb, double* part) {
+__device__ __forceinline__ void gram_cp(T* smem, const T* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, const T* A, long long lda,
+                                                   const T* B1, const T* B2, long long ldb, double* part) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
-  T* sh = reinterpret_cast<T*>(sh_raw);
-  const int qt = q * nb2;                    // output columns over [B1 | B2]
+  T* sh = reinterpret_cast<T*>(sh_raw);      // two stages of GR x W
+  const int q = p;
+  const int qt = q * nb2;
   const int ta_n = (p + 3) / 4, tb_n = (qt + 3) / 4;
   const int pp = 4 * ta_n, qp = 4 * tb_n;
-  const int W = pp + qp + 4;                 // shared row stride (multiple of 4)
+  const int W = pp + qp + 4;                 // shared row stride (multiple of 4): A | B1 | B2
   const int tid = threadIdx.x, nth = blockDim.x;
-  // padding columns stay zero (tile loads write only the real columns)
-  for (int t = tid; t < GR * W; t += nth) sh[t] = T(0);
+  // padding columns stay zero (the copies write only the real columns)
+  for (int t = tid; t < 2 * GR * W; t += nth) sh[t] = T(0);
+  __syncthreads();
   const bool active = tid < ta_n * tb_n;
   const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
   double acc[16];
 #pragma unroll
   for (int s = 0; s < 16; ++s) acc[s] = 0.0;
   const long long ntiles = (n + GR - 1) / GR;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long r0 = tile * GR;
-    __syncthreads();
-    for (int t = tid; t < (p + qt) * GR; t += nth) {
-      const int col = t / GR, rr = t % GR;
-      const long long row = r0 + rr;
-      T v = T(0);
-      int sc;
-      if (col < p) {
-        if (row < n) v = A[col * lda + row];
-        sc = col;
-      } else {
-        const int bc = col - p;
-        if (row < n) v = bc < q ? B1[bc * ldb + row] : B2[(bc - q) * ldb + row];
-        sc = pp + bc;
+  auto issue = [&](long long tile, int stage) {
+    if (tile < ntiles) {
+      const long long r0 = tile * GR;
+      T* st = sh + (size_t)stage * GR * W;
+      for (int t = tid; t < (p + qt) * GR; t += nth) {
+        const int col = t / GR, rr = t % GR;
+        const long long row = r0 + rr;
+        const bool ok = row < n;
+        const T* src;
+        int sc;
+        if (col < p) {
+          src = A + col * lda + (ok ? row : 0);
+          sc = col;
+        } else {
+          const int bc = col - p;
+          src = (bc < q ? B1 + bc * ldb : B2 + (bc - q) * ldb) + (ok ? row : 0);
+          sc = pp + bc;
+        }
+        gram_cp<T>(st + rr * W + sc, src, ok);
       }
-      sh[rr * W + sc] = v;
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int stage = 0;
+  issue(blockIdx.x, 0);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    issue(tile + gridDim.x, stage ^ 1);  // next tile into the other stage
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
     if (active) {
+      const T* st = sh + (size_t)stage * GR * W;
       T s16[16];
 #pragma unroll
       for (int s = 0; s < 16; ++s) s16[s] = T(0);
 #pragma unroll 4
       for (int rr = 0; rr < GR; ++rr) {
-        const T* row = sh + rr * W;
+        const T* row = st + rr * W;
         T av[4], bv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          av[u] = row[4 * ta + u];
-          bv[u] = row[pp + 4 * tb + u];
-        }
+        gram_ld4(row + 4 * ta, av);
+        gram_ld4(row + pp + 4 * tb, bv);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -217,9 +249,12 @@ __global__ void __launch_bounds__(1024) gram_kernel(long long n, int p, int q, i
 #pragma unroll
       for (int s = 0; s < 16; ++s) acc[s] += (double)s16[s];
     }
+    __syncthreads();  // the stage is refilled by the next iteration's copies
+    stage ^= 1;
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (!active) return;
-  // slot layout: G1 block (p*q) then G2 block (p*q)
+  // slot layout: product 0 (p*q) then product 1
   double* out = part + (size_t)blockIdx.x * p * qt;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -229,21 +264,29 @@ __global__ void __launch_bounds__(1024) gram_kernel(long long n, int p, int q, i
     for (int v = 0; v < 4; ++v) {
       const int bc = 4 * tb + v;
       if (bc >= qt) continue;
-      const int o = bc < q ? a * q + bc : p * q + a * q + (bc - q);
-      out[o] = acc[4 * u + v];
+      out[bc < q ? a * q + bc : p * q + a * q + (bc - q)] = acc[4 * u + v];
     }
   }
 }
 
-__global__ void gram_reduce_kernel(int nblk, int p, int q, int nb2, const double* part, double* G1, double* G2) {
-  const int tot = p * q * nb2;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < tot; o += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * tot + o];
-    if (o < p * q)
-      G1[o] = s;
+// Sum of the per-block partials in a fixed order: 32 outputs per block, 8 warps each summing
+// every 8th partial, then the 8 sums in order.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(int nblk, int tot, int pq, const double* part, double* G1,
+                                                          double* G2) {
+  __shared__ double red[8][32];
+  const int o = blockIdx.x * 32 + threadIdx.x;
+  double s = 0.0;
+  if (o < tot)
+    for (int b = threadIdx.y; b < nblk; b += 8) s += part[(size_t)b * tot + o];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && o < tot) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    if (o < pq)
+      G1[o] = t;
     else
-      G2[o - p * q] = s;
+      G2[o - pq] = t;
   }
 }
 
@@ -252,18 +295,19 @@ size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 
 template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
                  double* G1, double* G2, double* part, cudaStream_t s) {
+  (void)q;  // the products of LOBPCG are square: q == p
   const int nb2 = B2 ? 2 : 1;
-  const int qt = q * nb2;
-  const int ta_n = (p + 3) / 4, tb_n = (qt + 3) / 4;
-  const int nth = std::max(32, ((ta_n * tb_n + 31) / 32) * 32);
+  const int ta_n = (p + 3) / 4, tb_n = (p * nb2 + 3) / 4;
+  const int nth = std::min(512, std::max(256, ((ta_n * tb_n + 31) / 32) * 32));
   const long long ntiles = (n + GR - 1) / GR;
   const int nblk = (int)std::max<long long>(1, std::min<long long>(GRAM_MAX_BLOCKS, ntiles));
-  const size_t shm = (size_t)GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T);
+  const size_t shm = (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T);
   static bool attr = false;
-  if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024) ==
+  if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
                     cudaSuccess;
-  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, q, nb2, A, lda, B1, B2, ldb, part);
-  note_launch(), gram_reduce_kernel<<<(p * qt + 255) / 256, 256, 0, s>>>(nblk, p, q, nb2, part, G1, G2);
+  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part);
+  const int tot = p * p * nb2;
+  note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
 }
 template void launch_gram<float>(long long, int, int, const float*, long long, const float*, const float*, long long,
                                  double*, double*, double*, cudaStream_t);

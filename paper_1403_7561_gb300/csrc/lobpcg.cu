@@ -32,6 +32,20 @@ void build_grid(GridDev<T>& gd, const GridTables& t, const std::vector<double>& 
 double host_h2m0();
 void set_message(const std::string& msg);
 
+// Stream and scratch of one eigensolve: the mesh's own, or a second set so that an
+// eigensolve can run concurrently with another call on the mesh stream.
+struct EigIo {
+  cudaStream_t s;
+  double* stats;    // device scratch, >= 64 doubles
+  double* h_small;  // pinned host scratch, >= 64 doubles
+};
+static EigIo mesh_io(qcad_mesh_s* m) { return EigIo{m->stream, m->stats.as<double>(), m->h_small}; }
+
+static int debug_level() {
+  static const int lvl = std::getenv("QCAD_DEBUG") ? std::max(1, std::atoi(std::getenv("QCAD_DEBUG"))) : 0;
+  return lvl;
+}
+
 struct SubSetup {
   SubdomainMap sm;
   long long ns;     // subdomain nodes
@@ -44,11 +58,11 @@ struct SubSetup {
 };
 
 static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, const double* m_eff, int need32,
-                      SubSetup& S) {
+                      SubSetup& S, const EigIo& io) {
   if (!m->has_sub) throw Error(QCAD_ERR_INVALID_ARG, "mesh has no Schrodinger subdomain");
   for (int d = 0; d < 3; ++d)
     if (!(m_eff[d] > 0)) throw Error(QCAD_ERR_INVALID_ARG, "effective masses must be > 0");
-  cudaStream_t s = m->stream;
+  cudaStream_t s = io.s;
   SubdomainMap& sm = S.sm;
   sm.i0 = m->sub[0];
   sm.j0 = m->sub[2];
@@ -85,7 +99,7 @@ static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, con
   const Phys P = make_phys(m, b);
   const long long nes = (long long)sm.nxs * sm.nys * sm.nzs;
   S.cV64.ensure(nes * 8 * sizeof(double) + 64);
-  double* vmin_d = m->stats.as<double>() + 40;
+  double* vmin_d = io.stats + 40;
   const double big = 1e300;
   CK(cudaMemcpyAsync(vmin_d, &big, sizeof(double), cudaMemcpyHostToDevice, s));
   launch_potential<double>(sm, phi, P.phi_ref - P.chi, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz,
@@ -166,7 +180,7 @@ qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* 
   if (!b || !phi || !m_eff || !X || nvec < 1) throw Error(QCAD_ERR_INVALID_ARG, "null pointer or nvec < 1");
   if (precision != 0 && precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "precision must be 0 or 1");
   SubSetup S;
-  setup_sub(m, b, phi, m_eff, precision, S);
+  setup_sub(m, b, phi, m_eff, precision, S, mesh_io(m));
   cudaStream_t s = m->stream;
   DevBuf full, tmp;
   full.ensure(3 * S.ns * nvec * sizeof(double) + 64);
@@ -188,10 +202,11 @@ qcad_status schrodinger_apply(qcad_mesh_s* m, const qcad_bias* b, const double* 
 // Chebyshev-Jacobi preconditioner of the LOBPCG residual block, applied in FP32 in both
 // phases (a preconditioner needs no more precision than that): W = p_k(D^-1 H) D^-1 R with
 // the Chebyshev polynomial of the interval [b / (4k^2), b] of D^-1 H, b = 1.1 lambda_max
-// (power iteration). k <= 1 means plain Jacobi.
+// (power iteration). The degree is odd, so the preconditioner stays positive definite above
+// an underestimated lambda_max. k <= 1 means plain Jacobi.
 struct ChebPre {
   int k = 0;
-  double theta = 0.0, delta = 0.0;
+  double theta = 0.0, delta = 0.0, lam_max = 0.0;
   qcad_mesh_s* m = nullptr;
   SubSetup* S = nullptr;
   int nb = 0;
@@ -199,6 +214,7 @@ struct ChebPre {
   DevBuf buf;
   float *R32 = nullptr, *W = nullptr, *D = nullptr, *HD = nullptr;
   const float* dinv = nullptr;
+  EigIo io{};
 
   void hmul(const float* X, float* HX, int nvec) {
     HmArgs<float> a{};
@@ -209,10 +225,11 @@ struct ChebPre {
     a.ld = ns;
     a.nvec = nvec;
     a.mscale = S->inv_kx;
-    launch_hm_apply<float>(S->g32.g, a, LaunchCfg{8, 16}, m->stream);
+    launch_hm_apply<float>(S->g32.g, a, LaunchCfg{8, 16}, io.s);
   }
-  void init(qcad_mesh_s* m_, SubSetup* S_, int nb_, int k_, const float* dinv32) {
+  void init(qcad_mesh_s* m_, const EigIo& io_, SubSetup* S_, int nb_, int k_, const float* dinv32) {
     m = m_;
+    io = io_;
     S = S_;
     nb = nb_;
     ns = S->ns;
@@ -224,18 +241,18 @@ struct ChebPre {
     W = R32 + nb * ns;
     D = W + nb * ns;
     HD = D + nb * ns;
-    cudaStream_t s = m->stream;
+    cudaStream_t s = io.s;
     // largest eigenvalue of D^-1 H by power iteration on one vector (uses W and D as scratch)
     launch_random_block<float>(ns, 1, ns, S->interior.as<unsigned char>(), 0xC4EB5EEDull, W, s);
-    double* acc = m->stats.as<double>() + 48;
+    double* acc = io.stats + 48;
     double lam = 0.0;
     for (int it = 0; it < 12; ++it) {
       hmul(W, HD, 1);
       CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
       launch_power_sub<float>(ns, W, HD, dinv, D, acc, s);
-      CK(cudaMemcpyAsync(m->h_small + 40, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(io.h_small + 40, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      const double a0 = m->h_small[40], a1 = m->h_small[41], a2 = m->h_small[42];
+      const double a0 = io.h_small[40], a1 = io.h_small[41], a2 = io.h_small[42];
       if (!(a1 > 0.0) || !(a2 > 0.0)) break;
       lam = a0 / a1;
       launch_scale<float>(ns, D, 1.0 / std::sqrt(a2), s);
@@ -245,13 +262,20 @@ struct ChebPre {
       k = 0;
       return;
     }
-    const double b = 1.1 * lam, a = b / (4.0 * k * k);
+    lam_max = lam;
+    set_degree(k);
+  }
+  // Polynomial degree k >= 2 on the interval [b / 4k^2, b], b = 1.1 lambda_max.
+  void set_degree(int k_) {
+    if (!(lam_max > 0.0) || k_ < 2) return;
+    k = k_;
+    const double b = 1.1 * lam_max, a = b / (4.0 * k * k);
     theta = 0.5 * (a + b);
     delta = 0.5 * (b - a);
   }
   // Z = p_k(D^-1 H) D^-1 R for nb columns (Z may alias R).
   void apply(const float* R, float* Z) {
-    cudaStream_t s = m->stream;
+    cudaStream_t s = io.s;
     launch_cheb_block_init<float>(ns, nb, ns, R, dinv, 1.0 / theta, W, D, Z, s);
     const double sigma = theta / delta;
     double rho_prev = 1.0 / sigma, rho = rho_prev;
@@ -267,9 +291,9 @@ struct ChebPre {
 // FP32 preconditioning of a residual block stored in precision T.
 static void precondition_block(ChebPre& P, float* Rb, long long) { P.apply(Rb, Rb); }
 static void precondition_block(ChebPre& P, double* Rb, long long tot) {
-  launch_d2f(tot, Rb, P.R32, P.m->stream);
+  launch_d2f(tot, Rb, P.R32, P.io.s);
   P.apply(P.R32, P.R32);
-  launch_f2d(tot, P.R32, Rb, P.m->stream);
+  launch_f2d(tot, P.R32, Rb, P.io.s);
 }
 
 // One LOBPCG run in storage/apply precision T (FP32 for the iteration phase,
@@ -428,7 +452,11 @@ struct LobpcgRun {
       int nwp = haveP ? 2 * nb : nb;
       gram_async(nwp, nwp, blk(Sx, 1), blk(MS, 1), nullptr);
       sync();
-      if (converged(tol)) return true;
+      const bool conv = converged(tol);
+      if (debug_level() >= 2)
+        std::fprintf(stderr, "[qcad] lobpcg %s it %d worst %.3e\n", sizeof(T) == 4 ? "fp32" : "fp64", it,
+                     *std::max_element(rel.begin(), rel.begin() + nev));
+      if (conv) return true;
       if (it > maxit) break;
       if (stall > 0) {
         const double worst = *std::max_element(rel.begin(), rel.begin() + nev);
@@ -510,10 +538,11 @@ template <> const Grid<double>& LobpcgRun<double>::grid() { return S->g64.g; }
 template <> const Grid<float>& LobpcgRun<float>::grid() { return S->g32.g; }
 
 template <class T>
-static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, SubSetup* S, int nb, int nev, DevBuf& work, const T* dinv) {
+static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, const EigIo& io, SubSetup* S, int nb, int nev, DevBuf& work,
+                     const T* dinv) {
   L.m = m;
   L.S = S;
-  L.s = m->stream;
+  L.s = io.s;
   L.nb = nb;
   L.nev = nev;
   L.ns = S->ns;
@@ -534,17 +563,18 @@ static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, SubSetup* S, int nb, int n
   CK(cudaMallocHost(&L.hC, (size_t)9 * nb * nb * 2 * sizeof(T) + 64));
 }
 
-qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
-                             double tol, double* evals, double* evecs, qcad_solve_report* rep) {
+qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias* b, const double* phi, int nev,
+                                const double* m_eff, double tol, double* evals, double* evecs,
+                                qcad_solve_report* rep) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!b || !phi || !m_eff || !evals) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
   if (nev < 1 || nev > 16) throw Error(QCAD_ERR_INVALID_ARG, "nev must be in [1, 16]");
   if (!(tol > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tol must be > 0");
   SubSetup S;
-  setup_sub(m, b, phi, m_eff, 1, S);
+  setup_sub(m, b, phi, m_eff, 1, S, io);
   const double t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (S.ndof < 3 * (nev + 4)) throw Error(QCAD_ERR_INVALID_ARG, "subdomain too small for nev");
-  cudaStream_t s = m->stream;
+  cudaStream_t s = io.s;
   const int nb = (int)std::min<long long>(nev + std::max(2, nev / 4), S.ndof / 3);
   const long long ns = S.ns;
   DevBuf lam_d, norms_d, dinv32;
@@ -557,22 +587,22 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
   // Rayleigh-Ritz) until the residuals reach the single-precision level.
   DevBuf w32, w64;
   ChebPre pre;
-  static const char* kenv = std::getenv("QCAD_LOBPCG_CHEB");
-  pre.init(m, &S, nb, kenv ? std::atoi(kenv) : 6, dinv32.as<float>());
+  pre.init(m, io, &S, nb, 5, dinv32.as<float>());
   LobpcgRun<float> A;
-  init_run<float>(A, m, &S, nb, nev, w32, dinv32.as<float>());
+  init_run<float>(A, m, io, &S, nb, nev, w32, dinv32.as<float>());
   A.pre = &pre;
   launch_random_block<float>(ns, nb, ns, S.interior.as<unsigned char>(), 0x51ED5EEDull, A.Sx, s);
   A.apply(0);
   A.rr_x();
-  // the FP32 phase runs until its residuals stop improving (about 1e-6) or reach tol
-  const double tol32 = std::max(tol, 2e-7);
+  // the FP32 phase stops at 3e-6 relative residual, above where single-precision LOBPCG loses
+  // the P block's conditioning (near 2e-6 on these devices), or when it stops improving
+  const double tol32 = std::max(tol, 3e-6);
   A.run(tol32, 3000, lam_d, norms_d, 15);
   const double t_a = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 
   // Phase 2: FP64 from the FP32 Ritz vectors to the requested tolerance.
   LobpcgRun<double> B;
-  init_run<double>(B, m, &S, nb, nev, w64, S.dinv.as<double>());
+  init_run<double>(B, m, io, &S, nb, nev, w64, S.dinv.as<double>());
   B.pre = &pre;
   launch_f2d(ns * nb, A.Sx, B.Sx, s);
   B.apply(0);
@@ -607,6 +637,29 @@ qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* p
   }
   if (!converged) set_message("LOBPCG did not reach the requested tolerance");
   return converged ? QCAD_OK : QCAD_ERR_NOT_CONVERGED;
+}
+
+qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
+                             double tol, double* evals, double* evecs, qcad_solve_report* rep) {
+  return schrodinger_eigs_io(m, mesh_io(m), b, phi, nev, m_eff, tol, evals, evecs, rep);
+}
+
+// The eigensolve on the mesh's second stream and scratch (created on first use), for running
+// concurrently with work on the mesh stream (the two share only read-only mesh data).
+qcad_status schrodinger_eigs_stream2(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev,
+                                     const double* m_eff, double tol, double* evals, double* evecs,
+                                     qcad_solve_report* rep) {
+  if (!m->stream2) {
+    // the eigensolve issues short, latency-bound kernels between host synchronizations: the
+    // highest priority lets its blocks start ahead of the concurrent work's queued blocks
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&m->stream2, cudaStreamNonBlocking, hi));
+  }
+  m->stats2.ensure(64 * sizeof(double));
+  if (!m->h_small2) CK(cudaMallocHost(&m->h_small2, 64 * sizeof(double)));
+  return schrodinger_eigs_io(m, EigIo{m->stream2, m->stats2.as<double>(), m->h_small2}, b, phi, nev, m_eff, tol,
+                             evals, evecs, rep);
 }
 
 }  // namespace qcad

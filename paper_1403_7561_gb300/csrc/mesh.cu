@@ -31,19 +31,28 @@ cudaEvent_t Profiler::get() {
   return e;
 }
 void Profiler::begin(int cls, cudaStream_t s, Pair& out) {
+  std::lock_guard<std::mutex> lk(mu);
   out.a = get();
   out.b = get();
   out.cls = cls;
   CK(cudaEventRecord(out.a, s));
 }
 void Profiler::end(Pair& p, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(mu);
   CK(cudaEventRecord(p.b, s));
   open.push_back(p);
 }
 void Profiler::harvest() {
+  std::lock_guard<std::mutex> lk(mu);
+  std::vector<Pair> keep;  // pairs of another stream that has not reached them yet
   for (auto& p : open) {
+    const cudaError_t q = cudaEventQuery(p.b);
+    if (q == cudaErrorNotReady) {
+      keep.push_back(p);
+      continue;
+    }
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+    if (q == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
       ms[p.cls] += t;
       launches[p.cls] += 1;
     } else {
@@ -52,7 +61,12 @@ void Profiler::harvest() {
     pool.push_back(p.a);
     pool.push_back(p.b);
   }
-  open.clear();
+  open.swap(keep);
+}
+void Profiler::add(int cls, double ms_) {
+  std::lock_guard<std::mutex> lk(mu);
+  ms[cls] += ms_;
+  launches[cls] += 1;
 }
 Profiler::~Profiler() {
   for (auto& p : open) {
@@ -389,4 +403,6 @@ qcad_mesh_s::~qcad_mesh_s() {
   if (owns_stream && stream) cudaStreamDestroy(stream);
   if (h_scal) cudaFreeHost(h_scal);
   if (h_small) cudaFreeHost(h_small);
+  if (h_small2) cudaFreeHost(h_small2);
+  if (stream2) cudaStreamDestroy(stream2);
 }

@@ -6,6 +6,7 @@
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/qcad.h"
@@ -68,6 +69,7 @@ struct GridDev {
 enum ProfClass { PROF_APPLY32 = 0, PROF_APPLY64, PROF_UPDATE32, PROF_UPDATE64, PROF_RESIDUAL, PROF_HM, PROF_NCLASS };
 
 struct Profiler {
+  std::mutex mu;  // begin/end/harvest/add may come from two host threads
   bool on = false;
   long long launches[PROF_NCLASS] = {};
   double ms[PROF_NCLASS] = {};
@@ -81,7 +83,8 @@ struct Profiler {
   cudaEvent_t get();
   void begin(int cls, cudaStream_t s, Pair& out);
   void end(Pair& p, cudaStream_t s);
-  void harvest();  // after a stream sync: accumulate elapsed times of recorded pairs
+  void harvest();  // after a stream sync: accumulate elapsed times of completed pairs
+  void add(int cls, double ms_);
   ~Profiler();
 };
 
@@ -134,6 +137,10 @@ struct qcad_mesh_s {
   qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
   qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror
   double* h_small = nullptr;               // pinned host scratch (64 doubles)
+  // second stream and scratch for an eigensolve that runs concurrently with the mesh stream
+  cudaStream_t stream2 = nullptr;
+  qcad::DevBuf stats2;
+  double* h_small2 = nullptr;
   qcad::PcgGraph graph64, graph32;
   qcad::LaunchCfg cfg_res, cfg64, cfg32;
   int cheb_auto[2] = {0, 0};               // autotuned Chebyshev degree per precision (0 = not yet)
@@ -143,7 +150,7 @@ struct qcad_mesh_s {
   long long lin_ver[2] = {0, 0};
   long long lam_ver[2] = {-1, -1};
   double lam_cache[2] = {0.0, 0.0};
-  qcad::Profiler prof;
+  qcad::Profiler prof;                     // thread-safe: concurrent calls may record
   // Schrodinger workspace
   qcad::DevBuf s_mx, s_kx, s_my, s_ky, s_mzx, s_mzy, s_kzz, s_cV, s_dinv, s_interior, s_blocks, s_gram;
   ~qcad_mesh_s();

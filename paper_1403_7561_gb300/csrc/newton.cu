@@ -203,7 +203,8 @@ static double cheb_alpha(int degree) {
 // Solves J x = b (b, dinv, c already in the precision's buffers) to ||r|| <= rtol ||b||
 // with Jacobi (degree 1) or Chebyshev-Jacobi (degree >= 2) preconditioning.
 template <class T>
-static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1) {
+static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree, double lam_factor,
+                              int fresh_steps) {
   PcgVecs<T> v = ensure_pcg<T>(m);
   PcgGraph& G = Prec<T>::graph(m);
   degree = std::max(1, std::min(degree, 16));
@@ -216,10 +217,11 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
   double lam = 0.0;
   const int pi = sizeof(T) == 8 ? 0 : 1;
   if (degree >= 2) {
-    if (m->lam_ver[pi] == m->lin_ver[pi]) {
+    if (fresh_steps == 0 && m->lam_ver[pi] == m->lin_ver[pi]) {
       lam = m->lam_cache[pi];
     } else {
-      lam = lambda_max<T>(m, 12);
+      // the cache keeps the estimate scaled so that the default margin reproduces this bound
+      lam = lambda_max<T>(m, fresh_steps > 0 ? fresh_steps : 12) * (lam_factor / 1.1);
       m->lam_cache[pi] = lam;
       m->lam_ver[pi] = m->lin_ver[pi];
     }
@@ -231,7 +233,7 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
   h->degree = degree;
   if (degree >= 2) {
     // Chebyshev interval [b/alpha, b] of D^-1 J with b = 1.1 lambda_max
-    const double bmax = 1.1 * (lam > 0 ? lam : 2.0), amin = bmax / cheb_alpha(degree);
+    const double bmax = 1.1 * (lam > 0 ? lam : 2.0), amin = bmax / cheb_alpha(degree);  // lam carries the margin
     h->theta = 0.5 * (bmax + amin);
     h->delta = 0.5 * (bmax - amin);
   } else {
@@ -262,8 +264,7 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
           Profiler::Pair& p = G.events[it * per_it + q];
           float ms = 0.f;
           if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            m->prof.ms[p.cls] += ms;
-            m->prof.launches[p.cls] += 1;
+            m->prof.add(p.cls, ms);
           } else {
             cudaGetLastError();
           }
@@ -283,11 +284,26 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
 
 // Chebyshev degree autotuner: times complete solves of the current system for each
 // candidate degree and keeps the fastest for the mesh and precision (once per mesh).
+// PCG with the given preconditioner degree. A Chebyshev breakdown (the polynomial is not
+// positive on the whole spectrum when the power iteration underestimates its top) is retried
+// once with a 60-step estimate and a 30 % margin, then with Jacobi.
+template <class T>
+static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1) {
+  PcgResult r = pcg_run_once<T>(m, rtol, maxit, degree, 1.1, 0);
+  if (!r.nonfinite || degree < 2) return r;
+  if (debug_on()) std::fprintf(stderr, "[qcad] chebyshev breakdown at degree %d: re-estimating\n", degree);
+  r = pcg_run_once<T>(m, rtol, maxit, degree, 1.3, 60);
+  if (!r.nonfinite) return r;
+  return pcg_run_once<T>(m, rtol, maxit, 1, 1.1, 0);
+}
+
 template <class T>
 static int choose_degree(qcad_mesh_s* m, double rtol, int maxit) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   if (m->cheb_auto[prec] > 0) return m->cheb_auto[prec];
-  const int cand[5] = {1, 2, 3, 4, 6};
+  // odd degrees only: their polynomial stays positive above the estimated top of the spectrum,
+  // so an underestimated lambda_max slows the solve but cannot make it break down
+  const int cand[4] = {1, 3, 5, 7};
   int best = 1;
   double best_t = 1e300;
   for (int d : cand) {
@@ -446,6 +462,9 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
     const double nR = std::sqrt(R.r2);
     double eta = R0 > 0 ? std::min(1e-2, nR / R0) : 1e-2;
     eta = std::max(eta, floor_eta);
+    // no tighter than the tolerance needs: the linear part of the next residual, eta ||R||_2,
+    // at a tenth of tol_R bounds its max norm below tol_R
+    if (nR > 0) eta = std::max(eta, std::min(1e-2, 0.1 * o->newton_tol_R / nR));
     if (degree <= 0) degree = choose_degree<T>(m, eta, maxk);
     PcgResult pr = pcg_run<T>(m, eta, maxk, degree);
     kry += pr.iters;
@@ -631,8 +650,11 @@ static void adjoint_solve(qcad_mesh_s* m, int prec, const double* g, double* lam
   CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double g2 = m->h_small[20];
+  double r2 = g2;
   for (int rf = 0; rf < 12; ++rf) {
-    PcgResult pr = pcg_run<float>(m, 1e-5, maxk, std::max(1, m->cheb_auto[1]));
+    // each correction needs only to bring the residual to a tenth of the 1e-13 target
+    const double rt = std::max(1e-5, std::min(1e-2, 1e-14 * std::sqrt(g2 / std::max(r2, 1e-300))));
+    PcgResult pr = pcg_run<float>(m, rt, maxk, std::max(1, m->cheb_auto[1]));
     if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint refinement produced a non-finite value");
     launch_axpy<float>(n, 1.0, w.x, lam, s);
     ApplyArgs<double> a{};
@@ -645,7 +667,8 @@ static void adjoint_solve(qcad_mesh_s* m, int prec, const double* g, double* lam
     launch_dot<double>(n, r, r, d2, s);
     CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (m->h_small[20] <= 1e-26 * g2) break;
+    r2 = m->h_small[20];
+    if (r2 <= 1e-26 * g2) break;
   }
 }
 
@@ -897,6 +920,7 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
       any = true;
       const double nR = std::sqrt(R[i].r2);
       rtol[i] = std::max(1e-5, R0[i] > 0 ? std::min(1e-2, nR / R0[i]) : 1e-2);
+      if (nR > 0) rtol[i] = std::max(rtol[i], std::min(1e-2, 0.1 * o->newton_tol_R / nR));
     }
     if (!any) break;
     batch_pcg(B, rtol, maxk, iters, nonf);

@@ -22,8 +22,8 @@ void launch_potential(const SubdomainMap& sm, const double* phi, double V0, cons
                       const double* hz, T* cV, double* vmin, cudaStream_t s);
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s);
-// G1 = A^T B1 and, if B2 is not null, G2 = A^T B2 (p x q each, row-major, FP64, overwritten).
-// part: device scratch of gram_part_doubles(p, q) doubles. p <= 64, q <= 64.
+// G1 = A^T B1 and, if B2 is not null, G2 = A^T B2 (p x p each, row-major, FP64, overwritten;
+// q must equal p). part: device scratch of gram_part_doubles(p, p) doubles. p <= 64.
 template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
                  double* G1, double* G2, double* part, cudaStream_t s);

@@ -176,3 +176,28 @@ def test_dot_charge_autograd(q, dqd):
     fd = (f(V.detach(), theta.detach() + ht * d) - f(V.detach(), theta.detach() - ht * d)) / (2 * ht)
     ad = torch.dot(theta.grad, d).item()
     assert abs(ad - fd) <= 1e-5 * max(abs(fd), abs(ad))
+
+
+def test_adjoint_and_eigs_concurrently(q, dqd):
+    # qcad_adjoint_eigs (eigensolve on a second stream and host thread) gives the results of the
+    # two calls made one after the other
+    dev, P, phi = dqd
+    theta = np.array(W.interface_fixed_charge(dev, seed=5))
+    m = q.qcad_mesh_create(dev)
+    th = dt(theta)
+    phig = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), phig, fixed_charge=th)
+    opts = q.make_opts(precision=1)
+    dq1 = torch.empty(m.n_dots * m.n_elems, dtype=torch.float64, device="cuda")
+    V1 = np.array(q.qcad_adjoint(m, dev["bias"], phig, opts, fixed_charge=th, dN_dq=dq1))
+    E1, _ = q.qcad_schrodinger_eigs(m, dev["bias"], phig, nev=6, tol=1e-9)
+    for _ in range(2):
+        dq2 = torch.empty_like(dq1)
+        V2, E2, rep = q.qcad_adjoint_eigs(m, dev["bias"], phig, opts, fixed_charge=th, dN_dq=dq2, nev=6, tol=1e-9)
+        assert rep["status"] == "OK"
+        assert np.max(np.abs(np.array(V2) - V1)) <= 1e-12 * np.max(np.abs(V1))
+        assert torch.max(torch.abs(dq2 - dq1)).item() <= 1e-12 * torch.max(torch.abs(dq1)).item()
+        assert np.max(np.abs(np.array(E2) - E1) / np.abs(E1)) <= 1e-10
+    # errors of either half surface as the call's status
+    with pytest.raises(q.QcadError):
+        q.qcad_adjoint_eigs(m, dev["bias"], phig, opts, nev=17)
