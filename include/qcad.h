@@ -267,8 +267,8 @@ qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches
  * and packed f32x2 arithmetic (FP32 only; FP64 runs variant 0), 2
  * plane-factorized kernel with one node row per thread, 3 plane-factorized
  * with two node rows per thread. Shapes a variant does not support are
- * clamped to the nearest supported one (FP64 plane-factorized: at most 16
- * warps, 8 with two rows). Defaults: variant 3, 8 warps, z chunk 16.
+ * clamped to the nearest supported one (FP64 plane-factorized: at most 8
+ * warps). Defaults: variant 3, 8 warps, z chunk 16.
  * qcad_autotune times the Jacobian apply of the given precision (0 FP64,
  * 1 FP32) over variants, tile rows and z chunks on the mesh, keeps the
  * fastest for that family and returns it (outputs may be NULL); best_ms is

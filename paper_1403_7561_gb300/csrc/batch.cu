@@ -44,7 +44,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* var
   if (precision == 1)
     for (int r : {4, 8, 16}) shapes.push_back({1, r});
   for (int r : {4, 8, 16, 32})
-    if (precision == 1 || r <= 16) shapes.push_back({2, r});
+    if (precision == 1 || r <= 8) shapes.push_back({2, r});
   for (int r : {4, 8, 16})
     if (precision == 1 || r <= 8) shapes.push_back({3, r});
   for (const auto& sh : shapes) {

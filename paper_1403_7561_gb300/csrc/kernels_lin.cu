@@ -29,7 +29,7 @@ static void lin_launch(const Grid<T>& g, const Op& op, int kchunk, cudaStream_t 
   note_launch(), lin_march_kernel<T, BY, R, Op><<<grid, dim3(32, BY), S::dyn_bytes, s>>>(g, op, kchunk);
 }
 
-// Supported (warps, rows per thread): FP32 4/8/16/32 x 1 and 4/8/16 x 2; FP64 4/8/16 x 1 and
+// Supported (warps, rows per thread): FP32 4/8/16/32 x 1 and 4/8/16 x 2; FP64 4/8 x 1 and
 // 4/8 x 2 (shared memory). Other requests are clamped to the nearest supported shape.
 template <class T, class Op>
 static void run_lin(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s) {
@@ -52,7 +52,6 @@ static void run_lin(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t 
       else lin_launch<T, 8, 2>(g, op, kc, s);
     } else {
       if (cfg.by == 4) lin_launch<T, 4, 1>(g, op, kc, s);
-      else if (cfg.by >= 16) lin_launch<T, 16, 1>(g, op, kc, s);
       else lin_launch<T, 8, 1>(g, op, kc, s);
     }
   }
@@ -183,8 +182,7 @@ int lin_blocks_per_sm(int precision, int by, int rows) {
                                                              : lin_occupancy<float, 8, 1>();
   }
   if (rows == 2) return by == 4 ? lin_occupancy<double, 4, 2>() : lin_occupancy<double, 8, 2>();
-  return by == 4 ? lin_occupancy<double, 4, 1>() : by >= 16 ? lin_occupancy<double, 16, 1>()
-                                                            : lin_occupancy<double, 8, 1>();
+  return by == 4 ? lin_occupancy<double, 4, 1>() : lin_occupancy<double, 8, 1>();
 }
 
 }  // namespace qcad

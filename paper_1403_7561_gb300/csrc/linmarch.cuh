@@ -75,15 +75,26 @@ __device__ __forceinline__ void lin_lds_c8<double>(const uint4* p, double* c) {
   }
 }
 
+// Packed row-exchange values (one shared access per pair or quadruple).
+template <class T>
+struct alignas(2 * sizeof(T)) LinV2 {
+  T x, y;
+};
+template <class T>
+struct alignas(16) LinV4 {
+  T x, y, z, w;
+};
+
 // Dynamic shared memory: the row-exchange buffers (two parities of X, the upper-row
-// gather and the stiffness z stage), then NST coefficient stages.
+// gather and the stiffness z stage), the chunk's plane tables, three planes of raw inputs,
+// then NST coefficient stages.
 template <class T, int BY, int R>
 struct LinShape {
   static constexpr int TR = BY * R;                  // node rows of a tile (incl. two halo rows)
   static constexpr int NCH = (8 * sizeof(T)) / 16;   // 16-byte chunks of one element's coefficients
   static constexpr int NST = 3;                      // coefficient stages in flight
   static constexpr int ZMAX = 128;                   // longest z chunk (plane tables held in shared memory)
-  static constexpr size_t xch_bytes = (size_t)2 * (2 + 2 + 6) * BY * 32 * sizeof(T);
+  static constexpr size_t xch_bytes = (size_t)2 * BY * 32 * (2 * sizeof(LinV2<T>) + 2 * sizeof(LinV4<T>));
   static constexpr size_t zt_bytes = (size_t)(ZMAX + 1) * 12 * sizeof(T);
   static constexpr size_t vst_bytes = (size_t)3 * 2 * TR * 32 * sizeof(T);  // 3 planes x 2 raw inputs
   static constexpr size_t dyn_bytes = xch_bytes + zt_bytes + vst_bytes + (size_t)NST * TR * NCH * 32 * 16;
@@ -113,11 +124,11 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
   Op op = op_in;
   op.set_vec(bz / nch);
   // [relative plane parity][...][BY][32]: X (qx = 0, 1) of each warp's first row; upper-row
-  // gather (qx = 0, 1) of each warp's last row; stiffness z stage (3 fields) of the first and
-  // of the last row
-  T(*xch_x)[2][BY][32] = reinterpret_cast<T(*)[2][BY][32]>(dyn);
-  T(*xch_y)[2][BY][32] = xch_x + 2;
-  T(*xch_s)[6][BY][32] = reinterpret_cast<T(*)[6][BY][32]>(xch_y + 2);
+  // gather (qx = 0, 1) of each warp's last row; stiffness z stage (3 fields + pad) of the first
+  // and of the last row
+  LinV2<T>(*xch_x)[BY][32] = reinterpret_cast<LinV2<T>(*)[BY][32]>(dyn);
+  LinV2<T>(*xch_y)[BY][32] = xch_x + 2;
+  LinV4<T>(*xch_s)[2][BY][32] = reinterpret_cast<LinV4<T>(*)[2][BY][32]>(xch_y + 2);
   T* zts = reinterpret_cast<T*>(dyn + S::xch_bytes);  // plane tables of planes k0 .. k1-1
   T* vst = reinterpret_cast<T*>(dyn + S::xch_bytes + S::zt_bytes);  // [3 planes][2 inputs][TR][32]
   uint4* cst = reinterpret_cast<uint4*>(dyn + S::xch_bytes + S::zt_bytes + S::vst_bytes);
@@ -232,17 +243,14 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
     }
     for (int q = ty * 32 + lane; q < 12 * (k1 - k0); q += 32 * BY) zts[q] = g.zt[12 * k0 + q];
     // the stiffness buffer of parity 1: the first march step writes parity 0
-    T(*pro)[BY][32] = xch_s[1];
-    pro[0][ty][lane] = X0[0][0];
-    pro[1][ty][lane] = X0[0][1];
-    pro[2][ty][lane] = X1[0][0];
-    pro[3][ty][lane] = X1[0][1];
-    pro[4][ty][lane] = X2[0][0];
-    pro[5][ty][lane] = X2[0][1];
+    LinV4<T>(*pro)[BY][32] = xch_s[1];
+    pro[0][ty][lane] = LinV4<T>{X0[0][0], X0[0][1], X1[0][0], X1[0][1]};
+    pro[1][ty][lane] = LinV4<T>{X2[0][0], X2[0][1], T(0), T(0)};
     __syncthreads();
-    const T A0[2] = {pro[0][tyu][lane], pro[1][tyu][lane]};
-    const T A1[2] = {pro[2][tyu][lane], pro[3][tyu][lane]};
-    const T A2[2] = {pro[4][tyu][lane], pro[5][tyu][lane]};
+    const LinV4<T> p0 = pro[0][tyu][lane], p1 = pro[1][tyu][lane];
+    const T A0[2] = {p0.x, p0.y};
+    const T A1[2] = {p0.z, p0.w};
+    const T A2[2] = {p1.x, p1.y};
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       uinterp(X0[r], r + 1 < R ? X0[r + 1 < R ? r + 1 : r] : A0, Um[r]);
@@ -283,8 +291,7 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
     T Xq[R][2];
 #pragma unroll
     for (int r = 0; r < R; ++r) xinterp(vq[r], Xq[r]);
-    xch_x[P][0][ty][lane] = Xq[0][0];
-    xch_x[P][1][ty][lane] = Xq[0][1];
+    xch_x[P][ty][lane] = LinV2<T>{Xq[0][0], Xq[0][1]};
     // element layer k: the lower corners feed plane k, the upper ones are carried to k+1
     // (the wait also completes the raw inputs of plane k+3)
     lin_cp_wait<2>();
@@ -307,10 +314,20 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       Yhi[r][0] = B * W[0] + A * W[2];
       Yhi[r][1] = B * W[1] + A * W[3];
     }
-    xch_y[P][0][ty][lane] = Yhi[R - 1][0];
-    xch_y[P][1][ty][lane] = Yhi[R - 1][1];
+    xch_y[P][ty][lane] = LinV2<T>{Yhi[R - 1][0], Yhi[R - 1][1]};
     // stiffness, z stage
-    const T* z = zts + 12 * (k - k0);
+    T z[12];
+    {
+      const LinV4<T>* zp = reinterpret_cast<const LinV4<T>*>(zts + 12 * (k - k0));
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        const LinV4<T> t4 = zp[h];
+        z[4 * h] = t4.x;
+        z[4 * h + 1] = t4.y;
+        z[4 * h + 2] = t4.z;
+        z[4 * h + 3] = t4.w;
+      }
+    }
     T ax[R], ay[R], az[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -318,21 +335,17 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
       ay[r] = z[3] * vm[r] + z[4] * vc[r] + z[5] * vp[r];
       az[r] = z[6] * vm[r] + z[7] * vc[r] + z[8] * vp[r];
     }
-    xch_s[P][0][ty][lane] = ax[0];
-    xch_s[P][1][ty][lane] = ay[0];
-    xch_s[P][2][ty][lane] = az[0];
-    if (R > 1) {
-      xch_s[P][3][ty][lane] = ax[R - 1];
-      xch_s[P][4][ty][lane] = ay[R - 1];
-      xch_s[P][5][ty][lane] = az[R - 1];
-    }
+    xch_s[P][0][ty][lane] = LinV4<T>{ax[0], ay[0], az[0], T(0)};
+    if (R > 1) xch_s[P][1][ty][lane] = LinV4<T>{ax[R - 1], ay[R - 1], az[R - 1], T(0)};
     __syncthreads();
     // neighbours across warps: the row above the last row, the row below the first row
-    constexpr int LAST = R > 1 ? 3 : 0;
-    const T Xa[2] = {xch_x[P][0][tyu][lane], xch_x[P][1][tyu][lane]};
-    const T Yb[2] = {xch_y[P][0][tyd][lane], xch_y[P][1][tyd][lane]};
-    const T sa[3] = {xch_s[P][0][tyu][lane], xch_s[P][1][tyu][lane], xch_s[P][2][tyu][lane]};
-    const T sb[3] = {xch_s[P][LAST][tyd][lane], xch_s[P][LAST + 1][tyd][lane], xch_s[P][LAST + 2][tyd][lane]};
+    constexpr int LAST = R > 1 ? 1 : 0;
+    const LinV2<T> xa2 = xch_x[P][tyu][lane], yb2 = xch_y[P][tyd][lane];
+    const LinV4<T> sa4 = xch_s[P][0][tyu][lane], sb4 = xch_s[P][LAST][tyd][lane];
+    const T Xa[2] = {xa2.x, xa2.y};
+    const T Yb[2] = {yb2.x, yb2.y};
+    const T sa[3] = {sa4.x, sa4.y, sa4.z};
+    const T sb[3] = {sb4.x, sb4.y, sb4.z};
     const bool pdir = dov && ((g.dir_bottom && k == 0) || (g.dir_boundary && (k == 0 || k == g.nz)));
     const bool ptop = k == g.nz;
 #pragma unroll

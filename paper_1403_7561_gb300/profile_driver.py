@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--workload", default="dqd_128x128x96_4K")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--launch", default=None, help="variant,tile_rows,z_chunk instead of the autotuner")
     a = ap.parse_args()
     import torch
 
@@ -42,7 +43,11 @@ def main():
     m = q.qcad_mesh_create(dev)
     phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
     if a.mode in ("step", "solve"):
-        q.qcad_autotune(m, bias, precision=1)
+        if a.launch:
+            v, r, c = (int(x) for x in a.launch.split(","))
+            q.qcad_set_launch(m, 2, v, r, c)
+        else:
+            q.qcad_autotune(m, bias, precision=1)
         opts = q.make_opts(precision=1, cheb_degree=0)
     if a.mode == "solve":
         rep = q.qcad_poisson_solve(m, bias, opts, phi)
