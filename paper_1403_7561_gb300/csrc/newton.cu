@@ -430,10 +430,11 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
   qcad_status st = QCAD_OK;
   int degree = o->cheb_degree > 0 ? o->cheb_degree : m->cheb_auto[prec];
   if (!o->warm_start) {
-    // Laplace initial guess with the contact values (rho = 0)
+    // Laplace initial guess with the contact values (rho = 0), solved to 1e-3: it only starts
+    // the Newton iteration, whose first step replaces it by the nonlinear correction
     eval_residual(m, P, pa, theta, 1, prec, nullptr);
-    if (degree <= 0) degree = choose_degree<T>(m, prec == 0 ? 1e-10 : 1e-6, maxk);
-    PcgResult pr = pcg_run<T>(m, prec == 0 ? 1e-10 : 1e-6, maxk, degree);
+    if (degree <= 0) degree = choose_degree<T>(m, 1e-3, maxk);
+    PcgResult pr = pcg_run<T>(m, 1e-3, maxk, degree);
     kry += pr.iters;
     if (debug_on()) std::fprintf(stderr, "[qcad] laplace pcg iters %d conv %d\n", pr.iters, (int)pr.converged);
     if (pr.nonfinite) {
