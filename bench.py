@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--sequential", action="store_true",
                     help="run the adjoint and the eigensolve one after the other (per-kernel profiles)")
+    ap.add_argument("--cheb-degree", type=int, default=0,
+                    help="Chebyshev degree of the Krylov solves (0: the mesh's autotuner chooses)")
     ap.add_argument("--launch", default=None,
                     help="variant,tile_rows,z_chunk of the FP32 operators instead of the autotuner's choice "
                          "(profiling runs, whose timings the profiler distorts)")
@@ -149,6 +151,13 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# DRAM bytes (read + write) per launch of a kernel class from one ncu capture, keyed by the
+# workload and the launch shape (variant, tile rows, z chunk) it was taken with; see
+# profiles/apply32_dqd_128x128x96_4K.md for the command. Valid for the kernel source it was
+# measured on: retake it when the kernel changes.
+NCU_TRAFFIC = {("apply32", "dqd_128x128x96_4K", 3, 8, 16): 65.3e6}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -229,7 +238,7 @@ def native_arm(args):
     bias = dev["bias"]
     m = q.qcad_mesh_create(dev)
     n_nodes, n_elems = m.n_nodes, m.n_elems
-    mixed = q.make_opts(precision=1, cheb_degree=0)  # Chebyshev degree autotuned per mesh
+    mixed = q.make_opts(precision=1, cheb_degree=args.cheb_degree)  # 0: degree autotuned per mesh
     phi = torch.zeros(n_nodes, dtype=torch.float64, device="cuda")
     evecs = torch.empty(NEV, m.n_sub_dof, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -360,9 +369,12 @@ def native_arm(args):
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas x%d" % world,
                        "apply_launch": {"variant": tune32[0], "tile_rows": tune32[1], "z_chunk": tune32[2],
                                         "chosen_by": "--launch" if args.launch else "autotuner"},
+                       "cheb_degree": args.cheb_degree or q.qcad_launch_info(m, 2)[3],
                        "adjoint_eigensolve": "sequential" if args.sequential else "concurrent (two streams)"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "traffic": NCU_TRAFFIC.get((dom, args.workload) + tuple(tune32[:3])),
+                         "traffic_unit": "bytes per launch (ncu dram read + write, cold cache)",
                          "peak_kind": peak_kind, "launches": nl, "avg_ms": ms / nl if nl else None,
                          "timed_launches": "inside the Newton solves of the timed steps (no concurrent work)",
                          "share_of_profiled_time": share},

@@ -274,6 +274,11 @@ qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches
  * fastest for that family and returns it (outputs may be NULL); best_ms is
  * its time per apply. */
 qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_rows, int z_chunk);
+/* The current launch shape of a family (as qcad_set_launch) and, for families 1 (FP64) and
+ * 2 (FP32), the Chebyshev degree the mesh's autotuner chose (0: not tuned yet). Outputs may be
+ * NULL. */
+qcad_status qcad_launch_info(qcad_mesh_t m, int family, int* variant, int* tile_rows, int* z_chunk,
+                             int* cheb_degree);
 qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* variant, int* tile_rows,
                           int* z_chunk, float* best_ms);
 

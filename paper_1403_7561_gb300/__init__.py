@@ -101,6 +101,8 @@ _sigs = {
     "qcad_adjoint": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), _P, _P, _D, _P],
     "qcad_schrodinger_apply": [_P, C.POINTER(Bias), _P, _D, C.c_int, _P, _P, _P, C.c_int],
     "qcad_schrodinger_eigs": [_P, C.POINTER(Bias), _P, C.c_int, _D, C.c_double, _D, _P, C.POINTER(SolveReport)],
+    "qcad_launch_info": [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                         C.POINTER(C.c_int)],
     "qcad_adjoint_eigs": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), _P, _P, _D, _P, C.c_int, _D, C.c_double, _D,
                           _P, C.POINTER(SolveReport)],
     "qcad_poisson_solve_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P),
@@ -427,6 +429,13 @@ def qcad_launch_count():
     n = C.c_int64()
     _check(_lib.qcad_launch_count(C.byref(n)))
     return n.value
+
+
+def qcad_launch_info(mesh: Mesh, family: int):
+    """(variant, tile_rows, z_chunk, autotuned Chebyshev degree or 0) of a kernel family."""
+    v, r, z, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.qcad_launch_info(mesh.handle, int(family), C.byref(v), C.byref(r), C.byref(z), C.byref(d)))
+    return v.value, r.value, z.value, d.value
 
 
 def qcad_autotune(mesh: Mesh, bias: dict, precision=1):

@@ -272,6 +272,20 @@ qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_row
   });
 }
 
+qcad_status qcad_launch_info(qcad_mesh_t m, int family, int* variant, int* tile_rows, int* z_chunk,
+                             int* cheb_degree) {
+  return guarded([&] {
+    if (!m) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null mesh");
+    if (family < 0 || family > 2) throw qcad::Error(QCAD_ERR_INVALID_ARG, "family must be 0, 1 or 2");
+    const qcad::LaunchCfg& c = family == 0 ? m->cfg_res : family == 1 ? m->cfg64 : m->cfg32;
+    if (variant) *variant = c.variant;
+    if (tile_rows) *tile_rows = c.by;
+    if (z_chunk) *z_chunk = c.kchunk;
+    if (cheb_degree) *cheb_degree = family == 0 ? 0 : m->cheb_auto[family == 1 ? 0 : 1];
+    return QCAD_OK;
+  });
+}
+
 qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* variant, int* tile_rows,
                           int* z_chunk, float* best_ms) {
   return guarded([&] {
