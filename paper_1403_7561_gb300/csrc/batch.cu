@@ -116,8 +116,8 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* var
 qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                      double* const* phis, qcad_solve_report* reps);
 
-// z-chunk of the batched FP32 apply (8-row tiles, one node per thread) for one mesh: the
-// fastest of a few lengths, timed on the mesh's own grid.
+// z-chunk of the batched FP32 apply (plane-factorized, 8 warps, two rows per thread) for one
+// mesh: the fastest of a few lengths, timed on the mesh's own grid.
 static int tune_batch_kchunk(qcad_mesh_s* m) {
   cudaStream_t s = m->stream;
   const long long n = m->n_nodes;
@@ -136,7 +136,7 @@ static int tune_batch_kchunk(qcad_mesh_s* m) {
     LaunchCfg cfg;
     cfg.by = 8;
     cfg.kchunk = ch;
-    cfg.variant = 0;
+    cfg.variant = 3;
     ApplyArgs<float> a{};
     a.v = v.as<float>();
     a.y = y.as<float>();

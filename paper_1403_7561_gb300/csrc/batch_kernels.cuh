@@ -53,6 +53,43 @@ __global__ void batch_status_kernel(const BatchVecEntry* tab, int n_inst, int* s
   }
 }
 
+template <int BY>
+__global__ void __launch_bounds__(QCAD_BX * BY) batch_residual_kernel(const BatchResEntry* tab, int n_inst) {
+  const int b = blockIdx.x;
+  const BatchResEntry& e = tab[batch_find(tab, n_inst, b)];
+  const int local = b - e.begin;
+  const int bx = local % e.tiles_x;
+  const int by = (local / e.tiles_x) % e.tiles_y;
+  const int bz = local / (e.tiles_x * e.tiles_y);
+  ResidualOp op = {};
+  op.a = e.a;
+  march_body<double, BY, ResidualOp>(e.g, op, e.kchunk, bx, by, bz);
+}
+
+__global__ void batch_stats_kernel(const BatchResEntry* tab, int n_inst, int mode, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
+    double* st = tab[i].a.stats;
+    if (mode == 0) {
+      st[0] = 0.0;
+      st[1] = 0.0;
+    } else if (mode == 1) {
+      st[8] = 0.0;
+    } else {
+      out[3 * i + 0] = st[0];
+      out[3 * i + 1] = st[1];
+      out[3 * i + 2] = st[8];
+    }
+  }
+}
+
+void launch_batch_residual(const BatchResEntry* tab, int n_inst, int total_blocks, cudaStream_t s) {
+  note_launch(), batch_residual_kernel<8><<<total_blocks, dim3(QCAD_BX, 8), 0, s>>>(tab, n_inst);
+}
+
+void launch_batch_stats(const BatchResEntry* tab, int n_inst, int mode, double* out, cudaStream_t s) {
+  note_launch(), batch_stats_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(tab, n_inst, mode, out);
+}
+
 void launch_batch_pcg_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, int by, cudaStream_t s) {
   if (by == 16)
     note_launch(), batch_pcg_apply_kernel<16><<<total_blocks, dim3(QCAD_BX, 16), 0, s>>>(tab, n_inst);

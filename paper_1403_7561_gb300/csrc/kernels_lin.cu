@@ -157,6 +157,49 @@ void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg,
 template void launch_hm_apply_lin<float>(const Grid<float>&, const HmArgs<float>&, LaunchCfg, cudaStream_t);
 template void launch_hm_apply_lin<double>(const Grid<double>&, const HmArgs<double>&, LaunchCfg, cudaStream_t);
 
+// Batched PCG apply: a work table maps each block to (instance, tile) of instances of different
+// sizes; plane-factorized march with 8 warps and two rows per thread.
+__device__ __forceinline__ int lin_batch_find(const BatchApplyEntry* tab, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].begin <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256, (lin_min_blocks<float, 8, 2>()))
+    batch_lin_apply_kernel(const BatchApplyEntry* tab, int n_inst) {
+  extern __shared__ __align__(16) unsigned char lin_dyn[];
+  const int b = blockIdx.x;
+  const BatchApplyEntry& e = tab[lin_batch_find(tab, n_inst, b)];
+  const int local = b - e.begin;
+  const int bx = local % e.tiles_x;
+  const int by = (local / e.tiles_x) % e.tiles_y;
+  const int bz = local / (e.tiles_x * e.tiles_y);
+  PcgApplyOp<float> op = {};
+  op.v = e.v;
+  op.sc = e.sc;
+  lin_body<float, 8, 2, PcgApplyOp<float>>(e.g, op, e.kchunk, bx, by, bz, lin_dyn);
+}
+
+void launch_batch_lin_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, cudaStream_t s) {
+  using S = LinShape<float, 8, 2>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(batch_lin_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::dyn_bytes) == cudaSuccess &&
+        cudaFuncSetAttribute(batch_lin_apply_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) ==
+            cudaSuccess)
+      attr_set[dev] = true;
+  }
+  note_launch(), batch_lin_apply_kernel<<<total_blocks, dim3(32, 8), S::dyn_bytes, s>>>(tab, n_inst);
+}
+
 // Resident blocks per SM of the plane-factorized apply (0 if the query fails).
 template <class T, int BY, int R>
 static int lin_occupancy() {

@@ -750,23 +750,28 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
 
 // ---------------------------------------------------------------------------
 // Batched form: n independent meshes (uneven sizes, own biases) solved by a
-// lockstep Newton iteration whose linear solves advance all instances with one
-// apply launch and one update launch per PCG iteration (work tables map blocks
-// to instance tiles), a status gather per chunk, and the chunk of iterations
-// captured once as a CUDA graph. Instances converge and drop out
-// independently through their own device-resident scalars. FP32 Krylov,
-// Jacobi preconditioning, FP64 residual and Newton update per instance.
+// lockstep Newton iteration. Every device pass covers all instances at once:
+// the FP64 residual (with the FP32 linearization) is one launch over a work
+// table of (instance, tile), each PCG iteration is one apply launch and one
+// update launch over work tables (chunks of 8 iterations captured once as a
+// CUDA graph, instances dropping out on their own device-resident scalars),
+// and the line search evaluates the trial points of all instances still
+// searching in one residual launch. FP32 Krylov with Jacobi preconditioning,
+// FP64 residual and Newton update per instance.
 struct BatchCtx {
   int n = 0;
   cudaStream_t s = nullptr;
   std::vector<qcad_mesh_s*> ms;
-  DevBuf tab_a, tab_v, status;
-  int total_a = 0, total_v = 0, by = 8;
+  std::vector<Phys> P;
+  DevBuf tab_a, tab_v, tab_r, status, rstats;
+  int total_a = 0, total_v = 0;
   int* h_status = nullptr;
+  double* h_rstats = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~BatchCtx() {
     if (exec) cudaGraphExecDestroy(exec);
     if (h_status) cudaFreeHost(h_status);
+    if (h_rstats) cudaFreeHost(h_rstats);
   }
 };
 
@@ -781,9 +786,9 @@ static void batch_setup(BatchCtx& B) {
     a.g = m->g32.g;
     a.v = v;
     a.sc = m->scal.as<PcgScalars>();
-    a.kchunk = std::max(2, m->batch_kchunk > 0 ? m->batch_kchunk : m->cfg32.kchunk);
-    a.tiles_x = (m->g32.g.nxn + QCAD_BX - 3) / (QCAD_BX - 2);
-    a.tiles_y = (m->g32.g.nyn + B.by - 3) / (B.by - 2);
+    a.kchunk = std::min(128, std::max(2, m->batch_kchunk > 0 ? m->batch_kchunk : 16));
+    a.tiles_x = (m->g32.g.nxn + 29) / 30;  // plane-factorized tiles: 30 x 14 interior nodes
+    a.tiles_y = (m->g32.g.nyn + 13) / 14;
     a.begin = ba;
     ba += a.tiles_x * a.tiles_y * ((m->g32.g.nzn + a.kchunk - 1) / a.kchunk);
     BatchVecEntry& e = tv[i];
@@ -798,15 +803,18 @@ static void batch_setup(BatchCtx& B) {
   B.total_v = bv;
   B.tab_a.ensure(ta.size() * sizeof(BatchApplyEntry) + 64);
   B.tab_v.ensure(tv.size() * sizeof(BatchVecEntry) + 64);
+  B.tab_r.ensure((size_t)B.n * sizeof(BatchResEntry) + 64);
   B.status.ensure((size_t)4 * B.n * sizeof(int) + 64);
+  B.rstats.ensure((size_t)3 * B.n * sizeof(double) + 64);
   CK(cudaMemcpyAsync(B.tab_a.p, ta.data(), ta.size() * sizeof(BatchApplyEntry), cudaMemcpyHostToDevice, B.s));
   CK(cudaMemcpyAsync(B.tab_v.p, tv.data(), tv.size() * sizeof(BatchVecEntry), cudaMemcpyHostToDevice, B.s));
   CK(cudaMallocHost(&B.h_status, (size_t)4 * B.n * sizeof(int)));
+  CK(cudaMallocHost(&B.h_rstats, (size_t)3 * B.n * sizeof(double)));
   CK(cudaStreamSynchronize(B.s));
   const long long before = launch_count();
   CK(cudaStreamBeginCapture(B.s, cudaStreamCaptureModeThreadLocal));
   for (int it = 0; it < PCG_CHUNK; ++it) {
-    launch_batch_pcg_apply(B.tab_a.as<BatchApplyEntry>(), B.n, B.total_a, B.by, B.s);
+    launch_batch_lin_apply(B.tab_a.as<BatchApplyEntry>(), B.n, B.total_a, B.s);
     launch_batch_pcg_update(B.tab_v.as<BatchVecEntry>(), B.n, B.total_v, B.s);
   }
   launch_batch_status(B.tab_v.as<BatchVecEntry>(), B.n, B.status.as<int>(), B.s);
@@ -816,6 +824,58 @@ static void batch_setup(BatchCtx& B) {
   cudaError_t e = cudaGraphInstantiate(&B.exec, graph, 0);
   cudaGraphDestroy(graph);
   CK(e);
+}
+
+// FP64 residuals of the instances `idx` at phi[i] in one launch (mixed linearization written
+// for each); R[i] = {max |R|, sum R^2} and, when `trial`, step[i] = the trial slot (max |alpha
+// delta| written by the trial kernels before).
+static void batch_residual(BatchCtx& B, const std::vector<int>& idx, const std::vector<double*>& phi, int linear,
+                           std::vector<ResStats>& R, std::vector<double>* step) {
+  if (idx.empty()) return;
+  std::vector<BatchResEntry> tr(idx.size());
+  int total = 0;
+  for (size_t q = 0; q < idx.size(); ++q) {
+    const int i = idx[q];
+    qcad_mesh_s* m = B.ms[i];
+    PcgVecs<float> v = ensure_pcg<float>(m);
+    BatchResEntry& e = tr[q];
+    e = BatchResEntry{};
+    e.g = m->g64.g;
+    ResidualArgs& a = e.a;
+    a.phi = phi[i];
+    a.R = m->R.as<double>();
+    a.c32 = const_cast<float*>(v.c);
+    a.dinv32 = const_cast<float*>(v.dinv);
+    a.b32 = const_cast<float*>(v.b);
+    a.layer_semi = m->d_layer_semi.as<unsigned char>();
+    a.xn = m->d_xn.as<double>();
+    a.yn = m->d_yn.as<double>();
+    a.zn = m->d_zn.as<double>();
+    a.P = B.P[i];
+    a.dots = m->dots;
+    a.linear = linear;
+    a.stats = m->stats.as<double>();
+    e.kchunk = std::max(2, m->cfg_res.kchunk);
+    e.tiles_x = (e.g.nxn + QCAD_BX - 3) / (QCAD_BX - 2);
+    e.tiles_y = (e.g.nyn + 8 - 3) / (8 - 2);
+    e.begin = total;
+    total += e.tiles_x * e.tiles_y * ((e.g.nzn + e.kchunk - 1) / e.kchunk);
+    m->lin_ver[1] += 1;  // the FP32 linearization of this mesh is rewritten
+  }
+  const int nq = (int)idx.size();
+  CK(cudaMemcpyAsync(B.tab_r.p, tr.data(), tr.size() * sizeof(BatchResEntry), cudaMemcpyHostToDevice, B.s));
+  const BatchResEntry* tab = B.tab_r.as<BatchResEntry>();
+  launch_batch_stats(tab, nq, 0, nullptr, B.s);
+  launch_batch_residual(tab, nq, total, B.s);
+  launch_batch_stats(tab, nq, 2, B.rstats.as<double>(), B.s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(B.h_rstats, B.rstats.p, (size_t)3 * nq * sizeof(double), cudaMemcpyDeviceToHost, B.s));
+  CK(cudaStreamSynchronize(B.s));
+  for (int q = 0; q < nq; ++q) {
+    R[idx[q]].rmax = B.h_rstats[3 * q];
+    R[idx[q]].r2 = B.h_rstats[3 * q + 1];
+    if (step) (*step)[idx[q]] = B.h_rstats[3 * q + 2];
+  }
 }
 
 // One batched linear solve: instance i solves its J x = b to rtol[i] (rtol[i] <= 0: skipped).
@@ -875,41 +935,48 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
   batch_setup(B);
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   const int maxn = o->max_newton > 0 ? o->max_newton : 100;
-  std::vector<Phys> P(n);
+  B.P.resize(n);
   std::vector<double*> pa(n), pb(n);
-  std::vector<ResStats> R(n);
-  std::vector<double> R0(n), step(n, 0.0), rtol(n);
-  std::vector<int> kry(n, 0), its(n, 0), conv(n, 0), bad(n, 0), iters, nonf;
+  std::vector<ResStats> R(n), Rt(n);
+  std::vector<double> R0(n), step(n, 0.0), rtol(n), alpha(n);
+  std::vector<int> kry(n, 0), its(n, 0), conv(n, 0), bad(n, 0), iters, nonf, all(n);
   for (int i = 0; i < n; ++i) {
     qcad_mesh_s* m = ms[i];
-    P[i] = make_phys(m, &bs[i]);
+    all[i] = i;
+    B.P[i] = make_phys(m, &bs[i]);
     pa[i] = m->phi_a.as<double>();
     pb[i] = m->phi_b.as<double>();
     if (o->warm_start)
       CK(cudaMemcpyAsync(pa[i], phis[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
     else
       CK(cudaMemsetAsync(pa[i], 0, m->n_nodes * sizeof(double), m->stream));
-    set_contacts(m, &bs[i], P[i], pa[i], nullptr, nullptr);
+    set_contacts(m, &bs[i], B.P[i], pa[i], nullptr, nullptr);  // synchronizes the mesh stream
   }
-  if (!o->warm_start) {
-    for (int i = 0; i < n; ++i) {
-      eval_residual(ms[i], P[i], pa[i], nullptr, 1, 1, nullptr);
-      rtol[i] = 1e-6;
+  // trial points pb = pa + alpha x for the instances `idx` (max |alpha x| into each stats slot)
+  auto trials = [&](const std::vector<int>& idx) {
+    if (idx.empty()) return;
+    for (int i : idx) {
+      qcad_mesh_s* m = ms[i];
+      CK(cudaMemsetAsync(m->stats.as<double>() + 8, 0, sizeof(double), B.s));
+      launch_newton_trial<float>(m->n_nodes, pa[i], ensure_pcg<float>(m).x, alpha[i], pb[i],
+                                 m->stats.as<double>() + 8, B.s);
     }
+  };
+  if (!o->warm_start) {
+    // Laplace initial guesses to 1e-3 (rho = 0), all instances at once
+    batch_residual(B, all, pa, 1, R, nullptr);
+    for (int i = 0; i < n; ++i) rtol[i] = 1e-3;
     batch_pcg(B, rtol, maxk, iters, nonf);
     for (int i = 0; i < n; ++i) {
-      qcad_mesh_s* m = ms[i];
       kry[i] += iters[i];
       if (nonf[i]) bad[i] = 1;
-      CK(cudaMemsetAsync(m->stats.p, 0, sizeof(double), m->stream));
-      launch_newton_trial<float>(m->n_nodes, pa[i], ensure_pcg<float>(m).x, 1.0, pb[i], m->stats.as<double>(),
-                                 m->stream);
-      CK(cudaStreamSynchronize(m->stream));
-      std::swap(pa[i], pb[i]);
+      alpha[i] = 1.0;
     }
+    trials(all);
+    for (int i = 0; i < n; ++i) std::swap(pa[i], pb[i]);
   }
+  batch_residual(B, all, pa, o->linear, R, nullptr);
   for (int i = 0; i < n; ++i) {
-    R[i] = eval_residual(ms[i], P[i], pa[i], nullptr, o->linear, 1, nullptr);
     R0[i] = std::sqrt(R[i].r2);
     if (!std::isfinite(R[i].r2)) bad[i] = 1;
   }
@@ -925,43 +992,47 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
     }
     if (!any) break;
     batch_pcg(B, rtol, maxk, iters, nonf);
+    std::vector<int> search;
     for (int i = 0; i < n; ++i) {
       if (!(rtol[i] > 0)) continue;
-      qcad_mesh_s* m = ms[i];
       kry[i] += iters[i];
       its[i] = it;
       if (nonf[i]) {
         bad[i] = 1;
         continue;
       }
-      const double nR = std::sqrt(R[i].r2);
-      double alpha = 1.0;
-      ResStats Rt{};
-      for (int ls = 0; ls <= 30; ++ls) {
-        CK(cudaMemsetAsync(m->stats.p, 0, sizeof(double), m->stream));
-        launch_newton_trial<float>(m->n_nodes, pa[i], ensure_pcg<float>(m).x, alpha, pb[i], m->stats.as<double>(),
-                                   m->stream);
-        CK(cudaMemcpyAsync(m->h_small + 4, m->stats.p, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
-        Rt = eval_residual(m, P[i], pb[i], nullptr, o->linear, 1, nullptr);
-        step[i] = m->h_small[4];
-        if (std::isfinite(Rt.r2) && std::sqrt(Rt.r2) <= (1.0 - 1e-4 * alpha) * nR) break;
-        alpha *= 0.5;
+      alpha[i] = 1.0;
+      search.push_back(i);
+    }
+    // backtracking on ||R||_2 for every searching instance at once (halving up to 30 times)
+    for (int ls = 0; ls <= 30 && !search.empty(); ++ls) {
+      trials(search);
+      batch_residual(B, search, pb, o->linear, Rt, &step);
+      std::vector<int> next;
+      for (int i : search) {
+        const double nR = std::sqrt(R[i].r2);
+        const bool ok = std::isfinite(Rt[i].r2) && std::sqrt(Rt[i].r2) <= (1.0 - 1e-4 * alpha[i]) * nR;
+        if (ok || ls == 30) {
+          std::swap(pa[i], pb[i]);
+          R[i] = Rt[i];
+          if (!std::isfinite(R[i].r2)) bad[i] = 1;
+          if (R[i].rmax < o->newton_tol_R && step[i] < o->newton_tol_dphi) conv[i] = 1;
+        } else {
+          alpha[i] *= 0.5;
+          next.push_back(i);
+        }
       }
-      std::swap(pa[i], pb[i]);
-      R[i] = Rt;
-      if (!std::isfinite(R[i].r2)) bad[i] = 1;
-      if (R[i].rmax < o->newton_tol_R && step[i] < o->newton_tol_dphi) conv[i] = 1;
+      search.swap(next);
     }
   }
   qcad_status worst = QCAD_OK;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < n; ++i) {
     qcad_mesh_s* m = ms[i];
-    CK(cudaMemcpyAsync(phis[i], pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(phis[i], pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, B.s));
     // the mesh's own buffers now hold this iterate in phi_a (keep single-mesh solves consistent)
     if (pa[i] != m->phi_a.as<double>())
-      CK(cudaMemcpyAsync(m->phi_a.p, pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+      CK(cudaMemcpyAsync(m->phi_a.p, pa[i], m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, B.s));
     if (reps) {
       reps[i].newton_iters = its[i];
       reps[i].krylov_iters_total = kry[i];
@@ -974,6 +1045,7 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
     const qcad_status st = bad[i] ? QCAD_ERR_NONFINITE : (conv[i] ? QCAD_OK : QCAD_ERR_NOT_CONVERGED);
     if (worst == QCAD_OK && st != QCAD_OK) worst = st;
   }
+  CK(cudaStreamSynchronize(B.s));
   if (worst != QCAD_OK) set_message("at least one batch instance did not converge or produced a non-finite value");
   return worst;
 }

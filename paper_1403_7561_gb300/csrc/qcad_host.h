@@ -205,7 +205,22 @@ struct BatchVecEntry {
   int blocks;
   int begin;
 };
+// Work-table entry of the batched FP64 residual (element-gather march, 8 warps).
+struct BatchResEntry {
+  Grid<double> g;
+  ResidualArgs a;
+  int kchunk;
+  int tiles_x, tiles_y;
+  int begin;
+};
 void launch_batch_pcg_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, int by, cudaStream_t s);
+// Plane-factorized batched PCG apply (8 warps, two rows per thread: tiles of 30 x 14 interior nodes).
+void launch_batch_lin_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
+void launch_batch_residual(const BatchResEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
+// Per-instance stats slots: mode 0 zeroes the residual slots (stats[0] max |R| as ordered bits,
+// stats[1] sum R^2), mode 1 zeroes the trial-step slot stats[8], mode 2 gathers the three into
+// out[3i .. 3i+2].
+void launch_batch_stats(const BatchResEntry* tab, int n_inst, int mode, double* out, cudaStream_t s);
 void launch_batch_pcg_update(const BatchVecEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
 void launch_batch_status(const BatchVecEntry* tab, int n_inst, int* status, cudaStream_t s);
 }  // namespace qcad
