@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <mutex>
@@ -134,6 +135,9 @@ struct qcad_mesh_s {
   // solver state
   qcad::PcgBufs<double> k64;
   qcad::PcgBufs<float> k32;
+  qcad::PcgBufs<float> k32x[QCAD_MAX_DOTS - 1];  // further FP32 right-hand sides (adjoint of dots 1, 2, ...)
+  qcad::DevBuf scal_x;                           // their PCG scalars
+  std::shared_ptr<void> adj_ctx;                 // cached batched-PCG context of the adjoint
   qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
   qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror
   double* h_small = nullptr;               // pinned host scratch (64 doubles)

@@ -624,130 +624,6 @@ qcad_status capacitance(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_op
   return QCAD_OK;
 }
 
-// Solve J lam = g on free rows (g zero on Dirichlet rows) in FP64, or by
-// iterative refinement around FP32 PCG in mixed precision.
-static void adjoint_solve(qcad_mesh_s* m, int prec, const double* g, double* lam, int maxk) {
-  cudaStream_t s = m->stream;
-  const long long n = m->n_nodes;
-  PcgVecs<double> v = ensure_pcg<double>(m);
-  if (prec == 0) {
-    CK(cudaMemcpyAsync(const_cast<double*>(v.b), g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    PcgResult pr = pcg_run<double>(m, 1e-13, maxk, std::max(1, m->cheb_auto[0]));
-    if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint linear solve produced a non-finite value");
-    CK(cudaMemcpyAsync(lam, v.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    return;
-  }
-  PcgVecs<float> w = ensure_pcg<float>(m);
-  m->scratch.ensure(3 * n * sizeof(double) + 64);
-  double* y = m->scratch.as<double>();
-  double* r = y + n;
-  CK(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
-  CK(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  launch_d2f(n, g, const_cast<float*>(w.b), s);
-  double* d2 = m->stats.as<double>() + 8;
-  CK(cudaMemsetAsync(d2, 0, sizeof(double), s));
-  launch_dot<double>(n, g, g, d2, s);
-  CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const double g2 = m->h_small[20];
-  double r2 = g2;
-  for (int rf = 0; rf < 12; ++rf) {
-    // each correction needs only to bring the residual to a tenth of the 1e-13 target
-    const double rt = std::max(1e-5, std::min(1e-2, 1e-14 * std::sqrt(g2 / std::max(r2, 1e-300))));
-    PcgResult pr = pcg_run<float>(m, rt, maxk, std::max(1, m->cheb_auto[1]));
-    if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint refinement produced a non-finite value");
-    launch_axpy<float>(n, 1.0, w.x, lam, s);
-    ApplyArgs<double> a{};
-    a.v = lam;
-    a.y = y;
-    a.c = v.c;
-    launch_apply<double>(m->g64.g, a, m->cfg64, s);
-    launch_sub(n, g, y, r, const_cast<float*>(w.b), s);
-    CK(cudaMemsetAsync(d2, 0, sizeof(double), s));
-    launch_dot<double>(n, r, r, d2, s);
-    CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    r2 = m->h_small[20];
-    if (r2 <= 1e-26 * g2) break;
-  }
-}
-
-qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
-                    const double* theta, double* dN_dV, double* dN_dq) {
-  validate_bias(m, b);
-  validate_opts(o);
-  if (!phi || !dN_dV) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
-  cudaStream_t s = m->stream;
-  const long long n = m->n_nodes;
-  ensure_newton(m);
-  const Phys P = make_phys(m, b);
-  // linearization at phi in FP64 (and FP32 for the mixed refinement)
-  eval_residual(m, P, phi, theta, 0, 0, nullptr);
-  if (o->precision == 1) eval_residual(m, P, phi, theta, 0, 1, nullptr);
-  DevBuf work;
-  work.ensure(4 * n * sizeof(double) + 64);
-  double* g = work.as<double>();
-  double* lam = g + n;
-  double* eg = g + 2 * n;
-  double* Jeg = g + 3 * n;
-  double* zero_v = m->stats.as<double>() + 32;  // 16 zeros for masking Dirichlet rows
-  CK(cudaMemsetAsync(zero_v, 0, 16 * sizeof(double), s));
-  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
-  std::vector<double> gD(m->n_gates * QCAD_MAX_DOTS_K, 0.0);
-  for (int d = 0; d < m->dots.n; ++d) {
-    launch_count_gradient(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), m->d_xn.as<double>(),
-                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, g, m->cfg_res, s);
-    // dN/dphi_D . e_g before masking
-    for (int gi = 0; gi < m->n_gates; ++gi) {
-      CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));
-      std::vector<double> one(m->n_gates, 0.0);
-      one[gi] = 1.0;
-      std::memcpy(m->h_small + 16, one.data(), sizeof(double) * m->n_gates);
-      CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * m->n_gates, cudaMemcpyHostToDevice, s));
-      launch_set_dirichlet(m->nxn, m->nyn, m->nzn, 0, 0.0, m->d_gate_top.as<signed char>(), m->d_vgate.as<double>(),
-                           eg, s);
-      double* acc = m->stats.as<double>() + 10;
-      CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
-      launch_dot<double>(n, g, eg, acc, s);
-      CK(cudaMemcpyAsync(m->h_small + 30, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      gD[d * m->n_gates + gi] = m->h_small[30];
-    }
-    // zero the Dirichlet rows of the right-hand side
-    launch_set_dirichlet(m->nxn, m->nyn, m->nzn, m->bottom_ohmic, 0.0, m->d_gate_top.as<signed char>(), zero_v, g, s);
-    adjoint_solve(m, o->precision, g, lam, maxk);
-    for (int gi = 0; gi < m->n_gates; ++gi) {
-      CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));
-      std::vector<double> one(m->n_gates, 0.0);
-      one[gi] = 1.0;
-      std::memcpy(m->h_small + 16, one.data(), sizeof(double) * m->n_gates);
-      CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * m->n_gates, cudaMemcpyHostToDevice, s));
-      launch_set_dirichlet(m->nxn, m->nyn, m->nzn, 0, 0.0, m->d_gate_top.as<signed char>(), m->d_vgate.as<double>(),
-                           eg, s);
-      ApplyArgs<double> a{};
-      a.v = eg;
-      a.y = Jeg;
-      a.c = ensure_pcg<double>(m).c;
-      a.raw = 1;
-      launch_apply<double>(m->g64.g, a, m->cfg64, s);
-      double* acc = m->stats.as<double>() + 11;
-      CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
-      launch_dot<double>(n, lam, Jeg, acc, s);
-      CK(cudaMemcpyAsync(m->h_small + 31, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      dN_dV[d * m->n_gates + gi] = gD[d * m->n_gates + gi] - m->h_small[31];
-    }
-    if (dN_dq) {
-      launch_theta_gradient(m->nx, m->ny, m->nz, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, lam, P.qe,
-                            dN_dq + (long long)d * m->n_elems, s);
-    }
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));
-  }
-  return QCAD_OK;
-}
-
 // ---------------------------------------------------------------------------
 // Batched form: n independent meshes (uneven sizes, own biases) solved by a
 // lockstep Newton iteration. Every device pass covers all instances at once:
@@ -761,17 +637,22 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
 struct BatchCtx {
   int n = 0;
   cudaStream_t s = nullptr;
-  std::vector<qcad_mesh_s*> ms;
+  std::vector<qcad_mesh_s*> ms;       // mesh of each entry (entries may share a mesh)
+  std::vector<PcgVecs<float>> vecs;   // FP32 PCG vectors of each entry
+  std::vector<PcgScalars*> scd;       // device PCG scalars of each entry
+  std::vector<int> kch;               // z chunk of each entry's apply
   std::vector<Phys> P;
   DevBuf tab_a, tab_v, tab_r, status, rstats;
   int total_a = 0, total_v = 0;
   int* h_status = nullptr;
   double* h_rstats = nullptr;
+  PcgScalars* h_sc = nullptr;         // pinned host staging of the entries' scalars
   cudaGraphExec_t exec = nullptr;
   ~BatchCtx() {
     if (exec) cudaGraphExecDestroy(exec);
     if (h_status) cudaFreeHost(h_status);
     if (h_rstats) cudaFreeHost(h_rstats);
+    if (h_sc) cudaFreeHost(h_sc);
   }
 };
 
@@ -781,12 +662,12 @@ static void batch_setup(BatchCtx& B) {
   int ba = 0, bv = 0;
   for (int i = 0; i < B.n; ++i) {
     qcad_mesh_s* m = B.ms[i];
-    PcgVecs<float> v = ensure_pcg<float>(m);
+    const PcgVecs<float>& v = B.vecs[i];
     BatchApplyEntry& a = ta[i];
     a.g = m->g32.g;
     a.v = v;
-    a.sc = m->scal.as<PcgScalars>();
-    a.kchunk = std::min(128, std::max(2, m->batch_kchunk > 0 ? m->batch_kchunk : 16));
+    a.sc = B.scd[i];
+    a.kchunk = std::min(128, std::max(2, B.kch[i] > 0 ? B.kch[i] : 16));
     a.tiles_x = (m->g32.g.nxn + 29) / 30;  // plane-factorized tiles: 30 x 14 interior nodes
     a.tiles_y = (m->g32.g.nyn + 13) / 14;
     a.begin = ba;
@@ -810,6 +691,7 @@ static void batch_setup(BatchCtx& B) {
   CK(cudaMemcpyAsync(B.tab_v.p, tv.data(), tv.size() * sizeof(BatchVecEntry), cudaMemcpyHostToDevice, B.s));
   CK(cudaMallocHost(&B.h_status, (size_t)4 * B.n * sizeof(int)));
   CK(cudaMallocHost(&B.h_rstats, (size_t)3 * B.n * sizeof(double)));
+  CK(cudaMallocHost(&B.h_sc, (size_t)B.n * sizeof(PcgScalars)));
   CK(cudaStreamSynchronize(B.s));
   const long long before = launch_count();
   CK(cudaStreamBeginCapture(B.s, cudaStreamCaptureModeThreadLocal));
@@ -882,8 +764,7 @@ static void batch_residual(BatchCtx& B, const std::vector<int>& idx, const std::
 static void batch_pcg(BatchCtx& B, const std::vector<double>& rtol, int maxit, std::vector<int>& iters,
                       std::vector<int>& nonfinite) {
   for (int i = 0; i < B.n; ++i) {
-    qcad_mesh_s* m = B.ms[i];
-    PcgScalars* h = m->h_scal;
+    PcgScalars* h = B.h_sc + i;
     std::memset(h, 0, sizeof(PcgScalars));
     h->tol2 = rtol[i] * rtol[i];
     h->maxit = maxit;
@@ -892,9 +773,12 @@ static void batch_pcg(BatchCtx& B, const std::vector<double>& rtol, int maxit, s
     h->theta = 1.0;
     h->delta = 0.5;
     if (!(rtol[i] > 0)) h->done = 1;
-    CK(cudaMemcpyAsync(m->scal.p, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
-    if (rtol[i] > 0) launch_pcg_init<float>(m->n_nodes, ensure_pcg<float>(m), m->scal.as<PcgScalars>(), B.s);
   }
+  CK(cudaMemcpyAsync(B.scd[0], B.h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
+  for (int i = 1; i < B.n; ++i)
+    CK(cudaMemcpyAsync(B.scd[i], B.h_sc + i, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
+  for (int i = 0; i < B.n; ++i)
+    if (rtol[i] > 0) launch_pcg_init<float>(B.ms[i]->n_nodes, B.vecs[i], B.scd[i], B.s);
   CK(cudaGetLastError());
   int guard = 0;
   for (;;) {
@@ -912,6 +796,200 @@ static void batch_pcg(BatchCtx& B, const std::vector<double>& rtol, int maxit, s
     iters[i] = rtol[i] > 0 ? B.h_status[4 * i + 1] : 0;
     nonfinite[i] = B.h_status[4 * i + 2];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint sensitivities of the dot counts (Sec. III's capacitance by the adjoint): one linear
+// solve J lam_d = dN_d/dphi per dot (free rows), then dN_d/dV_g = dN_d/dphi_D . e_g -
+// lam_d . (J e_g) with e_g the unit lift of gate g, and dN_d/dtheta_e = (q/eps0)(|e|/8) sum of
+// lam_d over the corners of e.
+
+// FP64 solve of one right-hand side (precision 0).
+static void adjoint_solve64(qcad_mesh_s* m, const double* g, double* lam, int maxk) {
+  cudaStream_t s = m->stream;
+  PcgVecs<double> v = ensure_pcg<double>(m);
+  CK(cudaMemcpyAsync(const_cast<double*>(v.b), g, m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PcgResult pr = pcg_run<double>(m, 1e-13, maxk, std::max(1, m->cheb_auto[0]));
+  if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint linear solve produced a non-finite value");
+  CK(cudaMemcpyAsync(lam, v.x, m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+struct AdjCtx {
+  int nd = 0, kc = 0;
+  const float* x0 = nullptr;
+  BatchCtx B;
+};
+
+// Mixed precision, all dots at once: FP32 Jacobi-PCG corrections of the nd systems advance
+// together (one apply launch and one update launch per iteration for every right-hand side,
+// the batched form's kernels over a table of nd entries on this mesh), each round followed by
+// the FP64 residuals g_d - J lam_d, until every residual is below 1e-13 ||g_d||.
+static void adjoint_solve_mixed(qcad_mesh_s* m, int nd, const double* G, double* LAM, int maxk) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  PcgVecs<double> v64 = ensure_pcg<double>(m);
+  PcgVecs<float> w0 = ensure_pcg<float>(m);
+  const int kc = (m->cfg32.variant == 3 && m->cfg32.by == 8) ? m->cfg32.kchunk : 16;
+  // the context (work tables and the captured PCG graph) is kept on the mesh while the
+  // right-hand side count, the chunk and the vectors stay the same
+  std::shared_ptr<AdjCtx> ctx = std::static_pointer_cast<AdjCtx>(m->adj_ctx);
+  if (!ctx || ctx->nd != nd || ctx->kc != kc || ctx->x0 != w0.x) {
+    m->adj_ctx.reset();
+    ctx = std::make_shared<AdjCtx>();
+    ctx->nd = nd;
+    ctx->kc = kc;
+    ctx->x0 = w0.x;
+    m->scal_x.ensure((size_t)nd * sizeof(PcgScalars) + 64);
+    BatchCtx& B = ctx->B;
+    B.n = nd;
+    B.s = s;
+    const size_t nb = (size_t)n * sizeof(float) + 64;
+    for (int d = 0; d < nd; ++d) {
+      PcgVecs<float> v = w0;
+      if (d > 0) {
+        PcgBufs<float>& k = m->k32x[d - 1];
+        k.x.ensure(nb);
+        k.r.ensure(nb);
+        k.z.ensure(nb);
+        k.p.ensure(2 * nb);
+        k.Ap.ensure(nb);
+        k.b.ensure(nb);
+        v.x = k.x.as<float>();
+        v.r = k.r.as<float>();
+        v.z = k.z.as<float>();
+        v.p[0] = k.p.as<float>();
+        v.p[1] = v.p[0] + nb / sizeof(float);
+        v.Ap = k.Ap.as<float>();
+        v.b = k.b.as<float>();  // dinv and c are the shared linearization
+      }
+      B.ms.push_back(m);
+      B.vecs.push_back(v);
+      B.scd.push_back(d == 0 ? m->scal.as<PcgScalars>() : m->scal_x.as<PcgScalars>() + d);
+      B.kch.push_back(kc);
+    }
+    batch_setup(B);
+    m->adj_ctx = ctx;
+  }
+  BatchCtx& B = ctx->B;
+  m->scratch.ensure((size_t)(nd + 1) * n * sizeof(double) + 64);
+  double* y = m->scratch.as<double>();
+  double* Rr = y + n;
+  double* d2 = m->stats.as<double>() + 12;  // nd <= 8 squared norms
+  CK(cudaMemsetAsync(LAM, 0, (size_t)nd * n * sizeof(double), s));
+  CK(cudaMemsetAsync(d2, 0, nd * sizeof(double), s));
+  for (int d = 0; d < nd; ++d) {
+    const double* g = G + (size_t)d * n;
+    CK(cudaMemcpyAsync(Rr + (size_t)d * n, g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_d2f(n, g, const_cast<float*>(B.vecs[d].b), s);
+    launch_dot<double>(n, g, g, d2 + d, s);
+  }
+  CK(cudaMemcpyAsync(m->h_small + 20, d2, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> g2(m->h_small + 20, m->h_small + 20 + nd), r2 = g2, rtol(nd);
+  std::vector<int> iters, nonf;
+  for (int rf = 0; rf < 12; ++rf) {
+    bool any = false;
+    for (int d = 0; d < nd; ++d) {
+      rtol[d] = 0.0;
+      if (r2[d] <= 1e-26 * g2[d]) continue;
+      any = true;
+      // each correction needs only to bring the residual to a tenth of the 1e-13 target
+      rtol[d] = std::max(1e-5, std::min(1e-2, 1e-14 * std::sqrt(g2[d] / std::max(r2[d], 1e-300))));
+    }
+    if (!any) break;
+    batch_pcg(B, rtol, maxk, iters, nonf);
+    CK(cudaMemsetAsync(d2, 0, nd * sizeof(double), s));
+    for (int d = 0; d < nd; ++d) {
+      if (!(rtol[d] > 0)) continue;
+      if (nonf[d]) throw Error(QCAD_ERR_NONFINITE, "adjoint refinement produced a non-finite value");
+      double* lam = LAM + (size_t)d * n;
+      double* r = Rr + (size_t)d * n;
+      launch_axpy<float>(n, 1.0, B.vecs[d].x, lam, s);
+      ApplyArgs<double> a{};
+      a.v = lam;
+      a.y = y;
+      a.c = v64.c;
+      launch_apply<double>(m->g64.g, a, m->cfg64, s);
+      launch_sub(n, G + (size_t)d * n, y, r, const_cast<float*>(B.vecs[d].b), s);
+      launch_dot<double>(n, r, r, d2 + d, s);
+    }
+    CK(cudaMemcpyAsync(m->h_small + 20, d2, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int d = 0; d < nd; ++d)
+      if (rtol[d] > 0) r2[d] = m->h_small[20 + d];
+  }
+}
+
+qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                    const double* theta, double* dN_dV, double* dN_dq) {
+  validate_bias(m, b);
+  validate_opts(o);
+  if (!phi || !dN_dV) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  const int nd = m->dots.n, ng = m->n_gates;
+  if (nd == 0) return QCAD_OK;
+  ensure_newton(m);
+  const Phys P = make_phys(m, b);
+  // linearization at phi in FP64 (and FP32 for the mixed refinement)
+  eval_residual(m, P, phi, theta, 0, 0, nullptr);
+  if (o->precision == 1) eval_residual(m, P, phi, theta, 0, 1, nullptr);
+  DevBuf work, accs;
+  work.ensure((size_t)(2 * nd + std::max(ng, 1) + 1) * n * sizeof(double) + 64);
+  double* G = work.as<double>();            // nd right-hand sides dN_d/dphi
+  double* LAM = G + (size_t)nd * n;         // nd adjoint solutions
+  double* JE = LAM + (size_t)nd * n;        // ng raw J e_g
+  double* eg = JE + (size_t)std::max(ng, 1) * n;
+  const size_t nacc = (size_t)2 * nd * ng + QCAD_MAX_GATES + 1;
+  accs.ensure(nacc * sizeof(double) + 64);
+  double* acc = accs.as<double>();          // [0, nd*ng): dN/dphi_D . e_g; then lam_d . J e_g
+  double* zero_v = acc + 2 * nd * ng;       // one zero per gate, for masking Dirichlet rows
+  CK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), s));
+  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
+  for (int d = 0; d < nd; ++d)
+    launch_count_gradient(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), m->d_xn.as<double>(),
+                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, G + (size_t)d * n, m->cfg_res,
+                          s);
+  // gate lifts e_g: their raw J e_g (shared by every dot) and dN_d/dphi . e_g before masking
+  for (int gi = 0; gi < ng; ++gi) {
+    CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));
+    for (int q = 0; q < ng; ++q) m->h_small[16 + q] = q == gi ? 1.0 : 0.0;
+    CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * ng, cudaMemcpyHostToDevice, s));
+    launch_set_dirichlet(m->nxn, m->nyn, m->nzn, 0, 0.0, m->d_gate_top.as<signed char>(), m->d_vgate.as<double>(),
+                         eg, s);
+    ApplyArgs<double> a{};
+    a.v = eg;
+    a.y = JE + (size_t)gi * n;
+    a.c = ensure_pcg<double>(m).c;
+    a.raw = 1;
+    launch_apply<double>(m->g64.g, a, m->cfg64, s);
+    for (int d = 0; d < nd; ++d) launch_dot<double>(n, G + (size_t)d * n, eg, acc + d * ng + gi, s);
+    CK(cudaStreamSynchronize(s));  // h_small is reused by the next gate's upload
+  }
+  // zero the Dirichlet rows of the right-hand sides, then solve
+  for (int d = 0; d < nd; ++d)
+    launch_set_dirichlet(m->nxn, m->nyn, m->nzn, m->bottom_ohmic, 0.0, m->d_gate_top.as<signed char>(), zero_v,
+                         G + (size_t)d * n, s);
+  if (o->precision == 1) {
+    adjoint_solve_mixed(m, nd, G, LAM, maxk);
+  } else {
+    for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
+  }
+  for (int d = 0; d < nd; ++d)
+    for (int gi = 0; gi < ng; ++gi)
+      launch_dot<double>(n, LAM + (size_t)d * n, JE + (size_t)gi * n, acc + nd * ng + d * ng + gi, s);
+  std::vector<double> h(2 * nd * ng);
+  CK(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (dN_dq)
+    for (int d = 0; d < nd; ++d)
+      launch_theta_gradient(m->nx, m->ny, m->nz, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, LAM + (size_t)d * n, P.qe,
+                            dN_dq + (long long)d * m->n_elems, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  for (int d = 0; d < nd; ++d)
+    for (int gi = 0; gi < ng; ++gi) dN_dV[d * ng + gi] = h[d * ng + gi] - h[nd * ng + d * ng + gi];
+  return QCAD_OK;
 }
 
 qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
@@ -932,6 +1010,11 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
     ensure_newton(ms[i]);
   }
   B.s = ms[0]->stream;
+  for (int i = 0; i < n; ++i) {
+    B.vecs.push_back(ensure_pcg<float>(ms[i]));
+    B.scd.push_back(ms[i]->scal.as<PcgScalars>());
+    B.kch.push_back(ms[i]->batch_kchunk);
+  }
   batch_setup(B);
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   const int maxn = o->max_newton > 0 ? o->max_newton : 100;
