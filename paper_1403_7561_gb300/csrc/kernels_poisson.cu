@@ -169,6 +169,144 @@ void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg 
   run_march<double>(g, op, c, s);
 }
 
+// ---------------------------------------------------------------------------
+// Two-pass residual: the same R, c, diagonal, norms and counts as ResidualOp, with the carrier
+// density (the FP64 transcendental part) evaluated exactly once per quadrature point.
+//
+// Pass 1: one thread per (element, quadrature point); the 8 lanes of an element hold its
+// corners and quadrature points under the same index (ix + 2 iy + 4 iz), so the Gauss
+// interpolation B (x) B (x) B and its transpose are three butterfly stages over lane bits 0, 1, 2
+// (B = [[a, b], [b, a]] along each axis). Writes c_q, the element's corner contributions to the
+// load -(q/eps0) int (rho + theta) N_i (elR) and to the mass diagonal sum_q c_q N_i(q)^2 (elD),
+// [8 e + corner] each, and the dot electron counts.
+__global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant__ Grid<double> g,
+                                                          const __grid_constant__ ResidualArgs a, double* elR,
+                                                          double* elD) {
+  const long long ne = (long long)g.nx * g.ny * g.nz;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  const bool valid = t < 8 * ne;  // an element's 8 lanes share one warp and one validity
+  const int e = valid ? (int)(t >> 3) : 0;
+  const int l = threadIdx.x & 7;
+  const int i = e % g.nx, r = e / g.nx;
+  const int j = r % g.ny, k = r / g.ny;
+  const bool semi = valid && a.layer_semi[k] && !a.linear;
+  const double A = GaussConst<double>::a(), B = GaussConst<double>::b();
+  double v = 0.0;
+  if (semi)
+    v = __ldg(a.phi + (i + (l & 1)) + (long long)g.nxn * ((j + ((l >> 1) & 1)) + (long long)g.nyn * (k + (l >> 2))));
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 1);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 2);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 4);
+  double f = 0.0, c = 0.0, nq = 0.0;
+  if (valid) {
+    const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
+    const double th = a.theta ? a.theta[e] : 0.0;
+    if (semi) {
+      const Charge ch = charge_at(a.P, v);
+      f = -a.P.qe * wdet * (ch.rho + th);
+      c = -a.P.qe * wdet * ch.drho;
+      nq = wdet * ch.n;
+    } else {
+      f = -a.P.qe * wdet * th;
+    }
+    if (a.c64) a.c64[t] = c;
+    if (a.c32) a.c32[t] = (float)c;
+  }
+  const double A2 = A * A, B2 = B * B;
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 1);
+  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 1);
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 2);
+  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 2);
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 4);
+  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 4);
+  if (valid) {
+    elR[t] = f;
+    elD[t] = c;
+  }
+  if (a.counts != nullptr) {
+    double s[2] = {0.0, 0.0};
+    if (semi) {
+      const int d = dot_of_element(a, i, j, k);
+      if (d == 0)
+        s[0] = nq;
+      else if (d == 1)
+        s[1] = nq;
+      else if (d > 1)
+        atomicAdd(a.counts + d, nq);
+    }
+    block_sum_atomic<2>(s, a.counts);
+  }
+}
+
+// Pass 2: the z-march node pass. Each node gathers the corner contributions of its elements
+// and adds the stiffness K phi (separable 27-point stencil); Dirichlet rows as in ResidualOp.
+struct ResidualGatherOp {
+  static constexpr int NF = 2;
+  static constexpr bool STIFF = true;
+  using ED = char;
+  const double* phi;
+  const double* elR;
+  const double* elD;
+  double *R, *diag, *dinv64, *b64, *stats;
+  float *dinv32, *b32;
+  double acc_r2, acc_rmax;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int) {}
+  __device__ double load(const Grid<double>&, int n, bool in, int, int, int) const { return in ? phi[n] : 0.0; }
+  __device__ char edata(const Grid<double>&, int, int, int) const { return 0; }
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double*, char, double (*out)[8], bool) const {
+    const long long e = elem_index(g, i, j, k);
+    load_c8<double>(elR, e, out[0]);
+    load_c8<double>(elD, e, out[1]);
+  }
+  __device__ void node(const Grid<double>& g, int n, int i, int j, int k, double, double stiff, const double* mass) {
+    double Rn = stiff + mass[0];
+    double dg = stiff_diag(g, i, j, k) + mass[1];
+    if (grid_is_dir(g, i, j, k)) {
+      Rn = 0.0;
+      dg = 1.0;
+    }
+    R[n] = Rn;
+    if (diag) diag[n] = dg;
+    if (dinv64) dinv64[n] = 1.0 / dg;
+    if (dinv32) dinv32[n] = (float)(1.0 / dg);
+    if (b64) b64[n] = -Rn;
+    if (b32) b32[n] = (float)(-Rn);
+    acc_r2 += Rn * Rn;
+    acc_rmax = fmax(acc_rmax, fabs(Rn));
+  }
+  __device__ void finish() {
+    if (stats) {
+      double s[1] = {acc_r2};
+      block_sum_atomic<1>(s, stats + 1);
+      block_max_atomic(acc_rmax, stats);
+    }
+  }
+};
+
+void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, double* el, LaunchCfg cfg,
+                           cudaStream_t s) {
+  const long long ne = (long long)g.nx * g.ny * g.nz;
+  double* elR = el;
+  double* elD = el + 8 * ne;
+  const int blocks = (int)((8 * ne + 255) / 256);
+  note_launch(), residual_qp_kernel<<<blocks, 256, 0, s>>>(g, args, elR, elD);
+  ResidualGatherOp op = {};
+  op.phi = args.phi;
+  op.elR = elR;
+  op.elD = elD;
+  op.R = args.R;
+  op.diag = args.diag;
+  op.dinv64 = args.dinv64;
+  op.b64 = args.b64;
+  op.stats = args.stats;
+  op.dinv32 = args.dinv32;
+  op.b32 = args.b32;
+  LaunchCfg c = cfg;
+  if (c.by == 32) c.by = 16;
+  run_march<double>(g, op, c, s);
+}
+
 template <class T>
 void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
   if (cfg.variant >= 2) {
@@ -189,31 +327,50 @@ template void launch_apply<float>(const Grid<float>&, const ApplyArgs<float>&, L
 template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// dN_d/dphi nodal vector of one dot.
-struct CountGradOp {
+// dN_d/dphi nodal vector of one dot, in two passes.
+
+// Pass 1 of the count gradient: wdet dn/dphi at the quadrature points of dot d's elements,
+// mapped to the element corners by the transposed interpolation (lane butterflies as in
+// residual_qp_kernel); [8 e + corner].
+__global__ void __launch_bounds__(256) count_grad_qp_kernel(const __grid_constant__ Grid<double> g,
+                                                            const __grid_constant__ ResidualArgs a, int d,
+                                                            double* el) {
+  const long long ne = (long long)g.nx * g.ny * g.nz;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  const bool valid = t < 8 * ne;
+  const int e = valid ? (int)(t >> 3) : 0;
+  const int l = threadIdx.x & 7;
+  const int i = e % g.nx, r = e / g.nx;
+  const int j = r % g.ny, k = r / g.ny;
+  const bool in = valid && a.layer_semi[k] && dot_of_element(a, i, j, k) == d;
+  const double A = GaussConst<double>::a(), B = GaussConst<double>::b();
+  double v = 0.0;
+  if (in)
+    v = __ldg(a.phi + (i + (l & 1)) + (long long)g.nxn * ((j + ((l >> 1) & 1)) + (long long)g.nyn * (k + (l >> 2))));
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 1);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 2);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 4);
+  double f = 0.0;
+  if (in) f = g.hx[i] * g.hy[j] * g.hz[k] * 0.125 * charge_at(a.P, v).dn;
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 1);
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 2);
+  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 4);
+  if (valid) el[t] = f;
+}
+
+// Pass 2: each node sums its elements' corner values.
+struct CornerGatherOp {
   static constexpr int NF = 1;
   static constexpr bool STIFF = false;
   using ED = char;
-  ResidualArgs a;  // phi, layer_semi, coordinates, P, dots
-  int d;
+  const double* el;
   double* out;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int) {}
-  __device__ double load(const Grid<double>&, int n, bool in, int, int, int) const { return in ? a.phi[n] : 0.0; }
+  __device__ double load(const Grid<double>&, int, bool, int, int, int) const { return 0.0; }
   __device__ char edata(const Grid<double>&, int, int, int) const { return 0; }
-  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double* v, char, double (*o)[8], bool) const {
-    double f[8];
-    if (a.layer_semi[k] && dot_of_element(a, i, j, k) == d) {
-      const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
-      double pq[8];
-      tp_apply(v, pq, GaussConst<double>::a(), GaussConst<double>::b());
-#pragma unroll
-      for (int q = 0; q < 8; ++q) f[q] = wdet * charge_at(a.P, pq[q]).dn;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) f[q] = 0.0;
-    }
-    tp_apply(f, o[0], GaussConst<double>::a(), GaussConst<double>::b());
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double*, char, double (*o)[8], bool) const {
+    load_c8<double>(el, elem_index(g, i, j, k), o[0]);
   }
   __device__ void node(const Grid<double>&, int n, int, int, int, double, double, const double* mass) {
     out[n] = mass[0];
@@ -223,16 +380,19 @@ struct CountGradOp {
 
 void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
                            const double* xn, const double* yn, const double* zn, const Phys& P,
-                           const DotBoxes& dots, int d, double* out, LaunchCfg cfg, cudaStream_t s) {
-  CountGradOp op = {};
-  op.a.phi = phi;
-  op.a.layer_semi = layer_semi;
-  op.a.xn = xn;
-  op.a.yn = yn;
-  op.a.zn = zn;
-  op.a.P = P;
-  op.a.dots = dots;
-  op.d = d;
+                           const DotBoxes& dots, int d, double* out, double* el, LaunchCfg cfg, cudaStream_t s) {
+  ResidualArgs a{};
+  a.phi = phi;
+  a.layer_semi = layer_semi;
+  a.xn = xn;
+  a.yn = yn;
+  a.zn = zn;
+  a.P = P;
+  a.dots = dots;
+  const long long ne = (long long)g.nx * g.ny * g.nz;
+  note_launch(), count_grad_qp_kernel<<<(int)((8 * ne + 255) / 256), 256, 0, s>>>(g, a, d, el);
+  CornerGatherOp op = {};
+  op.el = el;
   op.out = out;
   LaunchCfg c = cfg;
   if (c.by == 32) c.by = 16;

@@ -139,6 +139,7 @@ struct qcad_mesh_s {
   qcad::DevBuf scal_x;                           // their PCG scalars
   std::shared_ptr<void> adj_ctx;                 // cached batched-PCG context of the adjoint
   qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
+  qcad::DevBuf el_res;                     // residual corner contributions, 16 doubles per element
   qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror
   double* h_small = nullptr;               // pinned host scratch (64 doubles)
   // second stream and scratch for an eigensolve that runs concurrently with the mesh stream

@@ -360,7 +360,8 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   }
   Profiler::Pair pp;
   if (m->prof.on) m->prof.begin(PROF_RESIDUAL, s, pp);
-  launch_residual(m->g64.g, a, m->cfg_res, s);
+  m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
+  launch_residual_2pass(m->g64.g, a, m->el_res.as<double>(), m->cfg_res, s);
   m->lin_ver[prec == 0 ? 0 : 1] += 1;  // the stored linearization changed
   if (m->prof.on) m->prof.end(pp, s);
   CK(cudaGetLastError());
@@ -947,10 +948,11 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
   double* zero_v = acc + 2 * nd * ng;       // one zero per gate, for masking Dirichlet rows
   CK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), s));
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
+  m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
   for (int d = 0; d < nd; ++d)
     launch_count_gradient(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), m->d_xn.as<double>(),
-                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, G + (size_t)d * n, m->cfg_res,
-                          s);
+                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, G + (size_t)d * n,
+                          m->el_res.as<double>(), m->cfg_res, s);
   // gate lifts e_g: their raw J e_g (shared by every dot) and dN_d/dphi . e_g before masking
   for (int gi = 0; gi < ng; ++gi) {
     CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));

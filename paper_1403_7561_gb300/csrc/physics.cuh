@@ -38,14 +38,21 @@ __device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
   dF = -dD * F * F;
 }
 
-// s = 1/(1 + g e^z) and 1 - s without overflow.
+// s = 1/(1 + g e^z) and 1 - s without overflow. Beyond |z| = 746, e^{-|z|} is below half the
+// smallest subnormal, so those arguments take it as zero and skip the call (and, for z < -746,
+// the reciprocal of 1).
 __device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms) {
   if (z > 0.0) {
-    const double e = exp(-z);
+    const double e = (z > 746.0) ? 0.0 : exp(-z);
     const double r = 1.0 / (e + g);
     s = e * r;
     oms = g * r;
   } else {
+    if (z < -746.0) {
+      s = 1.0;
+      oms = 0.0;
+      return;
+    }
     const double ge = g * exp(z);
     const double r = 1.0 / (1.0 + ge);
     s = r;

@@ -89,6 +89,8 @@ struct LaunchCfg {
 };
 
 void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg, cudaStream_t s);
+// Same outputs in two passes (carrier density once per quadrature point); el: 16 doubles per element.
+void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& a, double* el, LaunchCfg cfg, cudaStream_t s);
 
 template <class T>
 void launch_apply(const Grid<T>& g, const ApplyArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
@@ -134,7 +136,8 @@ void launch_f2d(long long n, const float* a, double* b, cudaStream_t s);
 // dN_d/dphi as a nodal vector for dot d: sum over dot elements of w|J| n'(phi_q) N_a(q).
 void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
                            const double* xn, const double* yn, const double* zn, const Phys& P,
-                           const DotBoxes& dots, int d, double* out, LaunchCfg cfg, cudaStream_t s);
+                           const DotBoxes& dots, int d, double* out, double* el /* 8 per element */,
+                           LaunchCfg cfg, cudaStream_t s);
 
 // theta-gradient of N_d: out[e] = qe * (|e|/8) * sum of lam over the 8 corners of e (lam is
 // zero on Dirichlet nodes); |e|/8 = int_e N_a exactly on a box.
