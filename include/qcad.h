@@ -113,7 +113,8 @@ typedef struct {
   double newton_tol_dphi; /* ... and the last max |alpha delta| < this (V) */
   int max_newton;
   int max_krylov;         /* per linear solve */
-  int cheb_degree;        /* Chebyshev-Jacobi preconditioner degree; 1 = Jacobi; 0 = autotuned */
+  int cheb_degree;        /* preconditioner: k >= 1 Chebyshev-Jacobi of degree k (1 = Jacobi);
+                             -1 geometric multigrid V-cycle (mixed precision only); 0 = autotuned */
   int warm_start;         /* 1: phi holds the initial guess; 0: Laplace solve with the contact values */
   int linear;             /* 1: rho = 0 (dielectric-only solve) */
 } qcad_solver_opts;
@@ -252,7 +253,8 @@ qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bi
  * classes on the mesh stream (including those inside captured CUDA graphs) is
  * bracketed by CUDA events and its duration accumulated. Classes: 0 FP32
  * Jacobian apply (PCG), 1 FP64 Jacobian apply (PCG), 2 FP32 PCG update,
- * 3 FP64 PCG update, 4 FP64 residual, 5 Schrodinger H/M apply.
+ * 3 FP64 PCG update, 4 FP64 residual, 5 Schrodinger H/M apply, 6 multigrid
+ * PCG iteration tail (update and V-cycle, timed as one span).
  * qcad_profile_read returns the launch count and total milliseconds of one
  * class; qcad_profile_reset clears the counters. Profiling is off by default. */
 qcad_status qcad_profile_enable(qcad_mesh_t m, int enable);
@@ -275,8 +277,8 @@ qcad_status qcad_profile_read(qcad_mesh_t m, int kernel_class, int64_t* launches
  * its time per apply. */
 qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_rows, int z_chunk);
 /* The current launch shape of a family (as qcad_set_launch) and, for families 1 (FP64) and
- * 2 (FP32), the Chebyshev degree the mesh's autotuner chose (0: not tuned yet). Outputs may be
- * NULL. */
+ * 2 (FP32), the preconditioner the mesh's autotuner chose, coded as cheb_degree in
+ * qcad_solver_opts (0: not tuned yet). Outputs may be NULL. */
 qcad_status qcad_launch_info(qcad_mesh_t m, int family, int* variant, int* tile_rows, int* z_chunk,
                              int* cheb_degree);
 qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int* variant, int* tile_rows,

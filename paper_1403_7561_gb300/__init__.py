@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 
 QCAD_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "NONFINITE", 6: "TIMEOUT"}
-PROF_CLASSES = {"apply32": 0, "apply64": 1, "update32": 2, "update64": 3, "residual": 4, "hm": 5}
+PROF_CLASSES = {"apply32": 0, "apply64": 1, "update32": 2, "update64": 3, "residual": 4, "hm": 5, "mg": 6}
 
 
 class QcadError(RuntimeError):

@@ -6,6 +6,7 @@
 #include <type_traits>
 
 #include "linmarch.cuh"
+#include "mg.h"
 #include "pcg_ops.cuh"
 
 namespace qcad {
@@ -91,6 +92,83 @@ template void launch_cheb_step_lin<float>(const Grid<float>&, PcgVecs<float>, Pc
                                           cudaStream_t);
 template void launch_cheb_step_lin<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, int, int, LaunchCfg,
                                            cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle on level 0 (the mesh itself): the residual after pre-smoothing,
+// w = r - J zp with zp = d[0] = omega D^-1 r, and the post-smoothing step that also closes the
+// PCG iteration, z = zq + omega D^-1 (r - J zq) with zq = d[1] = zp + P e (coarse correction),
+// accumulating r.z and running the last block's bookkeeping as the Chebyshev step does.
+struct MgResid0Op {
+  static constexpr int NIN = 1;
+  static constexpr bool SEPM = false;
+  struct Pre {
+    float r;
+  };
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {}
+  __device__ const float* coeffs() const { return v.c; }
+  __device__ const float* lin_src(int) const { return v.d[0]; }
+  __device__ float lin_mix(float x0, float) const { return x0; }
+  __device__ float lin_in(int n) const { return v.d[0][n]; }
+  __device__ Pre lin_pre(int n) const { return Pre{v.r[n]}; }
+  __device__ bool lin_dir() const { return true; }
+  __device__ void lin_out(int n, const Pre& p, float, float y) { v.w[n] = p.r - y; }
+  __device__ void finish() {}
+};
+
+struct MgPost0Op {
+  static constexpr int NIN = 1;
+  static constexpr bool SEPM = false;
+  struct Pre {
+    float r, dinv;
+  };
+  PcgVecs<float> v;
+  PcgScalars* sc;
+  const float* par;
+  float om;
+  int t, slot;
+  float acc;
+  __device__ bool skip() const { return sc->done != 0; }
+  __device__ void set_vec(int) {
+    t = sc->t;
+    slot = sc->phase == 0 ? 0 : ((t + 1) & 3);
+    om = mg_omega(par, 0);
+  }
+  __device__ const float* coeffs() const { return v.c; }
+  __device__ const float* lin_src(int) const { return v.d[1]; }
+  __device__ float lin_mix(float x0, float) const { return x0; }
+  __device__ float lin_in(int n) const { return v.d[1][n]; }
+  __device__ Pre lin_pre(int n) const { return Pre{v.r[n], v.dinv[n]}; }
+  __device__ bool lin_dir() const { return true; }
+  __device__ void lin_out(int n, const Pre& p, float zq, float y) {
+    const float z = zq + om * p.dinv * (p.r - y);
+    v.z[n] = z;
+    acc += p.r * z;
+  }
+  __device__ void finish() {
+    double s1[1] = {(double)acc};
+    block_sum_atomic<1>(s1, &sc->rz[slot]);
+    if (last_block(&sc->counter) && threadIdx.x == 0 && threadIdx.y == 0) pcg_finish(sc, t, 1.0);
+  }
+};
+
+void launch_mg_resid0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  MgResid0Op op = {};
+  op.v = v;
+  op.sc = sc;
+  run_lin<float>(g, op, cfg, s);
+}
+
+void launch_mg_post0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, const float* par, LaunchCfg cfg,
+                     cudaStream_t s) {
+  MgPost0Op op = {};
+  op.v = v;
+  op.sc = sc;
+  op.par = par;
+  run_lin<float>(g, op, cfg, s);
+}
 
 // Schrodinger operators for nvec vectors (blockIdx.z runs over (vector, z chunk)): H = kinetic
 // stencil (kappa_d = hbar^2/(2 m_d)) plus the V quadrature-point mass term, M = consistent mass,

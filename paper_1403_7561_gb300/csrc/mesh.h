@@ -67,7 +67,7 @@ struct GridDev {
 };
 
 // Kernel classes timed with CUDA events when profiling is enabled.
-enum ProfClass { PROF_APPLY32 = 0, PROF_APPLY64, PROF_UPDATE32, PROF_UPDATE64, PROF_RESIDUAL, PROF_HM, PROF_NCLASS };
+enum ProfClass { PROF_APPLY32 = 0, PROF_APPLY64, PROF_UPDATE32, PROF_UPDATE64, PROF_RESIDUAL, PROF_HM, PROF_MG, PROF_NCLASS };
 
 struct Profiler {
   std::mutex mu;  // begin/end/harvest/add may come from two host threads
@@ -138,6 +138,7 @@ struct qcad_mesh_s {
   qcad::PcgBufs<float> k32x[QCAD_MAX_DOTS - 1];  // further FP32 right-hand sides (adjoint of dots 1, 2, ...)
   qcad::DevBuf scal_x;                           // their PCG scalars
   std::shared_ptr<void> adj_ctx;                 // cached batched-PCG context of the adjoint
+  std::shared_ptr<void> mg;                      // multigrid hierarchy (built on first use)
   qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
   qcad::DevBuf el_res;                     // residual corner contributions, 16 doubles per element
   qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "mesh.h"
+#include "mg.h"
 
 namespace qcad {
 
@@ -29,6 +30,8 @@ static bool debug_on() {
 }
 
 static const int PCG_CHUNK = 8;
+// Preconditioner code of the geometric multigrid V-cycle (other codes: Chebyshev degree >= 1).
+static const int DEG_MG = -1;
 
 template <class T> struct Prec;
 template <> struct Prec<double> {
@@ -98,6 +101,13 @@ static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* s
   launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s);
   rec(e++, false);
   rec(e, true);
+  if constexpr (std::is_same<T, float>::value) {
+    if (degree == DEG_MG) {
+      mg_enqueue_update(m, v, sc, s);
+      rec(e++, false);
+      return;
+    }
+  }
   if (degree <= 1)
     launch_pcg_update<T>(m->n_nodes, v, sc, s);
   else
@@ -126,7 +136,7 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
   G.events.clear();
   cudaStream_t s = m->stream;
   const bool prof = m->prof.on;
-  const int per_it = 1 + std::max(1, degree);
+  const int per_it = 1 + std::max(1, degree);  // event pairs per iteration (MG: apply, tail)
   std::vector<Profiler::Pair> evs;
   if (prof) {
     for (int i = 0; i < per_it * PCG_CHUNK; ++i) {
@@ -134,7 +144,7 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
       CK(cudaEventCreate(&p.a));
       CK(cudaEventCreate(&p.b));
       const int q = i % per_it;
-      p.cls = (q == 1) ? Prec<T>::prof_update : Prec<T>::prof_apply;
+      p.cls = (q == 1) ? (degree == DEG_MG ? PROF_MG : Prec<T>::prof_update) : Prec<T>::prof_apply;
       evs.push_back(p);
     }
   }
@@ -207,7 +217,9 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
                               int fresh_steps) {
   PcgVecs<T> v = ensure_pcg<T>(m);
   PcgGraph& G = Prec<T>::graph(m);
-  degree = std::max(1, std::min(degree, 16));
+  bool mg = false;
+  if constexpr (std::is_same<T, float>::value) mg = degree == DEG_MG && mg_prepare(m);
+  degree = mg ? DEG_MG : std::max(1, std::min(degree, 16));
   const bool prof_match = m->prof.on == !G.events.empty();
   if (!G.exec || G.key != (const void*)v.x || !prof_match || G.degree != degree) {
     build_graph<T>(m, v, degree);
@@ -242,7 +254,12 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
   }
   PcgScalars* sc = m->scal.as<PcgScalars>();
   CK(cudaMemcpyAsync(sc, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-  if (degree <= 1) {
+  if (mg) {
+    if constexpr (std::is_same<T, float>::value) {
+      mg_setup(m, s);
+      mg_enqueue_init(m, v, sc, s);
+    }
+  } else if (degree <= 1) {
     launch_pcg_init<T>(m->n_nodes, v, sc, s);
   } else {
     launch_pcg_init_cheb<T>(m->n_nodes, v, sc, s);
@@ -251,10 +268,11 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
   CK(cudaGetLastError());
   int t_prev = 0;
   int guard = 0;
-  const int per_it = 1 + degree;
+  const int per_it = mg ? 2 : 1 + degree;  // event pairs per iteration
+  const int launches_it = mg ? mg_launches_per_iteration(m) : 1 + degree;
   for (;;) {
     CK(cudaGraphLaunch(G.exec, s));
-    note_launch(per_it * PCG_CHUNK);
+    note_launch(launches_it * PCG_CHUNK);
     CK(cudaMemcpyAsync(h, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (m->prof.on) {
@@ -290,6 +308,10 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
 template <class T>
 static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1) {
   PcgResult r = pcg_run_once<T>(m, rtol, maxit, degree, 1.1, 0);
+  if (r.nonfinite && degree == DEG_MG) {
+    if (debug_on()) std::fprintf(stderr, "[qcad] multigrid PCG breakdown: retrying with Jacobi\n");
+    return pcg_run_once<T>(m, rtol, maxit, 1, 1.1, 0);
+  }
   if (!r.nonfinite || degree < 2) return r;
   if (debug_on()) std::fprintf(stderr, "[qcad] chebyshev breakdown at degree %d: re-estimating\n", degree);
   r = pcg_run_once<T>(m, rtol, maxit, degree, 1.3, 60);
@@ -300,13 +322,23 @@ static PcgResult pcg_run(qcad_mesh_s* m, double rtol, int maxit, int degree = 1)
 template <class T>
 static int choose_degree(qcad_mesh_s* m, double rtol, int maxit) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
-  if (m->cheb_auto[prec] > 0) return m->cheb_auto[prec];
+  if (m->cheb_auto[prec] != 0) return m->cheb_auto[prec];
   // odd degrees only: their polynomial stays positive above the estimated top of the spectrum,
-  // so an underestimated lambda_max slows the solve but cannot make it break down
-  const int cand[4] = {1, 3, 5, 7};
+  // so an underestimated lambda_max slows the solve but cannot make it break down; in mixed
+  // precision the multigrid V-cycle competes too
+  std::vector<int> cand = {1, 3, 5, 7};
+  if constexpr (std::is_same<T, float>::value)
+    if (mg_prepare(m)) cand.push_back(DEG_MG);
   int best = 1;
   double best_t = 1e300;
   for (int d : cand) {
+    // a first untimed run builds the candidate's graph; the timed run then pays what every
+    // new linearization pays (the power iteration, or the multigrid setup)
+    pcg_run<T>(m, rtol, maxit, d);
+    if constexpr (std::is_same<T, float>::value)
+      if (d == DEG_MG) mg_invalidate(m);
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    m->lam_ver[pi] = -1;
     CK(cudaStreamSynchronize(m->stream));
     const auto t0 = std::chrono::steady_clock::now();
     PcgResult r = pcg_run<T>(m, rtol, maxit, d);
@@ -429,12 +461,12 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   int kry = 0;
   qcad_status st = QCAD_OK;
-  int degree = o->cheb_degree > 0 ? o->cheb_degree : m->cheb_auto[prec];
+  int degree = o->cheb_degree != 0 ? o->cheb_degree : m->cheb_auto[prec];
   if (!o->warm_start) {
     // Laplace initial guess with the contact values (rho = 0), solved to 1e-3: it only starts
     // the Newton iteration, whose first step replaces it by the nonlinear correction
     eval_residual(m, P, pa, theta, 1, prec, nullptr);
-    if (degree <= 0) degree = choose_degree<T>(m, 1e-3, maxk);
+    if (degree == 0) degree = choose_degree<T>(m, 1e-3, maxk);
     PcgResult pr = pcg_run<T>(m, 1e-3, maxk, degree);
     kry += pr.iters;
     if (debug_on()) std::fprintf(stderr, "[qcad] laplace pcg iters %d conv %d\n", pr.iters, (int)pr.converged);
@@ -467,7 +499,7 @@ static qcad_status newton_impl(qcad_mesh_s* m, const qcad_bias* b, const qcad_so
     // no tighter than the tolerance needs: the linear part of the next residual, eta ||R||_2,
     // at a tenth of tol_R bounds its max norm below tol_R
     if (nR > 0) eta = std::max(eta, std::min(1e-2, 0.1 * o->newton_tol_R / nR));
-    if (degree <= 0) degree = choose_degree<T>(m, eta, maxk);
+    if (degree == 0) degree = choose_degree<T>(m, eta, maxk);
     PcgResult pr = pcg_run<T>(m, eta, maxk, degree);
     kry += pr.iters;
     if (pr.nonfinite) {
@@ -527,6 +559,9 @@ static void validate_opts(const qcad_solver_opts* o) {
   if (!o) throw Error(QCAD_ERR_INVALID_ARG, "null solver options");
   if (o->precision != 0 && o->precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "precision must be 0 or 1");
   if (!(o->newton_tol_R > 0) || !(o->newton_tol_dphi > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tolerances must be > 0");
+  if (o->cheb_degree < -1 || o->cheb_degree > 16) throw Error(QCAD_ERR_INVALID_ARG, "cheb_degree must be in [-1, 16]");
+  if (o->cheb_degree == -1 && o->precision != 1)
+    throw Error(QCAD_ERR_INVALID_ARG, "the multigrid preconditioner (cheb_degree -1) runs in mixed precision only");
 }
 
 qcad_status poisson_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* theta,
@@ -816,6 +851,44 @@ static void adjoint_solve64(qcad_mesh_s* m, const double* g, double* lam, int ma
   CK(cudaStreamSynchronize(s));
 }
 
+// Mixed precision, one right-hand side with the multigrid-preconditioned FP32 PCG: corrections
+// to a tenth of the 1e-13 target of ||g - J lam|| / ||g||, each followed by the FP64 residual.
+static void adjoint_solve_mixed_mg(qcad_mesh_s* m, const double* g, double* lam, int maxk) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  PcgVecs<double> v = ensure_pcg<double>(m);
+  PcgVecs<float> w = ensure_pcg<float>(m);
+  m->scratch.ensure(2 * n * sizeof(double) + 64);
+  double* y = m->scratch.as<double>();
+  double* r = y + n;
+  CK(cudaMemsetAsync(lam, 0, n * sizeof(double), s));
+  launch_d2f(n, g, const_cast<float*>(w.b), s);
+  double* d2 = m->stats.as<double>() + 12;
+  CK(cudaMemsetAsync(d2, 0, sizeof(double), s));
+  launch_dot<double>(n, g, g, d2, s);
+  CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double g2 = m->h_small[20];
+  double r2 = g2;
+  for (int rf = 0; rf < 12 && r2 > 1e-26 * g2; ++rf) {
+    const double rt = std::max(1e-5, std::min(1e-2, 1e-14 * std::sqrt(g2 / std::max(r2, 1e-300))));
+    PcgResult pr = pcg_run<float>(m, rt, maxk, DEG_MG);
+    if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint refinement produced a non-finite value");
+    launch_axpy<float>(n, 1.0, w.x, lam, s);
+    ApplyArgs<double> a{};
+    a.v = lam;
+    a.y = y;
+    a.c = v.c;
+    launch_apply<double>(m->g64.g, a, m->cfg64, s);
+    launch_sub(n, g, y, r, const_cast<float*>(w.b), s);
+    CK(cudaMemsetAsync(d2, 0, sizeof(double), s));
+    launch_dot<double>(n, r, r, d2, s);
+    CK(cudaMemcpyAsync(m->h_small + 20, d2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    r2 = m->h_small[20];
+  }
+}
+
 struct AdjCtx {
   int nd = 0, kc = 0;
   const float* x0 = nullptr;
@@ -973,7 +1046,10 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
   for (int d = 0; d < nd; ++d)
     launch_set_dirichlet(m->nxn, m->nyn, m->nzn, m->bottom_ohmic, 0.0, m->d_gate_top.as<signed char>(), zero_v,
                          G + (size_t)d * n, s);
-  if (o->precision == 1) {
+  const int degree = o->cheb_degree != 0 ? o->cheb_degree : m->cheb_auto[1];
+  if (o->precision == 1 && degree == DEG_MG && mg_prepare(m)) {
+    for (int d = 0; d < nd; ++d) adjoint_solve_mixed_mg(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
+  } else if (o->precision == 1) {
     adjoint_solve_mixed(m, nd, G, LAM, maxk);
   } else {
     for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);

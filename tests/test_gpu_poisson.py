@@ -219,6 +219,37 @@ def test_chebyshev_preconditioned_solve(q, name, precision, degree):
     assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_multigrid_preconditioned_solve(q, name):
+    # geometric multigrid V-cycle PCG (mixed precision) converges to the same unique solution;
+    # meshes too small for a coarse level fall back to Jacobi
+    dev = CASES[name]()
+    P = PoissonProblem(dev)
+    phi_o, rep_o = P.solve()
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1, cheb_degree=-1), phi)
+    assert rep["status"] == "OK", rep
+    assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
+    if name == "dqd_61x62x40_4K":
+        # the V-cycle needs several times fewer Krylov iterations than Jacobi on this mesh
+        m2 = q.qcad_mesh_create(dev)
+        phi2 = torch.zeros(m2.n_nodes, dtype=torch.float64, device="cuda")
+        rep2 = q.qcad_poisson_solve(m2, dev["bias"], q.make_opts(precision=1, cheb_degree=1), phi2)
+        assert rep2["status"] == "OK", rep2
+        assert 4 * rep["krylov_iters_total"] < rep2["krylov_iters_total"], (rep, rep2)
+
+
+def test_multigrid_option_is_validated(q):
+    dev = CASES["dqd_24x24x16_4K"]()
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    for prec, deg in ((0, -1), (1, -2), (1, 17)):
+        with pytest.raises(q.QcadError) as e:
+            q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=prec, cheb_degree=deg), phi)
+        assert e.value.code == 1
+
+
 def batch_devices():
     # uneven sizes (ragged tiles, a mesh one tile wide) with their own seeds, so each
     # instance has its own gate voltages

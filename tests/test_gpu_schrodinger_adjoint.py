@@ -118,8 +118,8 @@ def test_particle_in_box_closed_form(q):
     assert np.max(np.abs(np.array(E) - ev) / np.abs(ev)) < 1e-10
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_adjoint_matches_oracle(q, dqd, precision):
+@pytest.mark.parametrize("precision,degree", [(0, 1), (1, 1), (1, -1)])
+def test_adjoint_matches_oracle(q, dqd, precision, degree):
     dev, P, phi = dqd
     theta = np.array(W.interface_fixed_charge(dev, seed=5))
     Pt = PoissonProblem(dev, fixed_charge=theta)
@@ -128,11 +128,12 @@ def test_adjoint_matches_oracle(q, dqd, precision):
     m = q.qcad_mesh_create(dev)
     th = dt(theta)
     phig = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    r = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision), phig, fixed_charge=th)
+    # degree 1: Jacobi (the dots' mixed-precision systems solved together); -1: multigrid
+    opts = q.make_opts(precision=precision, cheb_degree=degree)
+    r = q.qcad_poisson_solve(m, dev["bias"], opts, phig, fixed_charge=th)
     assert r["status"] == "OK"
     dq = torch.empty(m.n_dots * m.n_elems, dtype=torch.float64, device="cuda")
-    dNdV = np.array(q.qcad_adjoint(m, dev["bias"], phig, q.make_opts(precision=precision), fixed_charge=th,
-                                   dN_dq=dq))
+    dNdV = np.array(q.qcad_adjoint(m, dev["bias"], phig, opts, fixed_charge=th, dN_dq=dq))
     assert np.max(np.abs(dNdV - dNdV_o)) <= 1e-8 * np.max(np.abs(dNdV_o))
     g = dq.cpu().numpy().reshape(m.n_dots, m.n_elems)
     assert np.max(np.abs(g - dNdq_o)) <= 1e-8 * np.max(np.abs(dNdq_o))
