@@ -155,7 +155,19 @@ class ClockSampler:
 # workload and the launch shape (variant, tile rows, z chunk) it was taken with; see
 # profiles/apply32_dqd_128x128x96_4K.md for the command. Valid for the kernel source it was
 # measured on: retake it when the kernel changes.
-NCU_TRAFFIC = {("apply32", "dqd_128x128x96_4K", 3, 8, 16): 65.3e6}
+NCU_TRAFFIC = {("apply32", "dqd_128x128x96_4K", 3, 8, 16): 65.3e6,
+               # both passes of one residual evaluation; profiles/residual_fp64_dqd_128x128x96_4K.md
+               ("residual", "dqd_128x128x96_4K", 3, 8, 16): 441.3e6}
+
+# FP64 floating-point operations per residual evaluation (2 per DFMA, 1 per DADD and DMUL,
+# counted by ncu over both passes at the fourth residual of a solve; the count follows the
+# carrier regime, i.e. how many quadrature points take the exponential branches), with the
+# command in profiles/residual_fp64_dqd_128x128x96_4K.md.
+NCU_FP64_FLOPS = {("residual", "dqd_128x128x96_4K"): 1235.5e6}
+
+# FP64 peak of this part: 2 DFMA lanes per SM per clock (ncu
+# sm__sass_thread_inst_executed_op_dfma_pred_on.avg.peak_sustained) x 2 flops x 152 SMs.
+FP64_FLOPS_PER_CLOCK = 2 * 2 * 152
 
 
 def load_peaks():
@@ -302,13 +314,42 @@ def native_arm(args):
     for cls in q.PROF_CLASSES:
         nl, ms = q.qcad_profile_read(m, cls)
         prof[cls] = (nl, ms)
+    # single-kernel classes with a roofline model (the multigrid tail is many small kernels)
     dom = max((c for c in prof if algorithmic_bytes(c, n_nodes, n_elems) is not None), key=lambda c: prof[c][1])
     total_ms = sum(v[1] for v in prof.values())
     share = prof[dom][1] / total_ms if total_ms else None
-    # the roofline uses the dominant kernel's launches inside the Newton solves of the timed steps:
-    # the adjoint and the eigensolve run concurrently on two streams, so their launches overlap
-    nl, ms = solve_prof[dom]
-    achieved = algorithmic_bytes(dom, n_nodes, n_elems) / (ms / nl / 1000.0) / 1e9 if nl else None
+    tune_key = tuple(tune32[:3])
+
+    # rooflines use launches inside the Newton solves of the timed steps: the adjoint and the
+    # eigensolve run concurrently on two streams, so their launches overlap
+    def hbm_roofline(cls):
+        nl, ms = solve_prof[cls]
+        ach = algorithmic_bytes(cls, n_nodes, n_elems) / (ms / nl / 1000.0) / 1e9 if nl else None
+        return {"bound": "hbm", "kernel": cls, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": (ach / peak) if ach else None,
+                "traffic": NCU_TRAFFIC.get((cls, args.workload) + tune_key),
+                "traffic_unit": "bytes per launch (ncu dram read + write, cold cache)",
+                "peak_kind": peak_kind, "launches": nl, "avg_ms": ms / nl if nl else None,
+                "timed_launches": "inside the Newton solves of the timed steps (no concurrent work)"}
+
+    def fp64_roofline(cls):
+        nl, ms = solve_prof[cls]
+        flops = NCU_FP64_FLOPS.get((cls, args.workload))
+        mhz = clk.get("sm_mhz") or 2070.0
+        pk = FP64_FLOPS_PER_CLOCK * mhz * 1e6 / 1e12
+        ach = flops / (ms / nl / 1000.0) / 1e12 if (nl and flops) else None
+        return {"bound": "alu", "kernel": cls, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": (ach / pk) if ach else None,
+                "traffic": NCU_TRAFFIC.get((cls, args.workload) + tune_key),
+                "traffic_unit": "bytes per evaluation (ncu dram read + write, cold cache, both passes)",
+                "peak_kind": "derived: 2 DFMA lanes/SM/clock x 2 flops x 152 SMs x median SM clock under load",
+                "flops_kind": "FP64 flops per evaluation counted by ncu (2 DFMA + DADD + DMUL)",
+                "launches": nl, "avg_ms": ms / nl if nl else None,
+                "timed_launches": "residual evaluations inside the Newton solves of the timed steps"}
+
+    roof = fp64_roofline(dom) if dom == "residual" else hbm_roofline(dom)
+    roof["share_of_profiled_time"] = share
+    op_apply = hbm_roofline("apply32")
 
     # end to end through the public API with host buffers: the gate voltages go in from the host
     # (inside the library, pinned staging), phi comes back to pinned host memory every step
@@ -371,13 +412,8 @@ def native_arm(args):
                                         "chosen_by": "--launch" if args.launch else "autotuner"},
                        "cheb_degree": args.cheb_degree or q.qcad_launch_info(m, 2)[3],
                        "adjoint_eigensolve": "sequential" if args.sequential else "concurrent (two streams)"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                         "traffic": NCU_TRAFFIC.get((dom, args.workload) + tuple(tune32[:3])),
-                         "traffic_unit": "bytes per launch (ncu dram read + write, cold cache)",
-                         "peak_kind": peak_kind, "launches": nl, "avg_ms": ms / nl if nl else None,
-                         "timed_launches": "inside the Newton solves of the timed steps (no concurrent work)",
-                         "share_of_profiled_time": share},
+            "roofline": roof,
+            "op_apply_roofline": op_apply,
             "kernel_profile_ms": {c: round(v[1], 3) for c, v in prof.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

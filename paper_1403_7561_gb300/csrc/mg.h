@@ -10,7 +10,7 @@
 // (row-major, corner index ix + 2 iy + 4 iz). Smoothing is one damped-Jacobi step before and
 // after each coarse correction, weight 1/theta with theta the centre of [hi/8, hi] and hi the
 // Gershgorin bound of D^-1 J on that level; the coarsest level (at most 512 nodes) is solved
-// by a degree-32 Chebyshev iteration inside one thread block. Pre- and post-smoothing use the
+// by a degree-16 Chebyshev iteration inside one thread block. Pre- and post-smoothing use the
 // same polynomial, so the V-cycle is a symmetric positive definite preconditioner for CG.
 #pragma once
 #include <cuda_runtime.h>
@@ -24,7 +24,7 @@ namespace qcad {
 
 constexpr int MG_MAX_LEVELS = 16;
 constexpr int MG_COARSE_NODES = 512;   // the coarsest level has at most this many nodes
-constexpr int MG_COARSE_DEGREE = 32;   // Chebyshev degree of the coarsest solve
+constexpr int MG_COARSE_DEGREE = 16;   // Chebyshev degree of the coarsest solve
 constexpr float MG_ALPHA = 8.0f;       // smoothing interval [hi / MG_ALPHA, hi]
 
 // Transfer tables along one axis, from a level to the next coarser one.

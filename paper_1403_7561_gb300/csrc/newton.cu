@@ -30,6 +30,9 @@ static bool debug_on() {
 }
 
 static const int PCG_CHUNK = 8;
+// Iterations per captured graph with the multigrid preconditioner: its solves take a handful of
+// iterations, and the iterations captured after convergence still launch (and return at once)
+static const int MG_CHUNK = 4;
 // Preconditioner code of the geometric multigrid V-cycle (other codes: Chebyshev degree >= 1).
 static const int DEG_MG = -1;
 
@@ -120,7 +123,7 @@ static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* s
   }
 }
 
-// Captures PCG_CHUNK iterations into a graph; with profiling on, every kernel is
+// Captures PCG_CHUNK (MG_CHUNK) iterations into a graph; with profiling on, every kernel is
 // bracketed by external event-record nodes (recorded whenever the graph runs).
 template <class T>
 static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
@@ -137,9 +140,10 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
   cudaStream_t s = m->stream;
   const bool prof = m->prof.on;
   const int per_it = 1 + std::max(1, degree);  // event pairs per iteration (MG: apply, tail)
+  const int chunk = degree == DEG_MG ? MG_CHUNK : PCG_CHUNK;
   std::vector<Profiler::Pair> evs;
   if (prof) {
-    for (int i = 0; i < per_it * PCG_CHUNK; ++i) {
+    for (int i = 0; i < per_it * chunk; ++i) {
       Profiler::Pair p;
       CK(cudaEventCreate(&p.a));
       CK(cudaEventCreate(&p.b));
@@ -151,7 +155,7 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
   PcgScalars* sc = m->scal.as<PcgScalars>();
   const long long launches_before = launch_count();
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (int it = 0; it < PCG_CHUNK; ++it) {
+  for (int it = 0; it < chunk; ++it) {
     std::vector<Profiler::Pair> sub;
     if (prof) sub.assign(evs.begin() + it * per_it, evs.begin() + (it + 1) * per_it);
     enqueue_iteration<T>(m, v, sc, degree, s, prof ? &sub : nullptr);
@@ -163,7 +167,7 @@ static void build_graph(qcad_mesh_s* m, const PcgVecs<T>& v, int degree) {
   cudaGraphDestroy(graph);
   CK(e);
   G.events = evs;
-  G.chunk = PCG_CHUNK;
+  G.chunk = chunk;
   G.degree = degree;
 }
 
@@ -272,11 +276,11 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
   const int launches_it = mg ? mg_launches_per_iteration(m) : 1 + degree;
   for (;;) {
     CK(cudaGraphLaunch(G.exec, s));
-    note_launch(launches_it * PCG_CHUNK);
+    note_launch(launches_it * G.chunk);
     CK(cudaMemcpyAsync(h, sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (m->prof.on) {
-      const int ran = std::min(PCG_CHUNK, h->t - t_prev);
+      const int ran = std::min(G.chunk, h->t - t_prev);
       for (int it = 0; it < ran; ++it) {
         for (int q = 0; q < per_it; ++q) {
           Profiler::Pair& p = G.events[it * per_it + q];
@@ -291,7 +295,7 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
     }
     t_prev = h->t;
     if (h->done) break;
-    if (++guard > maxit / PCG_CHUNK + 4) break;
+    if (++guard > maxit / G.chunk + 4) break;
   }
   PcgResult r;
   r.iters = h->t;
