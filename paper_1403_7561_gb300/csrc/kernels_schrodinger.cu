@@ -3,6 +3,10 @@
 // Schrodinger3D) with the potential energy of Eq. SchrodPotEnergy (no V_xc).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
+
 #include <algorithm>
 
 #include "qcad_host.h"
@@ -292,6 +296,139 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(int nblk, int tot, int
 
 size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 * q; }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the FP64 phase's dense block products. This part runs FP32 at
+// about 57 times its FP64 rate, so a product-accumulate of two FP64 values carried as
+// unevaluated sums of two floats (hi + lo, a 48-bit significand) costs fewer cycles than one
+// DFMA. The product is exact up to the dropped lo*lo term (Dekker's product through the fused
+// multiply-add); the sum is Knuth's two-sum into the high word with the errors gathered in the
+// low word. Relative error of a length-p dot product: about p * 2^-48.
+__device__ __forceinline__ void df_split(double a, float& h, float& l) {
+  h = __double2float_rn(a);
+  l = __double2float_rn(a - (double)h);
+}
+
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float ph = ah * bh;
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float t = sh + ph;
+  const float bp = t - sh;
+  const float e = (sh - (t - bp)) + (ph - bp);
+  sh = t;
+  sl += e + pl;
+}
+
+// gram_kernel for FP64 blocks in double-float arithmetic: the double tile lands in shared
+// memory as before, is split once into hi and lo float tiles, and each 32-row tile is summed in
+// double-float before it is added to the FP64 accumulators.
+__global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb2, const double* A, long long lda,
+                                                      const double* B1, const double* B2, long long ldb,
+                                                      double* part) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  const int q = p;
+  const int qt = q * nb2;
+  const int ta_n = (p + 3) / 4, tb_n = (qt + 3) / 4;
+  const int pp = 4 * ta_n, qp = 4 * tb_n;
+  const int W = pp + qp + 4;
+  double* sh = reinterpret_cast<double*>(sh_raw);                 // two stages of GR x W doubles
+  float* fh = reinterpret_cast<float*>(sh + (size_t)2 * GR * W);  // GR x W hi words
+  float* fl = fh + (size_t)GR * W;                                // GR x W lo words
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int t = tid; t < 2 * GR * W; t += nth) sh[t] = 0.0;
+  __syncthreads();
+  const bool active = tid < ta_n * tb_n;
+  const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
+  double acc[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) acc[s] = 0.0;
+  const long long ntiles = (n + GR - 1) / GR;
+  auto issue = [&](long long tile, int stage) {
+    if (tile < ntiles) {
+      const long long r0 = tile * GR;
+      double* st = sh + (size_t)stage * GR * W;
+      for (int t = tid; t < (p + qt) * GR; t += nth) {
+        const int col = t / GR, rr = t % GR;
+        const long long row = r0 + rr;
+        const bool ok = row < n;
+        const double* src;
+        int sc;
+        if (col < p) {
+          src = A + col * lda + (ok ? row : 0);
+          sc = col;
+        } else {
+          const int bc = col - p;
+          src = (bc < q ? B1 + bc * ldb : B2 + (bc - q) * ldb) + (ok ? row : 0);
+          sc = pp + bc;
+        }
+        gram_cp<double>(st + rr * W + sc, src, ok);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int stage = 0;
+  issue(blockIdx.x, 0);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    issue(tile + gridDim.x, stage ^ 1);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    {
+      const double* st = sh + (size_t)stage * GR * W;
+      for (int t = tid; t < GR * W; t += nth) df_split(st[t], fh[t], fl[t]);
+    }
+    __syncthreads();
+    if (active) {
+      float sh16[16], sl16[16];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        sh16[s] = 0.0f;
+        sl16[s] = 0.0f;
+      }
+#pragma unroll 2
+      for (int rr = 0; rr < GR; ++rr) {
+        float ah[4], al[4], bh[4], bl[4];
+        gram_ld4(fh + rr * W + 4 * ta, ah);
+        gram_ld4(fl + rr * W + 4 * ta, al);
+        gram_ld4(fh + rr * W + pp + 4 * tb, bh);
+        gram_ld4(fl + rr * W + pp + 4 * tb, bl);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) df_mac(sh16[4 * u + v], sl16[4 * u + v], ah[u], al[u], bh[v], bl[v]);
+      }
+#pragma unroll
+      for (int s = 0; s < 16; ++s) acc[s] += (double)sh16[s] + (double)sl16[s];
+    }
+    __syncthreads();
+    stage ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (!active) return;
+  double* out = part + (size_t)blockIdx.x * p * qt;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = 4 * ta + u;
+    if (a >= p) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int bc = 4 * tb + v;
+      if (bc >= qt) continue;
+      out[bc < q ? a * q + bc : p * q + a * q + (bc - q)] = acc[4 * u + v];
+    }
+  }
+}
+
+// Whether the FP64 phase's Gram and combine run in double-float (default) or in native FP64
+// (environment QCAD_FP64_DENSE=native).
+static bool dense_df() {
+  static const bool df = [] {
+    const char* e = std::getenv("QCAD_FP64_DENSE");
+    return !(e && std::strcmp(e, "native") == 0);
+  }();
+  return df;
+}
+
 template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
                  double* G1, double* G2, double* part, cudaStream_t s) {
@@ -305,6 +442,20 @@ void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* 
   static bool attr = false;
   if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
                     cudaSuccess;
+  if constexpr (std::is_same<T, double>::value) {
+    if (dense_df()) {
+      // two double stages plus the hi and lo float tiles
+      const size_t shm_df = shm + (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(float);
+      static bool attr_df = false;
+      if (!attr_df)
+        attr_df = cudaFuncSetAttribute(gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                  cudaSuccess;
+      note_launch(), gram_df_kernel<<<nblk, nth, shm_df, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part);
+      const int tot = p * p * nb2;
+      note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
+      return;
+    }
+  }
   note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part);
   const int tot = p * p * nb2;
   note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
@@ -351,11 +502,58 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q,
   }
 }
 
+// combine_kernel for FP64 blocks in double-float arithmetic: C is split into hi and lo float
+// tables in shared memory, each thread splits its row of A once, and every output is a
+// double-float dot product rounded to FP64 at the end.
+template <int PMAX>
+__global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int q, int q1, const double* A,
+                                                         long long lda, const double* C, double* Y1, double* Y2,
+                                                         long long ldy) {
+  extern __shared__ __align__(16) unsigned char sc_raw[];
+  const int pp = (p + 3) & ~3;
+  float* sCh = reinterpret_cast<float*>(sc_raw);  // [q][pp]
+  float* sCl = sCh + (size_t)pp * q;
+  for (int t = threadIdx.x; t < pp * q; t += blockDim.x) {
+    const int j = t / pp, i = t % pp;
+    df_split(i < p ? C[j * p + i] : 0.0, sCh[t], sCl[t]);
+  }
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    float ah[PMAX], al[PMAX];
+#pragma unroll
+    for (int i = 0; i < PMAX; ++i) df_split(i < p ? A[i * lda + r] : 0.0, ah[i], al[i]);
+    for (int j = 0; j < q; ++j) {
+      const float* ch = sCh + j * pp;
+      const float* cl = sCl + j * pp;
+      float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+      for (int i = 0; i < PMAX; ++i)
+        if (i < pp) df_mac(sh, sl, ah[i], al[i], ch[i], cl[i]);
+      const double y = (double)sh + (double)sl;
+      if (j < q1)
+        Y1[j * ldy + r] = y;
+      else
+        Y2[(j - q1) * ldy + r] = y;
+    }
+  }
+}
+
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
                     long long ldy, cudaStream_t s) {
   const size_t shm = (size_t)((p + 3) & ~3) * q * sizeof(T);
   const int nb = dblocks(n);
+  if constexpr (std::is_same<T, double>::value) {
+    if (dense_df()) {  // hi and lo float tables: the same bytes as the double table
+      if (p <= 16)
+        note_launch(), combine_df_kernel<16><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+      else if (p <= 32)
+        note_launch(), combine_df_kernel<32><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+      else
+        note_launch(), combine_df_kernel<64><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+      return;
+    }
+  }
   if (p <= 16)
     note_launch(), combine_kernel<T, 16><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
   else if (p <= 32)
