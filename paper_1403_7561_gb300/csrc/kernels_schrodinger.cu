@@ -504,36 +504,46 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q,
 
 // combine_kernel for FP64 blocks in double-float arithmetic: C is split into hi and lo float
 // tables in shared memory, each thread splits its row of A once, and every output is a
-// double-float dot product rounded to FP64 at the end.
+// double-float dot product rounded to FP64 at the end. Four outputs are formed together so that
+// four independent two-sum chains interleave.
 template <int PMAX>
 __global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int q, int q1, const double* A,
                                                          long long lda, const double* C, double* Y1, double* Y2,
                                                          long long ldy) {
   extern __shared__ __align__(16) unsigned char sc_raw[];
   const int pp = (p + 3) & ~3;
-  float* sCh = reinterpret_cast<float*>(sc_raw);  // [q][pp]
-  float* sCl = sCh + (size_t)pp * q;
-  for (int t = threadIdx.x; t < pp * q; t += blockDim.x) {
+  const int qq = (q + 3) & ~3;
+  float* sCh = reinterpret_cast<float*>(sc_raw);  // [qq][pp], zero beyond p and q
+  float* sCl = sCh + (size_t)pp * qq;
+  for (int t = threadIdx.x; t < pp * qq; t += blockDim.x) {
     const int j = t / pp, i = t % pp;
-    df_split(i < p ? C[j * p + i] : 0.0, sCh[t], sCl[t]);
+    df_split(i < p && j < q ? C[j * p + i] : 0.0, sCh[t], sCl[t]);
   }
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
     float ah[PMAX], al[PMAX];
 #pragma unroll
     for (int i = 0; i < PMAX; ++i) df_split(i < p ? A[i * lda + r] : 0.0, ah[i], al[i]);
-    for (int j = 0; j < q; ++j) {
-      const float* ch = sCh + j * pp;
-      const float* cl = sCl + j * pp;
-      float sh = 0.0f, sl = 0.0f;
+    for (int j0 = 0; j0 < q; j0 += 4) {
+      float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int i = 0; i < PMAX; ++i)
-        if (i < pp) df_mac(sh, sl, ah[i], al[i], ch[i], cl[i]);
-      const double y = (double)sh + (double)sl;
-      if (j < q1)
-        Y1[j * ldy + r] = y;
-      else
-        Y2[(j - q1) * ldy + r] = y;
+      for (int i = 0; i < PMAX; ++i) {
+        if (i < pp) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            df_mac(sh[u], sl[u], ah[i], al[i], sCh[(j0 + u) * pp + i], sCl[(j0 + u) * pp + i]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u;
+        if (j >= q) break;
+        const double y = (double)sh[u] + (double)sl[u];
+        if (j < q1)
+          Y1[j * ldy + r] = y;
+        else
+          Y2[(j - q1) * ldy + r] = y;
+      }
     }
   }
 }
@@ -544,13 +554,16 @@ void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda
   const size_t shm = (size_t)((p + 3) & ~3) * q * sizeof(T);
   const int nb = dblocks(n);
   if constexpr (std::is_same<T, double>::value) {
-    if (dense_df()) {  // hi and lo float tables: the same bytes as the double table
+    if (dense_df()) {  // hi and lo float tables, q padded to a multiple of 4
+      const size_t shm_df = (size_t)((p + 3) & ~3) * ((q + 3) & ~3) * 2 * sizeof(float);
       if (p <= 16)
-        note_launch(), combine_df_kernel<16><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<16><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
       else if (p <= 32)
-        note_launch(), combine_df_kernel<32><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<32><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+      else if (p <= 48)
+        note_launch(), combine_df_kernel<48><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
       else
-        note_launch(), combine_df_kernel<64><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<64><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
       return;
     }
   }

@@ -11,10 +11,15 @@ autotuned Chebyshev degree; used for captures of the PCG kernels
 ``apply``: the Jacobian apply of one precision on a device's linearization
 at the Laplace initial guess, repeated; used for single-kernel captures.
 
+``eigs``: one mixed Poisson solve, one warm-up eigensolve (10 eigenpairs to
+1e-8), then one more inside the NVTX range "eigs"; used for launch lists of the
+eigensolver (``ncu --nvtx --nvtx-include "eigs/"``).
+
 Usage:
   python -m paper_1403_7561_gb300.profile_driver step  [--workload NAME]
   python -m paper_1403_7561_gb300.profile_driver solve [--workload NAME]
   python -m paper_1403_7561_gb300.profile_driver apply [--workload NAME] [--precision 0|1] [--reps N]
+  python -m paper_1403_7561_gb300.profile_driver eigs  [--workload NAME]
 """
 import argparse
 import os
@@ -27,7 +32,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["step", "solve", "apply"])
+    ap.add_argument("mode", choices=["step", "solve", "apply", "eigs"])
     ap.add_argument("--workload", default="dqd_128x128x96_4K")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
@@ -42,14 +47,25 @@ def main():
     bias = dev["bias"]
     m = q.qcad_mesh_create(dev)
     phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    if a.mode in ("step", "solve"):
+    if a.mode in ("step", "solve", "eigs"):
         if a.launch:
             v, r, c = (int(x) for x in a.launch.split(","))
             q.qcad_set_launch(m, 2, v, r, c)
         else:
             q.qcad_autotune(m, bias, precision=1)
         opts = q.make_opts(precision=1, cheb_degree=0)
-    if a.mode == "solve":
+    if a.mode == "eigs":
+        q.qcad_poisson_solve(m, bias, opts, phi)
+        evecs = torch.empty(10, m.n_sub_dof, dtype=torch.float64, device="cuda")
+        q.qcad_schrodinger_eigs(m, bias, phi, nev=10, tol=1e-8, evecs=evecs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("eigs")
+        E, rep = q.qcad_schrodinger_eigs(m, bias, phi, nev=10, tol=1e-8, evecs=evecs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("eigs done: %d subdomain dof, %d FP32 + %d FP64 iterations" % (m.n_sub_dof, rep["newton_iters"],
+                                                                           rep["status_detail"]))
+    elif a.mode == "solve":
         rep = q.qcad_poisson_solve(m, bias, opts, phi)
         torch.cuda.synchronize()
         print("solve done: %d nodes, %d Newton, %d Krylov iterations" % (m.n_nodes, rep["newton_iters"],
