@@ -221,6 +221,35 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
                                   const double* m_eff, double tol, double* evals, double* evecs,
                                   qcad_solve_report* rep);
 
+/* Self-consistent Schrodinger-Poisson solve by the predictor-corrector scheme (Sec. II.C) for
+ * electrons confined in three dimensions. The quantum region is the Schrodinger subdomain; there
+ * the electron density of the Poisson equation is the predictor density of
+ * Eq. ApproxEDens3DConfined, n~(phi) = sum_i 4 |psi_i|^2 / (1 + exp((E_i - E_F - q(phi - phi_prev))
+ * / kT)) (exp(-a) for arguments a > 100), built from the nev lowest eigenpairs computed at phi_prev;
+ * elsewhere it stays semiclassical. The Schrodinger potential is V = q phi_ref - chi - q phi + V_xc(n)
+ * (Eq. SchrodPotEnergy) with the Hedin-Lundqvist V_xc of Eq. Vxc and the mass of Eq. mxc when
+ * use_vxc != 0. Steps: (1) semiclassical Newton solve; (2) eigenpairs (LOBPCG, relative residual
+ * eig_tol of the spectrum shifted so that the potential's minimum sits at 0.1 eV); (3) Newton solve
+ * with n~, warm-started at the previous potential, then n~ and V_xc at the new potential; (4) stop
+ * when k >= 2 and max |phi^(k) - phi^(k-1)| < tol_dphi (V), else repeat, at most max_iter times.
+ * tol_dphi <= 0 runs exactly max_iter iterations. phi: device, n_nodes, output. evals: host, nev
+ * (eV, from the last step (2)). nev must include every occupied level. NOT_CONVERGED when the
+ * tolerance is not reached; the report holds the per-iteration history. The mesh's residual uses the
+ * quantum density only inside this call. */
+#define QCAD_SP_HIST 64
+typedef struct {
+  int sp_iters;                  /* outer iterations run */
+  int converged;
+  double dphi_inf;               /* max |phi^(k) - phi^(k-1)| of the last iteration, V */
+  double n_quantum;              /* electrons in the quantum region (integral of n~ at the final phi) */
+  double seconds;                /* host wall clock of the call */
+  double dphi_hist[QCAD_SP_HIST];  /* max |phi^(k) - phi^(k-1)| per iteration */
+  double e1_hist[QCAD_SP_HIST];    /* lowest eigenvalue per iteration, eV */
+} qcad_sp_report;
+qcad_status qcad_sp_solve(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int nev,
+                          const double* m_eff, double eig_tol, double tol_dphi, int max_iter, int use_vxc,
+                          double* phi, double* evals, qcad_sp_report* rep);
+
 /* The adjoint capacitance (as qcad_adjoint) and the Schrodinger eigenpairs (as
  * qcad_schrodinger_eigs) at one converged potential phi, computed concurrently:
  * the eigensolve runs on a second stream of the mesh from a second host thread

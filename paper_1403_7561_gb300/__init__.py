@@ -85,6 +85,20 @@ class SolveReport(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+SP_HIST = 64
+
+
+class SpReport(C.Structure):
+    _fields_ = [("sp_iters", C.c_int), ("converged", C.c_int), ("dphi_inf", C.c_double), ("n_quantum", C.c_double),
+                ("seconds", C.c_double), ("dphi_hist", C.c_double * SP_HIST), ("e1_hist", C.c_double * SP_HIST)]
+
+    def as_dict(self):
+        k = min(self.sp_iters, SP_HIST)
+        return {"sp_iters": self.sp_iters, "converged": bool(self.converged), "dphi_inf": self.dphi_inf,
+                "n_quantum": self.n_quantum, "seconds": self.seconds, "dphi_hist": list(self.dphi_hist)[:k],
+                "e1_hist": list(self.e1_hist)[:k]}
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _sigs = {
@@ -107,6 +121,8 @@ _sigs = {
                           _P, C.POINTER(SolveReport)],
     "qcad_poisson_solve_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P),
                                  C.POINTER(SolveReport)],
+    "qcad_sp_solve": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), C.c_int, _D, C.c_double, C.c_double, C.c_int,
+                      C.c_int, _P, _D, C.POINTER(SpReport)],
     "qcad_profile_enable": [_P, C.c_int],
     "qcad_profile_reset": [_P],
     "qcad_profile_read": [_P, C.c_int, C.POINTER(C.c_int64), _D],
@@ -325,6 +341,22 @@ def qcad_schrodinger_eigs(mesh: Mesh, bias: dict, phi, nev=10, m_eff=(0.19, 0.19
                                              me, float(tol), ev,
                                              _dptr(evecs, mesh.n_sub_dof * nev, name="evecs", allow_none=True),
                                              C.byref(rep)), allow_not_converged)
+    d = rep.as_dict()
+    d["status"] = STATUS[code]
+    return list(ev), d
+
+
+def qcad_sp_solve(mesh: Mesh, bias: dict, phi, opts=None, nev=10, m_eff=(0.19, 0.19, 0.19), eig_tol=1e-9,
+                  tol_dphi=1e-5, max_iter=60, use_vxc=True, allow_not_converged=False):
+    """Self-consistent Schrodinger-Poisson solve (predictor-corrector); phi is written; returns (evals, report)."""
+    b = make_bias(bias)
+    o = opts if opts is not None else make_opts()
+    me = (C.c_double * 3)(*m_eff)
+    ev = (C.c_double * nev)()
+    rep = SpReport()
+    code = _check(_lib.qcad_sp_solve(mesh.handle, C.byref(b), C.byref(o), int(nev), me, float(eig_tol),
+                                     float(tol_dphi), int(max_iter), int(bool(use_vxc)),
+                                     _dptr(phi, mesh.n_nodes, name="phi"), ev, C.byref(rep)), allow_not_converged)
     d = rep.as_dict()
     d["status"] = STATUS[code]
     return list(ev), d

@@ -14,6 +14,9 @@
 namespace qcad {
 void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out);
 Phys make_phys(const qcad_mesh_s* m, const qcad_bias* b);
+qcad_status sp_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, int nev, const double* m_eff,
+                     double eig_tol, double tol_dphi, int max_iter, int use_vxc, double* phi, double* evals,
+                     qcad_sp_report* rep);
 void set_contacts(qcad_mesh_s* m, const qcad_bias* b, const Phys& P, double* phi, double* gate_vals, double* ohm_val);
 qcad_status poisson_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* theta,
                           double* phi, qcad_solve_report* rep);
@@ -174,6 +177,16 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
   return guarded([&] {
     need_mesh(m);
     return qcad::schrodinger_eigs(m, b, phi, nev, m_eff, tol, evals, evecs, rep);
+  });
+}
+
+qcad_status qcad_sp_solve(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int nev, const double* m_eff,
+                          double eig_tol, double tol_dphi, int max_iter, int use_vxc, double* phi, double* evals,
+                          qcad_sp_report* rep) {
+  return guarded([&] {
+    need_mesh(m);
+    if (!o) throw qcad::Error(QCAD_ERR_INVALID_ARG, "null solver options");
+    return qcad::sp_solve(m, b, o, nev, m_eff, eig_tol, tol_dphi, max_iter, use_vxc, phi, evals, rep);
   });
 }
 

@@ -202,7 +202,20 @@ __global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant_
     const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
     const double th = a.theta ? a.theta[e] : 0.0;
     if (semi) {
-      const Charge ch = charge_at(a.P, v);
+      Charge ch = charge_at(a.P, v);
+      if (a.qd.w != nullptr) {
+        // in the quantum region the predictor density n~ replaces the semiclassical n (Sec. II.C)
+        const int iq = i - a.qd.i0, jq = j - a.qd.j0, kq = k - a.qd.k0;
+        if (iq >= 0 && jq >= 0 && kq >= 0 && iq < a.qd.nx && jq < a.qd.ny && kq < a.qd.nz) {
+          double nt, dnt;
+          qd_density(a.qd, iq + (long long)a.qd.nx * (jq + (long long)a.qd.ny * kq), l, v, a.P.EF, a.P.inv_kT, nt,
+                     dnt);
+          ch.rho += ch.n - nt;
+          ch.drho += ch.dn - dnt;
+          ch.n = nt;
+          ch.dn = dnt;
+        }
+      }
       f = -a.P.qe * wdet * (ch.rho + th);
       c = -a.P.qe * wdet * ch.drho;
       nq = wdet * ch.n;

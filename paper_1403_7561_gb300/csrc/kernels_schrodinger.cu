@@ -80,7 +80,7 @@ static int dblocks(long long n) {
 // cV_q = (q phi_ref - chi - q phi(x_q)) * w|J| for every subdomain element (Eq. SchrodPotEnergy).
 template <class T>
 __global__ void potential_kernel(SubdomainMap sm, const double* phi, double V0, const double* hx,
-                                 const double* hy, const double* hz, T* cV, double* vmin) {
+                                 const double* hy, const double* hz, const double* vxq, T* cV, double* vmin) {
   const long long ne = (long long)sm.nxs * sm.nys * sm.nzs;
   double lo = 1e300;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
@@ -103,7 +103,7 @@ __global__ void potential_kernel(SubdomainMap sm, const double* phi, double V0, 
     const double wdet = hx[i] * hy[j] * hz[k] * 0.125;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const double V = V0 - q[s];
+      const double V = V0 - q[s] + (vxq ? vxq[8 * e + s] : 0.0);
       lo = fmin(lo, V);
       cV[8 * e + s] = (T)(V * wdet);
     }
@@ -118,14 +118,14 @@ __global__ void potential_kernel(SubdomainMap sm, const double* phi, double V0, 
 
 template <class T>
 void launch_potential(const SubdomainMap& sm, const double* phi, double V0, const double* hx, const double* hy,
-                      const double* hz, T* cV, double* vmin, cudaStream_t s) {
+                      const double* hz, const double* vxq, T* cV, double* vmin, cudaStream_t s) {
   const long long ne = (long long)sm.nxs * sm.nys * sm.nzs;
-  note_launch(), potential_kernel<T><<<dblocks(ne), DT, 0, s>>>(sm, phi, V0, hx, hy, hz, cV, vmin);
+  note_launch(), potential_kernel<T><<<dblocks(ne), DT, 0, s>>>(sm, phi, V0, hx, hy, hz, vxq, cV, vmin);
 }
 template void launch_potential<float>(const SubdomainMap&, const double*, double, const double*, const double*,
-                                      const double*, float*, double*, cudaStream_t);
+                                      const double*, const double*, float*, double*, cudaStream_t);
 template void launch_potential<double>(const SubdomainMap&, const double*, double, const double*, const double*,
-                                       const double*, double*, double*, cudaStream_t);
+                                       const double*, const double*, double*, double*, cudaStream_t);
 
 // Interior-DOF <-> full subdomain node vector (column-major blocks).
 __global__ void pack_kernel(SubdomainMap sm, int nvec, double* full, long long ldf, double* dof, long long ldd,

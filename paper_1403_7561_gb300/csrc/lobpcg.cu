@@ -55,10 +55,15 @@ struct SubSetup {
   DevBuf cV64, cV32, dinv, interior;
   double vmin;
   double inv_kx;    // 1 / kappa_x = 2 m_x / hbar^2 (scale of the separable mass stencil)
+  double shift = 0.0;  // constant added to the potential (eV)
 };
 
+// vxq: an extra potential energy at the subdomain's Gauss points (eV, [element][point]) or null;
+// shift_floor > 0: the whole potential is raised by the constant that brings its minimum to
+// shift_floor (returned in S.shift, subtracted from the eigenvalues), so that every eigenvalue
+// stays well away from zero for the relative residual test.
 static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, const double* m_eff, int need32,
-                      SubSetup& S, const EigIo& io) {
+                      SubSetup& S, const EigIo& io, const double* vxq = nullptr, double shift_floor = 0.0) {
   if (!m->has_sub) throw Error(QCAD_ERR_INVALID_ARG, "mesh has no Schrodinger subdomain");
   for (int d = 0; d < 3; ++d)
     if (!(m_eff[d] > 0)) throw Error(QCAD_ERR_INVALID_ARG, "effective masses must be > 0");
@@ -102,18 +107,27 @@ static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, con
   double* vmin_d = io.stats + 40;
   const double big = 1e300;
   CK(cudaMemcpyAsync(vmin_d, &big, sizeof(double), cudaMemcpyHostToDevice, s));
-  launch_potential<double>(sm, phi, P.phi_ref - P.chi, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz,
-                           S.cV64.as<double>(), vmin_d, s);
-  if (need32) {
-    S.cV32.ensure(nes * 8 * sizeof(float) + 64);
-    launch_potential<float>(sm, phi, P.phi_ref - P.chi, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, S.cV32.as<float>(),
-                            vmin_d, s);
+  auto potentials = [&](double V0) {
+    CK(cudaMemcpyAsync(vmin_d, &big, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_potential<double>(sm, phi, V0, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, vxq, S.cV64.as<double>(), vmin_d,
+                             s);
+    if (need32) {
+      S.cV32.ensure(nes * 8 * sizeof(float) + 64);
+      launch_potential<float>(sm, phi, V0, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, vxq, S.cV32.as<float>(), vmin_d,
+                              s);
+    }
+    CK(cudaGetLastError());
+    double vmin_shift = 0;
+    CK(cudaMemcpyAsync(&vmin_shift, vmin_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    S.vmin = vmin_shift - 100.0;
+  };
+  potentials(P.phi_ref - P.chi);
+  S.shift = 0.0;
+  if (shift_floor > 0.0 && S.vmin < shift_floor) {
+    S.shift = shift_floor - S.vmin;
+    potentials(P.phi_ref - P.chi + S.shift);
   }
-  CK(cudaGetLastError());
-  double vmin_shift = 0;
-  CK(cudaMemcpyAsync(&vmin_shift, vmin_d, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  S.vmin = vmin_shift - 100.0;
   // Jacobi preconditioner from the kinetic diagonal, interior mask
   std::vector<double> dinv(S.ns, 0.0);
   std::vector<unsigned char> inter(S.ns, 0);
@@ -565,13 +579,14 @@ static void init_run(LobpcgRun<T>& L, qcad_mesh_s* m, const EigIo& io, SubSetup*
 
 qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias* b, const double* phi, int nev,
                                 const double* m_eff, double tol, double* evals, double* evecs,
-                                qcad_solve_report* rep) {
+                                qcad_solve_report* rep, const double* vxq = nullptr, double shift_floor = 0.0,
+                                const double* x0 = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!b || !phi || !m_eff || !evals) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
   if (nev < 1 || nev > 16) throw Error(QCAD_ERR_INVALID_ARG, "nev must be in [1, 16]");
   if (!(tol > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tol must be > 0");
   SubSetup S;
-  setup_sub(m, b, phi, m_eff, 1, S, io);
+  setup_sub(m, b, phi, m_eff, 1, S, io, vxq, shift_floor);
   const double t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (S.ndof < 3 * (nev + 4)) throw Error(QCAD_ERR_INVALID_ARG, "subdomain too small for nev");
   cudaStream_t s = io.s;
@@ -592,6 +607,16 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   init_run<float>(A, m, io, &S, nb, nev, w32, dinv32.as<float>());
   A.pre = &pre;
   launch_random_block<float>(ns, nb, ns, S.interior.as<unsigned char>(), 0x51ED5EEDull, A.Sx, s);
+  if (x0) {
+    // warm start: the first nev columns from the given vectors (interior nodes), the guard
+    // columns stay random
+    DevBuf full;
+    full.ensure((size_t)ns * nev * sizeof(double) + 64);
+    CK(cudaMemsetAsync(full.p, 0, (size_t)ns * nev * sizeof(double), s));
+    launch_pack(S.sm, nev, full.as<double>(), ns, const_cast<double*>(x0), S.ndof, 1, s);
+    launch_d2f(ns * nev, full.as<double>(), A.Sx, s);
+    CK(cudaStreamSynchronize(s));
+  }
   A.apply(0);
   A.rr_x();
   // the FP32 phase stops at 3e-6 relative residual, above where single-precision LOBPCG loses
@@ -611,7 +636,7 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   // final Rayleigh-Ritz with fresh FP64 applies
   B.apply(0);
   B.rr_x();
-  for (int j = 0; j < nev; ++j) evals[j] = B.lam[j];
+  for (int j = 0; j < nev; ++j) evals[j] = B.lam[j] - S.shift;
   if (evecs) launch_pack(S.sm, nev, B.Sx, ns, evecs, S.ndof, 0, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
@@ -642,6 +667,16 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
 qcad_status schrodinger_eigs(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
                              double tol, double* evals, double* evecs, qcad_solve_report* rep) {
   return schrodinger_eigs_io(m, mesh_io(m), b, phi, nev, m_eff, tol, evals, evecs, rep);
+}
+
+// The eigensolve of the self-consistent loop: potential V(phi) + vxq, shifted so that its minimum
+// sits at 0.1 eV while LOBPCG runs (levels near the Fermi level would otherwise make the
+// relative residual test |lambda|-relative around lambda = 0).
+// x0 (interior nodes x nev, or null) starts the block: the previous iteration's eigenvectors.
+qcad_status schrodinger_eigs_sp(qcad_mesh_s* m, const qcad_bias* b, const double* phi, int nev, const double* m_eff,
+                                double tol, const double* vxq, const double* x0, double* evals, double* evecs,
+                                qcad_solve_report* rep) {
+  return schrodinger_eigs_io(m, mesh_io(m), b, phi, nev, m_eff, tol, evals, evecs, rep, vxq, 0.1, x0);
 }
 
 // The eigensolve on the mesh's second stream and scratch (created on first use), for running

@@ -139,6 +139,10 @@ struct qcad_mesh_s {
   qcad::DevBuf scal_x;                           // their PCG scalars
   std::shared_ptr<void> adj_ctx;                 // cached batched-PCG context of the adjoint
   std::shared_ptr<void> mg;                      // multigrid hierarchy (built on first use)
+  // self-consistent Schrodinger-Poisson loop: quantum density of the residual while active
+  qcad::QuantumDensity qd{};
+  bool qd_active = false;
+  qcad::DevBuf sp_w, sp_phiq, sp_vxq, sp_evecs, sp_prev;
   qcad::DevBuf phi_a, phi_b, R, diag, stats, counts, scal, scratch;
   qcad::DevBuf el_res;                     // residual corner contributions, 16 doubles per element
   qcad::PcgScalars* h_scal = nullptr;      // pinned host mirror

@@ -389,6 +389,7 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   a.linear = linear;
   a.diag = diag_out;
   a.stats = m->stats.as<double>();
+  if (m->qd_active) a.qd = m->qd;  // predictor density in the quantum region (Sec. II.C)
   CK(cudaMemsetAsync(a.stats, 0, 2 * sizeof(double), s));
   if (counts_out) {
     a.counts = m->counts.as<double>();

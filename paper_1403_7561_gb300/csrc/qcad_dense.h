@@ -19,7 +19,8 @@ struct SubdomainMap {
 
 template <class T>
 void launch_potential(const SubdomainMap& sm, const double* phi, double V0, const double* hx, const double* hy,
-                      const double* hz, T* cV, double* vmin, cudaStream_t s);
+                      const double* hz, const double* vxq /* extra potential at the Gauss points or null */, T* cV,
+                      double* vmin, cudaStream_t s);
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s);
 // G1 = A^T B1 and, if B2 is not null, G2 = A^T B2 (p x p each, row-major, FP64, overwritten;

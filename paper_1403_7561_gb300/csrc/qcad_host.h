@@ -67,6 +67,7 @@ struct ResidualArgs {
   double* counts;            // [n_dots] accumulated electron counts or null
   double* stats;             // [2] {max|R| (as ordered bits), sum R^2} or null
   int linear;
+  QuantumDensity qd;         // quantum density in the quantum region (inactive: qd.w null)
 };
 
 template <class T>

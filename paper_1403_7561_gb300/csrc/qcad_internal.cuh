@@ -74,6 +74,48 @@ struct DotBoxes {
   double b[8][6];         // x0, x1, y0, y1, z0, z1 of element centroids
 };
 
+// Quantum electron density of the self-consistent Schrodinger-Poisson loop (Sec. II.C) in the
+// quantum region (an element box): the predictor density of Eq. ApproxEDens3DConfined,
+// n~(phi) = sum_i w_i / (1 + exp((E_i - E_F - (phi - phi_prev)) / kT)) at the Gauss points, with
+// w_i = 4 |psi_i|^2 there. Inactive when w is null.
+constexpr int QD_MAX_STATES = 16;
+struct QuantumDensity {
+  const double* w;        // [quantum element][Gauss point][state]
+  const double* phiq;     // [quantum element][Gauss point]: phi the eigenpairs were computed at
+  double E[QD_MAX_STATES];  // eigenvalues, eV
+  int nev;
+  int i0, j0, k0, nx, ny, nz;  // first element and extent of the quantum region
+};
+
+// Occupation 1 / (1 + e^a) and g = -df/da, with exp(-a) for a > 100 (the paper's safeguard for
+// states far above the Fermi level; exp(-a) is below half the smallest subnormal beyond 746).
+__device__ __forceinline__ void qd_fermi(double a, double& f, double& g) {
+  if (a > 100.0) {
+    f = a > 746.0 ? 0.0 : exp(-a);
+    g = f;
+  } else {
+    const double e = exp(a);
+    f = 1.0 / (1.0 + e);
+    g = f * (1.0 - f);
+  }
+}
+
+// n~ and d n~/d phi at Gauss point q of quantum element qe, at potential phi (E_F in eV, ik = 1/kT).
+__device__ __forceinline__ void qd_density(const QuantumDensity& qd, long long qe, int q, double phi, double EF,
+                                           double ik, double& n, double& dn) {
+  const double dphi = phi - qd.phiq[8 * qe + q];
+  const double* w = qd.w + (8 * qe + q) * qd.nev;
+  double s = 0.0, ds = 0.0;
+  for (int i = 0; i < qd.nev; ++i) {
+    double f, g;
+    qd_fermi((qd.E[i] - EF - dphi) * ik, f, g);
+    s += w[i] * f;
+    ds += w[i] * g;
+  }
+  n = s;
+  dn = ds * ik;
+}
+
 // ---------------------------------------------------------------------------
 // Gauss-point interpolation on the reference element: the 1D matrix
 // B[node][qp] = [[a, b], [b, a]], a = (1 + 1/sqrt3)/2, b = (1 - 1/sqrt3)/2,

@@ -202,3 +202,74 @@ def test_adjoint_and_eigs_concurrently(q, dqd):
     # errors of either half surface as the call's status
     with pytest.raises(q.QcadError):
         q.qcad_adjoint_eigs(m, dev["bias"], phig, opts, nev=17)
+
+
+# ---------------------------------------------------------------------------
+# Self-consistent Schrodinger-Poisson loop (Sec. II.C), against the oracle's loop.
+
+def sp_device():
+    # plungers that put about ten electrons in the dot levels, the sixth level still empty
+    dev = W.five_gate_device(n=(16, 16, 12), T=4.0)
+    V = list(dev["bias"]["V_gate"])
+    V[1] = V[3] = 0.9
+    dev["bias"]["V_gate"] = V
+    return dev
+
+
+@pytest.fixture(scope="module")
+def sp_oracle_k3():
+    from oracle import sp as OSP
+    dev = sp_device()
+    return dev, OSP.sp_solve(dev, nev=6, fixed_iters=3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sp_iterations_match_oracle(q, sp_oracle_k3, precision):
+    # three predictor-corrector iterations: the same potential, levels, density and history
+    dev, (phi_o, E_o, rep_o) = sp_oracle_k3
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    E, rep = q.qcad_sp_solve(m, dev["bias"], phi, q.make_opts(precision=precision), nev=6, eig_tol=1e-10,
+                             tol_dphi=0.0, max_iter=3)
+    assert rep["status"] == "OK" and rep["sp_iters"] == 3
+    assert np.max(np.abs(phi.cpu().numpy() - phi_o)) <= 1e-9
+    assert np.max(np.abs(np.array(E) - E_o)) <= 1e-10          # eV; levels sit near E_F = 0
+    assert abs(rep["n_quantum"] - rep_o["n_quantum"]) <= 1e-8 * rep_o["n_quantum"]
+    assert np.max(np.abs(np.array(rep["dphi_hist"]) - np.array(rep_o["dphi"]))) <= 1e-9
+    assert np.max(np.abs(np.array(rep["e1_hist"]) - np.array(rep_o["E1"]))) <= 1e-10
+
+
+def test_sp_converges_to_the_oracle_fixed_point(q):
+    from oracle import sp as OSP
+    dev = sp_device()
+    phi_o, E_o, rep_o = OSP.sp_solve(dev, nev=6, tol=1e-8, max_iter=80)
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    E, rep = q.qcad_sp_solve(m, dev["bias"], phi, q.make_opts(precision=1), nev=6, eig_tol=1e-10, tol_dphi=1e-8,
+                             max_iter=80)
+    assert rep["status"] == "OK" and rep["converged"]
+    d = np.array(rep["dphi_hist"])
+    assert np.all(d[2:] <= d[1:-1] * (1 + 1e-6))                # monotonic after the first correction
+    assert np.max(np.abs(phi.cpu().numpy() - phi_o)) <= 1e-7     # both within 1e-8 of one fixed point
+    assert np.max(np.abs(np.array(E) - E_o)) <= 1e-8
+
+
+def test_sp_depleted_dot_and_bad_arguments(q):
+    # default gates: every level sits tens of meV above E_F, the quantum region holds no electrons
+    dev = W.five_gate_device(n=(16, 16, 12), T=4.0)
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    E, rep = q.qcad_sp_solve(m, dev["bias"], phi, q.make_opts(precision=1), nev=4, tol_dphi=1e-6, max_iter=10)
+    assert rep["status"] == "OK" and rep["sp_iters"] <= 3
+    assert rep["n_quantum"] < 1e-20 and min(E) > 0.02
+    for kw in (dict(nev=0), dict(nev=17), dict(max_iter=0), dict(eig_tol=0.0)):
+        args = dict(nev=4, tol_dphi=1e-6, max_iter=3)
+        args.update(kw)
+        with pytest.raises(q.QcadError) as e:
+            q.qcad_sp_solve(m, dev["bias"], phi, q.make_opts(precision=1), **args)
+        assert e.value.code == 1
+    # the mesh's own Poisson solve is semiclassical again after the loop
+    rep2 = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), phi)
+    from oracle.poisson import PoissonProblem
+    phi_o, _ = PoissonProblem(dev).solve()
+    assert np.max(np.abs(phi.cpu().numpy() - phi_o)) <= 1e-9
