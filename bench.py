@@ -37,6 +37,7 @@ METRIC = "Poisson solves/s & op-apply HBM GB/s; mixed vs FP64 at same residual"
 WORKLOAD = "dqd_128x128x96_4K"
 NEV = 10
 SAMPLE_N = (32, 32, 24)  # bounded CPU sample of the same device for the oracle timing
+SP_PLUNGER_V = 0.70  # both plunger gates in the Schrodinger-Poisson measurement (about 2.6 electrons)
 
 
 def parse():
@@ -47,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-sp", action="store_true", help="skip the self-consistent Schrodinger-Poisson solve")
     ap.add_argument("--sequential", action="store_true",
                     help="run the adjoint and the eigensolve one after the other (per-kernel profiles)")
     ap.add_argument("--cheb-degree", type=int, default=0,
@@ -392,6 +394,30 @@ def native_arm(args):
                 "krylov_iters": fp64_rep["krylov_iters_total"], "final_res_inf": fp64_rep["final_res_inf"],
                 "max_abs_dphi_vs_mixed_V": float(torch.max(torch.abs(phi - phi_mixed)).item())}
 
+    # Self-consistent Schrodinger-Poisson solve (Sec. II.C predictor-corrector, V_xc on) of the same
+    # device with both plungers at SP_PLUNGER_V (a few electrons in the dot levels), to the paper's
+    # potential tolerance 1e-5 V; timed with CUDA events around the whole call
+    sp = None
+    if not args.no_sp:
+        sp_bias = dict(bias, V_gate=list(bias["V_gate"]))
+        sp_bias["V_gate"][1] = sp_bias["V_gate"][3] = SP_PLUNGER_V
+        phi_sp = torch.zeros(n_nodes, dtype=torch.float64, device="cuda")
+        ts, rep_sp, E_sp = [], None, None
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            E_sp, rep_sp = q.qcad_sp_solve(m, sp_bias, phi_sp, mixed, nev=NEV, eig_tol=1e-8, tol_dphi=1e-5,
+                                           max_iter=100, use_vxc=True, allow_not_converged=True)
+            b_.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b_) / 1000.0)
+        sp = {"workload": "%s, plungers %.2f V, %d states, V_xc on" % (args.workload, SP_PLUNGER_V, NEV),
+              "seconds": min(ts), "sp_solves_per_s": 1.0 / min(ts), "status": rep_sp["status"],
+              "sp_iters": rep_sp["sp_iters"], "final_dphi_V": rep_sp["dphi_inf"],
+              "electrons_in_quantum_region": rep_sp["n_quantum"], "E_meV": [1e3 * e for e in E_sp]}
+
     cpu = None
     if rank == 0 and world == 1:
         dt, nodes = oracle_sample()
@@ -419,6 +445,7 @@ def native_arm(args):
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
+            "schrodinger_poisson": sp,
             "poisson_only": {"mixed": {"solves_per_s": mixed_rate, "newton_iters": mixed_rep["newton_iters"],
                                        "krylov_iters": mixed_rep["krylov_iters_total"],
                                        "final_res_inf": mixed_rep["final_res_inf"]},
