@@ -265,10 +265,14 @@ qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solv
 /* Batched form (no counterpart in the paper, which solves one device at a
  * time; the operator of every instance is the one of qcad_poisson_solve):
  * n independent meshes of any sizes, each with its own bias, solved by a
- * lockstep Newton iteration whose FP32 Jacobi-PCG iterations advance all
- * unconverged instances with one apply launch and one update launch (a work
- * table maps blocks to (instance, tile)); chunks of 8 iterations are replayed
- * from a captured CUDA graph and instances drop out on their own
+ * lockstep Newton iteration: one residual launch for all instances (a work
+ * table maps blocks to (instance, tile)), and the linear solves either as
+ * FP32 Jacobi-PCG iterations advancing all unconverged instances with one
+ * apply launch and one update launch (o->cheb_degree 1; chunks of 8 iterations
+ * replayed from a captured CUDA graph), or (o->cheb_degree 0 or -1, every mesh
+ * large enough for a coarse level) as each instance's multigrid-preconditioned
+ * PCG, its captured 4-iteration graph replayed back to back with the others'
+ * and one status read per round. Instances drop out on their own
  * device-resident convergence flags. ms, bs, phis: host arrays of n entries
  * (phis[i] device [n_nodes of ms[i]], FP64, also the warm start). reps: host
  * [n] or NULL. o->precision must be 1 (mixed). All meshes must be distinct and

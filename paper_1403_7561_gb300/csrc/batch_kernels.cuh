@@ -66,6 +66,40 @@ __global__ void __launch_bounds__(QCAD_BX * BY) batch_residual_kernel(const Batc
   march_body<double, BY, ResidualOp>(e.g, op, e.kchunk, bx, by, bz);
 }
 
+// Entry of block b for the Gauss-point pass (entries sorted by qbegin).
+__device__ __forceinline__ int batch_find_q(const BatchResEntry* tab, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].qbegin <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Two-pass residual over the instances: Gauss-point pass, then the node gather.
+__global__ void __launch_bounds__(256) batch_residual_qp_kernel(const BatchResEntry* tab, int n_inst) {
+  const int b = blockIdx.x;
+  const BatchResEntry& e = tab[batch_find_q(tab, n_inst, b)];
+  const long long ne = (long long)e.g.nx * e.g.ny * e.g.nz;
+  residual_qp_body(e.g, e.a, e.el, e.el + 8 * ne, (long long)(b - e.qbegin) * 256 + threadIdx.x);
+}
+
+template <int BY>
+__global__ void __launch_bounds__(QCAD_BX * BY) batch_residual_gather_kernel(const BatchResEntry* tab, int n_inst) {
+  const int b = blockIdx.x;
+  const BatchResEntry& e = tab[batch_find(tab, n_inst, b)];
+  const int local = b - e.begin;
+  const int bx = local % e.tiles_x;
+  const int by = (local / e.tiles_x) % e.tiles_y;
+  const int bz = local / (e.tiles_x * e.tiles_y);
+  const long long ne = (long long)e.g.nx * e.g.ny * e.g.nz;
+  const ResidualGatherOp op = make_gather_op(e.a, e.el, e.el + 8 * ne);
+  march_body<double, BY, ResidualGatherOp>(e.g, op, e.kchunk, bx, by, bz);
+}
+
 __global__ void batch_stats_kernel(const BatchResEntry* tab, int n_inst, int mode, double* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
     double* st = tab[i].a.stats;
@@ -84,6 +118,12 @@ __global__ void batch_stats_kernel(const BatchResEntry* tab, int n_inst, int mod
 
 void launch_batch_residual(const BatchResEntry* tab, int n_inst, int total_blocks, cudaStream_t s) {
   note_launch(), batch_residual_kernel<8><<<total_blocks, dim3(QCAD_BX, 8), 0, s>>>(tab, n_inst);
+}
+
+void launch_batch_residual_2pass(const BatchResEntry* tab, int n_inst, int qp_blocks, int node_blocks,
+                                 cudaStream_t s) {
+  note_launch(), batch_residual_qp_kernel<<<qp_blocks, 256, 0, s>>>(tab, n_inst);
+  note_launch(), batch_residual_gather_kernel<8><<<node_blocks, dim3(QCAD_BX, 8), 0, s>>>(tab, n_inst);
 }
 
 void launch_batch_stats(const BatchResEntry* tab, int n_inst, int mode, double* out, cudaStream_t s) {

@@ -179,11 +179,11 @@ void launch_residual(const Grid<double>& g, const ResidualArgs& args, LaunchCfg 
 // (B = [[a, b], [b, a]] along each axis). Writes c_q, the element's corner contributions to the
 // load -(q/eps0) int (rho + theta) N_i (elR) and to the mass diagonal sum_q c_q N_i(q)^2 (elD),
 // [8 e + corner] each, and the dot electron counts.
-__global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant__ Grid<double> g,
-                                                          const __grid_constant__ ResidualArgs a, double* elR,
-                                                          double* elD) {
+// Body of pass 1 for thread t of a mesh (the batched form calls it with its own block numbering;
+// t & 7 == threadIdx.x & 7 there too).
+__device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const ResidualArgs& a, double* elR,
+                                                 double* elD, long long t) {
   const long long ne = (long long)g.nx * g.ny * g.nz;
-  const long long t = blockIdx.x * 256LL + threadIdx.x;
   const bool valid = t < 8 * ne;  // an element's 8 lanes share one warp and one validity
   const int e = valid ? (int)(t >> 3) : 0;
   const int l = threadIdx.x & 7;
@@ -251,6 +251,12 @@ __global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant_
   }
 }
 
+__global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant__ Grid<double> g,
+                                                          const __grid_constant__ ResidualArgs a, double* elR,
+                                                          double* elD) {
+  residual_qp_body(g, a, elR, elD, blockIdx.x * 256LL + threadIdx.x);
+}
+
 // Pass 2: the z-march node pass. Each node gathers the corner contributions of its elements
 // and adds the stiffness K phi (separable 27-point stencil); Dirichlet rows as in ResidualOp.
 struct ResidualGatherOp {
@@ -297,13 +303,7 @@ struct ResidualGatherOp {
   }
 };
 
-void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, double* el, LaunchCfg cfg,
-                           cudaStream_t s) {
-  const long long ne = (long long)g.nx * g.ny * g.nz;
-  double* elR = el;
-  double* elD = el + 8 * ne;
-  const int blocks = (int)((8 * ne + 255) / 256);
-  note_launch(), residual_qp_kernel<<<blocks, 256, 0, s>>>(g, args, elR, elD);
+__host__ __device__ inline ResidualGatherOp make_gather_op(const ResidualArgs& args, double* elR, double* elD) {
   ResidualGatherOp op = {};
   op.phi = args.phi;
   op.elR = elR;
@@ -315,6 +315,17 @@ void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, doub
   op.stats = args.stats;
   op.dinv32 = args.dinv32;
   op.b32 = args.b32;
+  return op;
+}
+
+void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, double* el, LaunchCfg cfg,
+                           cudaStream_t s) {
+  const long long ne = (long long)g.nx * g.ny * g.nz;
+  double* elR = el;
+  double* elD = el + 8 * ne;
+  const int blocks = (int)((8 * ne + 255) / 256);
+  note_launch(), residual_qp_kernel<<<blocks, 256, 0, s>>>(g, args, elR, elD);
+  const ResidualGatherOp op = make_gather_op(args, elR, elD);
   LaunchCfg c = cfg;
   if (c.by == 32) c.by = 16;
   run_march<double>(g, op, c, s);

@@ -756,7 +756,7 @@ static void batch_residual(BatchCtx& B, const std::vector<int>& idx, const std::
                            std::vector<ResStats>& R, std::vector<double>* step) {
   if (idx.empty()) return;
   std::vector<BatchResEntry> tr(idx.size());
-  int total = 0;
+  int total = 0, total_q = 0;
   for (size_t q = 0; q < idx.size(); ++q) {
     const int i = idx[q];
     qcad_mesh_s* m = B.ms[i];
@@ -783,13 +783,17 @@ static void batch_residual(BatchCtx& B, const std::vector<int>& idx, const std::
     e.tiles_y = (e.g.nyn + 8 - 3) / (8 - 2);
     e.begin = total;
     total += e.tiles_x * e.tiles_y * ((e.g.nzn + e.kchunk - 1) / e.kchunk);
+    m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
+    e.el = m->el_res.as<double>();
+    e.qbegin = total_q;
+    total_q += (int)((8 * m->n_elems + 255) / 256);
     m->lin_ver[1] += 1;  // the FP32 linearization of this mesh is rewritten
   }
   const int nq = (int)idx.size();
   CK(cudaMemcpyAsync(B.tab_r.p, tr.data(), tr.size() * sizeof(BatchResEntry), cudaMemcpyHostToDevice, B.s));
   const BatchResEntry* tab = B.tab_r.as<BatchResEntry>();
   launch_batch_stats(tab, nq, 0, nullptr, B.s);
-  launch_batch_residual(tab, nq, total, B.s);
+  launch_batch_residual_2pass(tab, nq, total_q, total, B.s);
   launch_batch_stats(tab, nq, 2, B.rstats.as<double>(), B.s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(B.h_rstats, B.rstats.p, (size_t)3 * nq * sizeof(double), cudaMemcpyDeviceToHost, B.s));
@@ -830,6 +834,61 @@ static void batch_pcg(BatchCtx& B, const std::vector<double>& rtol, int maxit, s
     bool all = true;
     for (int i = 0; i < B.n; ++i) all = all && B.h_status[4 * i] != 0;
     if (all || ++guard > maxit / PCG_CHUNK + 4) break;
+  }
+  iters.assign(B.n, 0);
+  nonfinite.assign(B.n, 0);
+  for (int i = 0; i < B.n; ++i) {
+    iters[i] = rtol[i] > 0 ? B.h_status[4 * i + 1] : 0;
+    nonfinite[i] = B.h_status[4 * i + 2];
+  }
+}
+
+// The batched linear solve with each instance's multigrid-preconditioned PCG: every round
+// replays the captured 4-iteration graph of each unfinished instance back to back on the batch
+// stream, then one status gather and one host read serve all instances.
+static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit, std::vector<int>& iters,
+                         std::vector<int>& nonfinite) {
+  for (int i = 0; i < B.n; ++i) {
+    qcad_mesh_s* m = B.ms[i];
+    PcgGraph& G = m->graph32;
+    const bool prof_match = m->prof.on == !G.events.empty();
+    if (!G.exec || G.key != (const void*)B.vecs[i].x || !prof_match || G.degree != DEG_MG) {
+      build_graph<float>(m, B.vecs[i], DEG_MG);
+      G.key = (const void*)B.vecs[i].x;
+    }
+    PcgScalars* h = B.h_sc + i;
+    std::memset(h, 0, sizeof(PcgScalars));
+    h->tol2 = rtol[i] * rtol[i];
+    h->maxit = maxit;
+    h->degree = DEG_MG;
+    h->theta = 1.0;
+    h->delta = 0.5;
+    if (!(rtol[i] > 0)) h->done = 1;
+    CK(cudaMemcpyAsync(B.scd[i], h, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
+    if (rtol[i] > 0) {
+      mg_setup(m, B.s);
+      mg_enqueue_init(m, B.vecs[i], B.scd[i], B.s);
+    }
+  }
+  CK(cudaGetLastError());
+  std::vector<char> active(B.n);
+  for (int i = 0; i < B.n; ++i) active[i] = rtol[i] > 0;
+  int guard = 0;
+  for (;;) {
+    for (int i = 0; i < B.n; ++i) {
+      if (!active[i]) continue;
+      CK(cudaGraphLaunch(B.ms[i]->graph32.exec, B.s));
+      note_launch(mg_launches_per_iteration(B.ms[i]) * B.ms[i]->graph32.chunk);
+    }
+    launch_batch_status(B.tab_v.as<BatchVecEntry>(), B.n, B.status.as<int>(), B.s);
+    CK(cudaMemcpyAsync(B.h_status, B.status.p, (size_t)4 * B.n * sizeof(int), cudaMemcpyDeviceToHost, B.s));
+    CK(cudaStreamSynchronize(B.s));
+    bool any = false;
+    for (int i = 0; i < B.n; ++i) {
+      if (active[i] && B.h_status[4 * i] != 0) active[i] = 0;
+      any = any || active[i];
+    }
+    if (!any || ++guard > maxit / MG_CHUNK + 4) break;
   }
   iters.assign(B.n, 0);
   nonfinite.assign(B.n, 0);
@@ -1099,6 +1158,10 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
     B.kch.push_back(ms[i]->batch_kchunk);
   }
   batch_setup(B);
+  // the instances' multigrid-preconditioned PCG (cheb_degree 0 or -1) when every mesh has a
+  // hierarchy, else the one-launch-per-iteration batched Jacobi PCG (cheb_degree 1)
+  bool use_mg = o->cheb_degree == 0 || o->cheb_degree == -1;
+  for (int i = 0; i < n && use_mg; ++i) use_mg = mg_prepare(ms[i]);
   const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   const int maxn = o->max_newton > 0 ? o->max_newton : 100;
   B.P.resize(n);
@@ -1132,7 +1195,10 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
     // Laplace initial guesses to 1e-3 (rho = 0), all instances at once
     batch_residual(B, all, pa, 1, R, nullptr);
     for (int i = 0; i < n; ++i) rtol[i] = 1e-3;
-    batch_pcg(B, rtol, maxk, iters, nonf);
+    if (use_mg)
+      batch_pcg_mg(B, rtol, maxk, iters, nonf);
+    else
+      batch_pcg(B, rtol, maxk, iters, nonf);
     for (int i = 0; i < n; ++i) {
       kry[i] += iters[i];
       if (nonf[i]) bad[i] = 1;
@@ -1157,7 +1223,10 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
       if (nR > 0) rtol[i] = std::max(rtol[i], std::min(1e-2, 0.1 * o->newton_tol_R / nR));
     }
     if (!any) break;
-    batch_pcg(B, rtol, maxk, iters, nonf);
+    if (use_mg)
+      batch_pcg_mg(B, rtol, maxk, iters, nonf);
+    else
+      batch_pcg(B, rtol, maxk, iters, nonf);
     std::vector<int> search;
     for (int i = 0; i < n; ++i) {
       if (!(rtol[i] > 0)) continue;

@@ -215,12 +215,17 @@ struct BatchResEntry {
   ResidualArgs a;
   int kchunk;
   int tiles_x, tiles_y;
-  int begin;
+  int begin;       // first block of the node pass (z-march tiles)
+  int qbegin;      // first block of the Gauss-point pass (256 threads each)
+  double* el;      // the instance's corner-contribution scratch, 16 doubles per element
 };
 void launch_batch_pcg_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, int by, cudaStream_t s);
 // Plane-factorized batched PCG apply (8 warps, two rows per thread: tiles of 30 x 14 interior nodes).
 void launch_batch_lin_apply(const BatchApplyEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
 void launch_batch_residual(const BatchResEntry* tab, int n_inst, int total_blocks, cudaStream_t s);
+// Two-pass batched residual: Gauss-point pass over qp_blocks blocks, then the node pass.
+void launch_batch_residual_2pass(const BatchResEntry* tab, int n_inst, int qp_blocks, int node_blocks,
+                                 cudaStream_t s);
 // Per-instance stats slots: mode 0 zeroes the residual slots (stats[0] max |R| as ordered bits,
 // stats[1] sum R^2), mode 1 zeroes the trial-step slot stats[8], mode 2 gathers the three into
 // out[3i .. 3i+2].

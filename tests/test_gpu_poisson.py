@@ -257,11 +257,14 @@ def batch_devices():
     return [W.five_gate_device(n=s, seed=7, stream=i, T=4.0, with_subdomain=False) for i, s in enumerate(shapes)]
 
 
-def test_batched_solve_matches_oracle(q):
+@pytest.mark.parametrize("degree", [1, -1])
+def test_batched_solve_matches_oracle(q, degree):
+    # degree 1: one-launch batched Jacobi PCG; -1: each instance's multigrid PCG in lockstep
     devs = batch_devices()
     meshes = [q.qcad_mesh_create(d) for d in devs]
     phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
-    reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs], q.make_opts(precision=1), phis)
+    reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs],
+                                              q.make_opts(precision=1, cheb_degree=degree), phis)
     assert status == "OK", reps
     for d, phi, rep in zip(devs, phis, reps):
         P = PoissonProblem(d)
@@ -271,11 +274,13 @@ def test_batched_solve_matches_oracle(q):
         assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9, (d["nx"], d["ny"])
 
 
-def test_batched_solve_agrees_with_single_solves_and_warm_starts(q):
+@pytest.mark.parametrize("degree", [1, -1])
+def test_batched_solve_agrees_with_single_solves_and_warm_starts(q, degree):
     devs = batch_devices()[:3]
     meshes = [q.qcad_mesh_create(d) for d in devs]
     phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
-    _, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs], q.make_opts(precision=1), phis)
+    _, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs],
+                                           q.make_opts(precision=1, cheb_degree=degree), phis)
     assert status == "OK"
     for d, m, phi in zip(devs, meshes, phis):
         one = torch.zeros_like(phi)
@@ -283,7 +288,7 @@ def test_batched_solve_agrees_with_single_solves_and_warm_starts(q):
         assert torch.max(torch.abs(one - phi)).item() <= 1e-9
     # warm start from the converged potentials: every instance stops after at most one step
     reps, status = q.qcad_poisson_solve_batch(meshes, [d["bias"] for d in devs],
-                                              q.make_opts(precision=1, warm_start=1), phis)
+                                              q.make_opts(precision=1, warm_start=1, cheb_degree=degree), phis)
     assert status == "OK"
     assert all(r["newton_iters"] <= 1 for r in reps)
 
