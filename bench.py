@@ -159,13 +159,13 @@ class ClockSampler:
 # measured on: retake it when the kernel changes.
 NCU_TRAFFIC = {("apply32", "dqd_128x128x96_4K", 3, 8, 16): 65.3e6,
                # both passes of one residual evaluation; profiles/residual_fp64_dqd_128x128x96_4K.md
-               ("residual", "dqd_128x128x96_4K", 3, 8, 16): 441.3e6}
+               ("residual", "dqd_128x128x96_4K", 3, 8, 16): 440.7e6}
 
 # FP64 floating-point operations per residual evaluation (2 per DFMA, 1 per DADD and DMUL,
 # counted by ncu over both passes at the fourth residual of a solve; the count follows the
 # carrier regime, i.e. how many quadrature points take the exponential branches), with the
 # command in profiles/residual_fp64_dqd_128x128x96_4K.md.
-NCU_FP64_FLOPS = {("residual", "dqd_128x128x96_4K"): 1235.5e6}
+NCU_FP64_FLOPS = {("residual", "dqd_128x128x96_4K"): 1006.2e6}
 
 # FP64 peak of this part: 2 DFMA lanes per SM per clock (ncu
 # sm__sass_thread_inst_executed_op_dfma_pred_on.avg.peak_sustained) x 2 flops x 152 SMs.

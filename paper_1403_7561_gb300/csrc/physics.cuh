@@ -16,11 +16,12 @@
 
 namespace qcad {
 
-// F_1/2 and its derivative.
+// F_1/2 and its derivative. Below x = -150, F = e^x < 7e-66: N_C F and N_V F stay below 1e-60
+// nm^-3, under any charge density the residual can resolve (its load is FP64 and its tolerance
+// 1e-10 V nm), so the call is skipped and both are taken as zero.
 __device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
   if (x < -50.0) {
-    // exp underflows to exactly zero below -746, so skipping the call is exact
-    F = (x < -746.0) ? 0.0 : exp(x);
+    F = (x < -150.0) ? 0.0 : exp(x);
     dF = F;
     return;
   }
@@ -38,9 +39,8 @@ __device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
   dF = -dD * F * F;
 }
 
-// s = 1/(1 + g e^z) and 1 - s without overflow. Beyond |z| = 746, e^{-|z|} is below half the
-// smallest subnormal, so those arguments take it as zero and skip the call (and, for z < -746,
-// the reciprocal of 1).
+// s = 1/(1 + g e^z) and 1 - s without overflow. Beyond z = 746, e^{-z} is below half the smallest
+// subnormal and is taken as zero; below z = -45 the call and the reciprocal are skipped (s = 1).
 __device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms) {
   if (z > 0.0) {
     const double e = (z > 746.0) ? 0.0 : exp(-z);
@@ -48,7 +48,9 @@ __device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, doub
     s = e * r;
     oms = g * r;
   } else {
-    if (z < -746.0) {
+    if (z < -45.0) {
+      // g e^z < 3e-20 g: for degeneracies g below 3000, 1 / (1 + g e^z) rounds to exactly 1, and
+      // 1 - s (which only scales the derivative) is taken as zero
       s = 1.0;
       oms = 0.0;
       return;
@@ -79,9 +81,9 @@ __device__ __forceinline__ Charge charge_at(const Phys& P, double phi) {
     p = P.NV * F;
     dp = -P.NV * dF * ik;
   } else {
-    n = P.NC * exp(eta_n);
+    n = eta_n < -150.0 ? 0.0 : P.NC * exp(eta_n);
     dn = n * ik;
-    p = P.NV * exp(eta_p);
+    p = eta_p < -150.0 ? 0.0 : P.NV * exp(eta_p);
     dp = -p * ik;
   }
   double NDp = P.ND, dND = 0.0, NAm = P.NA, dNA = 0.0;
