@@ -221,6 +221,30 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
                                   const double* m_eff, double tol, double* evals, double* evecs,
                                   qcad_solve_report* rep);
 
+/* Interface-charge calibration (Sec. III: the effective interface charge Q_it is the tuning
+ * parameter chosen so that the dot holds the wanted number of electrons). The fixed charge is
+ * theta = sigma * pattern (pattern: device, n_elems, the per-element density of a unit sheet,
+ * nm^-3 per nm^-2); sigma (nm^-2) is found by Newton on N_dot(sigma) = target_N with the adjoint
+ * slope dN/dsigma = (dN/dtheta) . pattern, safeguarded by bisection inside the bracket the
+ * iterates establish, each step a semiclassical Newton solve (warm-started after the first) and
+ * the dot counts. Stops when |N_dot - target_N| <= tol_N; at most max_iter (<= 32) solves. phi
+ * (device, n_nodes) and theta (device, n_elems) receive the last solve's potential and charge;
+ * sigma (host) the last sigma. NOT_CONVERGED when tol_N is not reached. */
+#define QCAD_CALIB_HIST 32
+typedef struct {
+  int iters;                        /* Poisson solves run */
+  int converged;
+  double N;                         /* dot electrons at the last solve */
+  double dN_dsigma;                 /* last adjoint slope, electrons per nm^-2 */
+  double seconds;
+  double sigma_hist[QCAD_CALIB_HIST];
+  double N_hist[QCAD_CALIB_HIST];
+} qcad_calib_report;
+qcad_status qcad_calibrate_sheet_charge(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int dot,
+                                        double target_N, const double* pattern, double sigma0, double tol_N,
+                                        int max_iter, double* phi, double* theta, double* sigma,
+                                        qcad_calib_report* rep);
+
 /* Self-consistent Schrodinger-Poisson solve by the predictor-corrector scheme (Sec. II.C) for
  * electrons confined in three dimensions. The quantum region is the Schrodinger subdomain; there
  * the electron density of the Poisson equation is the predictor density of

@@ -77,3 +77,29 @@ def adjoint(problem: PoissonProblem, phi, solver="cg"):
         lam_free = np.where(f, lam, 0.0)
         dN_dth[d] = problem.qe * np.sum(intN * lam_free[m.conn], axis=1)
     return dN_dV, dN_dth
+
+
+def calibrate_sheet_charge(dev, dot, target, pattern, bracket=(-5e-3, 5e-3), xtol=1e-14, **solve_kw):
+    """Interface sheet charge sigma (nm^-2) with N_dot(sigma) = target (Sec. III: the effective
+    interface charge Q_it is tuned until the dot holds the target number of electrons).
+
+    The fixed charge is theta = sigma * pattern (pattern: theta of a unit sheet). A plain bracketed
+    root find (Brent) on N_dot(sigma) - target with the oracle's Newton solve at each sigma.
+    Returns (sigma, N_dot, phi).
+    """
+    from scipy.optimize import brentq
+    pattern = np.asarray(pattern, dtype=np.float64)
+    cache = {}
+
+    def f(sig):
+        P = PoissonProblem(dev, fixed_charge=sig * pattern)
+        phi, _ = P.solve(**solve_kw)
+        N = electron_counts(P, phi)[dot]
+        cache[sig] = (N, phi)
+        return N - target
+
+    sig = brentq(f, bracket[0], bracket[1], xtol=xtol, rtol=4 * np.finfo(float).eps, maxiter=200)
+    if sig not in cache:
+        f(sig)
+    N, phi = cache[sig]
+    return sig, N, phi

@@ -99,6 +99,19 @@ class SpReport(C.Structure):
                 "e1_hist": list(self.e1_hist)[:k]}
 
 
+CALIB_HIST = 32
+
+
+class CalibReport(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("N", C.c_double), ("dN_dsigma", C.c_double),
+                ("seconds", C.c_double), ("sigma_hist", C.c_double * CALIB_HIST), ("N_hist", C.c_double * CALIB_HIST)]
+
+    def as_dict(self):
+        k = min(self.iters, CALIB_HIST)
+        return {"iters": self.iters, "converged": bool(self.converged), "N": self.N, "dN_dsigma": self.dN_dsigma,
+                "seconds": self.seconds, "sigma_hist": list(self.sigma_hist)[:k], "N_hist": list(self.N_hist)[:k]}
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _sigs = {
@@ -121,6 +134,8 @@ _sigs = {
                           _P, C.POINTER(SolveReport)],
     "qcad_poisson_solve_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P),
                                  C.POINTER(SolveReport)],
+    "qcad_calibrate_sheet_charge": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), C.c_int, C.c_double, _P, C.c_double,
+                                    C.c_double, C.c_int, _P, _P, _D, C.POINTER(CalibReport)],
     "qcad_sp_solve": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), C.c_int, _D, C.c_double, C.c_double, C.c_int,
                       C.c_int, _P, _D, C.POINTER(SpReport)],
     "qcad_profile_enable": [_P, C.c_int],
@@ -344,6 +359,27 @@ def qcad_schrodinger_eigs(mesh: Mesh, bias: dict, phi, nev=10, m_eff=(0.19, 0.19
     d = rep.as_dict()
     d["status"] = STATUS[code]
     return list(ev), d
+
+
+def qcad_calibrate_sheet_charge(mesh: Mesh, bias: dict, pattern, opts=None, dot=0, target=1.0, sigma0=0.0,
+                                tol_N=1e-9, max_iter=30, phi=None, theta=None, allow_not_converged=False):
+    """Interface sheet density sigma with N_dot = target; returns (sigma, report, phi, theta)."""
+    b = make_bias(bias)
+    o = opts if opts is not None else make_opts()
+    if phi is None:
+        phi = torch.zeros(mesh.n_nodes, dtype=torch.float64, device="cuda")
+    if theta is None:
+        theta = torch.zeros(mesh.n_elems, dtype=torch.float64, device="cuda")
+    sig = C.c_double()
+    rep = CalibReport()
+    code = _check(_lib.qcad_calibrate_sheet_charge(mesh.handle, C.byref(b), C.byref(o), int(dot), float(target),
+                                                   _dptr(pattern, mesh.n_elems, name="pattern"), float(sigma0),
+                                                   float(tol_N), int(max_iter), _dptr(phi, mesh.n_nodes, name="phi"),
+                                                   _dptr(theta, mesh.n_elems, name="theta"), C.byref(sig),
+                                                   C.byref(rep)), allow_not_converged)
+    d = rep.as_dict()
+    d["status"] = STATUS[code]
+    return sig.value, d, phi, theta
 
 
 def qcad_sp_solve(mesh: Mesh, bias: dict, phi, opts=None, nev=10, m_eff=(0.19, 0.19, 0.19), eig_tol=1e-9,

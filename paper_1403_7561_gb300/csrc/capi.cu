@@ -14,6 +14,9 @@
 namespace qcad {
 void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out);
 Phys make_phys(const qcad_mesh_s* m, const qcad_bias* b);
+qcad_status calibrate_sheet(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, int dot, double target,
+                            const double* pattern, double sigma0, double tol_N, int max_iter, double* phi,
+                            double* theta, double* sigma_out, qcad_calib_report* rep);
 qcad_status sp_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, int nev, const double* m_eff,
                      double eig_tol, double tol_dphi, int max_iter, int use_vxc, double* phi, double* evals,
                      qcad_sp_report* rep);
@@ -177,6 +180,16 @@ qcad_status qcad_schrodinger_eigs(qcad_mesh_t m, const qcad_bias* b, const doubl
   return guarded([&] {
     need_mesh(m);
     return qcad::schrodinger_eigs(m, b, phi, nev, m_eff, tol, evals, evecs, rep);
+  });
+}
+
+qcad_status qcad_calibrate_sheet_charge(qcad_mesh_t m, const qcad_bias* b, const qcad_solver_opts* o, int dot,
+                                        double target_N, const double* pattern, double sigma0, double tol_N,
+                                        int max_iter, double* phi, double* theta, double* sigma,
+                                        qcad_calib_report* rep) {
+  return guarded([&] {
+    need_mesh(m);
+    return qcad::calibrate_sheet(m, b, o, dot, target_N, pattern, sigma0, tol_N, max_iter, phi, theta, sigma, rep);
   });
 }
 

@@ -1134,6 +1134,87 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
   return QCAD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Interface-charge calibration (Sec. III): the sheet density sigma of a fixed-charge pattern
+// (theta = sigma * pattern) such that dot `dot` holds target_N electrons, by Newton on sigma with
+// the adjoint slope dN/dsigma = (dN/dtheta) . pattern, kept inside the bracket the iterates
+// establish (N rises with sigma) and bisected when a step would leave it.
+qcad_status calibrate_sheet(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, int dot, double target,
+                            const double* pattern, double sigma0, double tol_N, int max_iter, double* phi,
+                            double* theta, double* sigma_out, qcad_calib_report* rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  validate_bias(m, b);
+  validate_opts(o);
+  if (dot < 0 || dot >= m->dots.n) throw Error(QCAD_ERR_INVALID_ARG, "dot index out of range");
+  if (!pattern || !phi || !theta || !sigma_out) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
+  if (!(tol_N > 0) || !std::isfinite(target) || !std::isfinite(sigma0))
+    throw Error(QCAD_ERR_INVALID_ARG, "tol_N must be > 0 and target_N, sigma0 finite");
+  if (max_iter < 1 || max_iter > QCAD_CALIB_HIST) throw Error(QCAD_ERR_INVALID_ARG, "max_iter must be in [1, 32]");
+  cudaStream_t s = m->stream;
+  const long long ne = m->n_elems;
+  DevBuf dq;
+  dq.ensure((size_t)m->dots.n * ne * sizeof(double) + 64);
+  std::vector<double> dNdV(std::max(1, m->dots.n * m->n_gates)), N(QCAD_MAX_DOTS_K);
+  qcad_calib_report r{};
+  double sigma = sigma0, lo = 0, hi = 0, slope = 0;
+  bool have_lo = false, have_hi = false, converged = false;
+  qcad_solver_opts ow = *o;
+  qcad_status st = QCAD_OK;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    CK(cudaMemcpyAsync(theta, pattern, ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_scale<double>(ne, theta, sigma, s);
+    st = poisson_solve(m, b, &ow, theta, phi, nullptr);
+    if (st != QCAD_OK) break;
+    ow.warm_start = 1;
+    electron_counts(m, b, theta, phi, N.data());
+    const double f = N[dot] - target;
+    r.sigma_hist[it - 1] = sigma;
+    r.N_hist[it - 1] = N[dot];
+    r.N = N[dot];
+    if (std::fabs(f) <= tol_N) {
+      converged = true;
+      break;
+    }
+    if (f > 0) {
+      hi = sigma;
+      have_hi = true;
+    } else {
+      lo = sigma;
+      have_lo = true;
+    }
+    st = adjoint(m, b, o, phi, theta, dNdV.data(), dq.as<double>());
+    if (st != QCAD_OK) break;
+    double* acc = m->stats.as<double>() + 60;
+    CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
+    launch_dot<double>(ne, dq.as<double>() + (size_t)dot * ne, pattern, acc, s);
+    CK(cudaMemcpyAsync(m->h_small + 60, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    slope = m->h_small[60];
+    r.dN_dsigma = slope;
+    double next = slope > 0 ? sigma - f / slope : NAN;
+    const bool inside = std::isfinite(next) && (!have_lo || next > lo) && (!have_hi || next < hi);
+    if (!inside) {
+      if (have_lo && have_hi)
+        next = 0.5 * (lo + hi);
+      else  // no bracket on that side yet: step away from the known side
+        next = sigma + (f > 0 ? -1.0 : 1.0) * std::max(1e-4, 2.0 * std::fabs(sigma - (have_lo ? lo : hi)));
+    }
+    sigma = next;
+  }
+  *sigma_out = sigma;
+  r.iters = std::min(it, max_iter);
+  r.converged = converged ? 1 : 0;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rep) *rep = r;
+  if (st != QCAD_OK) return st;
+  if (!converged) {
+    set_message("the sheet-charge calibration did not reach tol_N");
+    return QCAD_ERR_NOT_CONVERGED;
+  }
+  return QCAD_OK;
+}
+
 qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                      double* const* phis, qcad_solve_report* reps) {
   const auto t0 = std::chrono::steady_clock::now();

@@ -1,8 +1,9 @@
 """Workloads for kernel profiling (ncu) of the library.
 
 ``step``: launch autotuning, then one warm-up pass of the full hot path on a
-device (mixed Newton with autotuned Chebyshev degree, dot counts, adjoint,
-eigenpairs), then one more pass; prints the library's kernel-launch counts.
+device (mixed Newton with the autotuned preconditioner, dot counts, adjoint,
+eigenpairs, one after the other), then one more pass inside the NVTX range
+"step"; prints the library's kernel-launch counts.
 
 ``solve``: launch autotuning, then one mixed-precision Poisson solve with the
 autotuned Chebyshev degree; used for captures of the PCG kernels
@@ -81,7 +82,11 @@ def main():
         c0 = q.qcad_launch_count()
         step()
         c1 = q.qcad_launch_count()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("step")  # ncu --nvtx --nvtx-include "step/" keeps this pass only
         step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         c2 = q.qcad_launch_count()
         torch.cuda.synchronize()
         print("launches warmup=%d step=%d" % (c1 - c0, c2 - c1))

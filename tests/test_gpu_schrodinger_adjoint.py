@@ -273,3 +273,21 @@ def test_sp_depleted_dot_and_bad_arguments(q):
     from oracle.poisson import PoissonProblem
     phi_o, _ = PoissonProblem(dev).solve()
     assert np.max(np.abs(phi.cpu().numpy() - phi_o)) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sheet_charge_calibration_matches_oracle(q, precision):
+    # Sec. III: the interface charge that leaves one electron in the dot, by Newton on the adjoint
+    # slope here and by a bracketed root find on the oracle
+    dev = W.five_gate_device(n=(12, 12, 8), T=4.0, with_subdomain=False)
+    pat = np.array(W.interface_sheet_pattern(dev))
+    sig_o, N_o, phi_o = OC.calibrate_sheet_charge(dev, 0, 1.0, pat)
+    m = q.qcad_mesh_create(dev)
+    sig, rep, phi, theta = q.qcad_calibrate_sheet_charge(m, dev["bias"], dt(pat),
+                                                         q.make_opts(precision=precision, cheb_degree=0),
+                                                         dot=0, target=1.0, tol_N=1e-10, max_iter=30)
+    assert rep["status"] == "OK" and rep["converged"] and rep["iters"] <= 12, rep
+    assert abs(rep["N"] - 1.0) <= 1e-10
+    assert abs(sig - sig_o) <= 1e-9 * abs(sig_o)
+    assert np.max(np.abs(phi.cpu().numpy() - phi_o)) <= 1e-8
+    assert np.max(np.abs(theta.cpu().numpy() - sig * pat)) <= 1e-15 * np.max(np.abs(sig * pat))

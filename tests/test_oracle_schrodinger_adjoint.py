@@ -166,3 +166,30 @@ def test_fd_capacitance_agrees_with_adjoint(dqd):
     Ca = C.Q_AF * dN_dV[:, 1]
     assert np.all(Cf > 0)
     assert np.max(np.abs(Cf - Ca) / np.abs(Ca)) < 0.1
+
+
+def test_sheet_charge_calibration_reaches_the_target():
+    # Sec. III: the effective interface charge is tuned so that the dot holds one electron; the
+    # count rises monotonically with a positive sheet, and the adjoint slope dN/dsigma equals the
+    # finite-difference slope of the calibrated count
+    from oracle.poisson import PoissonProblem
+    dev = W.five_gate_device(n=(12, 12, 8), T=4.0, with_subdomain=False)
+    pat = np.array(W.interface_sheet_pattern(dev))
+    sig, N, phi = C.calibrate_sheet_charge(dev, 0, 1.0, pat)
+    assert abs(N - 1.0) < 1e-9
+    Ns = []
+    for s in (sig - 1e-4, sig, sig + 1e-4):
+        P = PoissonProblem(dev, fixed_charge=s * pat)
+        ph, _ = P.solve()
+        Ns.append(C.electron_counts(P, ph)[0])
+    assert Ns[0] < Ns[1] < Ns[2]
+    P = PoissonProblem(dev, fixed_charge=sig * pat)
+    _, dNdq = C.adjoint(P, phi)
+    slope = float(dNdq[0] @ pat)
+    h = 1e-6
+    Pp = PoissonProblem(dev, fixed_charge=(sig + h) * pat)
+    Pm = PoissonProblem(dev, fixed_charge=(sig - h) * pat)
+    php, _ = Pp.solve(phi0=phi)
+    phm, _ = Pm.solve(phi0=phi)
+    fd = (C.electron_counts(Pp, php)[0] - C.electron_counts(Pm, phm)[0]) / (2 * h)
+    assert abs(slope - fd) <= 1e-5 * abs(fd)

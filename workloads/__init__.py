@@ -172,6 +172,20 @@ def interface_fixed_charge(dev: dict, seed: int, sigma_std=1e-4):
     return theta
 
 
+def interface_sheet_pattern(dev: dict):
+    """Per-element fixed charge (nm^-3) of a uniform interface sheet of 1 nm^-2: 1/h_z on the Si
+    element layer touching the Si/SiO2 interface, 0 elsewhere (the layer of
+    interface_fixed_charge). Element order: i + nx*(j + ny*k)."""
+    nx, ny = dev["nx"], dev["ny"]
+    nz = sum(L["n"] for L in dev["layers"])
+    k_if = dev["layers"][0]["n"] - 1
+    hz = dev["layers"][0]["thickness"] / dev["layers"][0]["n"]
+    pat = [0.0] * (nx * ny * nz)
+    for e in range(nx * ny):
+        pat[nx * ny * k_if + e] = 1.0 / hz
+    return pat
+
+
 def batch_instances(count=96, seed=4, sizes=tuple(range(48, 113, 8)), T=4.0):
     """Batched form: `count` five-gate instances with N^3 elements, N drawn from `sizes`."""
     rng = SplitMix64(seed)
