@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-sp", action="store_true", help="skip the self-consistent Schrodinger-Poisson solve")
+    ap.add_argument("--no-calib", action="store_true", help="skip the interface-charge calibration")
     ap.add_argument("--sequential", action="store_true",
                     help="run the adjoint and the eigensolve one after the other (per-kernel profiles)")
     ap.add_argument("--cheb-degree", type=int, default=0,
@@ -418,6 +419,26 @@ def native_arm(args):
               "sp_iters": rep_sp["sp_iters"], "final_dphi_V": rep_sp["dphi_inf"],
               "electrons_in_quantum_region": rep_sp["n_quantum"], "E_meV": [1e3 * e for e in E_sp]}
 
+    # Interface-charge calibration (Sec. III): the uniform interface sheet that leaves one electron in
+    # dot 0 at the step's gate voltages, Newton on the adjoint slope; timed around the whole call
+    calib = None
+    if not args.no_calib:
+        pat = torch.tensor(W.interface_sheet_pattern(dev), dtype=torch.float64, device="cuda")
+        ts, sig, crep = [], None, None
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            sig, crep, _, _ = q.qcad_calibrate_sheet_charge(m, bias, pat, mixed, dot=0, target=1.0, tol_N=1e-6,
+                                                            max_iter=30, allow_not_converged=True)
+            b_.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b_) / 1000.0)
+        calib = {"workload": "%s, dot 0 to 1 electron, uniform interface sheet" % args.workload,
+                 "seconds": min(ts), "status": crep["status"], "solves": crep["iters"],
+                 "sigma_per_cm2": sig * 1e14, "N": crep["N"]}
+
     cpu = None
     if rank == 0 and world == 1:
         dt, nodes = oracle_sample()
@@ -446,6 +467,7 @@ def native_arm(args):
             "gpu_launches": launches,
             "clocks": clk,
             "schrodinger_poisson": sp,
+            "interface_charge_calibration": calib,
             "poisson_only": {"mixed": {"solves_per_s": mixed_rate, "newton_iters": mixed_rep["newton_iters"],
                                        "krylov_iters": mixed_rep["krylov_iters_total"],
                                        "final_res_inf": mixed_rep["final_res_inf"]},
