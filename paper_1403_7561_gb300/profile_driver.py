@@ -16,11 +16,17 @@ at the Laplace initial guess, repeated; used for single-kernel captures.
 1e-8), then one more inside the NVTX range "eigs"; used for launch lists of the
 eigensolver (``ncu --nvtx --nvtx-include "eigs/"``).
 
+``batch``: the 96-instance batch of uneven meshes (48^3 .. 112^3 elements, 61.7M
+nodes): the batched Newton with each instance's multigrid PCG and with the
+one-launch batched Jacobi PCG, and the same instances solved one after the
+other; prints instances/s (wall clock around each call, best of three).
+
 Usage:
   python -m paper_1403_7561_gb300.profile_driver step  [--workload NAME]
   python -m paper_1403_7561_gb300.profile_driver solve [--workload NAME]
   python -m paper_1403_7561_gb300.profile_driver apply [--workload NAME] [--precision 0|1] [--reps N]
   python -m paper_1403_7561_gb300.profile_driver eigs  [--workload NAME]
+  python -m paper_1403_7561_gb300.profile_driver batch
 """
 import argparse
 import os
@@ -33,7 +39,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("mode", choices=["step", "solve", "apply", "eigs"])
+    ap.add_argument("mode", choices=["step", "solve", "apply", "eigs", "batch"])
     ap.add_argument("--workload", default="dqd_128x128x96_4K")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
@@ -44,6 +50,9 @@ def main():
     import paper_1403_7561_gb300 as q
     import workloads as W
 
+    if a.mode == "batch":
+        run_batch(q, W, torch)
+        return
     dev = W.get(a.workload)
     bias = dev["bias"]
     m = q.qcad_mesh_create(dev)
@@ -98,6 +107,44 @@ def main():
             q.qcad_poisson_jv(m, bias, phi, v, y, a.precision)
         torch.cuda.synchronize()
         print("apply done: %d nodes, precision %d, %d reps" % (m.n_nodes, a.precision, a.reps))
+
+
+def run_batch(q, W, torch):
+    import time
+    devs = W.batch_instances()
+    nodes = sum(W.n_nodes(d) for d in devs)
+    meshes = [q.qcad_mesh_create(d) for d in devs]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    biases = [d["bias"] for d in devs]
+
+    def timed(fn):
+        best = None
+        for _ in range(3):
+            for p in phis:
+                p.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best, out
+
+    print("instances %d, nodes %d" % (len(devs), nodes))
+    for name, deg in (("batched Newton, multigrid PCG per instance", -1), ("batched Newton, batched Jacobi PCG", 1)):
+        dt, (reps, st) = timed(lambda: q.qcad_poisson_solve_batch(meshes, biases,
+                                                                  q.make_opts(precision=1, cheb_degree=deg), phis))
+        print("%s: %s, %.3f s, %.1f instances/s, Newton max %d, Krylov max %d" % (
+            name, st, dt, len(devs) / dt, max(r["newton_iters"] for r in reps),
+            max(r["krylov_iters_total"] for r in reps)))
+
+    def sequential():
+        for m, b, p in zip(meshes, biases, phis):
+            q.qcad_poisson_solve(m, b, q.make_opts(precision=1, cheb_degree=-1), p)
+        return None
+
+    dt, _ = timed(sequential)
+    print("one instance after the other, multigrid PCG: %.3f s, %.1f instances/s" % (dt, len(devs) / dt))
 
 
 if __name__ == "__main__":
