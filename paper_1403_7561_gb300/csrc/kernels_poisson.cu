@@ -351,6 +351,40 @@ template void launch_apply<float>(const Grid<float>&, const ApplyArgs<float>&, L
 template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// Electron count of one dot: the semiclassical n at the Gauss points of the dot's elements (an
+// element box), weighted by w|J| and summed into *out; corners to Gauss points by the lane
+// butterflies of residual_qp_kernel.
+__global__ void __launch_bounds__(256) dot_count_kernel(const __grid_constant__ Grid<double> g, const double* phi,
+                                                        const unsigned char* layer_semi, const __grid_constant__ Phys P,
+                                                        int i0, int j0, int k0, int bx, int by, int bz, double* out) {
+  const long long ne = (long long)bx * by * bz;
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  const bool valid = t < 8 * ne;
+  const long long be = valid ? (t >> 3) : 0;
+  const int l = threadIdx.x & 7;
+  const int i = i0 + (int)(be % bx), j = j0 + (int)((be / bx) % by), k = k0 + (int)(be / ((long long)bx * by));
+  const bool semi = valid && layer_semi[k];
+  const double A = GaussConst<double>::a(), B = GaussConst<double>::b();
+  double v = 0.0;
+  if (semi)
+    v = __ldg(phi + (i + (l & 1)) + (long long)g.nxn * ((j + ((l >> 1) & 1)) + (long long)g.nyn * (k + (l >> 2))));
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 1);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 2);
+  v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 4);
+  double s[1] = {0.0};
+  if (semi) s[0] = g.hx[i] * g.hy[j] * g.hz[k] * 0.125 * charge_at(P, v).n;
+  block_sum_atomic<1>(s, out);
+}
+
+void launch_dot_count(const Grid<double>& g, const double* phi, const unsigned char* layer_semi, const Phys& P,
+                      const int box[6], double* out, cudaStream_t s) {
+  const long long ne = (long long)(box[1] - box[0]) * (box[3] - box[2]) * (box[5] - box[4]);
+  if (ne <= 0) return;
+  note_launch(), dot_count_kernel<<<(int)((8 * ne + 255) / 256), 256, 0, s>>>(
+      g, phi, layer_semi, P, box[0], box[2], box[4], box[1] - box[0], box[3] - box[2], box[5] - box[4], out);
+}
+
+// ---------------------------------------------------------------------------
 // dN_d/dphi nodal vector of one dot, in two passes.
 
 // Pass 1 of the count gradient: wdet dn/dphi at the quadrature points of dot d's elements,

@@ -626,12 +626,58 @@ qcad_status poisson_jv(qcad_mesh_s* m, const qcad_bias* b, const double* phi, co
   return QCAD_OK;
 }
 
+// Element box of dot d: the elements whose centroid lies in its coordinate box (a box again, the
+// node planes being sorted); false when it is empty.
+static bool dot_element_box(const qcad_mesh_s* m, int d, int box[6]) {
+  const double* B = m->dots.b[d];
+  const std::vector<double>* c[3] = {&m->xc, &m->yc, &m->zc};
+  for (int a = 0; a < 3; ++a) {
+    const std::vector<double>& x = *c[a];
+    int lo = -1, hi = -1;
+    for (int i = 0; i + 1 < (int)x.size(); ++i) {
+      const double xc = 0.5 * (x[i] + x[i + 1]);
+      if (xc >= B[2 * a] && xc <= B[2 * a + 1]) {
+        if (lo < 0) lo = i;
+        hi = i + 1;
+      }
+    }
+    if (lo < 0) return false;
+    box[2 * a] = lo;
+    box[2 * a + 1] = hi;
+  }
+  return true;
+}
+
 qcad_status electron_counts(qcad_mesh_s* m, const qcad_bias* b, const double* theta, const double* phi, double* N) {
   validate_bias(m, b);
   if (!phi || !N) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
   ensure_newton(m);
   const Phys P = make_phys(m, b);
-  eval_residual(m, P, phi, theta, 0, 0, N);
+  // the dots' element boxes; overlapping boxes (an element counts for the first dot that holds it)
+  // take the residual's fused count instead
+  int boxes[QCAD_MAX_DOTS_K][6];
+  bool have[QCAD_MAX_DOTS_K];
+  bool overlap = false;
+  for (int d = 0; d < m->dots.n; ++d) {
+    have[d] = dot_element_box(m, d, boxes[d]);
+    for (int e = 0; e < d && have[d]; ++e)
+      if (have[e] && boxes[d][0] < boxes[e][1] && boxes[e][0] < boxes[d][1] && boxes[d][2] < boxes[e][3] &&
+          boxes[e][2] < boxes[d][3] && boxes[d][4] < boxes[e][5] && boxes[e][4] < boxes[d][5])
+        overlap = true;
+  }
+  if (overlap) {
+    eval_residual(m, P, phi, theta, 0, 0, N);
+    return QCAD_OK;
+  }
+  cudaStream_t s = m->stream;
+  double* acc = m->counts.as<double>();
+  CK(cudaMemsetAsync(acc, 0, QCAD_MAX_DOTS_K * sizeof(double), s));
+  for (int d = 0; d < m->dots.n; ++d)
+    if (have[d]) launch_dot_count(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), P, boxes[d], acc + d, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(m->h_small + 8, acc, QCAD_MAX_DOTS_K * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int d = 0; d < m->dots.n; ++d) N[d] = m->h_small[8 + d];
   return QCAD_OK;
 }
 

@@ -90,6 +90,9 @@ struct LaunchCfg {
 };
 
 void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg, cudaStream_t s);
+// Adds the electron count of the elements [box0, box1) x [box2, box3) x [box4, box5) to *out.
+void launch_dot_count(const Grid<double>& g, const double* phi, const unsigned char* layer_semi, const Phys& P,
+                      const int box[6], double* out, cudaStream_t s);
 // Same outputs in two passes (carrier density once per quadrature point); el: 16 doubles per element.
 void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& a, double* el, LaunchCfg cfg, cudaStream_t s);
 
