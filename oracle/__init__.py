@@ -17,8 +17,12 @@ of Semiconductor Quantum Dots", arXiv:1403.7561):
 - ``fem``          Q1 element quadrature and sparse assembly (Eq. 11, Eq. 18)
 - ``poisson``      nonlinear Poisson Newton solve (Sec. II.A)
 - ``schrodinger``  effective-mass Schrodinger eigenpairs (Sec. II.B, Eq. 26)
+- ``boundary``     surface terms: charged gates (Robin) and surface charges
+                   (Sec. II.A.4, Eq. NeuBC4fc)
 - ``capacitance``  dot electron counts, finite-difference capacitance
                    (Sec. III) and the adjoint sensitivities
+- ``sp``           self-consistent Schrodinger-Poisson predictor-corrector
+                   loop (Sec. II.C)
 
 Parity status of every function is listed in its docstring ("pinned by ...").
 """

@@ -8,8 +8,11 @@ Test infrastructure only.
 - Adjoint (reading of the differentiation form): with R(phi, V, theta) = 0 on
   the free nodes and phi held at the gate values on Dirichlet nodes,
       J_ff lambda = dN/dphi_f,
-      dN/dV_g   = dN/dphi_D . e_g - lambda . (J_fD e_g),
-      dN/dtheta_e = (q/eps0) sum_{a in e, free} lambda_a int_e N_a.
+      dN/dV_g   = dN/dphi_D . e_g - lambda . (J_fD e_g - db_f/dV_g),
+      dN/dtheta_e = (q/eps0) sum_{a in e, free} lambda_a int_e N_a,
+      dN/dsigma  = lambda . db_f/dsigma   (surface charges, charged gates),
+  b the surface load of ``oracle.boundary`` (db/dV_g nonzero only for a
+  charged gate, whose potential enters through the Robin condition).
   J is symmetric, so the adjoint system uses J itself.
 """
 from __future__ import annotations
@@ -73,10 +76,31 @@ def adjoint(problem: PoissonProblem, phi, solver="cg"):
         lam[f] = solve_spd(Jff, g[f], solver)
         for gi in range(n_g):
             e_g = (problem.gate[D] == gi).astype(np.float64)  # d phi_D / d V_g (Eq. ContOnIns)
-            dN_dV[d, gi] = g[D] @ e_g - lam[f] @ (JfD @ e_g)
+            db = problem.dV.get(gi, np.zeros(m.n_nodes))[f]
+            dN_dV[d, gi] = g[D] @ e_g - lam[f] @ (JfD @ e_g - db)
         lam_free = np.where(f, lam, 0.0)
         dN_dth[d] = problem.qe * np.sum(intN * lam_free[m.conn], axis=1)
     return dN_dV, dN_dth
+
+
+def surface_charge_sensitivity(problem: PoissonProblem, phi, solver="cg"):
+    """dN_d/dsigma (electrons per nm^-2) at a converged phi.
+
+    Returns (by_sheet [n_dots x n_surface_charges], by_gate {g: [n_dots]} for charged gates):
+    dN/dsigma = lambda . db_f/dsigma with J_ff lambda = dN/dphi_f.
+    """
+    f = problem.free
+    Jff = problem.jacobian(phi)[f][:, f]
+    n_d = len(problem.dev["dots"])
+    sheet = np.zeros((n_d, len(problem.dsig_sheet)))
+    gate = {g: np.zeros(n_d) for g in problem.dsig_gate}
+    for d in range(n_d):
+        lam = solve_spd(Jff, count_gradient(problem, phi, d)[f], solver)
+        for s, db in enumerate(problem.dsig_sheet):
+            sheet[d, s] = lam @ db[f]
+        for g, db in problem.dsig_gate.items():
+            gate[g][d] = lam @ db[f]
+    return sheet, gate
 
 
 def calibrate_sheet_charge(dev, dot, target, pattern, bracket=(-5e-3, 5e-3), xtol=1e-14, **solve_kw):
