@@ -190,6 +190,10 @@ class Mesh:
     """Owning handle of a qcad mesh built from a device description dictionary."""
 
     def __init__(self, dev: dict, stream=None):
+        unsupported = [G.get("name", str(i)) for i, G in enumerate(dev["gates"]) if G.get("robin")]
+        if unsupported or dev.get("surface_charges"):
+            raise NotImplementedError("libqcad solves Dirichlet gates only: charged (Robin) gates %s and surface "
+                                      "charges are not supported" % unsupported)
         if not torch.cuda.is_available():
             raise RuntimeError("libqcad needs a CUDA device")
         self.dev = dev

@@ -52,3 +52,20 @@ def test_invalid_mesh_is_rejected_without_gpu_work(lib_path):
     out = ctypes.c_void_p()
     assert lib.qcad_mesh_create(None, None, ctypes.byref(out)) == 1  # QCAD_ERR_INVALID_ARG
     assert b"null" in lib.qcad_last_error()
+
+
+def test_binding_rejects_surface_terms_it_does_not_solve(lib_path):
+    # charged gates and surface charges exist in the oracle only: the library must not ignore them
+    import copy
+
+    import paper_1403_7561_gb300 as q
+    import workloads as W
+    dev = W.five_gate_device(n=(8, 8, 6))
+    d1 = copy.deepcopy(dev)
+    d1["gates"][1]["robin"] = dict(sigma=1e-3, d=10.0)
+    with pytest.raises(NotImplementedError, match="P1"):
+        q.Mesh(d1)
+    d2 = copy.deepcopy(dev)
+    d2["surface_charges"] = [dict(z=90.0, x0=0.0, x1=200.0, y0=0.0, y1=200.0, sigma=1e-3)]
+    with pytest.raises(NotImplementedError):
+        q.Mesh(d2)
