@@ -69,3 +69,6 @@ def test_binding_rejects_surface_terms_it_does_not_solve(lib_path):
     d2["surface_charges"] = [dict(z=90.0, x0=0.0, x1=200.0, y0=0.0, y1=200.0, sigma=1e-3)]
     with pytest.raises(NotImplementedError):
         q.Mesh(d2)
+    if not q.torch.cuda.is_available():
+        with pytest.raises(RuntimeError, match="CUDA"):       # an ordinary device passes the check
+            q.Mesh(dev)
