@@ -6,6 +6,8 @@ each (near-)degenerate cluster; adjoint gate sensitivities and fixed-charge
 gradients 1e-8 relative to the largest entry; finite-difference capacitance
 1e-6 relative (two Newton solves to the FP64 residual 1e-10 on each side).
 """
+import copy
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -137,6 +139,37 @@ def test_adjoint_matches_oracle(q, dqd, precision, degree):
     assert np.max(np.abs(dNdV - dNdV_o)) <= 1e-8 * np.max(np.abs(dNdV_o))
     g = dq.cpu().numpy().reshape(m.n_dots, m.n_elems)
     assert np.max(np.abs(g - dNdq_o)) <= 1e-8 * np.max(np.abs(dNdq_o))
+
+
+@pytest.mark.parametrize("degree", [1, -1])
+def test_bias_sweep_in_one_batched_launch(q, dqd, degree):
+    # a plunger sweep of one device: each bias point an instance of the batched Newton (a mesh per
+    # point), then each point's dot counts and 2x5 dN/dV from the adjoint, against the oracle
+    dev, P, phi = dqd
+    biases = []
+    for dv in (-0.05, 0.0, 0.05):
+        b = copy.deepcopy(dev["bias"])
+        b["V_gate"][1] += dv
+        biases.append(b)
+    meshes = [q.qcad_mesh_create(dev) for _ in biases]
+    phis = [torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda") for m in meshes]
+    opts = q.make_opts(precision=1, cheb_degree=degree)
+    reps, status = q.qcad_poisson_solve_batch(meshes, biases, opts, phis)
+    assert status == "OK", reps
+    N0 = []
+    for m, b, ph in zip(meshes, biases, phis):
+        Pb = PoissonProblem(dev, bias=b)
+        phi_o, rep = Pb.solve(phi0=phi)
+        assert rep["converged"]
+        assert np.max(np.abs(ph.cpu().numpy() - phi_o)) <= 1e-9
+        N = np.array(q.qcad_electron_counts(m, b, ph))
+        N_o = OC.electron_counts(Pb, phi_o)
+        assert np.max(np.abs(N - N_o)) <= 1e-8 * np.max(np.abs(N_o))
+        dNdV = np.array(q.qcad_adjoint(m, b, ph, opts))
+        dNdV_o, _ = OC.adjoint(Pb, phi_o)
+        assert np.max(np.abs(dNdV - dNdV_o)) <= 1e-8 * np.max(np.abs(dNdV_o))
+        N0.append(N[0])
+    assert N0[0] < N0[1] < N0[2]                                 # dot 0 fills as its plunger rises
 
 
 def test_fd_capacitance_matches_oracle(q, dqd):
