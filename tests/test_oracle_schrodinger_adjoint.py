@@ -6,6 +6,10 @@
   t_d = k_d pi h_d / L_d (the paper's 2D/3D infinite-well check, Sec. II.B).
 - Harmonic oscillator: E_0 = (3/2) hbar omega with O(h^2) convergence (the
   paper's parabolic-well check, Sec. II.B).
+- Triangular well: levels (hbar^2 F^2 / 2m)^(1/3) |a_i| with a_i the zeros of the Airy
+  function, O(h^2); finite square well: the roots of the even and odd matching
+  conditions k tan(ka) = kappa, -k cot(ka) = kappa, O(h^2) (the paper's 1D wells,
+  Sec. II.B), both as z-strips whose one transverse mode has a closed-form energy.
 - Appendix B: the paper's triangular-well formula gives E_1 = 7.11 meV at
   F = 8.256e6 V/m after the 25.003 meV shift (Sec. III).
 - Adjoint sensitivities against central finite differences of full solves.
@@ -17,6 +21,8 @@ import os
 
 import numpy as np
 import pytest
+import scipy.optimize
+import scipy.special
 
 import workloads as W
 from oracle import capacitance as C
@@ -85,6 +91,52 @@ def test_harmonic_oscillator_convergence():
     # first excited level is threefold degenerate at 2.5 hbar omega
     assert np.max(np.abs(Es[1][1:4] - 2.5 * hw)) < 0.05 * hw
     assert np.max(Es[1][1:4]) - np.min(Es[1][1:4]) < 1e-9 * hw
+
+
+def _strip_levels(Lz, nz, V_of_z, m, nev):
+    """z-levels of a 2 nm x 2 nm strip with two elements across x and y (one transverse mode, whose
+    discrete energy 2 x (hbar^2/2m) (6/h^2)(1 - cos(pi/2))/(2 + cos(pi/2)) is subtracted)."""
+    dev = dict(Lx=2.0, Ly=2.0, nx=2, ny=2, layers=[dict(material=0, thickness=Lz, n=nz)],
+               materials=[dict(W.SI)], gates=[], bottom_ohmic=0, dots=[],
+               subdomain=dict(i0=0, i1=2, j0=0, j1=2, k0=0, k1=nz), bias=dict(T=4.0, V_gate=[]))
+    mesh = Mesh(dev)
+    sel, inter = mesh.subdomain_elements(), mesh.subdomain_interior_nodes()
+    zq = np.einsum("qa,ea->eq", fem.NQ, mesh.elem_coords[:, :, 2])
+    H, M, _ = S.operators(mesh, sel, inter, (m, m, m), V_of_z(zq))
+    E, _ = S.lowest_eigenpairs(H, M, nev, sigma=-0.01)
+    return E - 2.0 * (physics.hbar2_over_2m0() / m) * 6.0 * 0.5
+
+
+def test_triangular_well_airy_levels():
+    # V = F z above a hard wall at z = 0: E_i = (hbar^2 F^2 / 2m)^(1/3) |a_i| (a_i Airy zeros); the
+    # far wall at 25 nm is 16 decay lengths past the third level's turning point
+    m, F = 0.98, 0.01                                       # m_l, 10 mV/nm
+    exact = -scipy.special.ai_zeros(3)[0] * (physics.hbar2_over_2m0() / m * F ** 2) ** (1.0 / 3.0)
+    errs = [np.abs(_strip_levels(25.0, nz, lambda z: F * z, m, 3) - exact) / exact for nz in (50, 100)]
+    assert np.all(np.abs(np.log2(errs[0] / errs[1]) - 2.0) < 0.05), errs
+    assert np.max(errs[1]) < 3e-3
+
+
+def test_finite_square_well_levels():
+    # well of half-width a = 5 nm and depth 0.3 eV (edges on node planes), one mass: the levels solve
+    # k tan(ka) = kappa (even) and -k cot(ka) = kappa (odd), k = sqrt(E/h2m), kappa = sqrt((V0-E)/h2m)
+    m, V0, a = 0.19, 0.3, 5.0
+    h2m = physics.hbar2_over_2m0() / m
+
+    def match(E, odd):
+        k, kap = math.sqrt(E / h2m), math.sqrt((V0 - E) / h2m)
+        return (-k / math.tan(k * a) if odd else k * math.tan(k * a)) - kap
+
+    exact = []
+    for odd, (lo, hi) in ((0, (0.0, 0.5)), (1, (0.5, 1.0)), (0, (1.0, 1.5))):  # ka / pi brackets
+        e_lo = h2m * ((lo * math.pi + 1e-9) / a) ** 2
+        e_hi = min(h2m * ((hi * math.pi - 1e-9) / a) ** 2, V0 - 1e-12)
+        exact.append(scipy.optimize.brentq(lambda E: match(E, odd), e_lo, e_hi, xtol=1e-16, rtol=1e-15))
+    exact = np.array(exact)
+    well = lambda z: np.where(np.abs(z - 20.0) < a, 0.0, V0)
+    errs = [np.abs(_strip_levels(40.0, nz, well, m, 3) - exact) / exact for nz in (80, 160)]
+    assert np.all(np.abs(np.log2(errs[0] / errs[1]) - 2.0) < 0.05), errs
+    assert np.max(errs[1]) < 4e-3
 
 
 def test_appendix_b_triangular_well_e1():
