@@ -332,6 +332,10 @@ def native_arm(args):
     share = prof[dom][1] / total_ms if total_ms else None
     tune_key = tuple(tune32[:3])
 
+    # measured arithmetic peaks of this GPU (microbenchmarks, outside the timed region): the
+    # measured side of the FP64 residual's ALU roofline
+    alu = q.qcad_alu_peaks()
+
     # rooflines use launches inside the Newton solves of the timed steps: the adjoint and the
     # eigensolve run concurrently on two streams, so their launches overlap
     def hbm_roofline(cls):
@@ -356,6 +360,9 @@ def native_arm(args):
                 "traffic_unit": "bytes per evaluation (ncu dram read + write, cold cache, both passes)",
                 "peak_kind": "derived: 2 DFMA lanes/SM/clock x 2 flops x 152 SMs x median SM clock under load",
                 "flops_kind": "FP64 flops per evaluation counted by ncu (2 DFMA + DADD + DMUL)",
+                "peak_measured": alu["fp64_tflops"],
+                "frac_of_measured": (ach / alu["fp64_tflops"]) if ach else None,
+                "peak_measured_kind": "FP64 FMA microbenchmark on this GPU (qcad_alu_peaks)",
                 "launches": nl, "avg_ms": ms / nl if nl else None,
                 "timed_launches": "residual evaluations inside the Newton solves of the timed steps"}
 
@@ -469,6 +476,7 @@ def native_arm(args):
                        "cheb_degree": args.cheb_degree or q.qcad_launch_info(m, 2)[3],
                        "adjoint_eigensolve": "sequential" if args.sequential else "concurrent (two streams)"},
             "roofline": roof,
+            "alu_peaks": dict(alu, kind="microbenchmarks on this GPU: FMA chains (2 flops per FMA), FP64 exp()"),
             "op_apply_roofline": op_apply,
             "kernel_profile_ms": {c: round(v[1], 3) for c, v in prof.items()},
             "cpu_baseline": cpu,

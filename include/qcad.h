@@ -364,6 +364,18 @@ qcad_status qcad_poisson_residual_noalloc(const qcad_device* dev, const qcad_bia
                                           const double* fixed_charge_elem, const double* phi, double* R,
                                           double* stats);
 
+/* Arithmetic peaks of the current CUDA device, measured by microbenchmarks (no
+ * counterpart in the paper): the denominators of the roofline of a kernel bound
+ * by arithmetic rather than memory, such as the FP64 Newton residual, whose
+ * carrier statistics (Sec. II.A.1-3) evaluate FP64 exponentials at every Gauss
+ * point. fp64_tflops and fp32_tflops: fused multiply-add throughput in TFLOP/s
+ * (2 flops per FMA); fp64_exp_per_s: FP64 exp() evaluations per second. Each
+ * kernel runs eight independent dependency chains per thread on 8 blocks of
+ * 256 threads per SM, once untimed and then three times timed with CUDA events
+ * on a private stream; the best run is reported (about 0.15 s in all). Host
+ * outputs, each may be NULL. Errors: CUDA. */
+qcad_status qcad_alu_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_exp_per_s);
+
 /* Number of CUDA kernels this library has launched in the process (kernels
  * inside replayed CUDA graphs included). Host output *count. */
 qcad_status qcad_launch_count(int64_t* count);

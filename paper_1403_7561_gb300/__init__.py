@@ -145,6 +145,7 @@ _sigs = {
     "qcad_autotune": [_P, C.POINTER(Bias), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                       C.POINTER(C.c_float)],
     "qcad_launch_count": [C.POINTER(C.c_int64)],
+    "qcad_alu_peaks": [_D, _D, _D],
     "qcad_poisson_residual_noalloc": [C.POINTER(Device), C.POINTER(Bias), _P, _P, _P, _P, _D],
     "qcad_last_error": [],
 }
@@ -432,6 +433,13 @@ def qcad_poisson_solve_batch(meshes, biases, opts, phis, allow_not_converged=Fal
     reps = (SolveReport * n)()
     code = _check(_lib.qcad_poisson_solve_batch(n, hs, bs, C.byref(opts), ps, reps), allow_not_converged)
     return [r.as_dict() for r in reps], STATUS[code]
+
+
+def qcad_alu_peaks():
+    """Measured FP64 / FP32 FMA throughput (TFLOP/s) and FP64 exp() evaluations per second of the current device."""
+    f64, f32, ex = C.c_double(), C.c_double(), C.c_double()
+    _check(_lib.qcad_alu_peaks(C.byref(f64), C.byref(f32), C.byref(ex)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value, "fp64_exp_per_s": ex.value}
 
 
 def qcad_profile_enable(mesh: Mesh, enable=True):

@@ -45,6 +45,7 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* var
                      float* best);
 qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* stream, const double* theta,
                              const double* phi, double* R, double* stats);
+qcad_status alu_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_exp_per_s);
 }  // namespace qcad
 
 static thread_local std::string g_last_error;
@@ -240,6 +241,10 @@ qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solv
 qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                      double* const* phis, qcad_solve_report* reps) {
   return guarded([&] { return qcad::poisson_solve_batch(n, ms, bs, o, phis, reps); });
+}
+
+qcad_status qcad_alu_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_exp_per_s) {
+  return guarded([&] { return qcad::alu_peaks(fp64_tflops, fp32_tflops, fp64_exp_per_s); });
 }
 
 qcad_status qcad_profile_enable(qcad_mesh_t m, int enable) {

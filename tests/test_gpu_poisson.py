@@ -309,3 +309,12 @@ def test_batched_solve_rejects_bad_batches(q):
                                               allow_not_converged=True)
     assert status == "NOT_CONVERGED"
     assert all(r["newton_iters"] == 1 for r in reps)
+
+
+def test_alu_peaks_are_plausible(q):
+    # the FP64 pipe of this part runs at a small fraction of the FP32 rate; an exp() costs tens of
+    # FP64 operations; a measured peak outside these bands means the microbenchmark lost its work
+    p = q.qcad_alu_peaks()
+    assert 0.3 < p["fp64_tflops"] < 5.0, p
+    assert p["fp32_tflops"] > 10.0 * p["fp64_tflops"], p
+    assert 1e9 < p["fp64_exp_per_s"] < p["fp64_tflops"] * 1e12, p
