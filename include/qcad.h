@@ -59,9 +59,30 @@ typedef struct {
 typedef struct { double x0, x1, y0, y1; } qcad_rect;          /* closed rectangle on the top face */
 typedef struct { double x0, x1, y0, y1, z0, z1; } qcad_box;   /* element-centroid box */
 
+/* Charged gate (Sec. II.A.4, the Robin condition): gate `gate` is pinned to its
+ * potential phi_0 (Eq. ContOnIns) a distance d outside the top surface, with a
+ * sheet charge q sigma on the surface, so that the outward flux is
+ * eps_s dphi/dn = eps_s (phi_0 - phi)/d + q sigma. Its surface is the top-plane
+ * faces with all four corners in the gate's rectangle; its nodes are unknowns,
+ * not Dirichlet nodes; eps_s is the permittivity of the top element layer.
+ * sigma > 0 is positive charge. */
+typedef struct {
+  int gate;       /* index into gates */
+  double sigma;   /* nm^-2 */
+  double d;       /* nm, > 0 (the paper uses 10) */
+} qcad_charged_gate;
+
+/* Surface charge on an explicit surface (Sec. II.A.4, Eq. NeuBC4fc): the jump of
+ * the normal displacement across the node plane at height z is q sigma over the
+ * faces of that plane with all four corners in the rectangle (on an outer face,
+ * an applied flux). z must be a node plane of the mesh. sigma > 0 is positive
+ * charge, nm^-2. */
+typedef struct { double z, x0, x1, y0, y1, sigma; } qcad_surface_charge;
+
 /* Layered box device on a structured Q1 hexahedral mesh: uniform spacing in x
  * and y, uniform within each z layer group (bottom to top). Gates are
- * Dirichlet patches on the top face z = Lz; the bottom face is an Ohmic
+ * Dirichlet patches on the top face z = Lz (charged gates carry the Robin
+ * condition instead, see qcad_charged_gate); the bottom face is an Ohmic
  * contact when bottom_ohmic is set; every other boundary is natural Neumann
  * (Sec. II.A.4). Dots are the semiconductor elements whose centroid lies in a
  * box (the paper's quantum region, Sec. III). The Schrodinger subdomain is the
@@ -86,6 +107,15 @@ typedef struct {
   const qcad_box* dots;
   int has_subdomain;
   int sub[6];
+  /* surface terms of the weak form (both lists may be empty). A device with either
+   * runs the element-gather Jacobian kernels and Jacobi or Chebyshev-Jacobi PCG: the
+   * multigrid preconditioner falls back to Jacobi, and the batched solve, the
+   * self-consistent Schrodinger-Poisson loop and the allocation-free residual reject
+   * it (INVALID_ARG). */
+  int n_charged_gates;                       /* at most n_gates, each gate at most once */
+  const qcad_charged_gate* charged_gates;
+  int n_surface_charges;
+  const qcad_surface_charge* surface_charges;
 } qcad_device;
 
 #define QCAD_MAX_DOTS 8

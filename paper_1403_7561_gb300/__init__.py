@@ -54,6 +54,15 @@ class Box(C.Structure):
                 ("z0", C.c_double), ("z1", C.c_double)]
 
 
+class ChargedGate(C.Structure):
+    _fields_ = [("gate", C.c_int), ("sigma", C.c_double), ("d", C.c_double)]
+
+
+class SurfaceCharge(C.Structure):
+    _fields_ = [("z", C.c_double), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("sigma", C.c_double)]
+
+
 class Device(C.Structure):
     _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
                 ("n_layers", C.c_int), ("layer_n", C.POINTER(C.c_int)),
@@ -62,7 +71,9 @@ class Device(C.Structure):
                 ("n_gates", C.c_int), ("gates", C.POINTER(Rect)),
                 ("gate_work_function_set", C.c_int), ("gate_work_function", C.c_double),
                 ("bottom_ohmic", C.c_int), ("n_dots", C.c_int), ("dots", C.POINTER(Box)),
-                ("has_subdomain", C.c_int), ("sub", C.c_int * 6)]
+                ("has_subdomain", C.c_int), ("sub", C.c_int * 6),
+                ("n_charged_gates", C.c_int), ("charged_gates", C.POINTER(ChargedGate)),
+                ("n_surface_charges", C.c_int), ("surface_charges", C.POINTER(SurfaceCharge))]
 
 
 class Bias(C.Structure):
@@ -191,40 +202,10 @@ class Mesh:
     """Owning handle of a qcad mesh built from a device description dictionary."""
 
     def __init__(self, dev: dict, stream=None):
-        unsupported = [G.get("name", str(i)) for i, G in enumerate(dev["gates"]) if G.get("robin")]
-        if unsupported or dev.get("surface_charges"):
-            raise NotImplementedError("libqcad solves Dirichlet gates only: charged (Robin) gates %s and surface "
-                                      "charges are not supported" % unsupported)
         if not torch.cuda.is_available():
             raise RuntimeError("libqcad needs a CUDA device")
         self.dev = dev
-        L = dev["layers"]
-        mats = dev["materials"]
-        self._keep = []
-        ln = (C.c_int * len(L))(*[l["n"] for l in L])
-        lt = (C.c_double * len(L))(*[l["thickness"] for l in L])
-        lm = (C.c_int * len(L))(*[l["material"] for l in L])
-        ma = (Material * len(mats))(*[Material(*[float(m[k]) if k != "semiconductor" else int(m[k])
-                                                 for k, _ in Material._fields_]) for m in mats])
-        gates = dev.get("gates", [])
-        ga = (Rect * max(1, len(gates)))(*[Rect(g["x0"], g["x1"], g["y0"], g["y1"]) for g in gates])
-        dots = dev.get("dots", [])
-        da = (Box * max(1, len(dots)))(*[Box(d["x0"], d["x1"], d["y0"], d["y1"], d["z0"], d["z1"]) for d in dots])
-        d = Device()
-        d.Lx, d.Ly, d.nx, d.ny = dev["Lx"], dev["Ly"], dev["nx"], dev["ny"]
-        d.n_layers, d.layer_n, d.layer_thickness, d.layer_material = len(L), ln, lt, lm
-        d.n_materials, d.materials = len(mats), ma
-        d.n_gates, d.gates = len(gates), ga
-        wf = dev.get("gate_work_function")
-        d.gate_work_function_set = 0 if wf is None else 1
-        d.gate_work_function = 0.0 if wf is None else float(wf)
-        d.bottom_ohmic = int(dev.get("bottom_ohmic", 1))
-        d.n_dots, d.dots = len(dots), da
-        S = dev.get("subdomain")
-        d.has_subdomain = 0 if S is None else 1
-        if S is not None:
-            for q, k in enumerate(("i0", "i1", "j0", "j1", "k0", "k1")):
-                d.sub[q] = int(S[k])
+        d, self._keep = _device_struct(dev)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -488,6 +469,15 @@ def _device_struct(dev: dict):
     if S is not None:
         for q, k in enumerate(("i0", "i1", "j0", "j1", "k0", "k1")):
             d.sub[q] = int(S[k])
+    # surface terms: charged gates (a gate's "robin" entry) and surface charges
+    charged = [ChargedGate(g, float(G["robin"].get("sigma", 0.0)), float(G["robin"].get("d", 10.0)))
+               for g, G in enumerate(gates) if G.get("robin")]
+    sheets = [SurfaceCharge(S_["z"], S_["x0"], S_["x1"], S_["y0"], S_["y1"], S_["sigma"])
+              for S_ in dev.get("surface_charges", [])]
+    keep.append((ChargedGate * max(1, len(charged)))(*charged))
+    keep.append((SurfaceCharge * max(1, len(sheets)))(*sheets))
+    d.n_charged_gates, d.charged_gates = len(charged), keep[6]
+    d.n_surface_charges, d.surface_charges = len(sheets), keep[7]
     return d, keep
 
 

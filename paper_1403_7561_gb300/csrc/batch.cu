@@ -39,14 +39,15 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* var
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
   // (variant, warps) shapes: element-gather 0, element-gather with two nodes per thread 1
   // (FP32), plane-factorized with one 2 or two 3 node rows per thread
+  // (charged gates: the element-gather kernels alone carry the Robin face term)
   std::vector<std::pair<int, int>> shapes;
   for (int r : {4, 8, 16, 32}) shapes.push_back({0, r});
-  if (precision == 1)
+  if (precision == 1 && !m->has_robin)
     for (int r : {4, 8, 16}) shapes.push_back({1, r});
   for (int r : {4, 8, 16, 32})
-    if (precision == 1 || r <= 8) shapes.push_back({2, r});
+    if ((precision == 1 || r <= 8) && !m->has_robin) shapes.push_back({2, r});
   for (int r : {4, 8, 16})
-    if (precision == 1 || r <= 8) shapes.push_back({3, r});
+    if ((precision == 1 || r <= 8) && !m->has_robin) shapes.push_back({3, r});
   for (const auto& sh : shapes) {
     const int variant = sh.first, r = sh.second;
     // z-chunk lengths that put whole waves of resident blocks on the SMs, plus fixed ones
@@ -73,13 +74,13 @@ qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* var
           a.v = v.as<double>();
           a.y = y.as<double>();
           a.c = c.as<double>();
-          launch_apply<double>(m->g64.g, a, cfg, s);
+          launch_apply<double>(m->g64.g, a, cfg, s, m->has_robin ? m->d_face64.as<double>() : nullptr);
         } else {
           ApplyArgs<float> a{};
           a.v = v.as<float>();
           a.y = y.as<float>();
           a.c = c.as<float>();
-          launch_apply<float>(m->g32.g, a, cfg, s);
+          launch_apply<float>(m->g32.g, a, cfg, s, m->has_robin ? m->d_face32.as<float>() : nullptr);
         }
       };
       run();
@@ -167,6 +168,8 @@ qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* b
   std::vector<std::pair<std::array<int, 3>, int>> buckets;
   for (int i = 0; i < n; ++i) {
     if (!ms[i]) throw Error(QCAD_ERR_INVALID_ARG, "null mesh in batch");
+    if (ms[i]->has_surface)
+      throw Error(QCAD_ERR_INVALID_ARG, "the batched solve does not take charged gates or surface charges");
     const std::array<int, 3> key = {ms[i]->nx, ms[i]->ny, ms[i]->nz};
     int ch = -1;
     for (auto& b : buckets)

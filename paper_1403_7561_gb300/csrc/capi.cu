@@ -284,6 +284,8 @@ qcad_status qcad_set_launch(qcad_mesh_t m, int family, int variant, int tile_row
       throw qcad::Error(QCAD_ERR_INVALID_ARG, "tile_rows must be 4, 8, 16 or 32");
     if (z_chunk < 1 || z_chunk > 4096) throw qcad::Error(QCAD_ERR_INVALID_ARG, "z_chunk out of range");
     if (variant < 0 || variant > 3) throw qcad::Error(QCAD_ERR_INVALID_ARG, "variant must be 0..3");
+    if (m->has_robin && family != 0 && variant != 0)
+      throw qcad::Error(QCAD_ERR_INVALID_ARG, "a mesh with charged gates runs the element-gather variant 0 only");
     qcad::LaunchCfg c;
     c.by = tile_rows;
     c.kchunk = z_chunk;

@@ -155,6 +155,20 @@ static void run_march(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_
   }
 }
 
+// The skeleton with the charged gates' face term (alpha: [nx*ny] face coefficients, Robin
+// condition of Sec. II.A.4); 8 or 16 warps per block.
+template <class T, class Op>
+static void run_march_face(const Grid<T>& g, const Op& op, LaunchCfg cfg, cudaStream_t s, const T* alpha,
+                           int nvec = 1) {
+  if (cfg.by == 16 || cfg.by == 32) {
+    dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 16, cfg.kchunk, nvec);
+    note_launch(), march_face_kernel<T, 16, Op><<<grid, dim3(QCAD_BX, 16), 0, s>>>(g, op, cfg.kchunk, alpha);
+  } else {
+    dim3 grid = march_grid(g.nxn, g.nyn, g.nzn, 8, cfg.kchunk, nvec);
+    note_launch(), march_face_kernel<T, 8, Op><<<grid, dim3(QCAD_BX, 8), 0, s>>>(g, op, cfg.kchunk, alpha);
+  }
+}
+
 // FP32 pair-kernel launchers (two nodes per thread, packed f32x2), defined below.
 void launch_apply_pair(const Grid<float>& g, const ApplyArgs<float>& a, LaunchCfg cfg, cudaStream_t s);
 void launch_pcg_apply_pair(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
@@ -303,6 +317,31 @@ struct ResidualGatherOp {
   }
 };
 
+// Pass 2 of a device with surface terms (Sec. II.A.4): the constant surface load b of the charged
+// gates and surface charges is subtracted, and the charged gates' face mass adds to the diagonal
+// (the face term of K_R phi comes from the skeleton's FACE instantiation).
+struct SurfaceGatherOp : ResidualGatherOp {
+  const double* bsurf;
+  const double* face;  // charged gates' face coefficients or null
+  __device__ void node(const Grid<double>& g, int n, int i, int j, int k, double, double stiff, const double* mass) {
+    double Rn = stiff + mass[0] - bsurf[n];
+    double dg = stiff_diag(g, i, j, k) + mass[1];
+    if (face != nullptr && k == g.nz) dg += face_diag(g, face, i, j);
+    if (grid_is_dir(g, i, j, k)) {
+      Rn = 0.0;
+      dg = 1.0;
+    }
+    R[n] = Rn;
+    if (diag) diag[n] = dg;
+    if (dinv64) dinv64[n] = 1.0 / dg;
+    if (dinv32) dinv32[n] = (float)(1.0 / dg);
+    if (b64) b64[n] = -Rn;
+    if (b32) b32[n] = (float)(-Rn);
+    acc_r2 += Rn * Rn;
+    acc_rmax = fmax(acc_rmax, fabs(Rn));
+  }
+};
+
 __host__ __device__ inline ResidualGatherOp make_gather_op(const ResidualArgs& args, double* elR, double* elD) {
   ResidualGatherOp op = {};
   op.phi = args.phi;
@@ -319,7 +358,7 @@ __host__ __device__ inline ResidualGatherOp make_gather_op(const ResidualArgs& a
 }
 
 void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, double* el, LaunchCfg cfg,
-                           cudaStream_t s) {
+                           cudaStream_t s, const double* face) {
   const long long ne = (long long)g.nx * g.ny * g.nz;
   double* elR = el;
   double* elD = el + 8 * ne;
@@ -328,11 +367,28 @@ void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& args, doub
   const ResidualGatherOp op = make_gather_op(args, elR, elD);
   LaunchCfg c = cfg;
   if (c.by == 32) c.by = 16;
+  if (args.bsurf != nullptr) {
+    SurfaceGatherOp sop;
+    static_cast<ResidualGatherOp&>(sop) = op;
+    sop.bsurf = args.bsurf;
+    sop.face = face;
+    if (face != nullptr)
+      run_march_face<double>(g, sop, c, s, face);
+    else
+      run_march<double>(g, sop, c, s);
+    return;
+  }
   run_march<double>(g, op, c, s);
 }
 
 template <class T>
-void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s) {
+void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cudaStream_t s, const T* face) {
+  if (face != nullptr) {  // charged gates: the element-gather skeleton carries the face term
+    ApplyOp<T> op = {};
+    op.a = args;
+    run_march_face<T>(g, op, cfg, s, face);
+    return;
+  }
   if (cfg.variant >= 2) {
     launch_apply_lin<T>(g, args, cfg, s);
     return;
@@ -347,8 +403,10 @@ void launch_apply(const Grid<T>& g, const ApplyArgs<T>& args, LaunchCfg cfg, cud
   op.a = args;
   run_march<T>(g, op, cfg, s);
 }
-template void launch_apply<float>(const Grid<float>&, const ApplyArgs<float>&, LaunchCfg, cudaStream_t);
-template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t);
+template void launch_apply<float>(const Grid<float>&, const ApplyArgs<float>&, LaunchCfg, cudaStream_t,
+                                  const float*);
+template void launch_apply<double>(const Grid<double>&, const ApplyArgs<double>&, LaunchCfg, cudaStream_t,
+                                   const double*);
 
 // ---------------------------------------------------------------------------
 // Electron count of one dot: the semiclassical n at the Gauss points of the dot's elements (an
@@ -459,7 +517,15 @@ void launch_count_gradient(const Grid<double>& g, const double* phi, const unsig
 
 
 template <class T>
-void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s,
+                      const T* face) {
+  if (face != nullptr) {  // charged gates: the element-gather skeleton carries the face term
+    PcgApplyOp<T> op = {};
+    op.v = vecs;
+    op.sc = sc;
+    run_march_face<T>(g, op, cfg, s, face);
+    return;
+  }
   if (cfg.variant >= 2) {
     launch_pcg_apply_lin<T>(g, vecs, sc, cfg, s);
     return;
@@ -475,8 +541,10 @@ void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, LaunchC
   op.sc = sc;
   run_march<T>(g, op, cfg, s);
 }
-template void launch_pcg_apply<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t);
-template void launch_pcg_apply<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t);
+template void launch_pcg_apply<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t,
+                                      const float*);
+template void launch_pcg_apply<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t,
+                                       const double*);
 
 
 constexpr int VEC_THREADS = 256;
@@ -666,7 +734,16 @@ template void launch_pcg_init_cheb<double>(long long, PcgVecs<double>, PcgScalar
 
 template <class T>
 void launch_cheb_step(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int step, int last, LaunchCfg cfg,
-                      cudaStream_t s) {
+                      cudaStream_t s, const T* face) {
+  if (face != nullptr) {  // charged gates: the element-gather skeleton carries the face term
+    ChebStepOp<T> op = {};
+    op.v = vecs;
+    op.sc = sc;
+    op.step = step;
+    op.last = last;
+    run_march_face<T>(g, op, cfg, s, face);
+    return;
+  }
   if (cfg.variant >= 2) {
     launch_cheb_step_lin<T>(g, vecs, sc, step, last, cfg, s);
     return;
@@ -685,9 +762,9 @@ void launch_cheb_step(const Grid<T>& g, PcgVecs<T> vecs, PcgScalars* sc, int ste
   run_march<T>(g, op, cfg, s);
 }
 template void launch_cheb_step<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, int, int, LaunchCfg,
-                                      cudaStream_t);
+                                      cudaStream_t, const float*);
 template void launch_cheb_step<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, int, int, LaunchCfg,
-                                       cudaStream_t);
+                                       cudaStream_t, const double*);
 
 // ---------------------------------------------------------------------------
 // FP32 pair-kernel ops (march2_kernel): one node per callback, element pairs inside the skeleton.

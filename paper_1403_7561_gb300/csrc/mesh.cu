@@ -259,6 +259,84 @@ template void build_grid<float>(GridDev<float>&, const GridTables&, const std::v
 template void build_grid<double>(GridDev<double>&, const GridTables&, const std::vector<double>&,
                                  const std::vector<double>&, const std::vector<double>&, cudaStream_t);
 
+// Faces (fi, fj) of a node plane whose four corners lie in the closed rectangle: fi in [i0, i1),
+// fj in [j0, j1) (empty ranges when none).
+static void rect_faces(const qcad_mesh_s* m, double x0, double x1, double y0, double y1, int r[4]) {
+  r[0] = m->nx, r[1] = 0, r[2] = m->ny, r[3] = 0;
+  for (int i = 0; i < m->nx; ++i)
+    if (m->xc[i] >= x0 && m->xc[i + 1] <= x1) r[0] = std::min(r[0], i), r[1] = std::max(r[1], i + 1);
+  for (int j = 0; j < m->ny; ++j)
+    if (m->yc[j] >= y0 && m->yc[j + 1] <= y1) r[2] = std::min(r[2], j), r[3] = std::max(r[3], j + 1);
+}
+
+// Surface terms of the weak form (Sec. II.A.4): the charged gates' face coefficients eps_r/d and
+// their vectors (eps_r/d) int_f N_a, and the bias-independent load (q/eps0) sigma int_f N_a of the
+// charged gates' sheets and of the surface charges (int_f N_a = h_x h_y / 4 on a rectangle face).
+static void build_surface_terms(qcad_mesh_s* m, const qcad_device* dev) {
+  m->has_robin = dev->n_charged_gates > 0;
+  m->has_surface = m->has_robin || dev->n_surface_charges > 0;
+  if (!m->has_surface) return;
+  const long long plane = (long long)m->nxn * m->nyn;
+  const double qe = host_qe();
+  std::vector<double> b0((size_t)m->nxn * m->nyn * m->nzn, 0.0);
+  std::vector<double> alpha((size_t)m->nx * m->ny, 0.0);
+  auto add_faces = [&](const int r[4], long long base, double w, double* dst) {
+    for (int fj = r[2]; fj < r[3]; ++fj)
+      for (int fi = r[0]; fi < r[1]; ++fi) {
+        const double q = w * m->hxv[fi] * m->hyv[fj] * 0.25;
+        for (int a = 0; a < 4; ++a) dst[base + (fi + (a & 1)) + (long long)m->nxn * (fj + (a >> 1))] += q;
+      }
+  };
+  const double eps_top = m->mats[m->layer_mat[m->nz - 1]].eps_r;
+  const long long top = (long long)m->nz * plane;
+  for (int c = 0; c < dev->n_charged_gates; ++c) {
+    const qcad_charged_gate& C = dev->charged_gates[c];
+    const qcad_rect& G = dev->gates[C.gate];
+    int r[4];
+    rect_faces(m, G.x0, G.x1, G.y0, G.y1, r);
+    const double a = eps_top / C.d;
+    for (int fj = r[2]; fj < r[3]; ++fj)
+      for (int fi = r[0]; fi < r[1]; ++fi) alpha[fi + (size_t)m->nx * fj] += a;
+    std::vector<double> rv((size_t)plane, 0.0);
+    add_faces(r, 0, a, rv.data());
+    m->charged_gate.push_back(C.gate);
+    m->charged_r.push_back(std::move(rv));
+    add_faces(r, top, qe * C.sigma, b0.data());
+  }
+  for (int q = 0; q < dev->n_surface_charges; ++q) {
+    const qcad_surface_charge& S = dev->surface_charges[q];
+    if (!std::isfinite(S.z) || !std::isfinite(S.sigma)) throw Error(QCAD_ERR_INVALID_ARG, "non-finite surface charge");
+    int k = -1;
+    for (int kk = 0; kk <= m->nz; ++kk)
+      if (std::fabs(m->zc[kk] - S.z) <= 1e-9 * std::max(1.0, std::fabs(S.z))) k = kk;
+    if (k < 0) throw Error(QCAD_ERR_INVALID_ARG, "a surface charge's z is not a node plane of the mesh");
+    int r[4];
+    rect_faces(m, S.x0, S.x1, S.y0, S.y1, r);
+    add_faces(r, (long long)k * plane, qe * S.sigma, b0.data());
+  }
+  m->bsig_top.assign(b0.begin() + top, b0.begin() + top + plane);
+  m->btop = m->bsig_top;
+  cudaStream_t s = m->stream;
+  m->d_bsurf.ensure(b0.size() * sizeof(double) + 64);
+  CK(cudaMemcpyAsync(m->d_bsurf.p, b0.data(), b0.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (m->has_robin) {
+    std::vector<double> rall;
+    for (const auto& rv : m->charged_r) rall.insert(rall.end(), rv.begin(), rv.end());
+    m->d_charged_r.ensure(rall.size() * sizeof(double) + 64);
+    CK(cudaMemcpyAsync(m->d_charged_r.p, rall.data(), rall.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    std::vector<float> a32(alpha.begin(), alpha.end());
+    m->d_face64.ensure(alpha.size() * sizeof(double) + 64);
+    m->d_face32.ensure(alpha.size() * sizeof(float) + 64);
+    CK(cudaMemcpyAsync(m->d_face64.p, alpha.data(), alpha.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(m->d_face32.p, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    // the element-gather kernels carry the face term
+    m->cfg64.variant = 0;
+    m->cfg32.variant = 0;
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
 void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
   if (!dev || !out) throw Error(QCAD_ERR_INVALID_ARG, "null device description or output");
   if (dev->nx < 1 || dev->ny < 1 || dev->n_layers < 1 || !dev->layer_n || !dev->layer_thickness ||
@@ -334,6 +412,20 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
     m->wf_set = dev->gate_work_function_set;
     m->wf = dev->gate_work_function;
     m->bottom_ohmic = dev->bottom_ohmic;
+    // charged gates (Robin condition): their nodes stay unknowns
+    if (dev->n_charged_gates < 0 || dev->n_charged_gates > dev->n_gates ||
+        (dev->n_charged_gates > 0 && !dev->charged_gates) || dev->n_surface_charges < 0 ||
+        (dev->n_surface_charges > 0 && !dev->surface_charges))
+      throw Error(QCAD_ERR_INVALID_ARG, "invalid charged-gate or surface-charge list");
+    std::vector<char> charged(std::max(1, dev->n_gates), 0);
+    for (int c = 0; c < dev->n_charged_gates; ++c) {
+      const qcad_charged_gate& C = dev->charged_gates[c];
+      if (C.gate < 0 || C.gate >= dev->n_gates || charged[C.gate])
+        throw Error(QCAD_ERR_INVALID_ARG, "charged gate index out of range or repeated");
+      if (!(C.d > 0) || !std::isfinite(C.d) || !std::isfinite(C.sigma))
+        throw Error(QCAD_ERR_INVALID_ARG, "a charged gate needs d > 0 and a finite sigma");
+      charged[C.gate] = 1;
+    }
     m->gate_top.assign(m->nxn * m->nyn, -1);
     std::vector<unsigned char> dir_top(m->nxn * m->nyn, 0);
     for (long long j = 0; j < m->nyn; ++j)
@@ -341,12 +433,15 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
         for (int gi = 0; gi < dev->n_gates; ++gi) {
           const qcad_rect& G = dev->gates[gi];
           if (m->xc[i] >= G.x0 && m->xc[i] <= G.x1 && m->yc[j] >= G.y0 && m->yc[j] <= G.y1) {
-            m->gate_top[i + m->nxn * j] = (signed char)gi;
-            dir_top[i + m->nxn * j] = 1;
+            if (!charged[gi]) {
+              m->gate_top[i + m->nxn * j] = (signed char)gi;
+              dir_top[i + m->nxn * j] = 1;
+            }
             break;
           }
         }
       }
+    build_surface_terms(m, dev);
     m->dots.n = dev->n_dots;
     for (int d = 0; d < dev->n_dots; ++d) {
       const qcad_box& B = dev->dots[d];

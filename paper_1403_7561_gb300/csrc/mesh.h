@@ -132,6 +132,18 @@ struct qcad_mesh_s {
   qcad::GridDev<double> g64;
   qcad::GridDev<float> g32;
   qcad::DevBuf d_xn, d_yn, d_zn, d_layer_semi, d_gate_top, d_dir_top, d_vgate;
+  // surface terms (charged gates under the Robin condition, surface charges): the face
+  // coefficients eps_r/d of the top plane (FP64 and FP32, in the grids' face_alpha), the
+  // constant load b = sum_sheets (q/eps0) sigma int N + sum_charged ((eps_r/d) phi_0 + (q/eps0)
+  // sigma) int N (nodal FP64; its top plane is rebuilt for every bias), and per charged gate
+  // its top-plane vector (eps_r/d) int N (host, nxn*nyn), the d b / d V_g of the adjoint
+  bool has_surface = false;                      // any surface term (the residual carries b)
+  bool has_robin = false;                        // charged gates (the linear operators carry K_R)
+  std::vector<int> charged_gate;                 // gate index of each charged gate
+  std::vector<std::vector<double>> charged_r;    // its (eps_r/d) int_f N_a on the top plane
+  std::vector<double> bsig_top;                  // bias-independent load on the top plane
+  std::vector<double> btop;                      // host staging of the top plane of b
+  qcad::DevBuf d_face64, d_face32, d_bsurf, d_charged_r;  // d_charged_r: charged_r concatenated
   // solver state
   qcad::PcgBufs<double> k64;
   qcad::PcgBufs<float> k32;

@@ -601,6 +601,8 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev L, con
 // Host.
 
 bool mg_prepare(qcad_mesh_s* m) {
+  // charged gates: the hierarchy's level-0 kernels carry no Robin face term (Jacobi instead)
+  if (m->has_robin) return false;
   if (m->mg) return hier(m)->ok;
   auto H = std::make_shared<MgHier>();
   m->mg = H;

@@ -42,6 +42,8 @@ template <> struct Prec<double> {
   static PcgGraph& graph(qcad_mesh_s* m) { return m->graph64; }
   static const Grid<double>& grid(qcad_mesh_s* m) { return m->g64.g; }
   static LaunchCfg cfg(qcad_mesh_s* m) { return m->cfg64; }
+  // the charged gates' face coefficients (Robin condition) or null
+  static const double* face(qcad_mesh_s* m) { return m->has_robin ? m->d_face64.as<double>() : nullptr; }
   static const int prof_apply = PROF_APPLY64, prof_update = PROF_UPDATE64;
 };
 template <> struct Prec<float> {
@@ -49,6 +51,7 @@ template <> struct Prec<float> {
   static PcgGraph& graph(qcad_mesh_s* m) { return m->graph32; }
   static const Grid<float>& grid(qcad_mesh_s* m) { return m->g32.g; }
   static LaunchCfg cfg(qcad_mesh_s* m) { return m->cfg32; }
+  static const float* face(qcad_mesh_s* m) { return m->has_robin ? m->d_face32.as<float>() : nullptr; }
   static const int prof_apply = PROF_APPLY32, prof_update = PROF_UPDATE32;
 };
 
@@ -101,7 +104,7 @@ static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* s
   };
   int e = 0;
   rec(e, true);
-  launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s);
+  launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s, Prec<T>::face(m));
   rec(e++, false);
   rec(e, true);
   if constexpr (std::is_same<T, float>::value) {
@@ -118,7 +121,7 @@ static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* s
   rec(e++, false);
   for (int j = 1; j < degree; ++j) {
     rec(e, true);
-    launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s);
+    launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s, Prec<T>::face(m));
     rec(e++, false);
   }
 }
@@ -194,7 +197,7 @@ static double lambda_max(qcad_mesh_s* m, int steps) {
     a.v = x;
     a.y = y;
     a.c = v.c;
-    launch_apply<T>(Prec<T>::grid(m), a, Prec<T>::cfg(m), s);
+    launch_apply<T>(Prec<T>::grid(m), a, Prec<T>::cfg(m), s, Prec<T>::face(m));
     CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
     launch_power_step<T>(n, x, y, v.dinv, xn, acc, s);
     CK(cudaMemcpyAsync(m->h_small + 40, acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -267,7 +270,7 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
     launch_pcg_init<T>(m->n_nodes, v, sc, s);
   } else {
     launch_pcg_init_cheb<T>(m->n_nodes, v, sc, s);
-    for (int j = 1; j < degree; ++j) launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s);
+    for (int j = 1; j < degree; ++j) launch_cheb_step<T>(Prec<T>::grid(m), v, sc, j, j == degree - 1, Prec<T>::cfg(m), s, Prec<T>::face(m));
   }
   CK(cudaGetLastError());
   int t_prev = 0;
@@ -390,6 +393,7 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   a.diag = diag_out;
   a.stats = m->stats.as<double>();
   if (m->qd_active) a.qd = m->qd;  // predictor density in the quantum region (Sec. II.C)
+  if (m->has_surface) a.bsurf = m->d_bsurf.as<double>();  // charged gates, surface charges
   CK(cudaMemsetAsync(a.stats, 0, 2 * sizeof(double), s));
   if (counts_out) {
     a.counts = m->counts.as<double>();
@@ -398,7 +402,7 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   Profiler::Pair pp;
   if (m->prof.on) m->prof.begin(PROF_RESIDUAL, s, pp);
   m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
-  launch_residual_2pass(m->g64.g, a, m->el_res.as<double>(), m->cfg_res, s);
+  launch_residual_2pass(m->g64.g, a, m->el_res.as<double>(), m->cfg_res, s, Prec<double>::face(m));
   m->lin_ver[prec == 0 ? 0 : 1] += 1;  // the stored linearization changed
   if (m->prof.on) m->prof.end(pp, s);
   CK(cudaGetLastError());
@@ -415,6 +419,22 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   return r;
 }
 
+// Top plane of the surface load b at the bias: the charged gates' (eps_r/d) phi_0 int_f N_a (the
+// Robin condition, Sec. II.A.4; phi_0 of Eq. ContOnIns) on top of the bias-independent sheets.
+static void update_surface_load(qcad_mesh_s* m, const qcad_bias* b, const Phys& P) {
+  if (!m->has_robin) return;
+  const long long plane = (long long)m->nxn * m->nyn;
+  m->btop = m->bsig_top;
+  for (size_t c = 0; c < m->charged_gate.size(); ++c) {
+    const double v = gate_value(m, b->V_gate[m->charged_gate[c]], P);
+    const std::vector<double>& r = m->charged_r[c];
+    for (long long q = 0; q < plane; ++q) m->btop[q] += v * r[q];
+  }
+  CK(cudaMemcpyAsync(m->d_bsurf.as<double>() + (size_t)m->nz * plane, m->btop.data(), plane * sizeof(double),
+                     cudaMemcpyHostToDevice, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+}
+
 void set_contacts(qcad_mesh_s* m, const qcad_bias* b, const Phys& P, double* phi, double* gate_vals,
                   double* ohm_val) {
   if (b->n_gates != m->n_gates || (m->n_gates > 0 && !b->V_gate))
@@ -426,6 +446,7 @@ void set_contacts(qcad_mesh_s* m, const qcad_bias* b, const Phys& P, double* phi
     for (int g = 0; g < m->n_gates; ++g) gate_vals[g] = vg[g];
   if (ohm_val) *ohm_val = vo;
   if (!phi) return;
+  update_surface_load(m, b, P);
   std::memcpy(m->h_small + 16, vg, sizeof(double) * std::max(1, m->n_gates));
   CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * std::max(1, m->n_gates),
                      cudaMemcpyHostToDevice, m->stream));
@@ -584,6 +605,7 @@ qcad_status poisson_residual(qcad_mesh_s* m, const qcad_bias* b, const double* t
   if (!phi || !R) throw Error(QCAD_ERR_INVALID_ARG, "null phi or R");
   ensure_newton(m);
   const Phys P = make_phys(m, b);
+  update_surface_load(m, b, P);
   ResStats st = eval_residual(m, P, phi, theta, 0, 0, nullptr, diag);
   cudaStream_t s = m->stream;
   CK(cudaMemcpyAsync(R, m->R.p, m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -610,7 +632,7 @@ qcad_status poisson_jv(qcad_mesh_s* m, const qcad_bias* b, const double* phi, co
     a.v = vin;
     a.y = y;
     a.c = v.c;
-    launch_apply<double>(m->g64.g, a, m->cfg64, s);
+    launch_apply<double>(m->g64.g, a, m->cfg64, s, Prec<double>::face(m));
   } else {
     PcgVecs<float> v = ensure_pcg<float>(m);
     launch_d2f(m->n_nodes, vin, v.r, s);
@@ -618,7 +640,7 @@ qcad_status poisson_jv(qcad_mesh_s* m, const qcad_bias* b, const double* phi, co
     a.v = v.r;
     a.y = v.Ap;
     a.c = v.c;
-    launch_apply<float>(m->g32.g, a, m->cfg32, s);
+    launch_apply<float>(m->g32.g, a, m->cfg32, s, Prec<float>::face(m));
     launch_f2d(m->n_nodes, v.Ap, y, s);
   }
   CK(cudaGetLastError());
@@ -989,7 +1011,7 @@ static void adjoint_solve_mixed_mg(qcad_mesh_s* m, const double* g, double* lam,
     a.v = lam;
     a.y = y;
     a.c = v.c;
-    launch_apply<double>(m->g64.g, a, m->cfg64, s);
+    launch_apply<double>(m->g64.g, a, m->cfg64, s, Prec<double>::face(m));
     launch_sub(n, g, y, r, const_cast<float*>(w.b), s);
     CK(cudaMemsetAsync(d2, 0, sizeof(double), s));
     launch_dot<double>(n, r, r, d2, s);
@@ -1094,7 +1116,7 @@ static void adjoint_solve_mixed(qcad_mesh_s* m, int nd, const double* G, double*
       a.v = lam;
       a.y = y;
       a.c = v64.c;
-      launch_apply<double>(m->g64.g, a, m->cfg64, s);
+      launch_apply<double>(m->g64.g, a, m->cfg64, s, Prec<double>::face(m));
       launch_sub(n, G + (size_t)d * n, y, r, const_cast<float*>(B.vecs[d].b), s);
       launch_dot<double>(n, r, r, d2 + d, s);
     }
@@ -1148,7 +1170,7 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
     a.y = JE + (size_t)gi * n;
     a.c = ensure_pcg<double>(m).c;
     a.raw = 1;
-    launch_apply<double>(m->g64.g, a, m->cfg64, s);
+    launch_apply<double>(m->g64.g, a, m->cfg64, s, Prec<double>::face(m));
     for (int d = 0; d < nd; ++d) launch_dot<double>(n, G + (size_t)d * n, eg, acc + d * ng + gi, s);
     CK(cudaStreamSynchronize(s));  // h_small is reused by the next gate's upload
   }
@@ -1159,14 +1181,30 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
   const int degree = o->cheb_degree != 0 ? o->cheb_degree : m->cheb_auto[1];
   if (o->precision == 1 && degree == DEG_MG && mg_prepare(m)) {
     for (int d = 0; d < nd; ++d) adjoint_solve_mixed_mg(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
-  } else if (o->precision == 1) {
+  } else if (o->precision == 1 && !m->has_robin) {
     adjoint_solve_mixed(m, nd, G, LAM, maxk);
   } else {
+    // (charged gates: the batched kernels of the mixed multi-dot solve carry no face term)
     for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
   }
   for (int d = 0; d < nd; ++d)
     for (int gi = 0; gi < ng; ++gi)
       launch_dot<double>(n, LAM + (size_t)d * n, JE + (size_t)gi * n, acc + nd * ng + d * ng + gi, s);
+  // charged gates (Robin condition): V_g enters through the load, d b / d V_g = (eps_r/d) int_f N_a
+  // on the gate's faces (top plane), so dN_d/dV_g gains lam_d . d b / d V_g (lam is 0 on Dirichlet rows)
+  const int nc = (int)m->charged_gate.size();
+  DevBuf racc;
+  std::vector<double> hr((size_t)std::max(1, nd * nc), 0.0);
+  if (nc > 0) {
+    const long long plane = (long long)m->nxn * m->nyn;
+    racc.ensure((size_t)nd * nc * sizeof(double) + 64);
+    CK(cudaMemsetAsync(racc.p, 0, (size_t)nd * nc * sizeof(double), s));
+    for (int d = 0; d < nd; ++d)
+      for (int c = 0; c < nc; ++c)
+        launch_dot<double>(plane, LAM + (size_t)d * n + (size_t)m->nz * plane,
+                           m->d_charged_r.as<double>() + (size_t)c * plane, racc.as<double>() + d * nc + c, s);
+    CK(cudaMemcpyAsync(hr.data(), racc.p, (size_t)nd * nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
   std::vector<double> h(2 * nd * ng);
   CK(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (dN_dq)
@@ -1177,6 +1215,8 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
   CK(cudaStreamSynchronize(s));
   for (int d = 0; d < nd; ++d)
     for (int gi = 0; gi < ng; ++gi) dN_dV[d * ng + gi] = h[d * ng + gi] - h[nd * ng + d * ng + gi];
+  for (int d = 0; d < nd; ++d)
+    for (int c = 0; c < nc; ++c) dN_dV[d * ng + m->charged_gate[c]] += hr[d * nc + c];
   return QCAD_OK;
 }
 
@@ -1272,6 +1312,8 @@ qcad_status poisson_solve_batch_impl(int n, const qcad_mesh_t* ms, const qcad_bi
   B.ms.assign(ms, ms + n);
   for (int i = 0; i < n; ++i) {
     if (!ms[i] || !phis[i]) throw Error(QCAD_ERR_INVALID_ARG, "null mesh or phi in batch");
+    if (ms[i]->has_surface)
+      throw Error(QCAD_ERR_INVALID_ARG, "the batched solve does not take charged gates or surface charges");
     if (ms[i]->device != ms[0]->device) throw Error(QCAD_ERR_INVALID_ARG, "batch meshes must share one device");
     for (int j = 0; j < i; ++j)
       if (ms[j] == ms[i]) throw Error(QCAD_ERR_INVALID_ARG, "a mesh appears twice in the batch");

@@ -101,6 +101,10 @@ qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* s
     set_message("invalid device description or bias");
     return QCAD_ERR_INVALID_ARG;
   }
+  if (dev->n_charged_gates != 0 || dev->n_surface_charges != 0) {
+    set_message("the allocation-free residual does not take charged gates or surface charges");
+    return QCAD_ERR_INVALID_ARG;
+  }
   int nz = 0;
   for (int L = 0; L < dev->n_layers; ++L) {
     const int mat = dev->layer_material[L];

@@ -68,6 +68,7 @@ struct ResidualArgs {
   double* stats;             // [2] {max|R| (as ordered bits), sum R^2} or null
   int linear;
   QuantumDensity qd;         // quantum density in the quantum region (inactive: qd.w null)
+  const double* bsurf;       // [n_nodes] constant surface load b (R -= b; two-pass residual) or null
 };
 
 template <class T>
@@ -94,15 +95,19 @@ void launch_residual(const Grid<double>& g, const ResidualArgs& a, LaunchCfg cfg
 void launch_dot_count(const Grid<double>& g, const double* phi, const unsigned char* layer_semi, const Phys& P,
                       const int box[6], double* out, cudaStream_t s);
 // Same outputs in two passes (carrier density once per quadrature point); el: 16 doubles per element.
-void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& a, double* el, LaunchCfg cfg, cudaStream_t s);
+// face: the charged gates' [nx*ny] face coefficients (Robin condition) or null; with a.bsurf set,
+// the surface load is subtracted and the face mass enters the stiffness and the diagonal.
+void launch_residual_2pass(const Grid<double>& g, const ResidualArgs& a, double* el, LaunchCfg cfg, cudaStream_t s,
+                           const double* face = nullptr);
 
 template <class T>
-void launch_apply(const Grid<T>& g, const ApplyArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+void launch_apply(const Grid<T>& g, const ApplyArgs<T>& a, LaunchCfg cfg, cudaStream_t s, const T* face = nullptr);
 
 template <class T>
 void launch_pcg_init(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
 template <class T>
-void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
+void launch_pcg_apply(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s,
+                      const T* face = nullptr);
 template <class T>
 void launch_pcg_update(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
 // Chebyshev-Jacobi form: the update kernel starts the recurrence (w = r, d = D^-1 r / theta,
@@ -114,7 +119,7 @@ template <class T>
 void launch_pcg_init_cheb(long long n, PcgVecs<T> v, PcgScalars* sc, cudaStream_t s);
 template <class T>
 void launch_cheb_step(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, int step, int last, LaunchCfg cfg,
-                      cudaStream_t s);
+                      cudaStream_t s, const T* face = nullptr);
 // One power step for the largest eigenvalue of D^-1 J: v_next = D^-1 (J v) / |.|; acc[0] += v.Jv,
 // acc[1] += v.D v, acc[2] += |D^-1 J v|^2 (the caller normalizes with acc[2]).
 template <class T>

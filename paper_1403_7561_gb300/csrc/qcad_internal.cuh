@@ -47,6 +47,45 @@ struct Grid {
   int dir_boundary;      // every boundary node is Dirichlet (Schrodinger subdomain)
 };
 
+// Charged gates (the Robin condition): alpha[fi + nx fj] = eps_r/d of every top-plane face (0 off
+// the charged gates); the linear operators add the face mass sum_f alpha_f int_f N_a N_b on the
+// top plane. The coefficients travel as a kernel argument of their own instantiations, not in
+// Grid, so the kernels of devices without charged gates are unchanged.
+//
+// Face term of node (i, j) of the top plane: sum over its (up to four) faces f of
+// alpha_f (h_x h_y / 36) (4 v_self + 2 v_x-neighbour + 2 v_y-neighbour + v_diagonal), the row of
+// the bilinear face mass; v(di, dj) returns the value at (i + di, j + dj).
+template <class T, class V>
+__device__ __forceinline__ T face_row(const Grid<T>& g, const T* alpha, int i, int j, V v) {
+  T y = 0;
+#pragma unroll
+  for (int sy = -1; sy <= 0; ++sy)
+#pragma unroll
+    for (int sx = -1; sx <= 0; ++sx) {
+      const int fi = i + sx, fj = j + sy;
+      if (fi < 0 || fj < 0 || fi >= g.nx || fj >= g.ny) continue;
+      const T a = alpha[fi + g.nx * fj];
+      if (a == T(0)) continue;
+      const int dx = sx == 0 ? 1 : -1, dy = sy == 0 ? 1 : -1;  // the face's other corner offsets
+      const T w = a * g.hx[fi] * g.hy[fj] * T(1.0 / 36.0);
+      y += w * (T(4) * v(0, 0) + T(2) * v(dx, 0) + T(2) * v(0, dy) + v(dx, dy));
+    }
+  return y;
+}
+
+// Diagonal of the face mass at node (i, j) of the top plane: sum_f alpha_f h_x h_y / 9.
+template <class T>
+__device__ __forceinline__ T face_diag(const Grid<T>& g, const T* alpha, int i, int j) {
+  T d = 0;
+  for (int sy = -1; sy <= 0; ++sy)
+    for (int sx = -1; sx <= 0; ++sx) {
+      const int fi = i + sx, fj = j + sy;
+      if (fi < 0 || fj < 0 || fi >= g.nx || fj >= g.ny) continue;
+      d += alpha[fi + g.nx * fj] * g.hx[fi] * g.hy[fj] * T(1.0 / 9.0);
+    }
+  return d;
+}
+
 template <class T>
 __device__ __forceinline__ bool grid_is_dir(const Grid<T>& g, int i, int j, int k) {
   if (g.dir_boundary && (i == 0 || j == 0 || k == 0 || i == g.nx || j == g.ny || k == g.nz)) return true;
@@ -282,8 +321,10 @@ __device__ __forceinline__ void block_max_atomic(double v, double* dst) {
 // 32-bit; mesh creation rejects meshes whose 8*n_elems or n_nodes exceed 2^31.
 // Body of the skeleton for tile (bx, by) and (vector, z chunk) index bz; called by
 // march_kernel with the block index and by the batched kernels with a tile from a work table.
-template <class T, int BY, class Op>
-__device__ __forceinline__ void march_body(const Grid<T>& g, const Op& op_in, int kchunk, int bx, int by, int bz) {
+// FACE: the charged gates' face term (face_alpha) is added to the stiffness of the top plane.
+template <class T, int BY, class Op, bool FACE = false>
+__device__ __forceinline__ void march_body(const Grid<T>& g, const Op& op_in, int kchunk, int bx, int by, int bz,
+                                           const T* face_alpha = nullptr) {
   constexpr int BX = QCAD_BX;
   constexpr int NF = Op::NF;
   using ED = typename Op::ED;
@@ -436,6 +477,12 @@ __device__ __forceinline__ void march_body(const Grid<T>& g, const Op& op_in, in
       const T dm = __shfl_up_sync(FULL_MASK, d, 1);
       const T dp = __shfl_down_sync(FULL_MASK, d, 1);
       stiff = ckx[0] * c1m + ckx[1] * c1 + ckx[2] * c1p + cmx[0] * dm + cmx[1] * d + cmx[2] * dp;
+      // charged gates: the Robin face mass on the top plane, from the ring's 3x3 neighbourhood
+      // (a writer's neighbours are inside its tile)
+      if constexpr (FACE) {
+        if (k == g.nz && writer)
+          stiff += face_row(g, face_alpha, i, j, [&](int dx, int dy) { return ring[k & 3][ty + dy][tx + dx]; });
+      }
     }
     if (writer) op.node(g, nij + k * plane, i, j, k, vc, stiff, mass);
   }
@@ -446,6 +493,13 @@ template <class T, int BY, class Op>
 __global__ void __launch_bounds__(QCAD_BX * BY)
 march_kernel(const Grid<T> g, const Op op_in, int kchunk) {
   march_body<T, BY, Op>(g, op_in, kchunk, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The skeleton with the charged gates' face term (alpha: [nx*ny] face coefficients).
+template <class T, int BY, class Op>
+__global__ void __launch_bounds__(QCAD_BX * BY)
+march_face_kernel(const Grid<T> g, const Op op_in, int kchunk, const T* alpha) {
+  march_body<T, BY, Op, true>(g, op_in, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, alpha);
 }
 
 // Launch geometry of the skeleton for a grid (nvec vectors along blockIdx.z).

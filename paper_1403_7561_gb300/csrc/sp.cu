@@ -123,6 +123,8 @@ qcad_status sp_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts*
                      qcad_sp_report* rep) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!m->has_sub) throw Error(QCAD_ERR_INVALID_ARG, "mesh has no Schrodinger subdomain (the quantum region)");
+  if (m->has_surface)
+    throw Error(QCAD_ERR_INVALID_ARG, "the Schrodinger-Poisson loop does not take charged gates or surface charges");
   if (!b || !o || !phi || !evals || !m_eff) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
   if (nev < 1 || nev > QD_MAX_STATES) throw Error(QCAD_ERR_INVALID_ARG, "nev must be in [1, 16]");
   if (max_iter < 1 || max_iter > 1000) throw Error(QCAD_ERR_INVALID_ARG, "max_iter must be in [1, 1000]");

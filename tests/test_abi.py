@@ -54,21 +54,49 @@ def test_invalid_mesh_is_rejected_without_gpu_work(lib_path):
     assert b"null" in lib.qcad_last_error()
 
 
-def test_binding_rejects_surface_terms_it_does_not_solve(lib_path):
-    # charged gates and surface charges exist in the oracle only: the library must not ignore them
+def test_binding_passes_surface_terms(lib_path):
+    # charged gates (a gate's "robin" entry) and surface charges reach the C description
     import copy
 
     import paper_1403_7561_gb300 as q
     import workloads as W
     dev = W.five_gate_device(n=(8, 8, 6))
-    d1 = copy.deepcopy(dev)
-    d1["gates"][1]["robin"] = dict(sigma=1e-3, d=10.0)
-    with pytest.raises(NotImplementedError, match="P1"):
-        q.Mesh(d1)
-    d2 = copy.deepcopy(dev)
-    d2["surface_charges"] = [dict(z=90.0, x0=0.0, x1=200.0, y0=0.0, y1=200.0, sigma=1e-3)]
-    with pytest.raises(NotImplementedError):
-        q.Mesh(d2)
-    if not q.torch.cuda.is_available():
-        with pytest.raises(RuntimeError, match="CUDA"):       # an ordinary device passes the check
-            q.Mesh(dev)
+    dev["gates"][3]["robin"] = dict(sigma=5e-4, d=10.0)
+    dev["surface_charges"] = [dict(z=90.0, x0=0.0, x1=200.0, y0=25.0, y1=175.0, sigma=-1e-3)]
+    d, keep = q._device_struct(dev)
+    assert d.n_charged_gates == 1 and d.charged_gates[0].gate == 3
+    assert (d.charged_gates[0].sigma, d.charged_gates[0].d) == (5e-4, 10.0)
+    assert d.n_surface_charges == 1
+    S = d.surface_charges[0]
+    assert (S.z, S.x0, S.x1, S.y0, S.y1, S.sigma) == (90.0, 0.0, 200.0, 25.0, 175.0, -1e-3)
+    d0, _ = q._device_struct(copy.deepcopy(W.five_gate_device(n=(8, 8, 6))))
+    assert d0.n_charged_gates == 0 and d0.n_surface_charges == 0
+
+
+def test_binding_structs_match_the_header(lib_path, tmp_path):
+    # every field of the ctypes mirrors sits at the offset the C compiler gives it
+    import shutil
+    import subprocess
+
+    import paper_1403_7561_gb300 as q
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"qcad_device": q.Device, "qcad_charged_gate": q.ChargedGate,
+               "qcad_surface_charge": q.SurfaceCharge, "qcad_material": q.Material, "qcad_bias": q.Bias,
+               "qcad_solver_opts": q.SolverOpts, "qcad_solve_report": q.SolveReport}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qcad.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
