@@ -13,7 +13,7 @@ Test infrastructure only (see ``oracle/__init__``). Sec. II.A.4 of Gao et al.:
   which adds (eps_r/d) int_Gamma phi w to the bilinear form and
   int_Gamma ((eps_r/d) phi_0 + (q/eps0) sigma_s) w to the load.
 
-Readings (listed in the design notes): the sign of the phi term is the one Gauss's
+Readings where the paper is silent or at odds with itself: the sign of the phi term is the one Gauss's
 law across the gap gives (the well-posed sign; the paper states the Robin
 coefficient and its figure with opposite signs); sigma_s > 0 is positive charge, as
 in the Neumann jump condition; eps_s is the permittivity of the element under the

@@ -22,7 +22,7 @@ al. for electrons confined in all three directions (quantum dots):
   with n~^(k), then n~^(k) and V^(k) with V_xc(n~^(k)) at the new potential;
   (4) stop when max |phi^(k) - phi^(k-1)| < delta for k >= 2.
 
-Readings (see the design notes): the quantum density and V_xc live on the
+Readings where the paper leaves a choice: the quantum density and V_xc live on the
 2x2x2 Gauss points of the quantum region's elements (where the Poisson load
 and the Schrodinger potential are integrated); q(phi - phi^(k)) in eV is
 numerically phi - phi^(k) in V.
