@@ -4,8 +4,8 @@ Test infrastructure only. Implements the weak forms the paper discretizes:
 the Poisson weak form, Sec. II.A.3, Eq. PoissonWeakForm (boundary term
 dropped = natural Neumann, Sec. II.A.4), and the Schrodinger weak form,
 Sec. II.B, Eq. SchrodEqnWeakForm. Every volume integral uses 2x2x2 Gauss
-quadrature on the trilinear map of each element (reading "Q": exact for
-stiffness and consistent mass on boxes, no lumping). The element geometry is
+quadrature on the trilinear map of each element (the paper names no rule; this one
+is exact for stiffness and consistent mass on boxes, no lumping). The element geometry is
 handled in the general isoparametric form (Jacobian of the trilinear map), so
 nothing here assumes axis-aligned boxes.
 """

@@ -79,7 +79,7 @@ class Mesh:
 
     # ---------------- regions ----------------
     def dot_elements(self, d):
-        """Semiconductor elements whose centroid lies in dot box d (reading "D")."""
+        """Semiconductor elements whose centroid lies in dot box d (the dot's quantum region)."""
         D = self.dev["dots"][d]
         cen = self.elem_coords.mean(axis=1)
         semi = np.array([self.materials[m]["semiconductor"] for m in self.elem_mat], dtype=bool)

@@ -27,7 +27,7 @@ def kT_eV(T):
 
 
 def q_over_eps0():
-    """q/eps0 in V*nm (the residual is scaled by 1/eps0, reading "U")."""
+    """q/eps0 in V*nm (the residual is scaled by 1/eps0)."""
     return Q_E / EPS0 * 1e9
 
 
@@ -110,8 +110,8 @@ def fd_half(x):
     """Bednarczyk approximation of F_1/2, Eq. FDIntApprox, with the x < -50 clamp.
 
     F(x) ~ ( e^-x + (3 sqrt(pi)/4) v^(-3/8) )^-1,
-    v = x^4 + 50 + 33.6 x [1 - 0.68 exp(-0.17 (x+1)^2)]   (reading G1 of the
-    unclosed bracket), and F(x) = e^x for x < -50 (Sec. II.A.1, last paragraph).
+    v = x^4 + 50 + 33.6 x [1 - 0.68 exp(-0.17 (x+1)^2)]   (the printed formula
+    leaves a bracket open; this closing reproduces its stated 0.4 % accuracy), and F(x) = e^x for x < -50 (Sec. II.A.1, last paragraph).
     Accepts scalars or numpy arrays.
     """
     x = np.asarray(x, dtype=np.float64)
@@ -126,7 +126,7 @@ def fd_half(x):
 
 
 def fd_half_deriv(x):
-    """dF/dx of the implemented approximation (reading G6: J differentiates what R uses).
+    """dF/dx of the implemented approximation (the Jacobian differentiates what the residual uses).
 
     With D = e^-x + C v^(-3/8):  F = 1/D,  F' = (e^-x + (3/8) C v^(-11/8) v') / D^2,
     v' = 4x^3 + 33.6 (1 - 0.68 g) + 33.6 x * 0.68 * 0.34 (x+1) g,  g = exp(-0.17 (x+1)^2).
@@ -168,7 +168,7 @@ def fd_half_inverse(u):
 # Sec. II.A.2, Eqs. qPhiRef and EcEv_phi
 # ---------------------------------------------------------------------------
 def phi_ref(mat, T):
-    """Reference potential q phi_ref = E_0 - E_i(Si), Eq. qPhiRef (reading "R").
+    """Reference potential q phi_ref = E_0 - E_i(Si), Eq. qPhiRef.
 
     E_i = (E_C + E_V)/2 + (kT/2) ln(N_V/N_C), so
     q phi_ref = chi + E_g/2 + (kT/2) ln(N_C/N_V).
@@ -187,7 +187,7 @@ def band_edges(phi, mat, phi_r):
 # Densities: Eqs. MBstatistics, FDstatistics, FinalIonization
 # ---------------------------------------------------------------------------
 def _sigmoid_pair(zeta, g):
-    """s = 1/(1 + g e^zeta) and 1 - s, overflow-safe (reading "X")."""
+    """s = 1/(1 + g e^zeta) and 1 - s, overflow-safe."""
     zeta = np.asarray(zeta, dtype=np.float64)
     s = np.empty_like(zeta)
     one_m_s = np.empty_like(zeta)
@@ -210,7 +210,7 @@ def carrier_terms(phi, mat, T, phi_r, E_F=0.0, statistics=1, incomplete=1):
     n = N_C F(eta_n), eta_n = (E_F - E_C)/kT; p = N_V F(eta_p), eta_p = (E_V - E_F)/kT
     with F = exp (MB, Eq. MBstatistics) or the Bednarczyk F_1/2 (FD, Eq. FDstatistics).
     Ionized dopants by Eq. FinalIonization (g_D, g_A of Sec. II.A.3); complete
-    ionization sets ND+ = N_D and NA- = N_A. Insulators carry no charge (reading "O").
+    ionization sets ND+ = N_D and NA- = N_A. Insulators carry no charge.
     """
     phi = np.asarray(phi, dtype=np.float64)
     zero = np.zeros_like(phi)
@@ -258,7 +258,7 @@ def carrier_terms(phi, mat, T, phi_r, E_F=0.0, statistics=1, incomplete=1):
 # Contacts, Sec. II.A.4
 # ---------------------------------------------------------------------------
 def gate_potential(V_g, phi_r, work_function=None):
-    """phi_ins = V_g - (Phi_m - q phi_ref)/q, Eq. ContOnIns. Phi_m defaults to q phi_ref (reading "Phi")."""
+    """phi_ins = V_g - (Phi_m - q phi_ref)/q, Eq. ContOnIns. Phi_m defaults to q phi_ref (the paper gives none)."""
     Phi_m = phi_r if work_function is None else work_function
     return V_g - (Phi_m - phi_r)
 
@@ -271,7 +271,8 @@ def ohmic_potential(mat, T, phi_r, V_a=0.0, statistics=1, incomplete=1):
 
     - MB, complete ionization: Eq. PotBC4MBCompIon.
     - MB, incomplete: Eq. PotBC4MBIncompIon with y_n, y_p of Eq. Yval4MBIncompIon,
-      or their logarithms by Eq. ApproxLogTerms when T < 50 K (reading "S").
+      or their logarithms by Eq. ApproxLogTerms when T < 50 K (the paper's
+      "very low temperatures", taken as below 50 K).
       For p-type the sign of E_a follows the derivation from y_p's definition,
       +E_a (the printed -E_a contradicts Eq. Yval4MBIncompIon; pinned by the
       neutral-root test).

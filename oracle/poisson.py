@@ -4,7 +4,7 @@ Test infrastructure only. Follows Sec. II.A of Gao et al.:
 -div(eps grad phi) = q (p - n + ND+ - NA-)   (Eq. Poisson)
 in the weak form of Eq. PoissonWeakForm with natural Neumann boundaries,
 gate Dirichlet values from Eq. ContOnIns and Ohmic values from the contact
-formulas of Sec. II.A.4. The residual is scaled by 1/eps0 (reading "U"):
+formulas of Sec. II.A.4. The residual is scaled by 1/eps0:
 
     R_i(phi) = sum_e int eps_r grad phi . grad N_i  -  (q/eps0) int rho(phi) N_i
 
@@ -14,7 +14,7 @@ the Robin condition, surface charges under Eq. NeuBC4fc): R gains K_R phi - b,
 K_R = sum over charged gates of (eps_r/d) int_Gamma N_a N_b and b the constant
 surface loads, both zero on every device without those keys.
 The Jacobian J = K + K_R - (q/eps0) M[rho'] is differentiated by hand (the paper
-uses automatic differentiation, Sec. II.C.2; reading "G6"). Every linear
+uses automatic differentiation, Sec. II.C.2). Every linear
 system is solved on the free-free block by a sparse direct solve (SuperLU) or
 by Jacobi-preconditioned CG to a relative residual of 1e-14.
 """
@@ -128,7 +128,7 @@ class PoissonProblem:
                 drho[sel] = t["drho"]
                 n[sel] = t["n"]
                 dn[sel] = t["dn"]
-        rho = rho + self.theta[:, None]  # fixed charge adds to rho (reading "F")
+        rho = rho + self.theta[:, None]  # fixed charge adds to rho
         return rho, drho, n, dn
 
     def residual(self, phi, full=False):
@@ -147,7 +147,7 @@ class PoissonProblem:
         return (self.K + self.KR + Mc).tocsr()
 
     def initial_guess(self, solver="cg"):
-        """Laplace solve with the contact values and surface terms (rho = 0), reading "L"."""
+        """Laplace solve with the contact values and surface terms (rho = 0), the initial guess (the paper states none)."""
         phi = self.g.copy()
         f, d = self.free, self.dir
         A = (self.K + self.KR).tocsr()
@@ -156,7 +156,8 @@ class PoissonProblem:
         return phi
 
     def solve(self, phi0=None, tol_R=1e-10, tol_dphi=1e-10, max_newton=200, solver="cg", verbose=False):
-        """Newton with backtracking on ||R||_2 (Armijo 1e-4, halving up to 30 times), reading "L".
+        """Newton with backtracking on ||R||_2 (Armijo 1e-4, halving up to 30 times); the paper
+        states no globalization.
 
         Stops when ||R||_inf < tol_R on free nodes and ||alpha delta||_inf < tol_dphi.
         Returns (phi, report).

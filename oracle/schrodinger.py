@@ -2,11 +2,11 @@
 
 Test infrastructure only. Follows Sec. II.B of Gao et al.: the weak form of
 Eq. SchrodEqnWeakForm with a diagonal mass tensor (Eq. Schrodinger3D: m_t in
-x, y and m_l in z; reading "M": the configurations use one isotropic mass),
+x, y and m_l in z; the devices here use one isotropic mass),
 psi = 0 on the subdomain boundary (Dirichlet, Sec. II.B) and the potential
 energy of Eq. SchrodPotEnergy without V_xc:
 
-    V = q phi_ref - chi - q phi      (eV, reading "V").
+    V = q phi_ref - chi - q phi      (eV).
 
 H = sum_d (hbar^2 / 2 m_d) int d_d N_a d_d N_b + int V N_a N_b,
 M = int N_a N_b, both by 2x2x2 Gauss quadrature, restricted to the interior

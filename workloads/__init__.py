@@ -56,7 +56,7 @@ def stream_seed(seed: int, stream: int) -> int:
 
 
 # ---------------------------------------------------------------------------
-# Materials (reading "C": the paper gives the formulas but not these values).
+# Materials (the paper gives the formulas but not these values).
 # Units: eps relative; chi, Eg, E_a, E_d in eV; masses in m0; doping in nm^-3.
 # ---------------------------------------------------------------------------
 SI = dict(name="Si", eps_r=11.7, chi=4.05, Eg=1.12, semiconductor=1,
@@ -158,7 +158,7 @@ def interface_fixed_charge(dev: dict, seed: int, sigma_std=1e-4):
 
     sigma_e ~ N(0, sigma_std nm^-2) on the single layer of Si elements that
     touches the Si/SiO2 interface, theta_e = sigma_e / h_z of that layer;
-    zero elsewhere (reading "F"). Element order: i + nx*(j + ny*k).
+    zero elsewhere. Element order: i + nx*(j + ny*k).
     """
     nx, ny = dev["nx"], dev["ny"]
     nz = sum(L["n"] for L in dev["layers"])
