@@ -77,6 +77,38 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         gpus = 2
 
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1) or (1.0, 100))
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1) or (1.0, 100, 1.0))
     bench.reference_arm(Args())
     assert called == [] and capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    # the reference arm's one JSON line: the contract's keys, the oracle's own cores and zero copies
+    import json
+
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+
+    class Args:
+        workload = "dqd_128x128x96_4K"
+        steps = 2
+        warmup = 1
+        gpus = 1
+
+    samples = iter([(3.0, 1000, 2.5), (2.0, 1000, 3.0), (4.0, 1000, 2.0)])
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: next(samples))
+    bench.reference_arm(Args())
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    full = d["config"]["nodes"]
+    assert abs(d["ms_per_step"] - 3000.0) < 1e-9                 # mean of the two timed samples
+    assert abs(d["value"] - (1.0 / 3.0) * 1000 / full) < 1e-15      # solves/s scaled by the node ratio
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 3.0
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
