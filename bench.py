@@ -249,7 +249,6 @@ def reference_arm(args):
 
 
 def native_arm(args):
-    import numpy as np
     import torch
 
     import paper_1403_7561_gb300 as q

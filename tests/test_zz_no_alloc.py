@@ -7,7 +7,6 @@ shared by all calls. This file is collected last so that a failure here does
 not hide the other tests; it passes both alone in a fresh process and after
 them.
 """
-import numpy as np
 import pytest
 import torch
 
