@@ -202,7 +202,6 @@ def oracle_sample(seconds_budget=30.0):
     plain numpy/scipy; its BLAS may run some products on several threads, so the cores it used are
     measured as process CPU time over wall time for the pass.
     """
-    import numpy as np
     import workloads as W
     from oracle import capacitance as OC
     from oracle import schrodinger as OS
