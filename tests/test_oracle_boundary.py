@@ -206,3 +206,54 @@ def test_charged_gate_and_surface_charge_sensitivities():
     fd = central(lambda d2, s: d2["gates"][3]["robin"].__setitem__("sigma", 5e-4 + s), 1e-5)
     assert np.max(np.abs(fd - gate[3])) < 1e-4 * np.max(np.abs(gate[3]))
     assert dN_dV[1, 3] > 1.0 and gate[3][1] > 0.0              # the plunger and its charge fill dot 1
+
+
+def test_random_stacks_match_the_capacitor_network():
+    # random linear stacks (layer permittivities, thicknesses and element counts), a charged top gate
+    # (random sigma and d) and sheets on random interfaces: at every layer boundary the potential is
+    # that of the lumped network of per-area capacitors eps_r/t with the sheets as node charges and the
+    # gate behind c = eps_top/d (Gauss's law; linear elements are nodally exact on such stacks)
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=25, deadline=None)
+    @hyp.given(st.lists(st.tuples(st.floats(1.5, 15.0), st.integers(1, 6), st.integers(1, 3)), min_size=1, max_size=4),
+               st.floats(-1.0, 1.0), st.floats(-3e-3, 3e-3), st.floats(0.5, 20.0),
+               st.lists(st.floats(-3e-3, 3e-3), min_size=3, max_size=3))
+    def check(layers, V, sig_g, d, sig_if):
+        mats = [dict(W.SI, eps_r=11.7)] + [dict(W.SIO2, eps_r=e) for e, _, _ in layers]
+        dev = dict(Lx=20.0, Ly=10.0, nx=2, ny=1,
+                   layers=[dict(material=q + 1, thickness=2.0 * t, n=n) for q, (_, t, n) in enumerate(layers)],
+                   materials=mats, gates=[dict(name="G", x0=0.0, x1=20.0, y0=0.0, y1=10.0, robin=dict(sigma=sig_g, d=d))],
+                   gate_work_function=None, bottom_ohmic=1, dots=[], subdomain=None,
+                   bias=dict(T=300.0, V_gate=[V], V_sub=0.0, statistics=1, incomplete_ionization=1))
+        zb = np.cumsum([0.0] + [2.0 * t for _, t, _ in layers])      # layer boundaries
+        sheets = [dict(z=float(zb[j]), x0=0.0, x1=20.0, y0=0.0, y1=10.0, sigma=sig_if[j - 1])
+                  for j in range(1, len(layers))]
+        dev["surface_charges"] = sheets
+        P = PoissonProblem(dev, linear=True)
+        phi = P.initial_guess(solver="direct")
+        m = len(layers)
+        c = [e / (2.0 * t) for e, t, _ in layers]
+        A = np.zeros((m, m))
+        b = np.zeros(m)
+        for j in range(1, m + 1):                # unknown u_j at boundary j (u_0 = phi_ohm)
+            A[j - 1, j - 1] += c[j - 1]
+            if j > 1:
+                A[j - 1, j - 2] -= c[j - 1]
+            else:
+                b[0] += c[0] * P.phi_ohm
+            if j < m:
+                A[j - 1, j - 1] += c[j]
+                A[j - 1, j] -= c[j]
+                b[j - 1] += P.qe * sig_if[j - 1]
+        cg = layers[-1][0] / d
+        A[m - 1, m - 1] += cg
+        b[m - 1] += cg * V + P.qe * sig_g
+        u = np.linalg.solve(A, b)
+        z = P.mesh.coords[:, 2]
+        for j in range(1, m + 1):
+            at = np.abs(z - zb[j]) < 1e-9
+            assert np.max(np.abs(phi[at] - u[j - 1])) < 1e-11 * max(1.0, np.max(np.abs(u)))
+
+    check()
