@@ -164,3 +164,32 @@ def test_bulk_neutrality_far_from_contacts():
     z = P.mesh.coords[:, 2]
     mid = np.abs(z - 150.0) < 12.0
     assert np.max(np.abs(phi[mid] - root)) < 1e-6
+
+
+def test_jacobian_matches_residual_differences_in_every_regime():
+    # random temperature (4-300 K), statistics (FD; MB from 77 K up, where it is meaningful), ionization
+    # model, gate voltages and potential perturbations: the hand-derived Jacobian against central
+    # differences of the residual (step 1e-3 kT), through every branch of the carrier statistics
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=20, deadline=None)
+    @hyp.given(st.sampled_from([4.0, 20.0, 77.0, 300.0]), st.booleans(), st.booleans(),
+               st.lists(st.floats(-0.5, 1.2), min_size=5, max_size=5), st.integers(0, 2 ** 31 - 1))
+    def check(T, mb, incomplete, V, seed):
+        stat = 0 if (mb and T >= 77.0) else 1
+        dev = W.five_gate_device(n=(6, 6, 5), T=T, statistics=stat, incomplete_ionization=int(incomplete))
+        dev["bias"]["V_gate"] = list(V)
+        P = PoissonProblem(dev)
+        rng = np.random.default_rng(seed)
+        ph = P.initial_guess(solver="direct")
+        ph[P.free] += 0.05 * rng.standard_normal(P.free.sum())
+        v = np.zeros_like(ph)
+        v[P.free] = rng.standard_normal(P.free.sum())
+        h = 1e-3 * physics.kT_eV(T)
+        fd = (P.residual(ph + h * v) - P.residual(ph - h * v)) / (2 * h)
+        Jv = P.jacobian(ph) @ v
+        Jv[P.dir] = 0.0
+        assert np.linalg.norm(Jv - fd) <= 1e-6 * np.linalg.norm(Jv)
+
+    check()
