@@ -98,8 +98,9 @@ def test_ohmic_contacts_are_neutral_roots(T, ntype):
     # MB, complete ionization: exact root of n + NA = p + ND (minority carriers negligible)
     r = P.neutral_root(mat, T, pr, 0.0, statistics=0, incomplete=0)
     assert abs(P.ohmic_potential(mat, T, pr, 0.0, statistics=0, incomplete=0) - r) < 1e-10
-    # MB, incomplete ionization: the y_n / y_p closed form is the exact root (its low-T log
-    # approximation below 50 K differs by far less than rounding there)
+    # MB, incomplete ionization: the y_n / y_p closed form is the exact root (at this doping its
+    # low-T log approximation below 50 K differs by far less than rounding; at 1e13 cm^-3 and 41 K
+    # the approximation alone moves the contact by 0.7 mV)
     r = P.neutral_root(mat, T, pr, 0.0, statistics=0, incomplete=1)
     assert abs(P.ohmic_potential(mat, T, pr, 0.0, statistics=0, incomplete=1) - r) < 1e-10
     # FD, complete ionization: the root uses the Bednarczyk F_1/2 (0.4 % in F, about 0.7 % in
