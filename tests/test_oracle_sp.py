@@ -130,3 +130,38 @@ def test_sp_loop_converges_monotonically_to_a_fixed_point(small_dot):
     P.set_quantum(E, rep["W"], phi)
     R = P.residual(phi)
     assert np.max(np.abs(R[P.free])) < 1e-5 * np.max(np.abs(P.K @ phi))
+
+
+def test_predictor_density_derivative_on_both_sides_of_the_cutoff():
+    # one level at a = (E_i - E_F - dphi)/kT drawn from [-150, 250], so the Fermi factor and its
+    # exp(-a) replacement above a = 100 both occur: d n~/d phi against central differences
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None)
+    @hyp.given(st.floats(0.5, 300.0), st.floats(-150.0, 250.0), st.integers(0, 2 ** 31 - 1))
+    def check(T, a_level, seed):
+        rng = np.random.default_rng(seed)
+        kT = physics.kT_eV(T)
+        E = np.array([a_level * kT])                      # E_F = 0
+        Wq = rng.uniform(0.1, 1.0, (3, 8, 1))
+        prev = rng.normal(0.0, 1.0, (3, 8))
+        ph = prev + 0.3 * kT * rng.standard_normal((3, 8))
+        n0, dn = sp.predictor_density(Wq, E, ph, prev, 0.0, kT)
+        h = 3e-4 * kT
+        n1, _ = sp.predictor_density(Wq, E, ph + h, prev, 0.0, kT)
+        n2, _ = sp.predictor_density(Wq, E, ph - h, prev, 0.0, kT)
+        fd = (n1 - n2) / (2 * h)
+        # (the difference quotient of n~ carries ~1e-16 n / h of rounding, which dominates for deeply
+        # occupied levels where d n~/d phi is tiny next to n~)
+        assert np.all(np.abs(fd - dn) <= 1e-6 * np.abs(dn) + 1e-14 * np.abs(n0) / h)
+        assert np.all(dn >= 0) and np.all(n0 >= 0)
+
+    check()
+    # and n~ joins continuously at the cutoff
+    kT = physics.kT_eV(4.0)
+    W1 = np.ones((1, 8, 1))
+    z = np.zeros((1, 8))
+    lo, _ = sp.predictor_density(W1, np.array([100.0 * kT * (1 - 1e-12)]), z, z, 0.0, kT)
+    hi, _ = sp.predictor_density(W1, np.array([100.0 * kT * (1 + 1e-12)]), z, z, 0.0, kT)
+    assert abs(hi[0, 0] / lo[0, 0] - 1.0) < 1e-9
