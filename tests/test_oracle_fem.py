@@ -193,3 +193,47 @@ def test_jacobian_matches_residual_differences_in_every_regime():
         assert np.linalg.norm(Jv - fd) <= 1e-6 * np.linalg.norm(Jv)
 
     check()
+
+
+def test_general_hexahedra_match_the_affine_closed_forms():
+    # the oracle's element geometry is general (isoparametric); the devices only use boxes, whose
+    # Jacobian is diagonal and would hide a transposed inverse. On random sheared affine elements
+    # x = A xi + b: mass = |det A| (x)_d [[2/3, 1/3], [1/3, 2/3]], and the stiffness equals
+    # |det A| int grad_xi N_a^T (A^-1 A^-T) grad_xi N_b, integrated here by 3x3x3 Gauss-Legendre
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]]) / 3.0
+    mass_ref = np.kron(m1, np.kron(m1, m1))               # corner a = ax + 2 ay + 4 az: z (x) y (x) x
+    g3, w3 = np.polynomial.legendre.leggauss(3)
+    sgn = np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1] for a in range(8)], float)
+
+    def grad_ref(xi):                                      # dN_a/dxi_d of (1 + s xi)(1 + s eta)(1 + s zeta)/8
+        g = np.empty((8, 3))
+        for a in range(8):
+            f = 1.0 + sgn[a] * xi
+            g[a] = sgn[a] * np.array([f[1] * f[2], f[0] * f[2], f[0] * f[1]]) / 8.0
+        return g
+
+    @hyp.settings(max_examples=20, deadline=None)
+    @hyp.given(st.lists(st.floats(0.5, 3.0), min_size=3, max_size=3),
+               st.lists(st.floats(-0.4, 0.4), min_size=6, max_size=6), st.lists(st.floats(-5, 5), min_size=3, max_size=3))
+    def check(diag, shear, shift):
+        A = np.diag(diag)
+        A[0, 1], A[0, 2], A[1, 2], A[1, 0], A[2, 0], A[2, 1] = [s * max(diag) for s in shear]
+        det = np.linalg.det(A)
+        hyp.assume(det > 0.05 * np.prod(diag))
+        X = (sgn @ A.T + np.array(shift))[None]              # (1, 8, 3) corners at xi = +-1
+        wdet, grad = fem.geometry(X)
+        Me = fem.element_mass(wdet, np.ones((1, 8)))[0]
+        assert np.max(np.abs(Me - det * mass_ref)) < 1e-12 * det
+        Ke = fem.element_stiffness(wdet, grad, np.ones((1, 3)))[0]
+        G = np.linalg.inv(A) @ np.linalg.inv(A).T
+        ref = np.zeros((8, 8))
+        for a, wa in zip(g3, w3):
+            for b, wb in zip(g3, w3):
+                for c, wc in zip(g3, w3):
+                    gr = grad_ref(np.array([a, b, c]))
+                    ref += wa * wb * wc * det * gr @ G @ gr.T
+        assert np.max(np.abs(Ke - ref)) < 1e-11 * np.max(np.abs(ref))
+
+    check()
