@@ -257,3 +257,29 @@ def test_random_stacks_match_the_capacitor_network():
             assert np.max(np.abs(phi[at] - u[j - 1])) < 1e-11 * max(1.0, np.max(np.abs(u)))
 
     check()
+
+
+def test_plane_faces_are_the_quads_inside_the_closed_rectangle():
+    # random rectangles, including edges on grid lines: the selected quads are exactly those whose
+    # four corners lie in the closed rectangle (brute force over every quad of the plane)
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+    dev = W.mos_capacitor(nx=7, ny=5, nz=2, L=35.0, t_si=4.0, t_ox=2.0, n_ox=1)
+    m = Mesh(dev)
+    coord = st.one_of(st.floats(-2.0, 37.0), st.sampled_from([0.0, 5.0, 10.0, 17.5, 25.0, 35.0]))
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(coord, coord, coord, coord, st.integers(0, 2))
+    def check(xa, xb, ya, yb, k):
+        R = dict(x0=min(xa, xb), x1=max(xa, xb), y0=min(ya, yb), y1=max(ya, yb))
+        got = {tuple(sorted(f)) for f in boundary.plane_faces(m, k, R).tolist()}
+        want = set()
+        for j in range(m.ny):
+            for i in range(m.nx):
+                ids = [m.node_id(i + (a & 1), j + (a >> 1), k) for a in range(4)]
+                xy = m.coords[ids][:, :2]
+                if np.all((xy[:, 0] >= R["x0"]) & (xy[:, 0] <= R["x1"]) & (xy[:, 1] >= R["y0"]) & (xy[:, 1] <= R["y1"])):
+                    want.add(tuple(sorted(ids)))
+        assert got == want
+
+    check()
