@@ -144,7 +144,9 @@ typedef struct {
   int max_newton;
   int max_krylov;         /* per linear solve */
   int cheb_degree;        /* preconditioner: k >= 1 Chebyshev-Jacobi of degree k (1 = Jacobi);
-                             -1 geometric multigrid V-cycle (mixed precision only); 0 = autotuned */
+                             -1 geometric multigrid V-cycle (in the solve's precision: FP32 for
+                             precision 1, FP64 for precision 0); 0 = autotuned per mesh and
+                             precision among Jacobi, odd Chebyshev degrees and the V-cycle */
   int warm_start;         /* 1: phi holds the initial guess; 0: Laplace solve with the contact values */
   int linear;             /* 1: rho = 0 (dielectric-only solve) */
 } qcad_solver_opts;
@@ -198,8 +200,10 @@ qcad_status qcad_poisson_jv(qcad_mesh_t m, const qcad_bias* b, const double* phi
                             double* y, int precision);
 
 /* Newton solve of the nonlinear Poisson equation (Sec. II.A; solved by a
- * Newton solver in the paper, Sec. II.A.3) with a Chebyshev-Jacobi PCG linear
- * solver, to the tolerances in o. phi: device [n_nodes]; input guess when
+ * Newton solver in the paper, Sec. II.A.3) with a PCG linear solver whose
+ * preconditioner o->cheb_degree selects (autotuned by default: on meshes that
+ * coarsen, the geometric multigrid V-cycle wins in both precisions), to the
+ * tolerances in o. phi: device [n_nodes]; input guess when
  * o->warm_start, output solution (Dirichlet entries set to contact values).
  * fixed_charge_elem: device [n_elems] or NULL. rep: host or NULL.
  * Errors: NOT_CONVERGED (phi holds the last iterate, rep filled),
@@ -241,7 +245,7 @@ qcad_status qcad_schrodinger_apply(qcad_mesh_t m, const qcad_bias* b, const doub
                                    int nvec, const double* X, double* HX, double* MX, int precision);
 
 /* Lowest nev eigenpairs of H psi = E M psi on the subdomain by LOBPCG with a
- * Jacobi preconditioner and FP64 Rayleigh-Ritz (the paper uses an Anasazi
+ * degree-5 Chebyshev-Jacobi preconditioner and FP64 Rayleigh-Ritz (the paper uses an Anasazi
  * eigensolver, Sec. II.B). phi: device [n_nodes]. evals: host [nev], eV,
  * ascending. evecs: device [n_sub_dof x nev] column-major, M-orthonormal, or
  * NULL. tol: relative residual ||H x - E M x|| / (|E| ||M x||) per pair.

@@ -98,52 +98,54 @@ template void launch_cheb_step_lin<double>(const Grid<double>&, PcgVecs<double>,
 // w = r - J zp with zp = d[0] = omega D^-1 r, and the post-smoothing step that also closes the
 // PCG iteration, z = zq + omega D^-1 (r - J zq) with zq = d[1] = zp + P e (coarse correction),
 // accumulating r.z and running the last block's bookkeeping as the Chebyshev step does.
+template <class T>
 struct MgResid0Op {
   static constexpr int NIN = 1;
   static constexpr bool SEPM = false;
   struct Pre {
-    float r;
+    T r;
   };
-  PcgVecs<float> v;
+  PcgVecs<T> v;
   PcgScalars* sc;
   __device__ bool skip() const { return sc->done != 0; }
   __device__ void set_vec(int) {}
-  __device__ const float* coeffs() const { return v.c; }
-  __device__ const float* lin_src(int) const { return v.d[0]; }
-  __device__ float lin_mix(float x0, float) const { return x0; }
-  __device__ float lin_in(int n) const { return v.d[0][n]; }
+  __device__ const T* coeffs() const { return v.c; }
+  __device__ const T* lin_src(int) const { return v.d[0]; }
+  __device__ T lin_mix(T x0, T) const { return x0; }
+  __device__ T lin_in(int n) const { return v.d[0][n]; }
   __device__ Pre lin_pre(int n) const { return Pre{v.r[n]}; }
   __device__ bool lin_dir() const { return true; }
-  __device__ void lin_out(int n, const Pre& p, float, float y) { v.w[n] = p.r - y; }
+  __device__ void lin_out(int n, const Pre& p, T, T y) { v.w[n] = p.r - y; }
   __device__ void finish() {}
 };
 
+template <class T>
 struct MgPost0Op {
   static constexpr int NIN = 1;
   static constexpr bool SEPM = false;
   struct Pre {
-    float r, dinv;
+    T r, dinv;
   };
-  PcgVecs<float> v;
+  PcgVecs<T> v;
   PcgScalars* sc;
-  const float* par;
-  float om;
+  const T* par;
+  T om;
   int t, slot;
-  float acc;
+  T acc;
   __device__ bool skip() const { return sc->done != 0; }
   __device__ void set_vec(int) {
     t = sc->t;
     slot = sc->phase == 0 ? 0 : ((t + 1) & 3);
-    om = mg_omega(par, 0);
+    om = mg_omega<T>(par, 0);
   }
-  __device__ const float* coeffs() const { return v.c; }
-  __device__ const float* lin_src(int) const { return v.d[1]; }
-  __device__ float lin_mix(float x0, float) const { return x0; }
-  __device__ float lin_in(int n) const { return v.d[1][n]; }
+  __device__ const T* coeffs() const { return v.c; }
+  __device__ const T* lin_src(int) const { return v.d[1]; }
+  __device__ T lin_mix(T x0, T) const { return x0; }
+  __device__ T lin_in(int n) const { return v.d[1][n]; }
   __device__ Pre lin_pre(int n) const { return Pre{v.r[n], v.dinv[n]}; }
   __device__ bool lin_dir() const { return true; }
-  __device__ void lin_out(int n, const Pre& p, float zq, float y) {
-    const float z = zq + om * p.dinv * (p.r - y);
+  __device__ void lin_out(int n, const Pre& p, T zq, T y) {
+    const T z = zq + om * p.dinv * (p.r - y);
     v.z[n] = z;
     acc += p.r * z;
   }
@@ -154,21 +156,28 @@ struct MgPost0Op {
   }
 };
 
-void launch_mg_resid0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
-  MgResid0Op op = {};
+template <class T>
+void launch_mg_resid0(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s) {
+  MgResid0Op<T> op = {};
   op.v = v;
   op.sc = sc;
-  run_lin<float>(g, op, cfg, s);
+  run_lin<T>(g, op, cfg, s);
 }
+template void launch_mg_resid0<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, LaunchCfg, cudaStream_t);
+template void launch_mg_resid0<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, LaunchCfg, cudaStream_t);
 
-void launch_mg_post0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, const float* par, LaunchCfg cfg,
-                     cudaStream_t s) {
-  MgPost0Op op = {};
+template <class T>
+void launch_mg_post0(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, const T* par, LaunchCfg cfg, cudaStream_t s) {
+  MgPost0Op<T> op = {};
   op.v = v;
   op.sc = sc;
   op.par = par;
-  run_lin<float>(g, op, cfg, s);
+  run_lin<T>(g, op, cfg, s);
 }
+template void launch_mg_post0<float>(const Grid<float>&, PcgVecs<float>, PcgScalars*, const float*, LaunchCfg,
+                                     cudaStream_t);
+template void launch_mg_post0<double>(const Grid<double>&, PcgVecs<double>, PcgScalars*, const double*, LaunchCfg,
+                                      cudaStream_t);
 
 // Schrodinger operators for nvec vectors (blockIdx.z runs over (vector, z chunk)): H = kinetic
 // stencil (kappa_d = hbar^2/(2 m_d)) plus the V quadrature-point mass term, M = consistent mass,

@@ -1,5 +1,5 @@
 // Geometric multigrid V-cycle preconditioner (see mg.h): hierarchy construction, Galerkin
-// setup per FP32 linearization, and the V-cycle kernels of the coarse levels.
+// setup per linearization (FP32 or FP64), and the V-cycle kernels of the coarse levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,21 +18,30 @@ namespace {
 
 constexpr int MG_THREADS = 256;
 
-// Host side of one level.
+// Host side of one level: geometry and transfers shared by both precisions, operator and
+// vectors per precision (index 0 FP64, 1 FP32, the mesh's linearization-version index).
 struct MgLevel {
   int nx = 0, ny = 0, nz = 0;
   long long n = 0, ne = 0;
   std::vector<double> xs[3];  // node coordinates along x, y, z
-  DevBuf A, dinv, mask, b, x, w;
+  DevBuf mask;
+  DevBuf A[2], dinv[2], b[2], x[2], w[2];
   DevBuf em[3], pr[3], rs[3], ch[3];  // transfers to the next coarser level
-  MgLevelDev dev{};
+  MgLevelDev<double> d64{};
+  MgLevelDev<float> d32{};
 };
+
+template <class T> constexpr int prec_index() { return sizeof(T) == 8 ? 0 : 1; }
+template <class T> MgLevelDev<T>& level_dev(MgLevel& l);
+template <> MgLevelDev<double>& level_dev<double>(MgLevel& l) { return l.d64; }
+template <> MgLevelDev<float>& level_dev<float>(MgLevel& l) { return l.d32; }
 
 struct MgHier {
   std::deque<MgLevel> L;  // a deque: levels are created in place and never move
-  DevBuf par;  // per level: Gershgorin bound hi of D^-1 J (float)
+  DevBuf par[2];          // per level: Gershgorin bound hi of D^-1 J (in the precision's type)
   bool ok = false;
-  int lin_ver = -1;   // FP32 linearization the operators were built for
+  bool alloc[2] = {false, false};  // the precision's operators and vectors exist
+  long long lin_ver[2] = {-1, -1}; // linearization the operators were built for
 };
 
 MgHier* hier(qcad_mesh_s* m) { return static_cast<MgHier*>(m->mg.get()); }
@@ -116,7 +125,8 @@ int blocks_for(long long n, int threads = MG_THREADS) {
 // ---------------------------------------------------------------------------
 // Kernels: masks and Galerkin setup.
 
-__device__ __forceinline__ void node_ijk(const MgLevelDev& L, long long n, int& i, int& j, int& k) {
+template <class T>
+__device__ __forceinline__ void node_ijk(const MgLevelDev<T>& L, long long n, int& i, int& j, int& k) {
   i = (int)(n % L.nxn);
   const long long r = n / L.nxn;
   j = (int)(r % L.nyn);
@@ -134,7 +144,7 @@ __global__ void mg_mask0_kernel(const Grid<float> g, unsigned char* mask) {
 }
 
 // Coarse node Dirichlet iff its coincident fine node is.
-__global__ void mg_mask_coarsen_kernel(const MgLevelDev F, const MgLevelDev C, unsigned char* cmask) {
+__global__ void mg_mask_coarsen_kernel(const MgLevelDev<float> F, const MgLevelDev<float> C, unsigned char* cmask) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)C.nxn * C.nyn * C.nzn;
   if (n >= nn) return;
@@ -147,13 +157,14 @@ __global__ void mg_mask_coarsen_kernel(const MgLevelDev F, const MgLevelDev C, u
 // Row `a` of a fine element matrix P-transformed from the right, accumulated into the coarse
 // element matrix: AE[R][C] += P[a][R] (row_a P)[C], with P = px (x) py (x) pz (2 x 2 factors,
 // [fine corner][coarse corner]).
-__device__ __forceinline__ void mg_accum_row(float (&AE)[64], const float (&row)[8], int a, const float (&px)[4],
-                                             const float (&py)[4], const float (&pz)[4]) {
-  float u[8], t[8];
+template <class T>
+__device__ __forceinline__ void mg_accum_row(T (&AE)[64], const T (&row)[8], int a, const T (&px)[4],
+                                             const T (&py)[4], const T (&pz)[4]) {
+  T u[8], t[8];
   // right multiplication by P, one axis at a time: t[C] = sum_b row[b] P[b][C]
 #pragma unroll
   for (int yz = 0; yz < 4; ++yz) {
-    const float r0 = row[2 * yz], r1 = row[2 * yz + 1];
+    const T r0 = row[2 * yz], r1 = row[2 * yz + 1];
     u[2 * yz] = r0 * px[0] + r1 * px[2];
     u[2 * yz + 1] = r0 * px[1] + r1 * px[3];
   }
@@ -161,150 +172,161 @@ __device__ __forceinline__ void mg_accum_row(float (&AE)[64], const float (&row)
   for (int z = 0; z < 2; ++z)
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
-      const float r0 = u[x + 4 * z], r1 = u[x + 2 + 4 * z];
+      const T r0 = u[x + 4 * z], r1 = u[x + 2 + 4 * z];
       t[x + 4 * z] = r0 * py[0] + r1 * py[2];
       t[x + 2 + 4 * z] = r0 * py[1] + r1 * py[3];
     }
 #pragma unroll
   for (int xy = 0; xy < 4; ++xy) {
-    const float r0 = t[xy], r1 = t[xy + 4];
+    const T r0 = t[xy], r1 = t[xy + 4];
     u[xy] = r0 * pz[0] + r1 * pz[2];
     u[xy + 4] = r0 * pz[1] + r1 * pz[3];
   }
   // P[a][R] factors by selection (a is a runtime index; indexing the arrays with it would
   // move them to local memory)
   const bool ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-  const float qx[2] = {ax ? px[2] : px[0], ax ? px[3] : px[1]};
-  const float qy[2] = {ay ? py[2] : py[0], ay ? py[3] : py[1]};
-  const float qz[2] = {az ? pz[2] : pz[0], az ? pz[3] : pz[1]};
+  const T qx[2] = {ax ? px[2] : px[0], ax ? px[3] : px[1]};
+  const T qy[2] = {ay ? py[2] : py[0], ay ? py[3] : py[1]};
+  const T qz[2] = {az ? pz[2] : pz[0], az ? pz[3] : pz[1]};
 #pragma unroll
   for (int R = 0; R < 8; ++R) {
-    const float pa = qx[R & 1] * qy[(R >> 1) & 1] * qz[R >> 2];
+    const T pa = qx[R & 1] * qy[(R >> 1) & 1] * qz[R >> 2];
 #pragma unroll
     for (int C = 0; C < 8; ++C) AE[8 * R + C] += pa * u[C];
   }
 }
 
-__device__ __forceinline__ void mg_store_masked(const MgLevelDev& Cl, int I, int J, int K, float (&AE)[64],
-                                                float* out) {
+__device__ __forceinline__ void store4(float* o, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* o, const double (&v)[4]) {
+  reinterpret_cast<double2*>(o)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(o)[1] = make_double2(v[2], v[3]);
+}
+
+template <class T>
+__device__ __forceinline__ void mg_store_masked(const MgLevelDev<T>& Cl, int I, int J, int K, T (&AE)[64], T* out) {
   bool dm[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const long long nd = (I + (c & 1)) + (long long)Cl.nxn * ((J + ((c >> 1) & 1)) + (long long)Cl.nyn * (K + (c >> 2)));
     dm[c] = Cl.mask[nd] != 0;
   }
-  float4* o = reinterpret_cast<float4*>(out);
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
-    float v[4];
+    T v[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int R = (4 * q + s) >> 3, C = (4 * q + s) & 7;
-      v[s] = (dm[R] || dm[C]) ? 0.0f : AE[4 * q + s];
+      v[s] = (dm[R] || dm[C]) ? T(0) : AE[4 * q + s];
     }
-    o[q] = make_float4(v[0], v[1], v[2], v[3]);
+    store4(out + 4 * q, v);
   }
 }
 
 // Row a of the fine-mesh element matrix of element (i, j, k) (stiffness from the 1D element
 // matrices, mass term from the 8 quadrature coefficients c), with the columns of Dirichlet
 // corners zeroed.
-__device__ __forceinline__ void mg_fine_row(const Grid<float>& g, int i, int j, int k, const float (&c)[8],
-                                            const bool (&dm)[8], int a, float (&row)[8]) {
-  const float mxo = g.mx[3 * i + 2], kxo = g.kx[3 * i + 2];
-  const float myo = g.my[3 * j + 2], kyo = g.ky[3 * j + 2];
-  const float mzxo = g.mzx[3 * k + 2], mzyo = g.mzy[3 * k + 2], kzo = g.kzz[3 * k + 2];
+template <class T>
+__device__ __forceinline__ void mg_fine_row(const Grid<T>& g, int i, int j, int k, const T (&c)[8],
+                                            const bool (&dm)[8], int a, T (&row)[8]) {
+  const T mxo = g.mx[3 * i + 2], kxo = g.kx[3 * i + 2];
+  const T myo = g.my[3 * j + 2], kyo = g.ky[3 * j + 2];
+  const T mzxo = g.mzx[3 * k + 2], mzyo = g.mzy[3 * k + 2], kzo = g.kzz[3 * k + 2];
   const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-  const float GA = GaussConst<float>::a(), GB = GaussConst<float>::b();
-  float u[8];
+  const T GA = GaussConst<T>::a(), GB = GaussConst<T>::b();
+  T u[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float bq = ((q & 1) == ax ? GA : GB) * (((q >> 1) & 1) == ay ? GA : GB) * ((q >> 2) == az ? GA : GB);
+    const T bq = ((q & 1) == ax ? GA : GB) * (((q >> 1) & 1) == ay ? GA : GB) * ((q >> 2) == az ? GA : GB);
     u[q] = c[q] * bq;
   }
-  float mrow[8];
-  tp_apply<float>(u, mrow, GA, GB);
+  T mrow[8];
+  tp_apply<T>(u, mrow, GA, GB);
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
-    const float Mx = (bx == ax ? 2.0f : 1.0f) * mxo, Kx = (bx == ax ? -kxo : kxo);
-    const float My = (by == ay ? 2.0f : 1.0f) * myo, Ky = (by == ay ? -kyo : kyo);
-    const float Mzx = (bz == az ? 2.0f : 1.0f) * mzxo, Mzy = (bz == az ? 2.0f : 1.0f) * mzyo;
-    const float Kz = (bz == az ? -kzo : kzo);
-    const float v = Kx * My * Mzx + Mx * Ky * Mzy + Mx * My * Kz + mrow[b];
-    row[b] = dm[b] ? 0.0f : v;
+    const T Mx = (bx == ax ? T(2) : T(1)) * mxo, Kx = (bx == ax ? -kxo : kxo);
+    const T My = (by == ay ? T(2) : T(1)) * myo, Ky = (by == ay ? -kyo : kyo);
+    const T Mzx = (bz == az ? T(2) : T(1)) * mzxo, Mzy = (bz == az ? T(2) : T(1)) * mzyo;
+    const T Kz = (bz == az ? -kzo : kzo);
+    const T v = Kx * My * Mzx + Mx * Ky * Mzy + Mx * My * Kz + mrow[b];
+    row[b] = dm[b] ? T(0) : v;
   }
 }
 
-// Level-1 element matrices from the mesh operator (FP32 coefficients c, 8 per element).
-__global__ void __launch_bounds__(128) mg_galerkin0_kernel(const Grid<float> g, const float* __restrict__ coef,
-                                                           const MgLevelDev F, const MgLevelDev Cl, float* Aout) {
+// Level-1 element matrices from the mesh operator (coefficients c, 8 per element).
+template <class T>
+__global__ void __launch_bounds__(128) mg_galerkin0_kernel(const Grid<T> g, const T* __restrict__ coef,
+                                                           const MgLevelDev<T> F, const MgLevelDev<T> Cl, T* Aout) {
   const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long ne = (long long)Cl.nx * Cl.ny * Cl.nz;
   if (E >= ne) return;
   const int I = (int)(E % Cl.nx);
   const long long r = E / Cl.nx;
   const int J = (int)(r % Cl.ny), K = (int)(r / Cl.ny);
-  float AE[64];
+  T AE[64];
 #pragma unroll
-  for (int q = 0; q < 64; ++q) AE[q] = 0.0f;
+  for (int q = 0; q < 64; ++q) AE[q] = T(0);
   const MgChild cx = F.ch[0][I], cy = F.ch[1][J], cz = F.ch[2][K];
   for (int k = cz.first; k < cz.first + cz.count; ++k)
     for (int j = cy.first; j < cy.first + cy.count; ++j)
       for (int i = cx.first; i < cx.first + cx.count; ++i) {
         const MgElemMap ex = F.em[0][i], ey = F.em[1][j], ez = F.em[2][k];
-        const float px[4] = {ex.p00, ex.p01, ex.p10, ex.p11};
-        const float py[4] = {ey.p00, ey.p01, ey.p10, ey.p11};
-        const float pz[4] = {ez.p00, ez.p01, ez.p10, ez.p11};
-        float c[8];
-        load_c8<float>(coef, i + (long long)g.nx * (j + (long long)g.ny * k), c);
+        const T px[4] = {(T)ex.p00, (T)ex.p01, (T)ex.p10, (T)ex.p11};
+        const T py[4] = {(T)ey.p00, (T)ey.p01, (T)ey.p10, (T)ey.p11};
+        const T pz[4] = {(T)ez.p00, (T)ez.p01, (T)ez.p10, (T)ez.p11};
+        T c[8];
+        load_c8<T>(coef, i + (long long)g.nx * (j + (long long)g.ny * k), c);
         bool dm[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           dm[q] = F.mask[(i + (q & 1)) + (long long)F.nxn * ((j + ((q >> 1) & 1)) + (long long)F.nyn * (k + (q >> 2)))] != 0;
         for (int a = 0; a < 8; ++a) {
           if (dm[a]) continue;
-          float row[8];
-          mg_fine_row(g, i, j, k, c, dm, a, row);
-          mg_accum_row(AE, row, a, px, py, pz);
+          T row[8];
+          mg_fine_row<T>(g, i, j, k, c, dm, a, row);
+          mg_accum_row<T>(AE, row, a, px, py, pz);
         }
       }
-  mg_store_masked(Cl, I, J, K, AE, Aout + 64 * E);
+  mg_store_masked<T>(Cl, I, J, K, AE, Aout + 64 * E);
 }
 
 // Level l+1 element matrices from the stored level-l ones.
-__global__ void __launch_bounds__(128) mg_galerkin_kernel(const MgLevelDev F, const MgLevelDev Cl, float* Aout) {
+template <class T>
+__global__ void __launch_bounds__(128) mg_galerkin_kernel(const MgLevelDev<T> F, const MgLevelDev<T> Cl, T* Aout) {
   const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long ne = (long long)Cl.nx * Cl.ny * Cl.nz;
   if (E >= ne) return;
   const int I = (int)(E % Cl.nx);
   const long long r = E / Cl.nx;
   const int J = (int)(r % Cl.ny), K = (int)(r / Cl.ny);
-  float AE[64];
+  T AE[64];
 #pragma unroll
-  for (int q = 0; q < 64; ++q) AE[q] = 0.0f;
+  for (int q = 0; q < 64; ++q) AE[q] = T(0);
   const MgChild cx = F.ch[0][I], cy = F.ch[1][J], cz = F.ch[2][K];
   for (int k = cz.first; k < cz.first + cz.count; ++k)
     for (int j = cy.first; j < cy.first + cy.count; ++j)
       for (int i = cx.first; i < cx.first + cx.count; ++i) {
         const MgElemMap ex = F.em[0][i], ey = F.em[1][j], ez = F.em[2][k];
-        const float px[4] = {ex.p00, ex.p01, ex.p10, ex.p11};
-        const float py[4] = {ey.p00, ey.p01, ey.p10, ey.p11};
-        const float pz[4] = {ez.p00, ez.p01, ez.p10, ez.p11};
-        const float4* Ae = reinterpret_cast<const float4*>(F.A + 64 * (i + (long long)F.nx * (j + (long long)F.ny * k)));
+        const T px[4] = {(T)ex.p00, (T)ex.p01, (T)ex.p10, (T)ex.p11};
+        const T py[4] = {(T)ey.p00, (T)ey.p01, (T)ey.p10, (T)ey.p11};
+        const T pz[4] = {(T)ez.p00, (T)ez.p01, (T)ez.p10, (T)ez.p11};
+        const T* Ae = F.A + 64 * (i + (long long)F.nx * (j + (long long)F.ny * k));
         for (int a = 0; a < 8; ++a) {
-          const float4 r0 = __ldg(Ae + 2 * a), r1 = __ldg(Ae + 2 * a + 1);
-          const float row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-          mg_accum_row(AE, row, a, px, py, pz);
+          T row[8];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) row[b] = __ldg(Ae + 8 * a + b);
+          mg_accum_row<T>(AE, row, a, px, py, pz);
         }
       }
-  mg_store_masked(Cl, I, J, K, AE, Aout + 64 * E);
+  mg_store_masked<T>(Cl, I, J, K, AE, Aout + 64 * E);
 }
 
 // For every element E of level L that contains node (i, j, k): f(row of the node in E's matrix,
 // E's first corner node, the node's corner in E).
-template <class F>
-__device__ __forceinline__ void mg_for_adjacent(const MgLevelDev& L, int i, int j, int k, F&& f) {
+template <class T, class F>
+__device__ __forceinline__ void mg_for_adjacent(const MgLevelDev<T>& L, int i, int j, int k, F&& f) {
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
@@ -317,81 +339,105 @@ __device__ __forceinline__ void mg_for_adjacent(const MgLevelDev& L, int i, int 
   }
 }
 
-__device__ __forceinline__ float mg_row_dot(const MgLevelDev& L, const float* row, long long n0, const float* x) {
+__device__ __forceinline__ void load_row8(const float* row, float (&r)[8]) {
   const float4 r0 = __ldg(reinterpret_cast<const float4*>(row)), r1 = __ldg(reinterpret_cast<const float4*>(row) + 1);
-  const long long sy = L.nxn, sz = (long long)L.nxn * L.nyn;
-  return r0.x * x[n0] + r0.y * x[n0 + 1] + r0.z * x[n0 + sy] + r0.w * x[n0 + sy + 1] + r1.x * x[n0 + sz] +
-         r1.y * x[n0 + sz + 1] + r1.z * x[n0 + sz + sy] + r1.w * x[n0 + sz + sy + 1];
+  r[0] = r0.x, r[1] = r0.y, r[2] = r0.z, r[3] = r0.w, r[4] = r1.x, r[5] = r1.y, r[6] = r1.z, r[7] = r1.w;
+}
+__device__ __forceinline__ void load_row8(const double* row, double (&r)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(row) + q);
+    r[2 * q] = v.x, r[2 * q + 1] = v.y;
+  }
 }
 
-__device__ __forceinline__ void mg_block_max(float v, float* dst) {
-  __shared__ float red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL_MASK, v, o));
+template <class T>
+__device__ __forceinline__ T mg_row_dot(const MgLevelDev<T>& L, const T* row, long long n0, const T* x) {
+  T r[8];
+  load_row8(row, r);
+  const long long sy = L.nxn, sz = (long long)L.nxn * L.nyn;
+  return r[0] * x[n0] + r[1] * x[n0 + 1] + r[2] * x[n0 + sy] + r[3] * x[n0 + sy + 1] + r[4] * x[n0 + sz] +
+         r[5] * x[n0 + sz + 1] + r[6] * x[n0 + sz + sy] + r[7] * x[n0 + sz + sy + 1];
+}
+
+// Maximum over the block of non-negative values, folded into *dst by an integer atomicMax on the
+// bit pattern (non-negative IEEE values order like their bit patterns; the FP64 overload is in
+// qcad_internal.cuh).
+__device__ __forceinline__ void atomic_max_nonneg(float* dst, float v) {
+  atomicMax(reinterpret_cast<int*>(dst), __float_as_int(v));
+}
+
+template <class T>
+__device__ __forceinline__ void mg_block_max(T v, T* dst) {
+  __shared__ T red[32];
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL_MASK, v, o));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL_MASK, v, o));
-    if (lane == 0 && v > 0.0f) atomicMax(reinterpret_cast<int*>(dst), __float_as_int(v));
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(0);
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL_MASK, v, o));
+    if (lane == 0 && v > T(0)) atomic_max_nonneg(dst, v);
   }
 }
 
 // Diagonal, D^-1 and the Gershgorin bound max_i sum_j |J_ij| / J_ii of a coarse level.
-__global__ void mg_diag_kernel(const MgLevelDev L, float* dinv, float* par_l) {
+template <class T>
+__global__ void mg_diag_kernel(const MgLevelDev<T> L, T* dinv, T* par_l) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)L.nxn * L.nyn * L.nzn;
-  float ratio = 0.0f;
+  T ratio = T(0);
   if (n < nn) {
     int i, j, k;
     node_ijk(L, n, i, j, k);
-    float dg = 0.0f, ra = 0.0f;
-    mg_for_adjacent(L, i, j, k, [&](const float* row, long long, int c) {
+    T dg = T(0), ra = T(0);
+    mg_for_adjacent(L, i, j, k, [&](const T* row, long long, int c) {
       dg += row[c];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ra += fabsf(row[q]);
+      for (int q = 0; q < 8; ++q) ra += fabs(row[q]);
     });
-    const bool dir = L.mask[n] != 0 || !(dg > 0.0f);
-    dinv[n] = dir ? 0.0f : 1.0f / dg;
-    ratio = dir ? 0.0f : ra / dg;
+    const bool dir = L.mask[n] != 0 || !(dg > T(0));
+    dinv[n] = dir ? T(0) : T(1) / dg;
+    ratio = dir ? T(0) : ra / dg;
   }
-  mg_block_max(ratio, par_l);
+  mg_block_max<T>(ratio, par_l);
 }
 
 // Gershgorin bound of D^-1 J on the mesh (rows of the element matrices rebuilt from the
 // coefficients; Dirichlet rows are identity rows there, ratio 1).
-__global__ void mg_gersh0_kernel(const Grid<float> g, const float* __restrict__ coef, const MgLevelDev F,
-                                 const float* dinv0, float* par0) {
+template <class T>
+__global__ void mg_gersh0_kernel(const Grid<T> g, const T* __restrict__ coef, const MgLevelDev<T> F,
+                                 const T* dinv0, T* par0) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)F.nxn * F.nyn * F.nzn;
-  float ratio = 0.0f;
+  T ratio = T(0);
   if (n < nn) {
     int i, j, k;
     node_ijk(F, n, i, j, k);
     if (F.mask[n]) {
-      ratio = 1.0f;
+      ratio = T(1);
     } else {
-      float ra = 0.0f;
+      T ra = T(0);
       for (int e = 0; e < 8; ++e) {
         const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
         const int I = i - 1 + ex, J = j - 1 + ey, K = k - 1 + ez;
         if (I < 0 || J < 0 || K < 0 || I >= F.nx || J >= F.ny || K >= F.nz) continue;
         const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-        float c[8];
-        load_c8<float>(coef, I + (long long)g.nx * (J + (long long)g.ny * K), c);
+        T c[8];
+        load_c8<T>(coef, I + (long long)g.nx * (J + (long long)g.ny * K), c);
         bool dm[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           dm[q] = F.mask[(I + (q & 1)) + (long long)F.nxn * ((J + ((q >> 1) & 1)) + (long long)F.nyn * (K + (q >> 2)))] != 0;
-        float row[8];
-        mg_fine_row(g, I, J, K, c, dm, a, row);
+        T row[8];
+        mg_fine_row<T>(g, I, J, K, c, dm, a, row);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ra += fabsf(row[q]);
+        for (int q = 0; q < 8; ++q) ra += fabs(row[q]);
       }
       ratio = ra * dinv0[n];
     }
   }
-  mg_block_max(ratio, par0);
+  mg_block_max<T>(ratio, par0);
 }
 
 // ---------------------------------------------------------------------------
@@ -400,12 +446,13 @@ __global__ void mg_gersh0_kernel(const Grid<float> g, const float* __restrict__ 
 
 // PCG start with the multigrid preconditioner: x = 0, r = b, ||r||^2, and the level-0
 // pre-smoothing zp = omega D^-1 r (into d[0]).
-__global__ void mg_pcg_init_kernel(int n, PcgVecs<float> v, PcgScalars* sc, const float* par) {
-  const float om = mg_omega(par, 0);
-  float rr = 0.0f;
+template <class T>
+__global__ void mg_pcg_init_kernel(int n, PcgVecs<T> v, PcgScalars* sc, const T* par) {
+  const T om = mg_omega<T>(par, 0);
+  T rr = T(0);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const float r = v.b[idx];
-    v.x[idx] = 0.0f;
+    const T r = v.b[idx];
+    v.x[idx] = T(0);
     v.r[idx] = r;
     v.d[0][idx] = om * v.dinv[idx] * r;
     rr += r * r;
@@ -415,7 +462,8 @@ __global__ void mg_pcg_init_kernel(int n, PcgVecs<float> v, PcgScalars* sc, cons
 }
 
 // PCG update (alpha = rz / pAp): x += alpha p, r -= alpha Ap, ||r||^2, then zp = omega D^-1 r.
-__global__ void mg_pcg_update_kernel(int n, PcgVecs<float> v, PcgScalars* sc, const float* par) {
+template <class T>
+__global__ void mg_pcg_update_kernel(int n, PcgVecs<T> v, PcgScalars* sc, const T* par) {
   if (sc->done) return;
   const int t = sc->t;
   const double alpha_d = sc->rz[t & 3] / sc->pAp[t & 3];
@@ -427,13 +475,13 @@ __global__ void mg_pcg_update_kernel(int n, PcgVecs<float> v, PcgScalars* sc, co
     }
     return;
   }
-  const float alpha = (float)alpha_d;
-  const float om = mg_omega(par, 0);
-  const float* __restrict__ p = (t & 1) ? v.p[1] : v.p[0];
-  float rr = 0.0f;
+  const T alpha = (T)alpha_d;
+  const T om = mg_omega<T>(par, 0);
+  const T* __restrict__ p = (t & 1) ? v.p[1] : v.p[0];
+  T rr = T(0);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     v.x[idx] += alpha * p[idx];
-    const float r = v.r[idx] - alpha * v.Ap[idx];
+    const T r = v.r[idx] - alpha * v.Ap[idx];
     v.r[idx] = r;
     v.d[0][idx] = om * v.dinv[idx] * r;
     rr += r * r;
@@ -444,112 +492,120 @@ __global__ void mg_pcg_update_kernel(int n, PcgVecs<float> v, PcgScalars* sc, co
 
 // Restriction to level l+1 of the fine residual wf: b = P^T wf on the coarse free nodes, and
 // the coarse pre-smoothing x = omega D^-1 b.
-__global__ void mg_restrict_kernel(const MgLevelDev F, const float* __restrict__ wf, const MgLevelDev C,
-                                   const float* par, int lc, const PcgScalars* sc) {
+template <class T>
+__global__ void mg_restrict_kernel(const MgLevelDev<T> F, const T* __restrict__ wf, const MgLevelDev<T> C,
+                                   const T* par, int lc, const PcgScalars* sc) {
   if (sc->done) return;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)C.nxn * C.nyn * C.nzn;
   if (n >= nn) return;
   int I, J, K;
   node_ijk(C, n, I, J, K);
-  float b = 0.0f;
+  T b = T(0);
   if (!C.mask[n]) {
     const MgRestr rx = F.rs[0][I], ry = F.rs[1][J], rz = F.rs[2][K];
     const int fx[3] = {rx.f0, rx.f1, rx.f2}, fy[3] = {ry.f0, ry.f1, ry.f2}, fz[3] = {rz.f0, rz.f1, rz.f2};
-    const float wx[3] = {rx.w0, rx.w1, rx.w2}, wy[3] = {ry.w0, ry.w1, ry.w2}, wz[3] = {rz.w0, rz.w1, rz.w2};
+    const T wx[3] = {(T)rx.w0, (T)rx.w1, (T)rx.w2}, wy[3] = {(T)ry.w0, (T)ry.w1, (T)ry.w2};
+    const T wz[3] = {(T)rz.w0, (T)rz.w1, (T)rz.w2};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      if (wz[c] == 0.0f) continue;
+      if (wz[c] == T(0)) continue;
 #pragma unroll
       for (int bb = 0; bb < 3; ++bb) {
-        if (wy[bb] == 0.0f) continue;
+        if (wy[bb] == T(0)) continue;
         const long long base = (long long)F.nxn * (fy[bb] + (long long)F.nyn * fz[c]);
-        const float wyz = wy[bb] * wz[c];
+        const T wyz = wy[bb] * wz[c];
         b += wyz * (wx[0] * wf[base + fx[0]] + wx[1] * wf[base + fx[1]] + wx[2] * wf[base + fx[2]]);
       }
     }
   }
   C.b[n] = b;
-  C.x[n] = mg_omega(par, lc) * C.dinv[n] * b;
+  C.x[n] = mg_omega<T>(par, lc) * C.dinv[n] * b;
 }
 
 // Residual after pre-smoothing on a coarse level: w = b - A x.
-__global__ void mg_resid_kernel(const MgLevelDev L, const PcgScalars* sc) {
+template <class T>
+__global__ void mg_resid_kernel(const MgLevelDev<T> L, const PcgScalars* sc) {
   if (sc->done) return;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)L.nxn * L.nyn * L.nzn;
   if (n >= nn) return;
   int i, j, k;
   node_ijk(L, n, i, j, k);
-  float y = 0.0f;
-  mg_for_adjacent(L, i, j, k, [&](const float* row, long long n0, int) { y += mg_row_dot(L, row, n0, L.x); });
+  T y = T(0);
+  mg_for_adjacent(L, i, j, k, [&](const T* row, long long n0, int) { y += mg_row_dot<T>(L, row, n0, L.x); });
   L.w[n] = L.b[n] - y;
 }
 
 // Coarse correction of level l from the solution ec of level l+1: out = base + P ec on free
 // nodes (base on Dirichlet nodes).
-__global__ void mg_prolong_kernel(const MgLevelDev F, const float* __restrict__ ec, const MgLevelDev C,
-                                  const float* base, float* out, const PcgScalars* sc) {
+template <class T>
+__global__ void mg_prolong_kernel(const MgLevelDev<T> F, const T* __restrict__ ec, const MgLevelDev<T> C,
+                                  const T* base, T* out, const PcgScalars* sc) {
   if (sc->done) return;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)F.nxn * F.nyn * F.nzn;
   if (n >= nn) return;
-  float v = base[n];
+  T v = base[n];
   if (!F.mask[n]) {
     int i, j, k;
     node_ijk(F, n, i, j, k);
     const MgProl px = F.pr[0][i], py = F.pr[1][j], pz = F.pr[2][k];
     const long long sy = C.nxn, sz = (long long)C.nxn * C.nyn;
     const long long z0 = pz.c0 * sz, z1 = pz.c1 * sz, y0 = py.c0 * sy, y1 = py.c1 * sy;
-    const float e00 = px.w0 * ec[z0 + y0 + px.c0] + px.w1 * ec[z0 + y0 + px.c1];
-    const float e01 = px.w0 * ec[z0 + y1 + px.c0] + px.w1 * ec[z0 + y1 + px.c1];
-    const float e10 = px.w0 * ec[z1 + y0 + px.c0] + px.w1 * ec[z1 + y0 + px.c1];
-    const float e11 = px.w0 * ec[z1 + y1 + px.c0] + px.w1 * ec[z1 + y1 + px.c1];
-    v += pz.w0 * (py.w0 * e00 + py.w1 * e01) + pz.w1 * (py.w0 * e10 + py.w1 * e11);
+    const T xw0 = px.w0, xw1 = px.w1, yw0 = py.w0, yw1 = py.w1, zw0 = pz.w0, zw1 = pz.w1;
+    const T e00 = xw0 * ec[z0 + y0 + px.c0] + xw1 * ec[z0 + y0 + px.c1];
+    const T e01 = xw0 * ec[z0 + y1 + px.c0] + xw1 * ec[z0 + y1 + px.c1];
+    const T e10 = xw0 * ec[z1 + y0 + px.c0] + xw1 * ec[z1 + y0 + px.c1];
+    const T e11 = xw0 * ec[z1 + y1 + px.c0] + xw1 * ec[z1 + y1 + px.c1];
+    v += zw0 * (yw0 * e00 + yw1 * e01) + zw1 * (yw0 * e10 + yw1 * e11);
   }
   out[n] = v;
 }
 
 // Post-smoothing on a coarse level: w = x + omega D^-1 (b - A x) (the level's solution).
-__global__ void mg_post_kernel(const MgLevelDev L, const float* par, int l, const PcgScalars* sc) {
+template <class T>
+__global__ void mg_post_kernel(const MgLevelDev<T> L, const T* par, int l, const PcgScalars* sc) {
   if (sc->done) return;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)L.nxn * L.nyn * L.nzn;
   if (n >= nn) return;
   int i, j, k;
   node_ijk(L, n, i, j, k);
-  float y = 0.0f;
-  mg_for_adjacent(L, i, j, k, [&](const float* row, long long n0, int) { y += mg_row_dot(L, row, n0, L.x); });
-  L.w[n] = L.x[n] + mg_omega(par, l) * L.dinv[n] * (L.b[n] - y);
+  T y = T(0);
+  mg_for_adjacent(L, i, j, k, [&](const T* row, long long n0, int) { y += mg_row_dot<T>(L, row, n0, L.x); });
+  L.w[n] = L.x[n] + mg_omega<T>(par, l) * L.dinv[n] * (L.b[n] - y);
 }
 
 // Coarsest level: Chebyshev iteration of degree MG_COARSE_DEGREE for A x = b on
 // [hi / 64, hi] inside one block of 1024 threads, with the element matrices and the vectors
 // in shared memory; the result goes to w.
-__global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev L, const float* par, int l,
+template <class T>
+__global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev<T> L, const T* par, int l,
                                                          const PcgScalars* sc) {
   if (sc->done) return;
-  extern __shared__ float sh[];
+  extern __shared__ __align__(16) unsigned char mg_coarse_sh[];
+  T* sh = reinterpret_cast<T*>(mg_coarse_sh);
   const int ne = L.nx * L.ny * L.nz;
   const int nn = L.nxn * L.nyn * L.nzn;
-  float* sA = sh;               // 64 ne
-  float* sd = sA + 64 * ne;     // direction
-  float* sr = sd + nn;          // residual
-  float* sx = sr + nn;          // solution
+  T* sA = sh;               // 64 ne
+  T* sd = sA + 64 * ne;     // direction
+  T* sr = sd + nn;          // residual
+  T* sx = sr + nn;          // solution
   for (int q = threadIdx.x; q < 64 * ne; q += blockDim.x) sA[q] = L.A[q];
-  const float hi = par[l];
+  const T hi = par[l];
   const int n = threadIdx.x;  // one node per thread: the coarsest level has at most 512 nodes
   const bool own = n < nn;
-  if (!(hi > 0.0f)) {
-    if (own) L.w[n] = 0.0f;
+  if (!(hi > T(0))) {
+    if (own) L.w[n] = T(0);
     return;
   }
-  const float lo = hi / 64.0f;
-  const float theta = 0.5f * (hi + lo), delta = 0.5f * (hi - lo), sigma = theta / delta;
-  const float dv = own ? L.dinv[n] : 0.0f;
+  const T lo = hi / T(64);
+  const T theta = T(0.5) * (hi + lo), delta = T(0.5) * (hi - lo), sigma = theta / delta;
+  const T dv = own ? L.dinv[n] : T(0);
   if (own) {
-    const float r = L.b[n];
-    const float d = dv * r / theta;
+    const T r = L.b[n];
+    const T d = dv * r / theta;
     sr[n] = r;
     sd[n] = d;
     sx[n] = d;
@@ -562,18 +618,18 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev L, con
     j = (n / L.nxn) % L.nyn;
     k = n / sz;
   }
-  float rho = 1.0f / sigma;
+  T rho = T(1) / sigma;
   for (int it = 1; it < MG_COARSE_DEGREE; ++it) {
-    const float rho_new = 1.0f / (2.0f * sigma - rho);
-    const float c1 = rho_new * rho, c2 = 2.0f * rho_new / delta;
-    float y = 0.0f;
+    const T rho_new = T(1) / (T(2) * sigma - rho);
+    const T c1 = rho_new * rho, c2 = T(2) * rho_new / delta;
+    T y = T(0);
     if (own) {
       for (int e = 0; e < 8; ++e) {
         const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
         const int I = i - 1 + ex, J = j - 1 + ey, K = k - 1 + ez;
         if (I < 0 || J < 0 || K < 0 || I >= L.nx || J >= L.ny || K >= L.nz) continue;
         const int c = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-        const float* row = sA + 64 * (I + L.nx * (J + L.ny * K)) + 8 * c;
+        const T* row = sA + 64 * (I + L.nx * (J + L.ny * K)) + 8 * c;
         const int n0 = I + sy * (J + L.nyn * K);
         y += row[0] * sd[n0] + row[1] * sd[n0 + 1] + row[2] * sd[n0 + sy] + row[3] * sd[n0 + sy + 1] +
              row[4] * sd[n0 + sz] + row[5] * sd[n0 + sz + 1] + row[6] * sd[n0 + sz + sy] +
@@ -582,8 +638,8 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev L, con
     }
     __syncthreads();
     if (own) {
-      const float r = sr[n] - y;
-      const float d = c1 * sd[n] + c2 * dv * r;
+      const T r = sr[n] - y;
+      const T d = c1 * sd[n] + c2 * dv * r;
       sr[n] = r;
       sd[n] = d;
       sx[n] += d;
@@ -599,6 +655,10 @@ __global__ void __launch_bounds__(1024) mg_coarse_kernel(const MgLevelDev L, con
 
 // ---------------------------------------------------------------------------
 // Host.
+
+// Shared memory of the coarsest solve in precision T.
+static size_t coarse_smem_bytes(const MgLevel& co, size_t elem) { return ((size_t)64 * co.ne + 3 * (size_t)co.n) * elem; }
+static constexpr size_t MG_COARSE_SMEM_MAX = 200 * 1024;
 
 bool mg_prepare(qcad_mesh_s* m) {
   // charged gates: the hierarchy's level-0 kernels carry no Robin face term (Jacobi instead)
@@ -639,119 +699,174 @@ bool mg_prepare(qcad_mesh_s* m) {
     for (int a = 0; a < 3; ++a) c.xs[a] = ax[a].xc;
   }
   const MgLevel& co = L.back();
-  // usable when there is at least one coarse level and the coarsest fits one block's shared memory
-  const size_t coarse_smem = ((size_t)64 * co.ne + 3 * (size_t)co.n) * sizeof(float);
-  H->ok = L.size() >= 2 && co.n <= MG_COARSE_NODES && coarse_smem <= 200 * 1024;
+  // usable when there is at least one coarse level and the coarsest fits one block's shared
+  // memory in FP64 (so that both precisions can use the hierarchy)
+  H->ok = L.size() >= 2 && co.n <= MG_COARSE_NODES && coarse_smem_bytes(co, sizeof(double)) <= MG_COARSE_SMEM_MAX;
   if (!H->ok) return false;
   for (size_t l = 0; l < L.size(); ++l) {
     MgLevel& v = L[l];
     v.mask.ensure((size_t)v.n + 64);
-    if (l > 0) {
-      v.A.ensure((size_t)64 * v.ne * sizeof(float) + 64);
-      v.dinv.ensure((size_t)v.n * sizeof(float) + 64);
-      v.b.ensure((size_t)v.n * sizeof(float) + 64);
-      v.x.ensure((size_t)v.n * sizeof(float) + 64);
-      v.w.ensure((size_t)v.n * sizeof(float) + 64);
-    }
-    MgLevelDev& d = v.dev;
+    MgLevelDev<float>& d = v.d32;
+    d = MgLevelDev<float>{};
     d.nx = v.nx;
     d.ny = v.ny;
     d.nz = v.nz;
     d.nxn = v.nx + 1;
     d.nyn = v.ny + 1;
     d.nzn = v.nz + 1;
-    d.A = v.A.as<float>();
-    d.dinv = v.dinv.as<float>();
     d.mask = v.mask.as<unsigned char>();
-    d.b = v.b.as<float>();
-    d.x = v.x.as<float>();
-    d.w = v.w.as<float>();
     for (int a = 0; a < 3; ++a) {
       d.em[a] = v.em[a].as<MgElemMap>();
       d.pr[a] = v.pr[a].as<MgProl>();
       d.rs[a] = v.rs[a].as<MgRestr>();
       d.ch[a] = v.ch[a].as<MgChild>();
     }
+    MgLevelDev<double>& e = v.d64;
+    e = MgLevelDev<double>{};
+    e.nx = d.nx, e.ny = d.ny, e.nz = d.nz, e.nxn = d.nxn, e.nyn = d.nyn, e.nzn = d.nzn;
+    e.mask = d.mask;
+    for (int a = 0; a < 3; ++a) e.em[a] = d.em[a], e.pr[a] = d.pr[a], e.rs[a] = d.rs[a], e.ch[a] = d.ch[a];
   }
-  H->par.ensure(MG_MAX_LEVELS * sizeof(float) + 64);
   mg_mask0_kernel<<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(m->g32.g, L[0].mask.as<unsigned char>());
   for (size_t l = 0; l + 1 < L.size(); ++l)
-    mg_mask_coarsen_kernel<<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(L[l].dev, L[l + 1].dev,
+    mg_mask_coarsen_kernel<<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(L[l].d32, L[l + 1].d32,
                                                                           L[l + 1].mask.as<unsigned char>());
   // the largest coarsest level any mesh may have (checked above), so one setting serves all
-  CK(cudaFuncSetAttribute(mg_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(mg_coarse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)MG_COARSE_SMEM_MAX));
+  CK(cudaFuncSetAttribute(mg_coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)MG_COARSE_SMEM_MAX));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return true;
 }
 
+// Operators and vectors of precision T on every coarse level (first use of that precision).
+// Kernel arguments carry these pointers by value, so this runs before any V-cycle is captured.
+template <class T>
+static void mg_alloc(MgHier* H) {
+  const int p = prec_index<T>();
+  if (H->alloc[p]) return;
+  std::deque<MgLevel>& L = H->L;
+  for (size_t l = 1; l < L.size(); ++l) {
+    MgLevel& v = L[l];
+    v.A[p].ensure((size_t)64 * v.ne * sizeof(T) + 64);
+    v.dinv[p].ensure((size_t)v.n * sizeof(T) + 64);
+    v.b[p].ensure((size_t)v.n * sizeof(T) + 64);
+    v.x[p].ensure((size_t)v.n * sizeof(T) + 64);
+    v.w[p].ensure((size_t)v.n * sizeof(T) + 64);
+    MgLevelDev<T>& d = level_dev<T>(v);
+    d.A = v.A[p].template as<T>();
+    d.dinv = v.dinv[p].template as<T>();
+    d.b = v.b[p].template as<T>();
+    d.x = v.x[p].template as<T>();
+    d.w = v.w[p].template as<T>();
+  }
+  H->par[p].ensure(MG_MAX_LEVELS * sizeof(T) + 64);
+  H->alloc[p] = true;
+}
+
+template <class T>
+void mg_reserve(qcad_mesh_s* m) {
+  mg_alloc<T>(hier(m));
+}
+template void mg_reserve<float>(qcad_mesh_s*);
+template void mg_reserve<double>(qcad_mesh_s*);
+
 void mg_invalidate(qcad_mesh_s* m) {
-  if (m->mg) hier(m)->lin_ver = -1;
+  if (m->mg) hier(m)->lin_ver[0] = hier(m)->lin_ver[1] = -1;
 }
 
 int mg_levels(qcad_mesh_s* m) { return (m->mg && hier(m)->ok) ? (int)hier(m)->L.size() : 0; }
 
+template <class T> static const Grid<T>& mesh_grid(qcad_mesh_s* m);
+template <> const Grid<double>& mesh_grid<double>(qcad_mesh_s* m) { return m->g64.g; }
+template <> const Grid<float>& mesh_grid<float>(qcad_mesh_s* m) { return m->g32.g; }
+template <class T> static PcgBufs<T>& mesh_bufs(qcad_mesh_s* m);
+template <> PcgBufs<double>& mesh_bufs<double>(qcad_mesh_s* m) { return m->k64; }
+template <> PcgBufs<float>& mesh_bufs<float>(qcad_mesh_s* m) { return m->k32; }
+template <class T> static LaunchCfg mesh_cfg(qcad_mesh_s* m);
+template <> LaunchCfg mesh_cfg<double>(qcad_mesh_s* m) { return m->cfg64; }
+template <> LaunchCfg mesh_cfg<float>(qcad_mesh_s* m) { return m->cfg32; }
+
+template <class T>
 void mg_setup(qcad_mesh_s* m, cudaStream_t s, bool force) {
   MgHier* H = hier(m);
-  if (!force && H->lin_ver == m->lin_ver[1]) return;
+  const int p = prec_index<T>();
+  mg_alloc<T>(H);
+  if (!force && H->lin_ver[p] == m->lin_ver[p]) return;
   std::deque<MgLevel>& L = H->L;
-  const PcgBufs<float>& k = m->k32;
-  float* par = H->par.as<float>();
-  CK(cudaMemsetAsync(par, 0, MG_MAX_LEVELS * sizeof(float), s));
-  mg_gersh0_kernel<<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(m->g32.g, k.c.as<float>(), L[0].dev,
-                                                             k.dinv.as<float>(), par);
-  mg_galerkin0_kernel<<<blocks_for(L[1].ne, 128), 128, 0, s>>>(m->g32.g, k.c.as<float>(), L[0].dev, L[1].dev,
-                                                          L[1].A.as<float>());
+  const PcgBufs<T>& k = mesh_bufs<T>(m);
+  T* par = H->par[p].template as<T>();
+  CK(cudaMemsetAsync(par, 0, MG_MAX_LEVELS * sizeof(T), s));
+  mg_gersh0_kernel<T><<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(mesh_grid<T>(m), k.c.template as<T>(),
+                                                                level_dev<T>(L[0]), k.dinv.template as<T>(), par);
+  mg_galerkin0_kernel<T><<<blocks_for(L[1].ne, 128), 128, 0, s>>>(mesh_grid<T>(m), k.c.template as<T>(),
+                                                                  level_dev<T>(L[0]), level_dev<T>(L[1]),
+                                                                  L[1].A[p].template as<T>());
   for (size_t l = 1; l < L.size(); ++l) {
     if (l > 1)
-      mg_galerkin_kernel<<<blocks_for(L[l].ne, 128), 128, 0, s>>>(L[l - 1].dev, L[l].dev, L[l].A.as<float>());
-    mg_diag_kernel<<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(L[l].dev, L[l].dinv.as<float>(), par + l);
+      mg_galerkin_kernel<T><<<blocks_for(L[l].ne, 128), 128, 0, s>>>(level_dev<T>(L[l - 1]), level_dev<T>(L[l]),
+                                                                     L[l].A[p].template as<T>());
+    mg_diag_kernel<T><<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(level_dev<T>(L[l]), L[l].dinv[p].template as<T>(),
+                                                                par + l);
   }
   note_launch(2 + 2 * ((int)L.size() - 1) - 1);
   CK(cudaGetLastError());
-  H->lin_ver = m->lin_ver[1];
+  H->lin_ver[p] = m->lin_ver[p];
 }
+template void mg_setup<float>(qcad_mesh_s*, cudaStream_t, bool);
+template void mg_setup<double>(qcad_mesh_s*, cudaStream_t, bool);
 
 // V-cycle after the level-0 pre-smoothing (zp in d[0]): ends with z and the PCG bookkeeping.
-static void enqueue_vcycle(qcad_mesh_s* m, const PcgVecs<float>& v, PcgScalars* sc, cudaStream_t s) {
+template <class T>
+static void enqueue_vcycle(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, cudaStream_t s) {
   MgHier* H = hier(m);
   std::deque<MgLevel>& L = H->L;
-  const float* par = H->par.as<float>();
+  const int p = prec_index<T>();
+  const T* par = H->par[p].template as<T>();
   const int nl = (int)L.size();
-  launch_mg_resid0(m->g32.g, v, sc, m->cfg32, s);
+  launch_mg_resid0<T>(mesh_grid<T>(m), v, sc, mesh_cfg<T>(m), s);
   for (int l = 0; l + 1 < nl; ++l) {
-    const float* wf = l == 0 ? v.w : L[l].w.as<float>();
-    note_launch(), mg_restrict_kernel<<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(L[l].dev, wf, L[l + 1].dev,
-                                                                                      par, l + 1, sc);
-    if (l + 1 < nl - 1) note_launch(), mg_resid_kernel<<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(L[l + 1].dev, sc);
+    const T* wf = l == 0 ? v.w : L[l].w[p].template as<T>();
+    note_launch(), mg_restrict_kernel<T><<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(
+                       level_dev<T>(L[l]), wf, level_dev<T>(L[l + 1]), par, l + 1, sc);
+    if (l + 1 < nl - 1)
+      note_launch(), mg_resid_kernel<T><<<blocks_for(L[l + 1].n), MG_THREADS, 0, s>>>(level_dev<T>(L[l + 1]), sc);
   }
   const MgLevel& co = L[nl - 1];
-  const int smem = (int)(((size_t)64 * co.ne + 3 * (size_t)co.n) * sizeof(float));
-  note_launch(), mg_coarse_kernel<<<1, 1024, smem, s>>>(co.dev, par, nl - 1, sc);
+  const int smem = (int)coarse_smem_bytes(co, sizeof(T));
+  note_launch(), mg_coarse_kernel<T><<<1, 1024, smem, s>>>(level_dev<T>(L[nl - 1]), par, nl - 1, sc);
   for (int l = nl - 2; l >= 1; --l) {
-    note_launch(), mg_prolong_kernel<<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(L[l].dev, L[l + 1].w.as<float>(),
-                                                                                 L[l + 1].dev, L[l].x.as<float>(),
-                                                                                 L[l].x.as<float>(), sc);
-    note_launch(), mg_post_kernel<<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(L[l].dev, par, l, sc);
+    note_launch(), mg_prolong_kernel<T><<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(
+                       level_dev<T>(L[l]), L[l + 1].w[p].template as<T>(), level_dev<T>(L[l + 1]),
+                       L[l].x[p].template as<T>(), L[l].x[p].template as<T>(), sc);
+    note_launch(), mg_post_kernel<T><<<blocks_for(L[l].n), MG_THREADS, 0, s>>>(level_dev<T>(L[l]), par, l, sc);
   }
-  note_launch(), mg_prolong_kernel<<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(L[0].dev, L[1].w.as<float>(), L[1].dev,
-                                                                              v.d[0], v.d[1], sc);
-  launch_mg_post0(m->g32.g, v, sc, par, m->cfg32, s);
+  note_launch(), mg_prolong_kernel<T><<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(
+                     level_dev<T>(L[0]), L[1].w[p].template as<T>(), level_dev<T>(L[1]), v.d[0], v.d[1], sc);
+  launch_mg_post0<T>(mesh_grid<T>(m), v, sc, par, mesh_cfg<T>(m), s);
 }
 
 static int vec_grid(long long n) { return (int)std::min<long long>(4 * 152, std::max<long long>(1, (n + 255) / 256)); }
 
-void mg_enqueue_init(qcad_mesh_s* m, const PcgVecs<float>& v, PcgScalars* sc, cudaStream_t s) {
-  note_launch(), mg_pcg_init_kernel<<<vec_grid(m->n_nodes), 256, 0, s>>>((int)m->n_nodes, v, sc,
-                                                                         hier(m)->par.as<float>());
-  enqueue_vcycle(m, v, sc, s);
+template <class T>
+void mg_enqueue_init(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, cudaStream_t s) {
+  note_launch(), mg_pcg_init_kernel<T><<<vec_grid(m->n_nodes), 256, 0, s>>>(
+                     (int)m->n_nodes, v, sc, hier(m)->par[prec_index<T>()].template as<T>());
+  enqueue_vcycle<T>(m, v, sc, s);
 }
+template void mg_enqueue_init<float>(qcad_mesh_s*, const PcgVecs<float>&, PcgScalars*, cudaStream_t);
+template void mg_enqueue_init<double>(qcad_mesh_s*, const PcgVecs<double>&, PcgScalars*, cudaStream_t);
 
-void mg_enqueue_update(qcad_mesh_s* m, const PcgVecs<float>& v, PcgScalars* sc, cudaStream_t s) {
-  note_launch(), mg_pcg_update_kernel<<<vec_grid(m->n_nodes), 256, 0, s>>>((int)m->n_nodes, v, sc,
-                                                                           hier(m)->par.as<float>());
-  enqueue_vcycle(m, v, sc, s);
+template <class T>
+void mg_enqueue_update(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, cudaStream_t s) {
+  note_launch(), mg_pcg_update_kernel<T><<<vec_grid(m->n_nodes), 256, 0, s>>>(
+                     (int)m->n_nodes, v, sc, hier(m)->par[prec_index<T>()].template as<T>());
+  enqueue_vcycle<T>(m, v, sc, s);
 }
+template void mg_enqueue_update<float>(qcad_mesh_s*, const PcgVecs<float>&, PcgScalars*, cudaStream_t);
+template void mg_enqueue_update<double>(qcad_mesh_s*, const PcgVecs<double>&, PcgScalars*, cudaStream_t);
 
 int mg_launches_per_iteration(qcad_mesh_s* m) {
   const int nl = mg_levels(m);

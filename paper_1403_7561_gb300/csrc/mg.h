@@ -1,6 +1,6 @@
-// Geometric multigrid V-cycle preconditioner for the FP32 Jacobian J = K + M_c of the
-// mixed-precision Newton-Krylov solve (a preconditioner choice: the paper leaves the linear
-// solver's preconditioner open).
+// Geometric multigrid V-cycle preconditioner for the Jacobian J = K + M_c of the Newton-Krylov
+// solve, in FP32 (mixed precision) or FP64 (plain FP64) (a preconditioner choice: the paper
+// leaves the linear solver's preconditioner open).
 //
 // Levels: level 0 is the mesh; each coarser level keeps every other node plane along each axis
 // that has at least two elements (plus the last plane when the element count is odd), so a
@@ -44,13 +44,16 @@ struct MgChild {     // per coarse element: its first fine element and how many 
   int first, count;
 };
 
-// One level as the kernels see it.
+// One level as the kernels see it, in the precision T of its operator and vectors (the
+// transfer weights are FP32 in both precisions: the same P serves restriction and
+// prolongation, so the V-cycle stays symmetric whatever their rounding).
+template <class T>
 struct MgLevelDev {
   int nx, ny, nz, nxn, nyn, nzn;
-  const float* A;             // 64 per element (levels >= 1)
-  float* dinv;                // 0 on Dirichlet rows (levels >= 1)
+  const T* A;                 // 64 per element (levels >= 1)
+  T* dinv;                    // 0 on Dirichlet rows (levels >= 1)
   const unsigned char* mask;  // 1 on Dirichlet nodes
-  float *b, *x, *w;
+  T *b, *x, *w;
   // to the next coarser level (absent on the coarsest)
   const MgElemMap* em[3];
   const MgProl* pr[3];
@@ -60,27 +63,38 @@ struct MgLevelDev {
 
 // Damping weight of level l: 1 / theta, theta = (hi + hi / MG_ALPHA) / 2.
 // (0 on a level whose bound is 0: every node of it is a Dirichlet node.)
-__device__ __forceinline__ float mg_omega(const float* par, int l) {
-  const float hi = par[l];
-  return hi > 0.0f ? 2.0f / (hi * (1.0f + 1.0f / MG_ALPHA)) : 0.0f;
+template <class T>
+__device__ __forceinline__ T mg_omega(const T* par, int l) {
+  const T hi = par[l];
+  return hi > T(0) ? T(2) / (hi * (T(1) + T(1) / T(MG_ALPHA))) : T(0);
 }
 
-// Host side (mg.cu).
+// Host side (mg.cu). The hierarchy (levels, transfers, masks) is built once per mesh and serves
+// both precisions; the Galerkin operators and the level vectors exist per precision T (float:
+// the mixed-precision solve, double: the plain FP64 solve), allocated on first use.
 bool mg_prepare(qcad_mesh_s* m);                    // builds the hierarchy once; false if unusable
-// Galerkin operators of the current FP32 linearization (nothing to do when they are current;
-// force = rebuild anyway).
+// Operators and vectors of precision T (allocated once; idempotent). Must run before a V-cycle of
+// that precision is enqueued or captured: the kernels take the level pointers by value.
+template <class T>
+void mg_reserve(qcad_mesh_s* m);
+// Galerkin operators of the current linearization in precision T (nothing to do when they are
+// current; force = rebuild anyway).
+template <class T>
 void mg_setup(qcad_mesh_s* m, cudaStream_t s, bool force = false);
-void mg_invalidate(qcad_mesh_s* m);                  // the next mg_setup rebuilds
+void mg_invalidate(qcad_mesh_s* m);                  // the next mg_setup rebuilds (both precisions)
 // PCG start: x = 0, r = b and z = V-cycle(r), ending with the phase-0 bookkeeping.
-void mg_enqueue_init(qcad_mesh_s* m, const PcgVecs<float>& v, PcgScalars* sc, cudaStream_t s);
+template <class T>
+void mg_enqueue_init(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, cudaStream_t s);
 // One PCG iteration after its apply kernel: update of x and r, then z = V-cycle(r).
-void mg_enqueue_update(qcad_mesh_s* m, const PcgVecs<float>& v, PcgScalars* sc, cudaStream_t s);
+template <class T>
+void mg_enqueue_update(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* sc, cudaStream_t s);
 int mg_launches_per_iteration(qcad_mesh_s* m);      // kernels of one PCG iteration, apply included
 int mg_levels(qcad_mesh_s* m);
 
 // Level-0 V-cycle kernels on the plane-factorized z-march (kernels_lin.cu).
-void launch_mg_resid0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
-void launch_mg_post0(const Grid<float>& g, PcgVecs<float> v, PcgScalars* sc, const float* par, LaunchCfg cfg,
-                     cudaStream_t s);
+template <class T>
+void launch_mg_resid0(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, LaunchCfg cfg, cudaStream_t s);
+template <class T>
+void launch_mg_post0(const Grid<T>& g, PcgVecs<T> v, PcgScalars* sc, const T* par, LaunchCfg cfg, cudaStream_t s);
 
 }  // namespace qcad

@@ -107,12 +107,10 @@ static void enqueue_iteration(qcad_mesh_s* m, const PcgVecs<T>& v, PcgScalars* s
   launch_pcg_apply<T>(Prec<T>::grid(m), v, sc, Prec<T>::cfg(m), s, Prec<T>::face(m));
   rec(e++, false);
   rec(e, true);
-  if constexpr (std::is_same<T, float>::value) {
-    if (degree == DEG_MG) {
-      mg_enqueue_update(m, v, sc, s);
-      rec(e++, false);
-      return;
-    }
+  if (degree == DEG_MG) {
+    mg_enqueue_update<T>(m, v, sc, s);
+    rec(e++, false);
+    return;
   }
   if (degree <= 1)
     launch_pcg_update<T>(m->n_nodes, v, sc, s);
@@ -225,7 +223,8 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
   PcgVecs<T> v = ensure_pcg<T>(m);
   PcgGraph& G = Prec<T>::graph(m);
   bool mg = false;
-  if constexpr (std::is_same<T, float>::value) mg = degree == DEG_MG && mg_prepare(m);
+  mg = degree == DEG_MG && mg_prepare(m);
+  if (mg) mg_reserve<T>(m);  // level buffers exist before the graph captures their pointers
   degree = mg ? DEG_MG : std::max(1, std::min(degree, 16));
   const bool prof_match = m->prof.on == !G.events.empty();
   if (!G.exec || G.key != (const void*)v.x || !prof_match || G.degree != degree) {
@@ -262,10 +261,8 @@ static PcgResult pcg_run_once(qcad_mesh_s* m, double rtol, int maxit, int degree
   PcgScalars* sc = m->scal.as<PcgScalars>();
   CK(cudaMemcpyAsync(sc, h, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
   if (mg) {
-    if constexpr (std::is_same<T, float>::value) {
-      mg_setup(m, s);
-      mg_enqueue_init(m, v, sc, s);
-    }
+    mg_setup<T>(m, s);
+    mg_enqueue_init<T>(m, v, sc, s);
   } else if (degree <= 1) {
     launch_pcg_init<T>(m->n_nodes, v, sc, s);
   } else {
@@ -331,19 +328,17 @@ static int choose_degree(qcad_mesh_s* m, double rtol, int maxit) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   if (m->cheb_auto[prec] != 0) return m->cheb_auto[prec];
   // odd degrees only: their polynomial stays positive above the estimated top of the spectrum,
-  // so an underestimated lambda_max slows the solve but cannot make it break down; in mixed
-  // precision the multigrid V-cycle competes too
+  // so an underestimated lambda_max slows the solve but cannot make it break down; the multigrid
+  // V-cycle (in the solve's own precision) competes too
   std::vector<int> cand = {1, 3, 5, 7};
-  if constexpr (std::is_same<T, float>::value)
-    if (mg_prepare(m)) cand.push_back(DEG_MG);
+  if (mg_prepare(m)) cand.push_back(DEG_MG);
   int best = 1;
   double best_t = 1e300;
   for (int d : cand) {
     // a first untimed run builds the candidate's graph; the timed run then pays what every
     // new linearization pays (the power iteration, or the multigrid setup)
     pcg_run<T>(m, rtol, maxit, d);
-    if constexpr (std::is_same<T, float>::value)
-      if (d == DEG_MG) mg_invalidate(m);
+    if (d == DEG_MG) mg_invalidate(m);
     const int pi = sizeof(T) == 8 ? 0 : 1;
     m->lam_ver[pi] = -1;
     CK(cudaStreamSynchronize(m->stream));
@@ -586,8 +581,6 @@ static void validate_opts(const qcad_solver_opts* o) {
   if (o->precision != 0 && o->precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "precision must be 0 or 1");
   if (!(o->newton_tol_R > 0) || !(o->newton_tol_dphi > 0)) throw Error(QCAD_ERR_INVALID_ARG, "tolerances must be > 0");
   if (o->cheb_degree < -1 || o->cheb_degree > 16) throw Error(QCAD_ERR_INVALID_ARG, "cheb_degree must be in [-1, 16]");
-  if (o->cheb_degree == -1 && o->precision != 1)
-    throw Error(QCAD_ERR_INVALID_ARG, "the multigrid preconditioner (cheb_degree -1) runs in mixed precision only");
 }
 
 qcad_status poisson_solve(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* theta,
@@ -920,6 +913,7 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
     qcad_mesh_s* m = B.ms[i];
     PcgGraph& G = m->graph32;
     const bool prof_match = m->prof.on == !G.events.empty();
+    mg_reserve<float>(m);  // level buffers exist before the graph captures their pointers
     if (!G.exec || G.key != (const void*)B.vecs[i].x || !prof_match || G.degree != DEG_MG) {
       build_graph<float>(m, B.vecs[i], DEG_MG);
       G.key = (const void*)B.vecs[i].x;
@@ -934,8 +928,8 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
     if (!(rtol[i] > 0)) h->done = 1;
     CK(cudaMemcpyAsync(B.scd[i], h, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
     if (rtol[i] > 0) {
-      mg_setup(m, B.s);
-      mg_enqueue_init(m, B.vecs[i], B.scd[i], B.s);
+      mg_setup<float>(m, B.s);
+      mg_enqueue_init<float>(m, B.vecs[i], B.scd[i], B.s);
     }
   }
   CK(cudaGetLastError());
@@ -973,11 +967,11 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
 // lam_d over the corners of e.
 
 // FP64 solve of one right-hand side (precision 0).
-static void adjoint_solve64(qcad_mesh_s* m, const double* g, double* lam, int maxk) {
+static void adjoint_solve64(qcad_mesh_s* m, const double* g, double* lam, int maxk, int degree) {
   cudaStream_t s = m->stream;
   PcgVecs<double> v = ensure_pcg<double>(m);
   CK(cudaMemcpyAsync(const_cast<double*>(v.b), g, m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  PcgResult pr = pcg_run<double>(m, 1e-13, maxk, std::max(1, m->cheb_auto[0]));
+  PcgResult pr = pcg_run<double>(m, 1e-13, maxk, degree);
   if (pr.nonfinite) throw Error(QCAD_ERR_NONFINITE, "adjoint linear solve produced a non-finite value");
   CK(cudaMemcpyAsync(lam, v.x, m->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -1185,7 +1179,11 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
     adjoint_solve_mixed(m, nd, G, LAM, maxk);
   } else {
     // (charged gates: the batched kernels of the mixed multi-dot solve carry no face term)
-    for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
+    // the preconditioner of the FP64 solves: the request, else the mesh's tuned FP64 choice
+    // (the multigrid V-cycle in FP64 where the mesh has a hierarchy), else Jacobi
+    int deg64 = o->cheb_degree != 0 ? o->cheb_degree : m->cheb_auto[0];
+    if (deg64 == 0 || (deg64 == DEG_MG && !mg_prepare(m))) deg64 = 1;
+    for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk, deg64);
   }
   for (int d = 0; d < nd; ++d)
     for (int gi = 0; gi < ng; ++gi)

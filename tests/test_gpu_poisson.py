@@ -220,31 +220,49 @@ def test_chebyshev_preconditioned_solve(q, name, precision, degree):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_multigrid_preconditioned_solve(q, name):
-    # geometric multigrid V-cycle PCG (mixed precision) converges to the same unique solution;
-    # meshes too small for a coarse level fall back to Jacobi
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_preconditioned_solve(q, name, precision):
+    # geometric multigrid V-cycle PCG (FP32 V-cycle in mixed precision, FP64 V-cycle in plain
+    # FP64) converges to the same unique solution; meshes too small for a coarse level fall back
+    # to Jacobi
     dev = CASES[name]()
     P = PoissonProblem(dev)
     phi_o, rep_o = P.solve()
     m = q.qcad_mesh_create(dev)
     phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1, cheb_degree=-1), phi)
+    rep = q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=precision, cheb_degree=-1), phi)
     assert rep["status"] == "OK", rep
     assert np.max(np.abs(host(phi) - phi_o)) <= 1e-9
     if name == "dqd_61x62x40_4K":
         # the V-cycle needs several times fewer Krylov iterations than Jacobi on this mesh
         m2 = q.qcad_mesh_create(dev)
         phi2 = torch.zeros(m2.n_nodes, dtype=torch.float64, device="cuda")
-        rep2 = q.qcad_poisson_solve(m2, dev["bias"], q.make_opts(precision=1, cheb_degree=1), phi2)
+        rep2 = q.qcad_poisson_solve(m2, dev["bias"], q.make_opts(precision=precision, cheb_degree=1), phi2)
         assert rep2["status"] == "OK", rep2
         assert 4 * rep["krylov_iters_total"] < rep2["krylov_iters_total"], (rep, rep2)
+
+
+def test_multigrid_in_both_precisions_takes_the_same_path(q):
+    # the FP64 and FP32 V-cycles are the same preconditioner in two precisions: the two Newton
+    # solves of one device reach the same solution with Krylov counts within a few iterations
+    dev = CASES["dqd_61x62x40_4K"]()
+    reps, phis = [], []
+    for prec in (0, 1):
+        m = q.qcad_mesh_create(dev)
+        phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+        reps.append(q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=prec, cheb_degree=-1), phi))
+        phis.append(host(phi))
+    assert reps[0]["status"] == "OK" and reps[1]["status"] == "OK"
+    assert np.max(np.abs(phis[0] - phis[1])) <= 1e-9
+    k64, k32 = reps[0]["krylov_iters_total"], reps[1]["krylov_iters_total"]
+    assert abs(k64 - k32) <= max(4, 0.25 * k64), (reps[0], reps[1])
 
 
 def test_multigrid_option_is_validated(q):
     dev = CASES["dqd_24x24x16_4K"]()
     m = q.qcad_mesh_create(dev)
     phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    for prec, deg in ((0, -1), (1, -2), (1, 17)):
+    for prec, deg in ((0, -2), (1, -2), (1, 17), (0, 17)):
         with pytest.raises(q.QcadError) as e:
             q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=prec, cheb_degree=deg), phi)
         assert e.value.code == 1

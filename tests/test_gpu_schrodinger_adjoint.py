@@ -120,7 +120,7 @@ def test_particle_in_box_closed_form(q):
     assert np.max(np.abs(np.array(E) - ev) / np.abs(ev)) < 1e-10
 
 
-@pytest.mark.parametrize("precision,degree", [(0, 1), (1, 1), (1, -1)])
+@pytest.mark.parametrize("precision,degree", [(0, 1), (0, -1), (1, 1), (1, -1)])
 def test_adjoint_matches_oracle(q, dqd, precision, degree):
     dev, P, phi = dqd
     theta = np.array(W.interface_fixed_charge(dev, seed=5))
@@ -130,7 +130,7 @@ def test_adjoint_matches_oracle(q, dqd, precision, degree):
     m = q.qcad_mesh_create(dev)
     th = dt(theta)
     phig = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
-    # degree 1: Jacobi (the dots' mixed-precision systems solved together); -1: multigrid
+    # degree 1: Jacobi (the dots' mixed-precision systems solved together); -1: multigrid (FP32 or FP64)
     opts = q.make_opts(precision=precision, cheb_degree=degree)
     r = q.qcad_poisson_solve(m, dev["bias"], opts, phig, fixed_charge=th)
     assert r["status"] == "OK"
