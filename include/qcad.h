@@ -376,24 +376,26 @@ qcad_status qcad_autotune(qcad_mesh_t m, const qcad_bias* b, int precision, int*
                           int* z_chunk, float* best_ms);
 
 /* Allocation-free residual, for callers that cannot allocate device memory
- * (code inside another framework's allocator or memory pool, under CUDA
- * graph capture or in a loop where cudaMalloc/cudaFree are not allowed). The
- * paper has no counterpart; this is a packaging of the residual above.
- * Computes the same R (and stats) as qcad_poisson_residual, but from the
- * device description directly: no mesh object, no cudaMalloc/cudaFree, no
- * host heap. Its scratch (geometry tables, contact masks, reduction
- * accumulators) is one static device array of 2 MiB that every GPU loading
- * this library holds until process exit; meshes whose tables do not fit
- * (roughly (nx+1)*(ny+1) + 60*(nx+ny+nz) bytes) are rejected with
- * QCAD_ERR_INVALID_ARG. All calls share that array and leave the last call's
- * contents in it; the accumulators are cleared at the start of every call.
- * Calls whose GPU work overlaps (on different streams or host threads) race
- * on the array. The first call on a device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture. dev, b: host; cuda_stream: cudaStream_t or NULL (legacy default
- * stream); fixed_charge_elem (device [n_elems] or NULL), phi, R: device;
- * stats: host [2] {max |R_i|, sum R_i^2} or NULL. Returns after the stream
- * has been synchronized. */
+ * (code inside another framework's allocator or memory pool, or in a loop
+ * where cudaMalloc/cudaFree are not allowed). The paper has no counterpart;
+ * this is a packaging of the residual above. Computes the same R (and stats)
+ * as qcad_poisson_residual, but from the device description directly: no mesh
+ * object, no cudaMalloc/cudaFree, no host heap on success. The description is
+ * checked as qcad_mesh_create checks it (sizes, layers, one semiconductor
+ * material, permittivities > 0, the 32-bit index limits); charged gates and
+ * surface charges are rejected. Its scratch (geometry tables, contact masks,
+ * reduction accumulators) is one static device array of 2 MiB that every GPU
+ * loading this library holds until process exit; meshes whose tables do not
+ * fit (roughly (nx+1)*(ny+1) + 60*(nx+ny+nz) bytes) are rejected with
+ * QCAD_ERR_INVALID_ARG before the device is touched. All calls share that
+ * array and leave the last call's contents in it; the accumulators are
+ * cleared at the start of every call. Calls whose GPU work overlaps (on
+ * different streams or host threads) race on the array. The first call on a
+ * device looks up the array's device address with that device current.
+ * dev, b: host; cuda_stream: cudaStream_t or NULL (legacy default stream);
+ * fixed_charge_elem (device [n_elems] or NULL), phi, R: device; stats: host
+ * [2] {max |R_i|, sum R_i^2} or NULL. Returns after the stream has been
+ * synchronized. */
 qcad_status qcad_poisson_residual_noalloc(const qcad_device* dev, const qcad_bias* b, void* cuda_stream,
                                           const double* fixed_charge_elem, const double* phi, double* R,
                                           double* stats);

@@ -106,8 +106,11 @@ static double fd_inverse(double u) {
 }
 
 Phys make_phys(const qcad_mesh_s* m, const qcad_bias* b) {
+  return make_phys_material(m->mats[m->semi >= 0 ? m->semi : 0], b);
+}
+
+Phys make_phys_material(const qcad_material& s, const qcad_bias* b) {
   Phys P{};
-  const qcad_material& s = m->mats[m->semi >= 0 ? m->semi : 0];
   P.kT = host_kT(b->T);
   P.inv_kT = 1.0 / P.kT;
   double mn, mp;
@@ -166,28 +169,34 @@ double gate_value(const qcad_mesh_s* m, double Vg, const Phys& P) {
 }
 
 // ---------------------------------------------------------------------------
-// 1D assembled linear-element operators on node coordinates x[0..n].
-static void row_ops(const std::vector<double>& x, const std::vector<double>& kappa, std::vector<double>& M,
-                    std::vector<double>& K) {
-  const int n = (int)x.size() - 1;
-  M.assign(3 * (n + 1), 0.0);
-  K.assign(3 * (n + 1), 0.0);
+// 1D assembled linear-element operators on node coordinates x[0..n]: rows (coefficients of
+// nodes i-1, i, i+1) of the mass and stiffness with per-element weights kappa (null: 1).
+void row_ops_raw(const double* x, int n, const double* kappa, double* M, double* K) {
+  for (int i = 0; i < 3 * (n + 1); ++i) M[i] = K[i] = 0.0;
   for (int i = 0; i <= n; ++i) {
     if (i > 0) {
-      const double h = x[i] - x[i - 1], kp = kappa[i - 1];
+      const double h = x[i] - x[i - 1], kp = kappa ? kappa[i - 1] : 1.0;
       M[3 * i + 0] += kp * h / 6.0;
       M[3 * i + 1] += kp * h / 3.0;
       K[3 * i + 0] += -kp / h;
       K[3 * i + 1] += kp / h;
     }
     if (i < n) {
-      const double h = x[i + 1] - x[i], kp = kappa[i];
+      const double h = x[i + 1] - x[i], kp = kappa ? kappa[i] : 1.0;
       M[3 * i + 1] += kp * h / 3.0;
       M[3 * i + 2] += kp * h / 6.0;
       K[3 * i + 1] += kp / h;
       K[3 * i + 2] += -kp / h;
     }
   }
+}
+
+static void row_ops(const std::vector<double>& x, const std::vector<double>& kappa, std::vector<double>& M,
+                    std::vector<double>& K) {
+  const int n = (int)x.size() - 1;
+  M.assign(3 * (n + 1), 0.0);
+  K.assign(3 * (n + 1), 0.0);
+  row_ops_raw(x.data(), n, kappa.data(), M.data(), K.data());
 }
 
 GridTables make_tables(const std::vector<double>& x, const std::vector<double>& y, const std::vector<double>& z,
@@ -337,8 +346,47 @@ static void build_surface_terms(qcad_mesh_s* m, const qcad_device* dev) {
   CK(cudaStreamSynchronize(s));
 }
 
+// Checks of a device description shared by every entry point that takes one (mesh_create and
+// the allocation-free residual): sizes, gate and dot lists, layers, materials (at most one
+// semiconductor material, permittivities > 0), and the limits of the kernels' 32-bit node and
+// coefficient indices and of the z-grid dimension. Returns the element-layer count.
+int validate_device(const qcad_device* dev) {
+  if (!dev) throw Error(QCAD_ERR_INVALID_ARG, "null device description");
+  if (dev->nx < 1 || dev->ny < 1 || dev->n_layers < 1 || !dev->layer_n || !dev->layer_thickness ||
+      !dev->layer_material || dev->n_materials < 1 || !dev->materials || !(dev->Lx > 0) || !(dev->Ly > 0))
+    throw Error(QCAD_ERR_INVALID_ARG, "invalid mesh sizes or layer description");
+  if (dev->n_gates < 0 || dev->n_gates > QCAD_MAX_GATES || (dev->n_gates > 0 && !dev->gates))
+    throw Error(QCAD_ERR_INVALID_ARG, "invalid gate list");
+  if (dev->n_dots < 0 || dev->n_dots > QCAD_MAX_DOTS || (dev->n_dots > 0 && !dev->dots))
+    throw Error(QCAD_ERR_INVALID_ARG, "invalid dot list");
+  if (dev->nx > 8192 || dev->ny > 8192) throw Error(QCAD_ERR_INVALID_ARG, "mesh too large along x or y");
+  int semi = -1;
+  for (int i = 0; i < dev->n_materials; ++i)
+    if (dev->materials[i].semiconductor) {
+      if (semi >= 0 && std::memcmp(&dev->materials[i], &dev->materials[semi], sizeof(qcad_material)) != 0)
+        throw Error(QCAD_ERR_INVALID_ARG, "at most one semiconductor material is supported");
+      semi = i;
+    }
+  for (int i = 0; i < dev->n_materials; ++i)
+    if (!(dev->materials[i].eps_r > 0)) throw Error(QCAD_ERR_INVALID_ARG, "material permittivity must be > 0");
+  long long nz = 0;
+  for (int L = 0; L < dev->n_layers; ++L) {
+    const int mat = dev->layer_material[L];
+    if (dev->layer_n[L] < 1 || !(dev->layer_thickness[L] > 0) || mat < 0 || mat >= dev->n_materials)
+      throw Error(QCAD_ERR_INVALID_ARG, "invalid layer group");
+    nz += dev->layer_n[L];
+  }
+  if (nz > 65535) throw Error(QCAD_ERR_INVALID_ARG, "too many element layers");
+  // kernels index nodes and element coefficient arrays with 32-bit integers
+  if ((long long)(dev->nx + 1) * (dev->ny + 1) * (nz + 1) >= (1LL << 31) ||
+      8LL * dev->nx * dev->ny * nz >= (1LL << 31))
+    throw Error(QCAD_ERR_INVALID_ARG, "mesh too large for 32-bit node and coefficient indices");
+  return (int)nz;
+}
+
 void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
   if (!dev || !out) throw Error(QCAD_ERR_INVALID_ARG, "null device description or output");
+  validate_device(dev);
   if (dev->nx < 1 || dev->ny < 1 || dev->n_layers < 1 || !dev->layer_n || !dev->layer_thickness ||
       !dev->layer_material || dev->n_materials < 1 || !dev->materials || !(dev->Lx > 0) || !(dev->Ly > 0))
     throw Error(QCAD_ERR_INVALID_ARG, "invalid mesh sizes or layer description");

@@ -54,6 +54,11 @@ struct DevBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Host helpers shared by mesh_create and the allocation-free residual (mesh.cu).
+int validate_device(const qcad_device* dev);  // throws Error(INVALID_ARG); returns the layer count
+Phys make_phys_material(const qcad_material& semiconductor, const qcad_bias* b);
+void row_ops_raw(const double* x, int n, const double* kappa, double* M, double* K);
+
 // Host description of one structured grid's 1D operator tables.
 struct GridTables {
   std::vector<double> mx, kx, my, ky, mzx, mzy, kzz;

@@ -1,24 +1,24 @@
 // Allocation-free residual evaluation.
 //
 // Some callers cannot allocate device memory: code running inside another
-// framework's memory pool or allocator hooks, under a CUDA graph or a
-// real-time loop that forbids cudaMalloc/cudaFree, or in a process whose
-// allocator is owned by someone else. qcad_poisson_residual_noalloc serves
-// them: it evaluates the same FP64 residual as qcad_poisson_residual without a
-// mesh object and without allocating anything. The caller passes the device
-// description, phi and R; the per-call scratch (geometry tables, contact
-// masks and the reduction accumulators) lives in one file-scope device array
-// of QCAD_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps
-// until process exit. Host-side tables are staged in a static host buffer of
-// the same size, so the call performs no heap allocation either.
+// framework's memory pool or allocator hooks, in a real-time loop that forbids
+// cudaMalloc/cudaFree, or in a process whose device allocator is owned by
+// someone else. qcad_poisson_residual_noalloc serves them: it evaluates the
+// same FP64 residual as qcad_poisson_residual without a mesh object and
+// without allocating device memory. The caller passes the device description,
+// phi and R; the per-call scratch (geometry tables, contact masks and the
+// reduction accumulators) lives in one file-scope device array of
+// QCAD_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps until
+// process exit. Host-side tables are staged in a static host buffer of the
+// same size, so a successful call performs no heap allocation either.
 //
-// Every call shares the array and leaves the last call's contents in it;
-// accumulators are cleared at the start of each call. Calls whose GPU work
-// overlaps (different streams, or different host threads on one device) race
-// on the array; the host side is serialized by a mutex, the device side is
-// not. The first call on a device looks up the array's device address
-// (cudaGetSymbolAddress) with that device current; make that first call
-// before any stream capture.
+// The description is checked exactly as qcad_mesh_create checks it (the same
+// host function), plus the scratch limit. Every call shares the array and
+// leaves the last call's contents in it; accumulators are cleared at the start
+// of each call. Calls whose GPU work overlaps (different streams, or different
+// host threads on one device) race on the array; the host side is serialized
+// by a mutex, the device side is not. The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress) with that device current.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,8 +27,7 @@
 #include <string>
 
 #include "../../include/qcad.h"
-#include "qcad_host.h"
-#include "qcad_internal.cuh"
+#include "mesh.h"
 
 #define QCAD_NOALLOC_SCRATCH_BYTES (2u << 20)
 #define QCAD_NOALLOC_MAX_DEVICES 64
@@ -43,9 +42,6 @@ namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[QCAD_NOALLOC_MAX_DEVICES] = {};
 alignas(256) unsigned char g_stage[QCAD_NOALLOC_SCRATCH_BYTES];
-
-const double kQ = 1.602176634e-19, kKB = 1.380649e-23, kHBAR = 1.054571817e-34, kM0 = 9.1093837015e-31,
-             kEPS0 = 8.8541878128e-12;
 
 // Bump allocator over a fixed region (host staging and device scratch share offsets).
 struct Arena {
@@ -62,31 +58,6 @@ struct Arena {
   }
 };
 
-// Assembled 1D mass / stiffness rows (coefficients of nodes n-1, n, n+1) of
-// linear elements on coordinates x[0..n] with per-element weights kappa.
-void rows_1d(const double* x, int n, const double* kappa, double* M, double* K) {
-  for (int i = 0; i <= n; ++i) {
-    double* m = M + 3 * i;
-    double* k = K + 3 * i;
-    m[0] = m[1] = m[2] = 0.0;
-    k[0] = k[1] = k[2] = 0.0;
-    if (i > 0) {
-      const double h = x[i] - x[i - 1], w = kappa ? kappa[i - 1] : 1.0;
-      m[0] += w * h / 6.0;
-      m[1] += w * h / 3.0;
-      k[0] += -w / h;
-      k[1] += w / h;
-    }
-    if (i < n) {
-      const double h = x[i + 1] - x[i], w = kappa ? kappa[i] : 1.0;
-      m[1] += w * h / 3.0;
-      m[2] += w * h / 6.0;
-      k[1] += w / h;
-      k[2] += -w / h;
-    }
-  }
-}
-
 }  // namespace
 
 qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* stream, const double* theta,
@@ -95,32 +66,39 @@ qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* s
     set_message("null device description, bias, phi or R");
     return QCAD_ERR_INVALID_ARG;
   }
-  if (dev->nx < 1 || dev->ny < 1 || dev->n_layers < 1 || !dev->layer_n || !dev->layer_thickness ||
-      !dev->layer_material || dev->n_materials < 1 || !dev->materials || !(dev->Lx > 0) || !(dev->Ly > 0) ||
-      dev->n_gates < 0 || dev->n_gates > QCAD_MAX_GATES || (dev->n_gates > 0 && !dev->gates) || !(b->T > 0)) {
-    set_message("invalid device description or bias");
+  if (!(b->T > 0) || !std::isfinite(b->T)) {
+    set_message("temperature must be > 0");
     return QCAD_ERR_INVALID_ARG;
   }
+  // the checks of qcad_mesh_create, including the 32-bit index limits of the kernels
+  const int nz = validate_device(dev);
   if (dev->n_charged_gates != 0 || dev->n_surface_charges != 0) {
     set_message("the allocation-free residual does not take charged gates or surface charges");
     return QCAD_ERR_INVALID_ARG;
   }
-  int nz = 0;
-  for (int L = 0; L < dev->n_layers; ++L) {
-    const int mat = dev->layer_material[L];
-    if (dev->layer_n[L] < 1 || !(dev->layer_thickness[L] > 0) || mat < 0 || mat >= dev->n_materials) {
-      set_message("invalid layer group");
-      return QCAD_ERR_INVALID_ARG;
-    }
-    nz += dev->layer_n[L];
-  }
   const int nx = dev->nx, ny = dev->ny;
   const long long nxn = nx + 1, nyn = ny + 1, nzn = nz + 1;
-  int semi = -1;
+  int semi = -1;  // the semiconductor material (validate_device allows one)
   for (int i = 0; i < dev->n_materials; ++i)
-    if (dev->materials[i].semiconductor) semi = (semi < 0) ? i : semi;
+    if (dev->materials[i].semiconductor) semi = i;
   const qcad_material& s = dev->materials[semi >= 0 ? semi : 0];
 
+  // Scratch layout (same offsets in the host staging buffer and the device array).
+  Arena A;
+  const size_t o_stats = A.take(2 * sizeof(double));
+  const size_t o_x = A.take(nxn * sizeof(double)), o_y = A.take(nyn * sizeof(double)),
+               o_z = A.take(nzn * sizeof(double));
+  const size_t o_hx = A.take(nx * sizeof(double)), o_hy = A.take(ny * sizeof(double)),
+               o_hz = A.take(nz * sizeof(double)), o_eps = A.take(nz * sizeof(double));
+  const size_t o_mx = A.take(3 * nxn * sizeof(double)), o_kx = A.take(3 * nxn * sizeof(double));
+  const size_t o_my = A.take(3 * nyn * sizeof(double)), o_ky = A.take(3 * nyn * sizeof(double));
+  const size_t o_mz = A.take(3 * nzn * sizeof(double)), o_kz = A.take(3 * nzn * sizeof(double));
+  const size_t o_semi = A.take(nz), o_dir = A.take(nxn * nyn);
+  if (!A.ok) {
+    set_message("mesh too large for the allocation-free scratch (" +
+                std::to_string(QCAD_NOALLOC_SCRATCH_BYTES) + " bytes)");
+    return QCAD_ERR_INVALID_ARG;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   int device = -1;
   cudaError_t e = cudaGetDevice(&device);
@@ -140,22 +118,6 @@ qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* s
   }
   unsigned char* dbase = static_cast<unsigned char*>(g_noalloc_addr[device]);
 
-  // Scratch layout (same offsets in the host staging buffer and the device array).
-  Arena A;
-  const size_t o_stats = A.take(2 * sizeof(double));
-  const size_t o_x = A.take(nxn * sizeof(double)), o_y = A.take(nyn * sizeof(double)),
-               o_z = A.take(nzn * sizeof(double));
-  const size_t o_hx = A.take(nx * sizeof(double)), o_hy = A.take(ny * sizeof(double)),
-               o_hz = A.take(nz * sizeof(double)), o_eps = A.take(nz * sizeof(double));
-  const size_t o_mx = A.take(3 * nxn * sizeof(double)), o_kx = A.take(3 * nxn * sizeof(double));
-  const size_t o_my = A.take(3 * nyn * sizeof(double)), o_ky = A.take(3 * nyn * sizeof(double));
-  const size_t o_mz = A.take(3 * nzn * sizeof(double)), o_kz = A.take(3 * nzn * sizeof(double));
-  const size_t o_semi = A.take(nz), o_dir = A.take(nxn * nyn);
-  if (!A.ok) {
-    set_message("mesh too large for the allocation-free scratch (" +
-                std::to_string(QCAD_NOALLOC_SCRATCH_BYTES) + " bytes)");
-    return QCAD_ERR_INVALID_ARG;
-  }
   unsigned char* H = g_stage;
   double* x = reinterpret_cast<double*>(H + o_x);
   double* y = reinterpret_cast<double*>(H + o_y);
@@ -183,9 +145,9 @@ qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* s
   for (int i = 0; i < nx; ++i) hx[i] = x[i + 1] - x[i];
   for (int j = 0; j < ny; ++j) hy[j] = y[j + 1] - y[j];
   for (int q = 0; q < nz; ++q) hz[q] = z[q + 1] - z[q];
-  rows_1d(x, nx, nullptr, reinterpret_cast<double*>(H + o_mx), reinterpret_cast<double*>(H + o_kx));
-  rows_1d(y, ny, nullptr, reinterpret_cast<double*>(H + o_my), reinterpret_cast<double*>(H + o_ky));
-  rows_1d(z, nz, eps, reinterpret_cast<double*>(H + o_mz), reinterpret_cast<double*>(H + o_kz));
+  row_ops_raw(x, nx, nullptr, reinterpret_cast<double*>(H + o_mx), reinterpret_cast<double*>(H + o_kx));
+  row_ops_raw(y, ny, nullptr, reinterpret_cast<double*>(H + o_my), reinterpret_cast<double*>(H + o_ky));
+  row_ops_raw(z, nz, eps, reinterpret_cast<double*>(H + o_mz), reinterpret_cast<double*>(H + o_kz));
   for (long long j = 0; j < nyn; ++j)
     for (long long i = 0; i < nxn; ++i) {
       unsigned char in = 0;
@@ -229,29 +191,7 @@ qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* s
   g.dir_bottom = dev->bottom_ohmic;
   g.dir_boundary = 0;
 
-  Phys P{};
-  const double T = b->T;
-  P.kT = kKB * T / kQ;
-  P.inv_kT = 1.0 / P.kT;
-  const double mn = std::pow(6.0, 2.0 / 3.0) * std::cbrt(s.m_l * s.m_t * s.m_t);
-  const double mp = std::pow(std::pow(s.m_hh, 1.5) + std::pow(s.m_lh, 1.5), 2.0 / 3.0);
-  const double an = mn * kM0 * kKB * T / (2.0 * M_PI * kHBAR * kHBAR) * 1e-18;
-  const double ap = mp * kM0 * kKB * T / (2.0 * M_PI * kHBAR * kHBAR) * 1e-18;
-  P.NC = 2.0 * an * std::sqrt(an);
-  P.NV = 2.0 * ap * std::sqrt(ap);
-  P.phi_ref = s.chi + 0.5 * s.Eg + 0.5 * P.kT * std::log(P.NC / P.NV);
-  P.chi = s.chi;
-  P.Eg = s.Eg;
-  P.EF = -b->V_sub;
-  P.NA = s.N_A;
-  P.ND = s.N_D;
-  P.Ea = s.E_a;
-  P.Ed = s.E_d;
-  P.gA = s.g_A;
-  P.gD = s.g_D;
-  P.qe = kQ / kEPS0 * 1e9;
-  P.statistics = b->statistics;
-  P.incomplete = b->incomplete_ionization;
+  const Phys P = make_phys_material(s, b);
 
   ResidualArgs a{};
   a.phi = phi;

@@ -100,3 +100,47 @@ def test_binding_structs_match_the_header(lib_path, tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def _noalloc_call(dev):
+    """Calls the allocation-free residual's C entry point directly with placeholder phi and R
+    pointers (never dereferenced: every case below is rejected by host-side checks, before the
+    entry point touches a device); returns (status, message)."""
+    import paper_1403_7561_gb300 as q
+    d, keep = q._device_struct(dev)
+    b = q.make_bias(dev["bias"])
+    fake = ctypes.c_void_p(1 << 20)
+    code = q._lib.qcad_poisson_residual_noalloc(ctypes.byref(d), ctypes.byref(b), None, None, fake, fake, None)
+    return code, q._lib.qcad_last_error().decode()
+
+
+@pytest.mark.parametrize("case", ["index_limit", "layers", "two_semiconductors", "permittivity", "charged_gate",
+                                  "scratch"])
+def test_noalloc_rejects_what_mesh_create_rejects(lib_path, case):
+    # the allocation-free residual checks a description with qcad_mesh_create's own host function
+    # (the kernels index nodes with 32-bit integers) before the scratch limit and before any device
+    # call; a description that passes these checks is never handed to a kernel here
+    import workloads as W
+    dev = W.five_gate_device(n=(16, 16, 8), T=4.0, with_subdomain=False)
+    expect = {"index_limit": "32-bit", "layers": "too many element layers",
+              "two_semiconductors": "one semiconductor", "permittivity": "permittivity",
+              "charged_gate": "charged gates", "scratch": "scratch"}[case]
+    if case == "index_limit":      # about 2.2e9 nodes: fits the 2 MiB scratch, overflows int indices
+        dev.update(nx=1000, ny=1000)
+        dev["layers"] = [dict(material=0, thickness=90.0, n=2190), dict(material=1, thickness=10.0, n=10)]
+    elif case == "layers":
+        dev.update(nx=1, ny=1)
+        dev["layers"] = [dict(material=0, thickness=90.0, n=70000), dict(material=1, thickness=10.0, n=10)]
+    elif case == "two_semiconductors":
+        other = dict(dev["materials"][0], N_A=2e-6)
+        dev["materials"].append(other)
+        dev["layers"][0]["material"] = 2
+        dev["layers"].insert(0, dict(material=0, thickness=10.0, n=2))
+    elif case == "permittivity":
+        dev["materials"][1]["eps_r"] = 0.0
+    elif case == "charged_gate":
+        dev["gates"][1]["robin"] = dict(sigma=1e-4, d=10.0)
+    else:                          # the top-plane contact mask alone (2049^2 bytes) exceeds 2 MiB
+        dev.update(nx=2048, ny=2048)
+    code, msg = _noalloc_call(dev)
+    assert code == 1 and expect in msg, (code, msg)

@@ -71,44 +71,79 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
 
     class Args:
-        workload = "dqd_128x128x96_4K"
+        workload = "dqd_256x256x128_0p5K"
         steps = 1
         warmup = 0
         gpus = 2
 
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1) or (1.0, 100, 1.0))
+    monkeypatch.setattr(bench, "oracle_pass", lambda *a, **k: called.append(1) or (1.0, 100, 1.0))
     bench.reference_arm(Args())
     assert called == [] and capsys.readouterr().out == ""
 
 
 def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
-    # the reference arm's one JSON line: the contract's keys, the oracle's own cores and zero copies
+    # the reference arm's one JSON line: the contract's keys, the oracle's own cores, zero copies,
+    # and the full-mesh time from the power law through the two sample sizes
     import json
+    import math
 
     import bench
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
 
     class Args:
-        workload = "dqd_128x128x96_4K"
-        steps = 2
+        workload = "dqd_256x256x128_0p5K"
+        steps = 4
         warmup = 1
         gpus = 1
 
-    samples = iter([(3.0, 1000, 2.5), (2.0, 1000, 3.0), (4.0, 1000, 2.0)])
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: next(samples))
+    # warm-up (small), then small, large, small, large: t = 1e-4 N^1.5 s exactly
+    sizes = {bench.SAMPLES[0]: 1000, bench.SAMPLES[1]: 8000}
+    cores = iter([2.0, 2.5, 3.0, 2.0, 1.5])
+    seen = []
+
+    def fake(workload, n):
+        seen.append(n)
+        N = sizes[n]
+        return 1e-4 * N ** 1.5, N, next(cores)
+
+    monkeypatch.setattr(bench, "oracle_pass", fake)
     bench.reference_arm(Args())
+    assert seen == [bench.SAMPLES[0], bench.SAMPLES[0], bench.SAMPLES[1], bench.SAMPLES[0], bench.SAMPLES[1]]
     lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
-    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["impl"] == "reference" and d["steps"] == 4 and d["warmup"] == 1
     full = d["config"]["nodes"]
-    assert abs(d["ms_per_step"] - 3000.0) < 1e-9                 # mean of the two timed samples
-    assert abs(d["value"] - (1.0 / 3.0) * 1000 / full) < 1e-15      # solves/s scaled by the node ratio
+    assert abs(d["config"]["size_exponent"] - 1.5) < 1e-12
+    assert math.isclose(d["value"], 1.0 / (1e-4 * full ** 1.5), rel_tol=1e-12)
+    # mean time of the four timed passes
+    assert math.isclose(d["ms_per_step"], 1000.0 * 1e-4 * (2 * 1000 ** 1.5 + 2 * 8000 ** 1.5) / 4, rel_tol=1e-12)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 3.0
+    assert "N^1.50" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_power_law_extrapolation():
+    import bench
+    t, p = bench.extrapolate([2.0, 16.0], [100, 400], 1600)
+    assert abs(p - 1.5) < 1e-12 and abs(t - 128.0) < 1e-9
+
+
+def test_kernel_source_hash_tracks_the_sources():
+    # the ncu counters are keyed by this hash: it is stable and covers every kernel source
+    import bench
+    h = bench.kernel_source_hash()
+    assert h == bench.kernel_source_hash() and len(h) == 16
+    counters = {"entries": [{"kernel": "apply32", "workload": "w", "launch": [3, 8, 16], "dram_bytes": 5.0,
+                             "source_hash": "0" * 16}]}
+    v, note = bench.counter(counters, h, "apply32", "w", (3, 8, 16), "dram_bytes")
+    assert v is None and note.startswith("stale")
+    counters["entries"][0]["source_hash"] = h
+    assert bench.counter(counters, h, "apply32", "w", (3, 8, 16), "dram_bytes")[0] == 5.0
+    assert bench.counter(counters, h, "apply32", "w", (3, 8, 19), "dram_bytes")[0] is None
