@@ -8,11 +8,17 @@ solution has zero residual; eigenpairs have small residuals in the oracle's
 assembled H and M and are M-orthonormal), and against central differences of
 the solution map (adjoint gradients).
 
+The 1.6M-node device is also compared element by element with the oracle's own
+full solve of it (potential, the 10 eigenvalues, the dot counts and the adjoint
+dN/dV), stored by tests/golden/make_dqd_128x128x96_oracle.py, which calls only
+the oracle.
+
 Sizes: dqd_128x128x96_4K (1.6M nodes), dqd_256x256x128_0p5K (8.5M nodes), a
 12-instance subset of the 96-instance batch covering all nine size buckets
 (N^3 elements, N = 48..112), and the 128x128x96 adjoint with the interface
 fixed-charge field.
 """
+import os
 import types
 
 import numpy as np
@@ -54,6 +60,31 @@ def c2(q):
     dev = W.get("dqd_128x128x96_4K")
     m, phi, rep = solve(q, dev)
     return dev, m, phi
+
+
+ORACLE_C2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dqd_128x128x96_4K_oracle.npz")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_matches_the_oracle_solution(q, precision):
+    # the oracle's Newton solve of the same device to ||R||inf < 1e-10 and its ARPACK eigenvalues:
+    # potentials to 1e-9 V and eigenvalues to 1e-9 relative, in plain FP64 and in mixed precision
+    ref = np.load(ORACLE_C2)
+    dev = W.get("dqd_128x128x96_4K")
+    assert np.array_equal(ref["V_gate"], np.array(dev["bias"]["V_gate"]))
+    m = q.qcad_mesh_create(dev)
+    phi = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    opts = q.make_opts(precision=precision, cheb_degree=-1)
+    rep = q.qcad_poisson_solve(m, dev["bias"], opts, phi)
+    assert rep["status"] == "OK", rep
+    assert np.max(np.abs(phi.cpu().numpy() - ref["phi"])) <= 1e-9
+    E, erep = q.qcad_schrodinger_eigs(m, dev["bias"], phi, nev=10, tol=1e-8)
+    assert erep["status"] == "OK"
+    assert np.max(np.abs(np.array(E) - ref["evals"]) / np.abs(ref["evals"])) <= 1e-9
+    N = np.array(q.qcad_electron_counts(m, dev["bias"], phi))
+    assert np.max(np.abs(N - ref["counts"]) / np.abs(ref["counts"])) <= 1e-8
+    dNdV = np.array(q.qcad_adjoint(m, dev["bias"], phi, opts))
+    assert np.max(np.abs(dNdV - ref["dN_dV"])) <= 1e-8 * np.max(np.abs(ref["dN_dV"]))
 
 
 def test_c2_residual_kernel_and_solution(q, c2):

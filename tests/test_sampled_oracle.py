@@ -26,3 +26,20 @@ def test_sampled_residual_reproduces_the_oracle(make):
     assert not np.any(P.dir[S.node(sub[:, 0], sub[:, 1], sub[:, 2])])
     assert np.max(np.abs(S.residual_at(phi, sub) - R[S.node(sub[:, 0], sub[:, 1], sub[:, 2])])) <= \
         1e-12 * np.max(np.abs(R))
+
+
+def test_stored_fullsize_oracle_solution_is_a_solution():
+    # the oracle's stored 128 x 128 x 96 solution (tests/golden, written by a script that calls
+    # only the oracle) zeroes the oracle's residual at sampled free nodes, carries the device's
+    # gate voltages and lists its eigenvalues in ascending order
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dqd_128x128x96_4K_oracle.npz")
+    ref = np.load(path)
+    dev = W.get("dqd_128x128x96_4K")
+    assert np.array_equal(ref["V_gate"], np.array(dev["bias"]["V_gate"]))
+    S = SampledPoisson(dev)
+    phi = ref["phi"]
+    assert phi.shape == (S.nxn * S.nyn * S.nzn,)
+    ijk = S.sample_nodes(300, seed=31)
+    assert np.max(np.abs(S.residual_at(phi, ijk))) < 1e-10
+    assert np.all(np.diff(ref["evals"]) > 0) and ref["counts"].shape == (2,) and ref["dN_dV"].shape == (2, 5)
