@@ -245,3 +245,102 @@ def test_sheet_charge_calibration_reaches_the_target():
     phm, _ = Pm.solve(phi0=phi)
     fd = (C.electron_counts(Pp, php)[0] - C.electron_counts(Pm, phm)[0]) / (2 * h)
     assert abs(slope - fd) <= 1e-5 * abs(fd)
+
+
+# ---------------------------------------------------------------------------
+# Pins of electron_counts (Sec. III: N is the integrated electron density of the dot region) and
+# of device_potential (Eq. SchrodPotEnergy: V = q phi_ref - chi - q phi).
+
+def _count_device(statistics):
+    # 100 x 100 nm, 10 x 10 elements of 10 nm; Si 50 nm in 10 layers of 5 nm under SiO2 10 nm in two;
+    # element centroids at x, y = 5, 15, ..., 95 and z = 2.5, 7.5, ..., 57.5
+    dev = W.mos_capacitor(nx=10, ny=10, nz=12, L=100.0, t_si=50.0, t_ox=10.0, n_ox=2, T=300.0,
+                          statistics=statistics)
+    dev["dots"] = [
+        # faces through element centroids: x centroids 15, 25, 35, y 45, 55, 65 (closed box), z centroids
+        # 42.5, 47.5 in Si and 52.5, 57.5 in the oxide (not semiconductor): 3 x 3 x 2 Si elements
+        dict(x0=15.0, x1=35.0, y0=45.0, y1=65.0, z0=42.5, z1=57.5),
+        # oxide only: no electrons
+        dict(x0=0.0, x1=100.0, y0=0.0, y1=100.0, z0=51.0, z1=60.0),
+        # faces just inside the centroids 15 and 35: the single column x = 25, one layer z = 2.5
+        dict(x0=15.000001, x1=34.999999, y0=55.0, y1=55.0, z0=0.0, z1=5.0),
+    ]
+    return dev
+
+
+@pytest.mark.parametrize("statistics", [0, 1])
+def test_electron_counts_uniform_potential_closed_form(statistics):
+    # at a uniform potential the density is one number n(phi) in every Si element, so
+    # N_d = n(phi) x (volume of the dot's Si elements) exactly: 18 elements of 500 nm^3, none, and 1
+    dev = _count_device(statistics)
+    P = PoissonProblem(dev)
+    phi0 = 0.31
+    n_pt = physics.carrier_terms(np.array([phi0]), P.si, P.T, P.phi_r, P.E_F, statistics, 1)["n"][0]
+    N = C.electron_counts(P, np.full(P.mesh.n_nodes, phi0))
+    vol = np.array([18 * 500.0, 0.0, 1 * 500.0])
+    assert N.shape == (3,)
+    assert np.max(np.abs(N - n_pt * vol)) <= 1e-12 * n_pt * vol[0]
+    if statistics == 0:
+        # Maxwell-Boltzmann: N scales as exp(q dphi / k_B T) (CODATA constants, no oracle physics)
+        dphi = 0.02
+        N2 = C.electron_counts(P, np.full(P.mesh.n_nodes, phi0 + dphi))
+        kT = 1.380649e-23 * 300.0 / 1.602176634e-19
+        assert abs(N2[0] / N[0] - math.exp(dphi / kT)) <= 1e-12 * math.exp(dphi / kT)
+
+
+def test_electron_counts_integrates_a_varying_density():
+    # potential linear in x across the dot: n varies exponentially (MB), and the 2x2x2 Gauss sum of
+    # each element approximates its integral (closed form of exp over an interval) to O(h^4) per element
+    dev = _count_device(0)
+    P = PoissonProblem(dev)
+    a = 0.004  # V/nm
+    phi = 0.25 + a * (P.mesh.coords[:, 0] - 50.0)
+    N = C.electron_counts(P, phi)
+    kT = 1.380649e-23 * 300.0 / 1.602176634e-19
+    n0 = physics.carrier_terms(np.array([0.25]), P.si, P.T, P.phi_r, P.E_F, 0, 1)["n"][0]
+    beta = a / kT  # n(x) = n0 exp(beta (x - 50))
+    ix = math.exp(beta * (35.0 + 5.0 - 50.0)) - math.exp(beta * (15.0 - 5.0 - 50.0))
+    exact = n0 * ix / beta * 30.0 * 10.0  # dot 0: x in [10, 40], y extent 30, z extent 10 (Si)
+    assert abs(N[0] - exact) <= 2e-3 * exact
+
+
+def _ramp_device():
+    # 2 x 2 nm strip (one transverse mode), Si 40 nm in 160 layers of 0.25 nm, gate -1 V on top,
+    # Ohmic bottom, 300 K; Schrodinger subdomain z in [10, 40] nm
+    dev = W.mos_capacitor(nx=2, ny=2, nz=160, L=2.0, t_si=40.0, t_ox=1.0, n_ox=1, V_gate=-1.0, T=300.0)
+    dev["layers"] = [dict(material=0, thickness=40.0, n=160)]
+    dev["subdomain"] = dict(i0=0, i1=2, j0=0, j1=2, k0=40, k1=160)
+    return dev
+
+
+def test_device_potential_on_a_linear_potential_and_its_airy_levels():
+    dev = _ramp_device()
+    P = PoissonProblem(dev, linear=True)
+    phi = P.initial_guess()  # the charge-free solution: linear in z, nodally exact for Q1
+    m = P.mesh
+    phib, phit = phi[m.nk == 0][0], phi[m.nk == m.nz][0]
+    assert abs(phit - (-1.0)) < 1e-14 and phib > phit
+    sel = m.subdomain_elements()
+    Vq = S.device_potential(P, phi, sel)
+    # Gauss points of each element in z: centre +- h / (2 sqrt 3)
+    h = 0.25
+    zc = m.elem_coords[sel][:, :, 2].mean(axis=1)
+    sz = np.array([2 * ((q >> 2) & 1) - 1 for q in range(8)], dtype=float)
+    zq = zc[:, None] + sz[None, :] * h / (2.0 * math.sqrt(3.0))
+    phiq = phib + (phit - phib) * zq / 40.0
+    assert np.max(np.abs(Vq - (P.phi_r - P.si["chi"] - phiq))) < 1e-13
+    # the energy rises with z (V = q phi_ref - chi - q phi, phi falls towards the gate): a triangular
+    # well on the subdomain's lower wall, E_1 = V(10 nm) + (hbar^2 F^2 / 2m)^(1/3) |a_1|
+    m_rel = 0.19
+    F = (phib - phit) / 40.0
+    kap = physics.hbar2_over_2m0() / m_rel
+    a1 = -scipy.special.ai_zeros(1)[0][0]
+    V0 = P.phi_r - P.si["chi"] - (phib + (phit - phib) * 10.0 / 40.0)
+    E_exact = V0 + (kap * F ** 2) ** (1.0 / 3.0) * a1
+    trans = 2.0 * kap * 6.0 * 0.5  # the strip's transverse mode (2 elements of 1 nm per axis)
+    E, _, _, _, _ = S.solve_device(P, phi, nev=1, m_eff=(m_rel,) * 3)
+    assert abs(E[0] - trans - E_exact) <= 3e-3 * (E_exact - V0), (E[0] - trans, E_exact)
+    # a sign slip (V = q phi_ref - chi + q phi) puts the well against the upper wall, tenths of an eV away
+    H, M, _ = S.operators(m, sel, m.subdomain_interior_nodes(), (m_rel,) * 3, P.phi_r - P.si["chi"] + phiq)
+    Ef, _ = S.lowest_eigenpairs(H, M, 1, sigma=float(np.min(P.phi_r - P.si["chi"] + phiq)) - 0.01)
+    assert abs(Ef[0] - trans - E_exact) > 0.1
