@@ -374,6 +374,41 @@ def other_configs(q, W, torch, flush):
                          "preconditioner_code": "-1 multigrid V-cycle, k >= 1 Chebyshev degree (autotuned)",
                          **arms}
     del m
+    # a plunger sweep of the same device (8 bias points, a mesh each): the batched Newton and one
+    # batched adjoint call for every point's 2 x 5 dN/dV, against the points solved one by one
+    pts = []
+    for k in range(8):
+        b = dict(bias, V_gate=list(bias["V_gate"]))
+        b["V_gate"][1] += 0.01 * (k - 3.5)
+        pts.append(b)
+    sm = [q.qcad_mesh_create(dev) for _ in pts]
+    sphi = [torch.zeros(mm.n_nodes, dtype=torch.float64, device="cuda") for mm in sm]
+    sopts = q.make_opts(precision=1, cheb_degree=-1)
+
+    def sweep_batched():
+        for p_ in sphi:
+            p_.zero_()
+        reps_, st_ = q.qcad_poisson_solve_batch(sm, pts, sopts, sphi)
+        return st_, q.qcad_adjoint_batch(sm, pts, sopts, sphi)
+
+    def sweep_one_by_one():
+        out_ = []
+        for mm, b, p_ in zip(sm, pts, sphi):
+            q.qcad_poisson_solve(mm, b, sopts, p_)
+            out_.append(q.qcad_adjoint(mm, b, p_, sopts))
+        return out_
+
+    sweep_batched()
+    tb, _, (sst, sdn) = timed_events(torch, sweep_batched, 2, flush)
+    sweep_one_by_one()
+    ts1, _, sdn1 = timed_events(torch, sweep_one_by_one, 2, flush)
+    out["bias_sweep"] = {"workload": "%s, plunger P1 swept over 8 points (-35..+35 mV), mixed, multigrid PCG"
+                         % FP64_WORKLOAD, "points": len(pts), "status": sst,
+                         "batched_points_per_s": len(pts) / tb, "one_by_one_points_per_s": len(pts) / ts1,
+                         "max_abs_dNdV_batched_vs_one_by_one": float(np.max(np.abs(np.array(sdn) - np.array(sdn1)))),
+                         "step": "Newton solve + 2 x 5 adjoint dN/dV per point (batched: qcad_poisson_solve_batch "
+                                 "then qcad_adjoint_batch)"}
+    del sm, sphi
     # the differentiation form: Newton with the interface fixed charge, then the adjoint with the
     # 2 x 5 capacitance and the gradient with respect to every element's fixed charge
     dev = W.get(ADJ_WORKLOAD)

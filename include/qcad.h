@@ -340,6 +340,20 @@ qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solv
 qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs,
                                      const qcad_solver_opts* o, double* const* phis, qcad_solve_report* reps);
 
+/* Batched adjoint sensitivities (Sec. III's capacitance C = q dN/dV by the adjoint) of several
+ * meshes at once, e.g. the bias points of a gate sweep solved by qcad_poisson_solve_batch: for
+ * every mesh i and dot d, J_i lam = dN_d/dphi on the free rows, with all (mesh, dot) systems in
+ * one batched FP32 Jacobi-PCG (one apply launch and one update launch per iteration over a work
+ * table of the systems, iteration chunks replayed from a captured CUDA graph), each round
+ * followed by every system's FP64 residual, until each is below 1e-13 of its right-hand side;
+ * then dN_d/dV_g as qcad_adjoint forms it. ms, bs, phis: host arrays of n entries (phis[i]:
+ * device [n_nodes of ms[i]], a converged potential at bs[i]). dN_dV: host, the meshes' blocks
+ * one after the other, block i = n_dots(i) x n_gates(i) row-major (1/V). o->precision must be
+ * 1; no fixed charge; meshes distinct, on one device, without charged gates or surface charges.
+ * Uses the stream of ms[0]. */
+qcad_status qcad_adjoint_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                               const double* const* phis, double* dN_dV);
+
 /* Kernel timing: with profiling enabled, every launch of the timed kernel
  * classes on the mesh stream (including those inside captured CUDA graphs) is
  * bracketed by CUDA events and its duration accumulated. Classes: 0 FP32

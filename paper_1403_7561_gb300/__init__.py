@@ -145,6 +145,7 @@ _sigs = {
                           _P, C.POINTER(SolveReport)],
     "qcad_poisson_solve_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P),
                                  C.POINTER(SolveReport)],
+    "qcad_adjoint_batch": [C.c_int, C.POINTER(_P), C.POINTER(Bias), C.POINTER(SolverOpts), C.POINTER(_P), _D],
     "qcad_calibrate_sheet_charge": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), C.c_int, C.c_double, _P, C.c_double,
                                     C.c_double, C.c_int, _P, _P, _D, C.POINTER(CalibReport)],
     "qcad_sp_solve": [_P, C.POINTER(Bias), C.POINTER(SolverOpts), C.c_int, _D, C.c_double, C.c_double, C.c_int,
@@ -414,6 +415,23 @@ def qcad_poisson_solve_batch(meshes, biases, opts, phis, allow_not_converged=Fal
     reps = (SolveReport * n)()
     code = _check(_lib.qcad_poisson_solve_batch(n, hs, bs, C.byref(opts), ps, reps), allow_not_converged)
     return [r.as_dict() for r in reps], STATUS[code]
+
+
+def qcad_adjoint_batch(meshes, biases, opts, phis):
+    """Batched adjoint of several meshes; returns [dN/dV of mesh i as n_dots x n_gates lists]."""
+    n = len(meshes)
+    hs = (C.c_void_p * n)(*[m.handle for m in meshes])
+    bs_list = [make_bias(b) for b in biases]
+    bs = (Bias * n)(*bs_list)
+    ps = (C.c_void_p * n)(*[_dptr(p, m.n_nodes, name="phi").value for p, m in zip(phis, meshes)])
+    tot = sum(m.n_dots * m.n_gates for m in meshes)
+    out = (C.c_double * max(1, tot))()
+    _check(_lib.qcad_adjoint_batch(n, hs, bs, C.byref(opts), ps, out))
+    flat, res, off = list(out), [], 0
+    for m in meshes:
+        res.append([flat[off + k * m.n_gates: off + (k + 1) * m.n_gates] for k in range(m.n_dots)])
+        off += m.n_dots * m.n_gates
+    return res
 
 
 def qcad_alu_peaks():

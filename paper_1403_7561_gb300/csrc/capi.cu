@@ -41,6 +41,8 @@ qcad_status schrodinger_eigs_stream2(qcad_mesh_s* m, const qcad_bias* b, const d
                                      qcad_solve_report* rep);
 qcad_status poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                 double* const* phis, qcad_solve_report* reps);
+qcad_status adjoint_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                          const double* const* phis, double* dN_dV);
 qcad_status autotune(qcad_mesh_s* m, const qcad_bias* b, int precision, int* variant, int* tile_rows, int* z_chunk,
                      float* best);
 qcad_status noalloc_residual(const qcad_device* dev, const qcad_bias* b, void* stream, const double* theta,
@@ -241,6 +243,11 @@ qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solv
 qcad_status qcad_poisson_solve_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
                                      double* const* phis, qcad_solve_report* reps) {
   return guarded([&] { return qcad::poisson_solve_batch(n, ms, bs, o, phis, reps); });
+}
+
+qcad_status qcad_adjoint_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                               const double* const* phis, double* dN_dV) {
+  return guarded([&] { return qcad::adjoint_batch(n, ms, bs, o, phis, dN_dV); });
 }
 
 qcad_status qcad_alu_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_exp_per_s) {

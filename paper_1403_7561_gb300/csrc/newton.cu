@@ -1121,32 +1121,43 @@ static void adjoint_solve_mixed(qcad_mesh_s* m, int nd, const double* G, double*
   }
 }
 
-qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
-                    const double* theta, double* dN_dV, double* dN_dq) {
-  validate_bias(m, b);
-  validate_opts(o);
-  if (!phi || !dN_dV) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
+// The adjoint of one mesh in three phases: prepare (linearizations at phi, the right-hand sides
+// G_d = dN_d/dphi with their Dirichlet rows zeroed, the gate lifts' raw J e_g and dN_d/dphi . e_g),
+// the linear solves J lam_d = G_d (filled into LAM by the caller), and finish (dN_d/dV_g and dN/dtheta).
+struct AdjWork {
+  qcad_mesh_s* m = nullptr;
+  const qcad_bias* b = nullptr;
+  Phys P{};
+  int nd = 0, ng = 0;
+  DevBuf work, accs;
+  double *G = nullptr, *LAM = nullptr, *JE = nullptr, *eg = nullptr, *acc = nullptr, *zero_v = nullptr;
+};
+
+static void adjoint_prepare(AdjWork& A, qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o,
+                            const double* phi, const double* theta) {
   cudaStream_t s = m->stream;
   const long long n = m->n_nodes;
-  const int nd = m->dots.n, ng = m->n_gates;
-  if (nd == 0) return QCAD_OK;
+  A.m = m;
+  A.b = b;
+  A.nd = m->dots.n;
+  A.ng = m->n_gates;
+  const int nd = A.nd, ng = A.ng;
   ensure_newton(m);
-  const Phys P = make_phys(m, b);
+  A.P = make_phys(m, b);
+  const Phys& P = A.P;
   // linearization at phi in FP64 (and FP32 for the mixed refinement)
   eval_residual(m, P, phi, theta, 0, 0, nullptr);
   if (o->precision == 1) eval_residual(m, P, phi, theta, 0, 1, nullptr);
-  DevBuf work, accs;
-  work.ensure((size_t)(2 * nd + std::max(ng, 1) + 1) * n * sizeof(double) + 64);
-  double* G = work.as<double>();            // nd right-hand sides dN_d/dphi
-  double* LAM = G + (size_t)nd * n;         // nd adjoint solutions
-  double* JE = LAM + (size_t)nd * n;        // ng raw J e_g
-  double* eg = JE + (size_t)std::max(ng, 1) * n;
+  A.work.ensure((size_t)(2 * nd + std::max(ng, 1) + 1) * n * sizeof(double) + 64);
+  double* G = A.G = A.work.as<double>();    // nd right-hand sides dN_d/dphi
+  A.LAM = G + (size_t)nd * n;               // nd adjoint solutions
+  double* JE = A.JE = A.LAM + (size_t)nd * n;  // ng raw J e_g
+  double* eg = A.eg = JE + (size_t)std::max(ng, 1) * n;
   const size_t nacc = (size_t)2 * nd * ng + QCAD_MAX_GATES + 1;
-  accs.ensure(nacc * sizeof(double) + 64);
-  double* acc = accs.as<double>();          // [0, nd*ng): dN/dphi_D . e_g; then lam_d . J e_g
-  double* zero_v = acc + 2 * nd * ng;       // one zero per gate, for masking Dirichlet rows
+  A.accs.ensure(nacc * sizeof(double) + 64);
+  double* acc = A.acc = A.accs.as<double>();  // [0, nd*ng): dN/dphi_D . e_g; then lam_d . J e_g
+  A.zero_v = acc + 2 * nd * ng;               // one zero per gate, for masking Dirichlet rows
   CK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), s));
-  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
   m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
   for (int d = 0; d < nd; ++d)
     launch_count_gradient(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), m->d_xn.as<double>(),
@@ -1168,10 +1179,64 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
     for (int d = 0; d < nd; ++d) launch_dot<double>(n, G + (size_t)d * n, eg, acc + d * ng + gi, s);
     CK(cudaStreamSynchronize(s));  // h_small is reused by the next gate's upload
   }
-  // zero the Dirichlet rows of the right-hand sides, then solve
+  // zero the Dirichlet rows of the right-hand sides
   for (int d = 0; d < nd; ++d)
-    launch_set_dirichlet(m->nxn, m->nyn, m->nzn, m->bottom_ohmic, 0.0, m->d_gate_top.as<signed char>(), zero_v,
+    launch_set_dirichlet(m->nxn, m->nyn, m->nzn, m->bottom_ohmic, 0.0, m->d_gate_top.as<signed char>(), A.zero_v,
                          G + (size_t)d * n, s);
+  CK(cudaStreamSynchronize(s));
+}
+
+static void adjoint_finish(AdjWork& A, double* dN_dV, double* dN_dq) {
+  qcad_mesh_s* m = A.m;
+  cudaStream_t s = m->stream;
+  const long long n = m->n_nodes;
+  const int nd = A.nd, ng = A.ng;
+  double* acc = A.acc;
+  for (int d = 0; d < nd; ++d)
+    for (int gi = 0; gi < ng; ++gi)
+      launch_dot<double>(n, A.LAM + (size_t)d * n, A.JE + (size_t)gi * n, acc + nd * ng + d * ng + gi, s);
+  // charged gates (Robin condition): V_g enters through the load, d b / d V_g = (eps_r/d) int_f N_a
+  // on the gate's faces (top plane), so dN_d/dV_g gains lam_d . d b / d V_g (lam is 0 on Dirichlet rows)
+  const int nc = (int)m->charged_gate.size();
+  DevBuf racc;
+  std::vector<double> hr((size_t)std::max(1, nd * nc), 0.0);
+  if (nc > 0) {
+    const long long plane = (long long)m->nxn * m->nyn;
+    racc.ensure((size_t)nd * nc * sizeof(double) + 64);
+    CK(cudaMemsetAsync(racc.p, 0, (size_t)nd * nc * sizeof(double), s));
+    for (int d = 0; d < nd; ++d)
+      for (int c = 0; c < nc; ++c)
+        launch_dot<double>(plane, A.LAM + (size_t)d * n + (size_t)m->nz * plane,
+                           m->d_charged_r.as<double>() + (size_t)c * plane, racc.as<double>() + d * nc + c, s);
+    CK(cudaMemcpyAsync(hr.data(), racc.p, (size_t)nd * nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  std::vector<double> h(2 * nd * ng);
+  CK(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (dN_dq)
+    for (int d = 0; d < nd; ++d)
+      launch_theta_gradient(m->nx, m->ny, m->nz, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, A.LAM + (size_t)d * n,
+                            A.P.qe, dN_dq + (long long)d * m->n_elems, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  for (int d = 0; d < nd; ++d)
+    for (int gi = 0; gi < ng; ++gi) dN_dV[d * ng + gi] = h[d * ng + gi] - h[nd * ng + d * ng + gi];
+  for (int d = 0; d < nd; ++d)
+    for (int c = 0; c < nc; ++c) dN_dV[d * ng + m->charged_gate[c]] += hr[d * nc + c];
+}
+
+qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* o, const double* phi,
+                    const double* theta, double* dN_dV, double* dN_dq) {
+  validate_bias(m, b);
+  validate_opts(o);
+  if (!phi || !dN_dV) throw Error(QCAD_ERR_INVALID_ARG, "null pointer");
+  const long long n = m->n_nodes;
+  const int nd = m->dots.n;
+  if (nd == 0) return QCAD_OK;
+  AdjWork A;
+  adjoint_prepare(A, m, b, o, phi, theta);
+  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
+  double* G = A.G;
+  double* LAM = A.LAM;
   const int degree = o->cheb_degree != 0 ? o->cheb_degree : m->cheb_auto[1];
   if (o->precision == 1 && degree == DEG_MG && mg_prepare(m)) {
     for (int d = 0; d < nd; ++d) adjoint_solve_mixed_mg(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk);
@@ -1185,36 +1250,180 @@ qcad_status adjoint(qcad_mesh_s* m, const qcad_bias* b, const qcad_solver_opts* 
     if (deg64 == 0 || (deg64 == DEG_MG && !mg_prepare(m))) deg64 = 1;
     for (int d = 0; d < nd; ++d) adjoint_solve64(m, G + (size_t)d * n, LAM + (size_t)d * n, maxk, deg64);
   }
-  for (int d = 0; d < nd; ++d)
-    for (int gi = 0; gi < ng; ++gi)
-      launch_dot<double>(n, LAM + (size_t)d * n, JE + (size_t)gi * n, acc + nd * ng + d * ng + gi, s);
-  // charged gates (Robin condition): V_g enters through the load, d b / d V_g = (eps_r/d) int_f N_a
-  // on the gate's faces (top plane), so dN_d/dV_g gains lam_d . d b / d V_g (lam is 0 on Dirichlet rows)
-  const int nc = (int)m->charged_gate.size();
-  DevBuf racc;
-  std::vector<double> hr((size_t)std::max(1, nd * nc), 0.0);
-  if (nc > 0) {
-    const long long plane = (long long)m->nxn * m->nyn;
-    racc.ensure((size_t)nd * nc * sizeof(double) + 64);
-    CK(cudaMemsetAsync(racc.p, 0, (size_t)nd * nc * sizeof(double), s));
-    for (int d = 0; d < nd; ++d)
-      for (int c = 0; c < nc; ++c)
-        launch_dot<double>(plane, LAM + (size_t)d * n + (size_t)m->nz * plane,
-                           m->d_charged_r.as<double>() + (size_t)c * plane, racc.as<double>() + d * nc + c, s);
-    CK(cudaMemcpyAsync(hr.data(), racc.p, (size_t)nd * nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+  adjoint_finish(A, dN_dV, dN_dq);
+  return QCAD_OK;
+}
+
+// Batched adjoint over several meshes (bias points of a sweep, or different devices). With a
+// multigrid hierarchy on every mesh (the default preconditioner), the systems advance one dot
+// index at a time: in each round every mesh's system J_i lam = dN_d/dphi runs its own
+// multigrid-preconditioned FP32 PCG (the captured 4-iteration graphs of all meshes replayed back
+// to back, one status read per round, as the batched Newton does). Otherwise (cheb_degree 1, or
+// a mesh without a coarse level) all (mesh, dot) systems advance together in one batched FP32
+// Jacobi-PCG: one apply launch and one update launch per iteration over a work table of every
+// system. Either way each round of corrections is followed by every system's FP64 residual,
+// until each is below 1e-13 of its right-hand side (as adjoint_solve_mixed does for the dots of
+// one mesh).
+qcad_status adjoint_batch(int n, const qcad_mesh_t* ms, const qcad_bias* bs, const qcad_solver_opts* o,
+                          const double* const* phis, double* dN_dV) {
+  if (n < 1 || !ms || !bs || !o || !phis || !dN_dV) throw Error(QCAD_ERR_INVALID_ARG, "invalid batch arguments");
+  validate_opts(o);
+  if (o->precision != 1) throw Error(QCAD_ERR_INVALID_ARG, "the batched adjoint runs in mixed precision (precision 1)");
+  int max_nd = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!ms[i] || !phis[i]) throw Error(QCAD_ERR_INVALID_ARG, "null mesh or phi in batch");
+    if (ms[i]->has_surface)
+      throw Error(QCAD_ERR_INVALID_ARG, "the batched adjoint does not take charged gates or surface charges");
+    if (ms[i]->device != ms[0]->device) throw Error(QCAD_ERR_INVALID_ARG, "batch meshes must share one device");
+    if (ms[i]->dots.n > QCAD_MAX_DOTS_K) throw Error(QCAD_ERR_INVALID_ARG, "too many dots");
+    for (int j = 0; j < i; ++j)
+      if (ms[j] == ms[i]) throw Error(QCAD_ERR_INVALID_ARG, "a mesh appears twice in the batch");
+    validate_bias(ms[i], &bs[i]);
+    max_nd = std::max(max_nd, ms[i]->dots.n);
   }
-  std::vector<double> h(2 * nd * ng);
-  CK(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (dN_dq)
-    for (int d = 0; d < nd; ++d)
-      launch_theta_gradient(m->nx, m->ny, m->nz, m->g64.g.hx, m->g64.g.hy, m->g64.g.hz, LAM + (size_t)d * n, P.qe,
-                            dN_dq + (long long)d * m->n_elems, s);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(s));
-  for (int d = 0; d < nd; ++d)
-    for (int gi = 0; gi < ng; ++gi) dN_dV[d * ng + gi] = h[d * ng + gi] - h[nd * ng + d * ng + gi];
-  for (int d = 0; d < nd; ++d)
-    for (int c = 0; c < nc; ++c) dN_dV[d * ng + m->charged_gate[c]] += hr[d * nc + c];
+  std::vector<AdjWork> A(n);
+  for (int i = 0; i < n; ++i) adjoint_prepare(A[i], ms[i], &bs[i], o, phis[i], nullptr);
+  bool use_mg = o->cheb_degree == 0 || o->cheb_degree == -1;
+  for (int i = 0; i < n && use_mg; ++i) use_mg = mg_prepare(ms[i]);
+  const int maxk = o->max_krylov > 0 ? o->max_krylov : 20000;
+  struct Sys {
+    int i, d;
+  };
+  // FP32 PCG vectors of system (mesh m, dot d): the mesh's own for dot 0 (or for every dot in the
+  // multigrid rounds, which solve one dot of each mesh at a time), an extra set otherwise
+  auto vecs_for = [&](qcad_mesh_s* m, int d) {
+    PcgVecs<float> v = ensure_pcg<float>(m);
+    if (d == 0) return v;
+    const size_t nb = (size_t)m->n_nodes * sizeof(float) + 64;
+    PcgBufs<float>& k = m->k32x[d - 1];
+    k.x.ensure(nb);
+    k.r.ensure(nb);
+    k.z.ensure(nb);
+    k.p.ensure(2 * nb);
+    k.Ap.ensure(nb);
+    k.b.ensure(nb);
+    v.x = k.x.as<float>();
+    v.r = k.r.as<float>();
+    v.z = k.z.as<float>();
+    v.p[0] = k.p.as<float>();
+    v.p[1] = v.p[0] + nb / sizeof(float);
+    v.Ap = k.Ap.as<float>();
+    v.b = k.b.as<float>();  // dinv and c are the mesh's shared linearization
+    return v;
+  };
+  // one round: the systems `sys` (entry q of B is system q) to 1e-13 by FP32 corrections and FP64
+  // residuals
+  auto refine = [&](BatchCtx& B, const std::vector<Sys>& sys) {
+    const int ns = (int)sys.size();
+    cudaStream_t s = B.s;
+    DevBuf d2buf;
+    d2buf.ensure((size_t)ns * sizeof(double) + 64);
+    double* d2 = d2buf.as<double>();
+    std::vector<double> g2(ns), r2(ns), rtol(ns), hd(ns);
+    std::vector<int> iters, nonf;
+    auto rhs = [&](int q) { return A[sys[q].i].G + (size_t)sys[q].d * ms[sys[q].i]->n_nodes; };
+    auto lam = [&](int q) { return A[sys[q].i].LAM + (size_t)sys[q].d * ms[sys[q].i]->n_nodes; };
+    // per mesh scratch: y (n) then one residual per dot (nd x n)
+    auto ybuf = [&](int q) { return ms[sys[q].i]->scratch.as<double>(); };
+    auto rbuf = [&](int q) {
+      return ms[sys[q].i]->scratch.as<double>() + (size_t)(1 + sys[q].d) * ms[sys[q].i]->n_nodes;
+    };
+    CK(cudaMemsetAsync(d2, 0, ns * sizeof(double), s));
+    for (int q = 0; q < ns; ++q) {
+      const long long nn = ms[sys[q].i]->n_nodes;
+      CK(cudaMemsetAsync(lam(q), 0, nn * sizeof(double), s));
+      CK(cudaMemcpyAsync(rbuf(q), rhs(q), nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch_d2f(nn, rhs(q), const_cast<float*>(B.vecs[q].b), s);
+      launch_dot<double>(nn, rhs(q), rhs(q), d2 + q, s);
+    }
+    CK(cudaMemcpyAsync(hd.data(), d2, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    g2 = hd;
+    r2 = hd;
+    for (int rf = 0; rf < 12; ++rf) {
+      bool any = false;
+      for (int q = 0; q < ns; ++q) {
+        rtol[q] = 0.0;
+        if (r2[q] <= 1e-26 * g2[q]) continue;
+        any = true;
+        // each correction needs only to bring the residual to a tenth of the 1e-13 target
+        rtol[q] = std::max(1e-5, std::min(1e-2, 1e-14 * std::sqrt(g2[q] / std::max(r2[q], 1e-300))));
+      }
+      if (!any) break;
+      if (use_mg)
+        batch_pcg_mg(B, rtol, maxk, iters, nonf);
+      else
+        batch_pcg(B, rtol, maxk, iters, nonf);
+      CK(cudaMemsetAsync(d2, 0, ns * sizeof(double), s));
+      for (int q = 0; q < ns; ++q) {
+        if (!(rtol[q] > 0)) continue;
+        if (nonf[q]) throw Error(QCAD_ERR_NONFINITE, "batched adjoint refinement produced a non-finite value");
+        qcad_mesh_s* m = ms[sys[q].i];
+        const long long nn = m->n_nodes;
+        launch_axpy<float>(nn, 1.0, B.vecs[q].x, lam(q), s);
+        ApplyArgs<double> a{};
+        a.v = lam(q);
+        a.y = ybuf(q);
+        a.c = ensure_pcg<double>(m).c;
+        launch_apply<double>(m->g64.g, a, m->cfg64, s, nullptr);
+        launch_sub(nn, rhs(q), ybuf(q), rbuf(q), const_cast<float*>(B.vecs[q].b), s);
+        launch_dot<double>(nn, rbuf(q), rbuf(q), d2 + q, s);
+      }
+      CK(cudaMemcpyAsync(hd.data(), d2, ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int q = 0; q < ns; ++q)
+        if (rtol[q] > 0) r2[q] = hd[q];
+    }
+  };
+  for (int i = 0; i < n; ++i) {
+    qcad_mesh_s* m = ms[i];
+    m->scratch.ensure((size_t)(A[i].nd + 1) * m->n_nodes * sizeof(double) + 64);
+    m->scal_x.ensure((size_t)std::max(1, A[i].nd) * sizeof(PcgScalars) + 64);
+    m->adj_ctx.reset();  // the single-mesh adjoint context shares these vectors: rebuild it next time
+  }
+  if (use_mg) {
+    for (int d = 0; d < max_nd; ++d) {
+      BatchCtx B;
+      B.s = ms[0]->stream;
+      std::vector<Sys> sys;
+      for (int i = 0; i < n; ++i) {
+        if (A[i].nd <= d) continue;
+        B.ms.push_back(ms[i]);
+        B.vecs.push_back(vecs_for(ms[i], 0));
+        B.scd.push_back(ms[i]->scal.as<PcgScalars>());
+        B.kch.push_back(ms[i]->batch_kchunk);
+        sys.push_back(Sys{i, d});
+      }
+      B.n = (int)sys.size();
+      batch_setup(B);
+      refine(B, sys);
+    }
+  } else {
+    BatchCtx B;
+    B.s = ms[0]->stream;
+    std::vector<Sys> sys;
+    for (int i = 0; i < n; ++i) {
+      qcad_mesh_s* m = ms[i];
+      const int kc = (m->cfg32.variant == 3 && m->cfg32.by == 8) ? m->cfg32.kchunk : 16;
+      for (int d = 0; d < A[i].nd; ++d) {
+        B.ms.push_back(m);
+        B.vecs.push_back(vecs_for(m, d));
+        B.scd.push_back(d == 0 ? m->scal.as<PcgScalars>() : m->scal_x.as<PcgScalars>() + d);
+        B.kch.push_back(kc);
+        sys.push_back(Sys{i, d});
+      }
+    }
+    if (!sys.empty()) {
+      B.n = (int)sys.size();
+      batch_setup(B);
+      refine(B, sys);
+    }
+  }
+  size_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    if (A[i].nd > 0) adjoint_finish(A[i], dN_dV + off, nullptr);
+    off += (size_t)A[i].nd * A[i].ng;
+  }
   return QCAD_OK;
 }
 

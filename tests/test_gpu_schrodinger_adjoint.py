@@ -156,8 +156,11 @@ def test_bias_sweep_in_one_batched_launch(q, dqd, degree):
     opts = q.make_opts(precision=1, cheb_degree=degree)
     reps, status = q.qcad_poisson_solve_batch(meshes, biases, opts, phis)
     assert status == "OK", reps
+    # every point's 2 x 5 dN/dV from one batched adjoint call (the 3 x 2 systems in one batched PCG)
+    batched = q.qcad_adjoint_batch(meshes, biases, q.make_opts(precision=1), phis)
+    assert len(batched) == 3
     N0 = []
-    for m, b, ph in zip(meshes, biases, phis):
+    for m, b, ph, dNdV_b in zip(meshes, biases, phis, batched):
         Pb = PoissonProblem(dev, bias=b)
         phi_o, rep = Pb.solve(phi0=phi)
         assert rep["converged"]
@@ -165,11 +168,27 @@ def test_bias_sweep_in_one_batched_launch(q, dqd, degree):
         N = np.array(q.qcad_electron_counts(m, b, ph))
         N_o = OC.electron_counts(Pb, phi_o)
         assert np.max(np.abs(N - N_o)) <= 1e-8 * np.max(np.abs(N_o))
-        dNdV = np.array(q.qcad_adjoint(m, b, ph, opts))
         dNdV_o, _ = OC.adjoint(Pb, phi_o)
+        assert np.max(np.abs(np.array(dNdV_b) - dNdV_o)) <= 1e-8 * np.max(np.abs(dNdV_o))
+        dNdV = np.array(q.qcad_adjoint(m, b, ph, opts))
         assert np.max(np.abs(dNdV - dNdV_o)) <= 1e-8 * np.max(np.abs(dNdV_o))
         N0.append(N[0])
     assert N0[0] < N0[1] < N0[2]                                 # dot 0 fills as its plunger rises
+
+
+def test_adjoint_batch_rejects_bad_batches(q, dqd):
+    dev, P, phi = dqd
+    m = q.qcad_mesh_create(dev)
+    ph = torch.zeros(m.n_nodes, dtype=torch.float64, device="cuda")
+    q.qcad_poisson_solve(m, dev["bias"], q.make_opts(precision=1), ph)
+    for opts, meshes in ((q.make_opts(precision=0), [m]), (q.make_opts(precision=1), [m, m])):
+        with pytest.raises(q.QcadError) as e:
+            q.qcad_adjoint_batch(meshes, [dev["bias"]] * len(meshes), opts, [ph] * len(meshes))
+        assert e.value.code == 1
+    # one mesh: the batched call equals the single-mesh adjoint
+    one = np.array(q.qcad_adjoint_batch([m], [dev["bias"]], q.make_opts(precision=1), [ph])[0])
+    ref = np.array(q.qcad_adjoint(m, dev["bias"], ph, q.make_opts(precision=1)))
+    assert np.max(np.abs(one - ref)) <= 1e-9 * np.max(np.abs(ref))
 
 
 def test_fd_capacitance_matches_oracle(q, dqd):
