@@ -61,15 +61,16 @@ struct ResidualOp {
       double pq[8];
       tp_apply(v, pq, GaussConst<double>::a(), GaussConst<double>::b());
       double nsum = 0.0;
+      // the residual's below-resolution cutoffs, except in the dots when their counts are formed
+      const int d = a.counts != nullptr ? dot_of_element(a, i, j, k) : -1;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const Charge ch = charge_at(a.P, pq[q]);
+        const Charge ch = d < 0 ? charge_resid(a.P, pq[q]) : charge_at(a.P, pq[q]);
         f[q] = -a.P.qe * wdet * (ch.rho + th);
         c[q] = -a.P.qe * wdet * ch.drho;
         nsum += ch.n;
       }
       if (a.counts != nullptr && own) {  // each element counted once
-        const int d = dot_of_element(a, i, j, k);
         if (d == 0)
           acc_dot0 += wdet * nsum;
         else if (d == 1)
@@ -208,15 +209,45 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
   double v = 0.0;
   if (semi)
     v = __ldg(a.phi + (i + (l & 1)) + (long long)g.nxn * ((j + ((l >> 1) & 1)) + (long long)g.nyn * (k + (l >> 2))));
+  // Flat elements: the Gauss-point potentials are convex combinations of the corner values, so
+  // when all eight corners lie in one of charge_resid's constant-charge zones, every Gauss point
+  // does, rho is that zone's constant and rho' = 0. The element's load is then
+  // -(q/eps0) w|J| (rho + theta) at each corner (the Gauss weights of each corner's shape function
+  // sum to 1) and its Jacobian coefficients vanish. A warp whose elements are all flat (or not
+  // semiconductor) skips the interpolation and the transposed interpolation.
+  if (a.counts == nullptr && a.qd.w == nullptr) {
+    const int zone = semi ? charge_zone(a.P, v) : -2;  // -2: no charge term at all (oxide, padding)
+    int zmin = zone, zmax = zone;
+#pragma unroll
+    for (int sft = 1; sft < 8; sft <<= 1) {
+      zmin = min(zmin, __shfl_xor_sync(FULL_MASK, zmin, sft));
+      zmax = max(zmax, __shfl_xor_sync(FULL_MASK, zmax, sft));
+    }
+    const bool eflat = zmin == zmax && zmin != -1;
+    if (__all_sync(FULL_MASK, eflat)) {
+      if (valid) {
+        const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
+        const double th = a.theta ? a.theta[e] : 0.0;
+        const double rho = zone >= 0 ? zone_charge(a.P, zone) : 0.0;
+        elR[t] = -a.P.qe * wdet * (rho + th);
+        elD[t] = 0.0;
+        if (a.c64) a.c64[t] = 0.0;
+        if (a.c32) a.c32[t] = 0.0f;
+      }
+      return;
+    }
+  }
   v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 1);
   v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 2);
   v = A * v + B * __shfl_xor_sync(FULL_MASK, v, 4);
   double f = 0.0, c = 0.0, nq = 0.0;
+  // the residual's below-resolution cutoffs, except in the dots when their counts are formed
+  const int dot = (semi && a.counts != nullptr) ? dot_of_element(a, i, j, k) : -1;
   if (valid) {
     const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
     const double th = a.theta ? a.theta[e] : 0.0;
     if (semi) {
-      Charge ch = charge_at(a.P, v);
+      Charge ch = dot < 0 ? charge_resid(a.P, v) : charge_at(a.P, v);
       if (a.qd.w != nullptr) {
         // in the quantum region the predictor density n~ replaces the semiclassical n (Sec. II.C)
         const int iq = i - a.qd.i0, jq = j - a.qd.j0, kq = k - a.qd.k0;
@@ -240,12 +271,20 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
     if (a.c32) a.c32[t] = (float)c;
   }
   const double A2 = A * A, B2 = B * B;
-  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 1);
-  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 1);
-  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 2);
-  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 2);
-  f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 4);
-  c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 4);
+  // the transposed interpolation of each field, skipped where the whole warp holds zeros (the
+  // neutral bulk, where every density is below resolution, and the fully ionized depletion
+  // region, where the Jacobian coefficients vanish): the warp-uniform branch keeps the shuffles
+  // converged
+  if (__any_sync(FULL_MASK, f != 0.0)) {
+    f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 1);
+    f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 2);
+    f = A * f + B * __shfl_xor_sync(FULL_MASK, f, 4);
+  }
+  if (__any_sync(FULL_MASK, c != 0.0)) {
+    c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 1);
+    c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 2);
+    c = A2 * c + B2 * __shfl_xor_sync(FULL_MASK, c, 4);
+  }
   if (valid) {
     elR[t] = f;
     elD[t] = c;
@@ -253,7 +292,7 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
   if (a.counts != nullptr) {
     double s[2] = {0.0, 0.0};
     if (semi) {
-      const int d = dot_of_element(a, i, j, k);
+      const int d = dot;
       if (d == 0)
         s[0] = nq;
       else if (d == 1)

@@ -131,6 +131,26 @@ Phys make_phys_material(const qcad_material& s, const qcad_bias* b) {
   P.qe = host_qe();
   P.statistics = b->statistics;
   P.incomplete = b->incomplete_ionization;
+  // below-resolution cutoffs (physics.cuh): N F(eta) < floor for eta < ln(floor / N) (F <= e^eta),
+  // N s < floor for s ~ e^-z / g below floor / N; never tighter than the count cutoffs (eta -150,
+  // z 746)
+  const double fl = RHO_RESID_FLOOR;
+  P.eta_min_n = std::max(-150.0, std::log(fl / P.NC));
+  P.eta_min_p = std::max(-150.0, std::log(fl / P.NV));
+  P.z_max_a = s.N_A > 0 ? std::min(746.0, std::log(s.N_A / (s.g_A * fl))) : 746.0;
+  P.z_max_d = s.N_D > 0 ? std::min(746.0, std::log(s.N_D / (s.g_D * fl))) : 746.0;
+  // as potentials, widened by 1e-9 V so that rounding of the argument never skips a term the
+  // FP64 test would evaluate: eta_n = (phi - cn) / kT, eta_p = (cp - phi) / kT, z_a = (ca - phi) / kT,
+  // z_d = (phi - cd) / kT
+  const double kT = P.kT, w = 1e-9;
+  const double cn = P.phi_ref - s.chi - P.EF, cp = P.phi_ref - s.chi - s.Eg - P.EF;
+  const double ca = -P.EF + s.E_a + P.phi_ref - s.chi - s.Eg, cd = -(P.EF + s.E_d - P.phi_ref + s.chi);
+  P.phi_n_on = cn + P.eta_min_n * kT - w;
+  P.phi_p_on = cp - P.eta_min_p * kT + w;
+  P.phi_a_lo = ca - P.z_max_a * kT - w;
+  P.phi_a_hi = ca + 45.0 * kT + w;
+  P.phi_d_lo = cd - 45.0 * kT - w;
+  P.phi_d_hi = cd + P.z_max_d * kT + w;
   return P;
 }
 

@@ -16,12 +16,17 @@
 
 namespace qcad {
 
-// F_1/2 and its derivative. Below x = -150, F = e^x < 7e-66: N_C F and N_V F stay below 1e-60
-// nm^-3, under any charge density the residual can resolve (its load is FP64 and its tolerance
-// 1e-10 V nm), so the call is skipped and both are taken as zero.
-__device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
+// F_1/2 and its derivative. Below x = xmin, F = e^x is taken as zero (xmin: -150, where
+// N_C F < 1e-60 nm^-3, for the dot counts; the residual's cutoff otherwise, see RHO_RESID_FLOOR
+// in qcad_internal.cuh).
+__device__ __forceinline__ void fd_half_d(double x, double& F, double& dF, double xmin = -150.0) {
+  if (x < xmin) {
+    F = 0.0;
+    dF = 0.0;
+    return;
+  }
   if (x < -50.0) {
-    F = (x < -150.0) ? 0.0 : exp(x);
+    F = exp(x);
     dF = F;
     return;
   }
@@ -39,11 +44,17 @@ __device__ __forceinline__ void fd_half_d(double x, double& F, double& dF) {
   dF = -dD * F * F;
 }
 
-// s = 1/(1 + g e^z) and 1 - s without overflow. Beyond z = 746, e^{-z} is below half the smallest
-// subnormal and is taken as zero; below z = -45 the call and the reciprocal are skipped (s = 1).
-__device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms) {
+// s = 1/(1 + g e^z) and 1 - s without overflow. Beyond z = zmax, e^{-z} is taken as zero (746:
+// below half the smallest subnormal; the residual's cutoff otherwise, see RHO_RESID_FLOOR); below
+// z = -45 the call and the reciprocal are skipped (s = 1).
+__device__ __forceinline__ void sigmoid_pair(double z, double g, double& s, double& oms, double zmax = 746.0) {
   if (z > 0.0) {
-    const double e = (z > 746.0) ? 0.0 : exp(-z);
+    if (z > zmax) {
+      s = 0.0;
+      oms = 1.0;
+      return;
+    }
+    const double e = exp(-z);
     const double r = 1.0 / (e + g);
     s = e * r;
     oms = g * r;
@@ -66,37 +77,40 @@ struct Charge {
   double rho, drho, n, dn;
 };
 
-__device__ __forceinline__ Charge charge_at(const Phys& P, double phi) {
+// resid: the residual's below-resolution cutoffs (elements outside the dots); else the 1e-60
+// nm^-3 cutoffs of the electron counts.
+__device__ __forceinline__ Charge charge_at(const Phys& P, double phi, bool resid = false) {
   Charge c;
   const double ik = P.inv_kT;
   const double eta_n = (P.EF + phi - P.phi_ref + P.chi) * ik;
   const double eta_p = (-phi + P.phi_ref - P.chi - P.Eg - P.EF) * ik;
+  const double xn = resid ? P.eta_min_n : -150.0, xp = resid ? P.eta_min_p : -150.0;
   double n, dn, p, dp;
   if (P.statistics == 1) {
     double F, dF;
-    fd_half_d(eta_n, F, dF);
+    fd_half_d(eta_n, F, dF, xn);
     n = P.NC * F;
     dn = P.NC * dF * ik;
-    fd_half_d(eta_p, F, dF);
+    fd_half_d(eta_p, F, dF, xp);
     p = P.NV * F;
     dp = -P.NV * dF * ik;
   } else {
-    n = eta_n < -150.0 ? 0.0 : P.NC * exp(eta_n);
+    n = eta_n < xn ? 0.0 : P.NC * exp(eta_n);
     dn = n * ik;
-    p = eta_p < -150.0 ? 0.0 : P.NV * exp(eta_p);
+    p = eta_p < xp ? 0.0 : P.NV * exp(eta_p);
     dp = -p * ik;
   }
   double NDp = P.ND, dND = 0.0, NAm = P.NA, dNA = 0.0;
   if (P.incomplete) {
     if (P.ND != 0.0) {
       double s, oms;
-      sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) * ik, P.gD, s, oms);
+      sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) * ik, P.gD, s, oms, resid ? P.z_max_d : 746.0);
       NDp = P.ND * s;
       dND = -P.ND * s * oms * ik;
     }
     if (P.NA != 0.0) {
       double s, oms;
-      sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) * ik, P.gA, s, oms);
+      sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) * ik, P.gA, s, oms, resid ? P.z_max_a : 746.0);
       NAm = P.NA * s;
       dNA = P.NA * s * oms * ik;
     }
@@ -106,6 +120,61 @@ __device__ __forceinline__ Charge charge_at(const Phys& P, double phi) {
   c.n = n;
   c.dn = dn;
   return c;
+}
+
+// The constant-charge zone of a potential for charge_resid: -1 where some term needs evaluating,
+// else A + 2 D with A (D) = 1 when the acceptors (donors) count as fully ionized.
+__device__ __forceinline__ int charge_zone(const Phys& P, double phi) {
+  if (!(phi < P.phi_n_on && phi > P.phi_p_on)) return -1;
+  int z = 0;
+  if (P.incomplete) {
+    if (P.NA != 0.0) {
+      if (phi > P.phi_a_hi)
+        z += 1;
+      else if (!(phi < P.phi_a_lo))
+        return -1;
+    }
+    if (P.ND != 0.0) {
+      if (phi < P.phi_d_lo)
+        z += 2;
+      else if (!(phi > P.phi_d_hi))
+        return -1;
+    }
+  }
+  return z;
+}
+
+// The charge of a constant-charge zone (the value charge_resid returns there).
+__device__ __forceinline__ double zone_charge(const Phys& P, int zone) {
+  if (!P.incomplete) return P.ND - P.NA;
+  double rho = 0.0;
+  if (P.NA != 0.0) rho -= (zone & 1) ? P.NA : 0.0;
+  if (P.ND != 0.0) rho += (zone & 2) ? P.ND : 0.0;
+  return rho;
+}
+
+// The residual's charge outside the dots: where phi lies outside every cutoff band (n and p below
+// resolution, each dopant fully ionized or below resolution) the charge is a constant and its
+// derivative zero, found by a few comparisons; elsewhere the full evaluation with the residual's
+// cutoffs. Both give the same values as charge_at(P, phi, true).
+__device__ __forceinline__ Charge charge_resid(const Phys& P, double phi) {
+  const bool no_n = phi < P.phi_n_on, no_p = phi > P.phi_p_on;
+  bool flat = no_n && no_p;
+  double rho = 0.0;
+  if (P.incomplete) {
+    if (P.NA != 0.0) {
+      flat = flat && (phi < P.phi_a_lo || phi > P.phi_a_hi);
+      rho -= phi > P.phi_a_hi ? P.NA : 0.0;  // z_a < -45: fully ionized; above the cutoff: none
+    }
+    if (P.ND != 0.0) {
+      flat = flat && (phi < P.phi_d_lo || phi > P.phi_d_hi);
+      rho += phi < P.phi_d_lo ? P.ND : 0.0;
+    }
+  } else {
+    rho = P.ND - P.NA;
+  }
+  if (flat) return Charge{rho, 0.0, 0.0, 0.0};
+  return charge_at(P, phi, true);
 }
 
 }  // namespace qcad

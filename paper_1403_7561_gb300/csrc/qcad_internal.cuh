@@ -94,6 +94,14 @@ __device__ __forceinline__ bool grid_is_dir(const Grid<T>& g, int i, int j, int 
   return false;
 }
 
+// Density below which a carrier or ionized-dopant term of the residual is not evaluated, outside
+// the dot regions (nm^-3; 1e-25 nm^-3 is 1e-4 carriers per cm^3). Its contribution to a residual
+// entry, (q/eps0) |e| rho N_a <= 18.1 V nm^-2 x |e| x 1e-25, stays below 1e-20 V nm on elements of
+// up to 5000 nm^3, and to the Jacobian, (q/eps0) |e| rho / kT, below 1e-16 of a stiffness entry
+// at 0.5 K: far under the FP64 rounding of the stiffness term K phi and the 1e-10 V nm
+// tolerance. The dot electron counts keep the 1e-60 nm^-3 cutoffs (eta -150, z 746).
+constexpr double RHO_RESID_FLOOR = 1e-25;
+
 // Semiconductor parameters at the bias point (one semiconductor per device).
 struct Phys {
   double kT, inv_kT;      // eV, 1/eV
@@ -106,6 +114,14 @@ struct Phys {
   double qe;              // q/eps0, V*nm
   int statistics;         // 0 MB, 1 FD
   int incomplete;         // 1: Eq. FinalIonization
+  // Below-resolution cutoffs of the residual outside the dots (densities under RHO_RESID_FLOOR,
+  // physics.cuh): n and p are not evaluated for eta below eta_min_n / eta_min_p, and the ionized
+  // acceptor (donor) density is taken as zero for an ionization argument above z_max_a (z_max_d).
+  double eta_min_n, eta_min_p, z_max_a, z_max_d;
+  // the same cutoffs as potentials (V): n needs evaluating only for phi >= phi_n_on, p only for
+  // phi <= phi_p_on; the acceptor (donor) ionization is a constant (0 or 1) outside
+  // [phi_a_lo, phi_a_hi] ([phi_d_lo, phi_d_hi]), where its argument is beyond the cutoff or below -45
+  double phi_n_on, phi_p_on, phi_a_lo, phi_a_hi, phi_d_lo, phi_d_hi;
 };
 
 struct DotBoxes {
