@@ -153,6 +153,78 @@ void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, 
   note_launch(), pack_kernel<<<dblocks(total), DT, 0, s>>>(sm, nvec, full, ldf, dof, ldd, unpack);
 }
 
+// Double-float arithmetic for the FP64 phase's dense block products. This part runs FP32 at
+// about 57 times its FP64 rate, so a product-accumulate of two FP64 values carried as
+// unevaluated sums of two floats (hi + lo, a 48-bit significand) costs fewer cycles than one
+// DFMA. The product is exact up to the dropped lo*lo term (Dekker's product through the fused
+// multiply-add); the sum is Knuth's two-sum into the high word with the errors gathered in the
+// low word. Relative error of a length-p dot product: about p * 2^-48.
+__device__ __forceinline__ void df_split(double a, float& h, float& l) {
+  h = __double2float_rn(a);
+  l = __double2float_rn(a - (double)h);
+}
+
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float ph = ah * bh;
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float t = sh + ph;
+  const float bp = t - sh;
+  const float e = (sh - (t - bp)) + (ph - bp);
+  sh = t;
+  sl += e + pl;
+}
+
+// The conversions between FP64 and FP32 run on the FP64 pipe of this part (2 lanes per SM per
+// clock), so splitting and joining in float arithmetic would cost more than the products
+// themselves. These do it with integer operations on the bit patterns instead.
+//
+// a = h + l for 2^-80 <= |a| < 2^127: h keeps the sign, exponent and top 23 mantissa bits of a
+// (truncation, exact), l the next 23 mantissa bits (bits 28..6), so |a - h - l| <= 2^-46 |a|.
+// Below 2^-80 l is dropped (|a - h| < 2^-23 |a|), below 2^-100 a is taken as zero; these
+// magnitudes do not occur in the eigensolver's blocks, whose entries are of order 1e-6 and above.
+__device__ __forceinline__ void df_split_i(double a, float& h, float& l) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const int e = (int)((hi32 >> 20) & 0x7FF);
+  const unsigned sgn = hi32 & 0x80000000u;
+  if (e < 923 || e > 1150) {  // tiny, zero, huge, inf or nan: the FP64 conversion
+    h = __double2float_rn(a);
+    l = 0.0f;
+    return;
+  }
+  h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+  if (e < 943) {
+    l = 0.0f;
+    return;
+  }
+  const float m = __uint_as_float(0x4B000000u | ((lo32 >> 6) & 0x7FFFFFu)) - 8388608.0f;  // bits 28..6 exactly
+  l = __uint_as_float(__float_as_uint(m * __uint_as_float((unsigned)(e - 942) << 23)) | sgn);
+}
+
+// The FP64 value of a float, by its bit pattern (exact for normal floats and zero).
+__device__ __forceinline__ double f2d_i(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)x;  // zero, subnormal, inf, nan
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// h + l rounded to FP64 with one FP64 addition.
+__device__ __forceinline__ double df_join(float h, float l) { return f2d_i(h) + f2d_i(l); }
+
+// (ah, al) += (bh, bl) in double-float (Knuth's two-sum on the high words, low words summed).
+__device__ __forceinline__ void df_acc(float& ah, float& al, float bh, float bl) {
+  const float t = ah + bh;
+  const float bp = t - ah;
+  const float e = (ah - (t - bp)) + (bh - bp);
+  ah = t;
+  al += e + bl;
+}
+
 // G1 = A^T B1 and optionally G2 = A^T B2 (p x p each, row-major o = a*p + b) for column-major
 // A (n x p, lda) and B1, B2 (n x p, ldb): the Gram matrices of the LOBPCG blocks. A block walks
 // 32-row tiles of its share of the rows, copied asynchronously (double-buffered) into shared
@@ -201,9 +273,16 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
   __syncthreads();
   const bool active = tid < ta_n * tb_n;
   const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
+  // across tiles: FP64 (double storage) or double-float on the FP32 pipes (float storage, where
+  // an FP64 add per output and tile would cost more than the tile's products)
   double acc[16];
+  float acch[16], accl[16];
 #pragma unroll
-  for (int s = 0; s < 16; ++s) acc[s] = 0.0;
+  for (int s = 0; s < 16; ++s) {
+    acc[s] = 0.0;
+    acch[s] = 0.0f;
+    accl[s] = 0.0f;
+  }
   const long long ntiles = (n + GR - 1) / GR;
   auto issue = [&](long long tile, int stage) {
     if (tile < ntiles) {
@@ -251,13 +330,22 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
           for (int v = 0; v < 4; ++v) s16[4 * u + v] += av[u] * bv[v];
       }
 #pragma unroll
-      for (int s = 0; s < 16; ++s) acc[s] += (double)s16[s];
+      for (int s = 0; s < 16; ++s) {
+        if constexpr (sizeof(T) == 4)
+          df_acc(acch[s], accl[s], (float)s16[s], 0.0f);
+        else
+          acc[s] += (double)s16[s];
+      }
     }
     __syncthreads();  // the stage is refilled by the next iteration's copies
     stage ^= 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (!active) return;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc[s] = df_join(acch[s], accl[s]);
+  }
   // slot layout: product 0 (p*q) then product 1
   double* out = part + (size_t)blockIdx.x * p * qt;
 #pragma unroll
@@ -297,29 +385,6 @@ __global__ void __launch_bounds__(256) gram_reduce_kernel(int nblk, int tot, int
 size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 * q; }
 
 // ---------------------------------------------------------------------------
-// Double-float arithmetic for the FP64 phase's dense block products. This part runs FP32 at
-// about 57 times its FP64 rate, so a product-accumulate of two FP64 values carried as
-// unevaluated sums of two floats (hi + lo, a 48-bit significand) costs fewer cycles than one
-// DFMA. The product is exact up to the dropped lo*lo term (Dekker's product through the fused
-// multiply-add); the sum is Knuth's two-sum into the high word with the errors gathered in the
-// low word. Relative error of a length-p dot product: about p * 2^-48.
-__device__ __forceinline__ void df_split(double a, float& h, float& l) {
-  h = __double2float_rn(a);
-  l = __double2float_rn(a - (double)h);
-}
-
-__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
-  const float ph = ah * bh;
-  float pl = fmaf(ah, bh, -ph);
-  pl = fmaf(ah, bl, pl);
-  pl = fmaf(al, bh, pl);
-  const float t = sh + ph;
-  const float bp = t - sh;
-  const float e = (sh - (t - bp)) + (ph - bp);
-  sh = t;
-  sl += e + pl;
-}
-
 // gram_kernel for FP64 blocks in double-float arithmetic: the double tile lands in shared
 // memory as before, is split once into hi and lo float tiles, and each 32-row tile is summed in
 // double-float before it is added to the FP64 accumulators.
@@ -340,9 +405,12 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
   __syncthreads();
   const bool active = tid < ta_n * tb_n;
   const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
-  double acc[16];
+  float acch[16], accl[16];  // double-float accumulation across tiles
 #pragma unroll
-  for (int s = 0; s < 16; ++s) acc[s] = 0.0;
+  for (int s = 0; s < 16; ++s) {
+    acch[s] = 0.0f;
+    accl[s] = 0.0f;
+  }
   const long long ntiles = (n + GR - 1) / GR;
   auto issue = [&](long long tile, int stage) {
     if (tile < ntiles) {
@@ -375,7 +443,7 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
     __syncthreads();
     {
       const double* st = sh + (size_t)stage * GR * W;
-      for (int t = tid; t < GR * W; t += nth) df_split(st[t], fh[t], fl[t]);
+      for (int t = tid; t < GR * W; t += nth) df_split_i(st[t], fh[t], fl[t]);
     }
     __syncthreads();
     if (active) {
@@ -398,13 +466,16 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
           for (int v = 0; v < 4; ++v) df_mac(sh16[4 * u + v], sl16[4 * u + v], ah[u], al[u], bh[v], bl[v]);
       }
 #pragma unroll
-      for (int s = 0; s < 16; ++s) acc[s] += (double)sh16[s] + (double)sl16[s];
+      for (int s = 0; s < 16; ++s) df_acc(acch[s], accl[s], sh16[s], sl16[s]);
     }
     __syncthreads();
     stage ^= 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   if (!active) return;
+  double acc[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) acc[s] = df_join(acch[s], accl[s]);
   double* out = part + (size_t)blockIdx.x * p * qt;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -523,7 +594,7 @@ __global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
     float ah[PMAX], al[PMAX];
 #pragma unroll
-    for (int i = 0; i < PMAX; ++i) df_split(i < p ? A[i * lda + r] : 0.0, ah[i], al[i]);
+    for (int i = 0; i < PMAX; ++i) df_split_i(i < p ? A[i * lda + r] : 0.0, ah[i], al[i]);
     for (int j0 = 0; j0 < q; j0 += 4) {
       float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -538,7 +609,7 @@ __global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int
       for (int u = 0; u < 4; ++u) {
         const int j = j0 + u;
         if (j >= q) break;
-        const double y = (double)sh[u] + (double)sl[u];
+        const double y = df_join(sh[u], sl[u]);
         if (j < q1)
           Y1[j * ldy + r] = y;
         else
