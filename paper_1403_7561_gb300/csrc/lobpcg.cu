@@ -462,9 +462,11 @@ struct LobpcgRun {
     for (int it = 1; it <= maxit + 1; ++it) {
       residual(lam_d, norms_d);
       apply(1);
-      // one Gram matrix of [W P] in the M inner product serves both Cholesky QRs
-      int nwp = haveP ? 2 * nb : nb;
-      gram_async(nwp, nwp, blk(Sx, 1), blk(MS, 1), nullptr);
+      // Rayleigh-Ritz Gram matrices of [X W P] with W and P as they are: the Cholesky QR of W and
+      // of P is applied to the small matrices on the host (G -> T^T G T), which gives the
+      // Rayleigh-Ritz problem of the orthonormalized blocks without forming them
+      int nuse = haveP ? 3 * nb : 2 * nb;
+      gram_async(nuse, nuse, Sx, HS, MS);
       sync();
       const bool conv = converged(tol);
       if (debug_level() >= 2)
@@ -482,53 +484,85 @@ struct LobpcgRun {
         }
       }
       ++iters;
-      std::vector<double> Gwp = gram_sym(nwp, 0), RW, RP;
-      if (!chol_inv(Gwp, nwp, 0, nb, RW)) {
+      const auto th = std::chrono::steady_clock::now();
+      std::vector<double> GH = gram_sym(nuse, 0), GM = gram_sym(nuse, (size_t)nuse * nuse), RW, RP;
+      if (!chol_inv(GM, nuse, nb, nb, RW)) {
         // W lost rank: restart it from a random block (and drop P)
         haveP = false;
-        nwp = nb;
+        nuse = 2 * nb;
         launch_random_block<T>(ns, nb, ns, S->interior.as<unsigned char>(), 0xABCDEF00ull + iters, blk(Sx, 1), s);
         apply(1);
-        gram_async(nb, nb, blk(Sx, 1), blk(MS, 1), nullptr);
+        gram_async(nuse, nuse, Sx, HS, MS);
         sync();
-        Gwp = gram_sym(nb, 0);
-        if (!chol_inv(Gwp, nb, 0, nb, RW)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
+        GH = gram_sym(nuse, 0);
+        GM = gram_sym(nuse, (size_t)nuse * nuse);
+        if (!chol_inv(GM, nuse, nb, nb, RW)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
       }
-      if (haveP && !chol_inv(Gwp, nwp, nb, nb, RP)) haveP = false;
-      if (haveP) {
-        std::vector<double> C((size_t)4 * nb * nb, 0.0);  // diag(RW, RP), 2nb x 2nb
-        for (int j = 0; j < nb; ++j)
-          for (int i = 0; i < nb; ++i) {
-            C[(size_t)j * 2 * nb + i] = RW[(size_t)j * nb + i];
-            C[(size_t)(nb + j) * 2 * nb + nb + i] = RP[(size_t)j * nb + i];
-          }
-        combine(1, 2 * nb, C, 2 * nb, 2 * nb, 1, 1);
-      } else {
-        combine(1, nb, RW, nb, nb, 1, 1);
-      }
-      // Rayleigh-Ritz on [X W P]
-      int nuse = haveP ? 3 * nb : 2 * nb;
-      gram_async(nuse, nuse, Sx, HS, MS);
-      sync();
-      const auto th = std::chrono::steady_clock::now();
-      std::vector<double> GH = gram_sym(nuse, 0), GM = gram_sym(nuse, (size_t)nuse * nuse), w(nuse),
-                          C((size_t)nuse * nuse);
-      bool ok = dense_gen_eig(nuse, GH.data(), GM.data(), w.data(), C.data());
-      if (!ok && haveP) {
-        haveP = false;
-        const int n2 = 2 * nb;
+      if (haveP && !chol_inv(GM, nuse, 2 * nb, nb, RP)) haveP = false;
+      // T = diag(I, RW, RP): the basis [X, W RW, P RP] has unit M-Gram blocks on its diagonal
+      auto reduce_to = [&](int n2) {
+        if (n2 == nuse) return;
         std::vector<double> gh2((size_t)n2 * n2), gm2((size_t)n2 * n2);
         for (int j = 0; j < n2; ++j)
           for (int i = 0; i < n2; ++i) {
             gh2[(size_t)j * n2 + i] = GH[(size_t)j * nuse + i];
             gm2[(size_t)j * n2 + i] = GM[(size_t)j * nuse + i];
           }
+        GH.swap(gh2);
+        GM.swap(gm2);
         nuse = n2;
-        w.resize(nuse);
-        C.resize((size_t)nuse * nuse);
-        ok = dense_gen_eig(nuse, gh2.data(), gm2.data(), w.data(), C.data());
+      };
+      if (!haveP) reduce_to(2 * nb);
+      auto make_T = [&]() {
+        std::vector<double> Tq((size_t)nuse * nuse, 0.0);
+        for (int i = 0; i < nb; ++i) Tq[(size_t)i * nuse + i] = 1.0;
+        for (int j = 0; j < nb; ++j)
+          for (int i = 0; i < nb; ++i) {
+            Tq[(size_t)(nb + j) * nuse + nb + i] = RW[(size_t)j * nb + i];
+            if (nuse == 3 * nb) Tq[(size_t)(2 * nb + j) * nuse + 2 * nb + i] = RP[(size_t)j * nb + i];
+          }
+        return Tq;
+      };
+      // G' = T^T G T (column-major n x n)
+      auto congruence = [&](const std::vector<double>& Tm, const std::vector<double>& Gm) {
+        const int n = nuse;
+        std::vector<double> GT((size_t)n * n, 0.0), out((size_t)n * n, 0.0);
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k) {
+            const double t = Tm[(size_t)j * n + k];
+            if (t == 0.0) continue;
+            for (int i = 0; i < n; ++i) GT[(size_t)j * n + i] += Gm[(size_t)k * n + i] * t;
+          }
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += Tm[(size_t)i * n + k] * GT[(size_t)j * n + k];
+            out[(size_t)j * n + i] = acc;
+          }
+        return out;
+      };
+      std::vector<double> Tm = make_T();
+      std::vector<double> GHt = congruence(Tm, GH), GMt = congruence(Tm, GM), w(nuse), Ct((size_t)nuse * nuse);
+      bool ok = dense_gen_eig(nuse, GHt.data(), GMt.data(), w.data(), Ct.data());
+      if (!ok && haveP) {
+        haveP = false;
+        reduce_to(2 * nb);
+        Tm = make_T();
+        GHt = congruence(Tm, GH);
+        GMt = congruence(Tm, GM);
+        w.assign(nuse, 0.0);
+        Ct.assign((size_t)nuse * nuse, 0.0);
+        ok = dense_gen_eig(nuse, GHt.data(), GMt.data(), w.data(), Ct.data());
       }
       if (!ok) throw Error(QCAD_ERR_NONFINITE, "LOBPCG Rayleigh-Ritz failed");
+      // the Ritz vectors in the stored basis: C = T C'
+      std::vector<double> C((size_t)nuse * nuse, 0.0);
+      for (int j = 0; j < nb; ++j)
+        for (int k = 0; k < nuse; ++k) {
+          const double c = Ct[(size_t)j * nuse + k];
+          if (c == 0.0) continue;
+          for (int i = 0; i < nuse; ++i) C[(size_t)j * nuse + i] += Tm[(size_t)k * nuse + i] * c;
+        }
       // new X = [X W P] C[:, :nb];  new P = [W P] C[nb:, :nb] = [X W P] (C[:, :nb] with the X rows zeroed)
       std::vector<double> Cxp((size_t)nuse * 2 * nb, 0.0);
       for (int j = 0; j < nb; ++j)
@@ -602,7 +636,13 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   // Rayleigh-Ritz) until the residuals reach the single-precision level.
   DevBuf w32, w64;
   ChebPre pre;
-  pre.init(m, io, &S, nb, 5, dinv32.as<float>());
+  // Chebyshev degrees of the two phases (environment QCAD_LOBPCG_DEG32 / QCAD_LOBPCG_DEG64 override)
+  auto env_int = [](const char* name, int def) {
+    const char* e = std::getenv(name);
+    return e ? std::max(1, std::atoi(e)) : def;
+  };
+  const int deg32 = env_int("QCAD_LOBPCG_DEG32", 5), deg64 = env_int("QCAD_LOBPCG_DEG64", 5);
+  pre.init(m, io, &S, nb, deg32, dinv32.as<float>());
   LobpcgRun<float> A;
   init_run<float>(A, m, io, &S, nb, nev, w32, dinv32.as<float>());
   A.pre = &pre;
@@ -629,6 +669,7 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   LobpcgRun<double> B;
   init_run<double>(B, m, io, &S, nb, nev, w64, S.dinv.as<double>());
   B.pre = &pre;
+  pre.set_degree(deg64);
   launch_f2d(ns * nb, A.Sx, B.Sx, s);
   B.apply(0);
   B.rr_x();
