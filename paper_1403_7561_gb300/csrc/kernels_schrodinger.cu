@@ -540,10 +540,15 @@ template void launch_gram<double>(long long, int, int, const double*, long long,
 // registers by one thread before any output of the row is written. Y = A C with A n x p
 // (lda), C p x q column-major (staged in shared memory with rows padded to a multiple of 4);
 // output columns j < q1 go to Y1 (ldy), columns j >= q1 to Y2 (ldy). PMAX >= p.
+// blockIdx.y selects one of several equally laid out block sets (A, Y1, Y2 offset by bstride
+// elements each): LOBPCG combines the S, H S and M S blocks with one C in one launch.
 template <class T, int PMAX>
 __global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q, int q1, const T* A, long long lda,
-                                                      const T* C, T* Y1, T* Y2, long long ldy) {
+                                                      const T* C, T* Y1, T* Y2, long long ldy, long long bstride) {
   extern __shared__ __align__(16) unsigned char sc_raw[];
+  A += blockIdx.y * bstride;
+  Y1 += blockIdx.y * bstride;
+  Y2 += blockIdx.y * bstride;
   T* sC = reinterpret_cast<T*>(sc_raw);  // [q][pp]
   const int pp = (p + 3) & ~3;
   for (int t = threadIdx.x; t < pp * q; t += blockDim.x) {
@@ -561,8 +566,10 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q,
 #pragma unroll
       for (int i = 0; i < PMAX; i += 4) {
         if (i < pp) {
-          s += a[i] * cj[i] + a[i + 1] * cj[i + 1];
-          s += a[i + 2] * cj[i + 2] + a[i + 3] * cj[i + 3];
+          T c4[4];
+          gram_ld4(cj + i, c4);  // 16-byte aligned: pp is a multiple of 4
+          s += a[i] * c4[0] + a[i + 1] * c4[1];
+          s += a[i + 2] * c4[2] + a[i + 3] * c4[3];
         }
       }
       if (j < q1)
@@ -578,10 +585,13 @@ __global__ void __launch_bounds__(256) combine_kernel(long long n, int p, int q,
 // double-float dot product rounded to FP64 at the end. Four outputs are formed together so that
 // four independent two-sum chains interleave.
 template <int PMAX>
-__global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int q, int q1, const double* A,
+__global__ void __launch_bounds__(256, 2) combine_df_kernel(long long n, int p, int q, int q1, const double* A,
                                                          long long lda, const double* C, double* Y1, double* Y2,
-                                                         long long ldy) {
+                                                         long long ldy, long long bstride) {
   extern __shared__ __align__(16) unsigned char sc_raw[];
+  A += blockIdx.y * bstride;
+  Y1 += blockIdx.y * bstride;
+  Y2 += blockIdx.y * bstride;
   const int pp = (p + 3) & ~3;
   const int qq = (q + 3) & ~3;
   float* sCh = reinterpret_cast<float*>(sc_raw);  // [qq][pp], zero beyond p and q
@@ -598,11 +608,16 @@ __global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int
     for (int j0 = 0; j0 < q; j0 += 4) {
       float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int i = 0; i < PMAX; ++i) {
+      for (int i = 0; i < PMAX; i += 4) {
         if (i < pp) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            df_mac(sh[u], sl[u], ah[i], al[i], sCh[(j0 + u) * pp + i], sCl[(j0 + u) * pp + i]);
+          for (int u = 0; u < 4; ++u) {
+            float ch[4], cl[4];  // 16-byte aligned loads: pp is a multiple of 4
+            gram_ld4(sCh + (j0 + u) * pp + i, ch);
+            gram_ld4(sCl + (j0 + u) * pp + i, cl);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) df_mac(sh[u], sl[u], ah[i + w], al[i + w], ch[w], cl[w]);
+          }
         }
       }
 #pragma unroll
@@ -621,34 +636,34 @@ __global__ void __launch_bounds__(256) combine_df_kernel(long long n, int p, int
 
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
-                    long long ldy, cudaStream_t s) {
+                    long long ldy, cudaStream_t s, int nbase, long long bstride) {
   const size_t shm = (size_t)((p + 3) & ~3) * q * sizeof(T);
-  const int nb = dblocks(n);
+  const dim3 grid(dblocks(n), std::max(1, nbase));
   if constexpr (std::is_same<T, double>::value) {
     if (dense_df()) {  // hi and lo float tables, q padded to a multiple of 4
       const size_t shm_df = (size_t)((p + 3) & ~3) * ((q + 3) & ~3) * 2 * sizeof(float);
       if (p <= 16)
-        note_launch(), combine_df_kernel<16><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<16><<<grid, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
       else if (p <= 32)
-        note_launch(), combine_df_kernel<32><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<32><<<grid, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
       else if (p <= 48)
-        note_launch(), combine_df_kernel<48><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<48><<<grid, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
       else
-        note_launch(), combine_df_kernel<64><<<nb, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+        note_launch(), combine_df_kernel<64><<<grid, 256, shm_df, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
       return;
     }
   }
   if (p <= 16)
-    note_launch(), combine_kernel<T, 16><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+    note_launch(), combine_kernel<T, 16><<<grid, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
   else if (p <= 32)
-    note_launch(), combine_kernel<T, 32><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+    note_launch(), combine_kernel<T, 32><<<grid, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
   else
-    note_launch(), combine_kernel<T, 64><<<nb, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy);
+    note_launch(), combine_kernel<T, 64><<<grid, 256, shm, s>>>(n, p, q, q1, A, lda, C, Y1, Y2, ldy, bstride);
 }
 template void launch_combine<float>(long long, int, int, int, const float*, long long, const float*, float*, float*,
-                                    long long, cudaStream_t);
+                                    long long, cudaStream_t, int, long long);
 template void launch_combine<double>(long long, int, int, int, const double*, long long, const double*, double*,
-                                     double*, long long, cudaStream_t);
+                                     double*, long long, cudaStream_t, int, long long);
 
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms[2j] += |R_j|^2,
 // norms[2j+1] += |MX_j|^2 (FP64 sums per thread, reduced per block, one atomic per block).

@@ -395,9 +395,9 @@ struct LobpcgRun {
   void combine(int src_blk, int p, const std::vector<double>& C, int q, int q1, int dst1, int dst2) {
     for (size_t t = 0; t < (size_t)p * q; ++t) hC[t] = (T)C[t];
     CK(cudaMemcpyAsync(Cd, hC, (size_t)p * q * sizeof(T), cudaMemcpyHostToDevice, s));
-    T* bases[3] = {Sx, HS, MS};
-    for (T* base : bases)
-      launch_combine<T>(ns, p, q, q1, blk(base, src_blk), ns, Cd, blk(base, dst1), blk(base, dst2), ns, s);
+    // S, H S and M S (laid out 3 nb ns apart) in one launch
+    launch_combine<T>(ns, p, q, q1, blk(Sx, src_blk), ns, Cd, blk(Sx, dst1), blk(Sx, dst2), ns, s, 3,
+                      (long long)3 * nb * ns);
   }
 
   // Rayleigh-Ritz on block 0 alone.

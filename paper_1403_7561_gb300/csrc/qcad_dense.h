@@ -29,10 +29,10 @@ template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
                  double* G1, double* G2, double* part, cudaStream_t s);
 size_t gram_part_doubles(int p, int q);
-// p <= 64.
+// p <= 64. nbase > 1: the same C applied to nbase block sets, set b at A, Y1, Y2 + b * bstride.
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
-                    long long ldy, cudaStream_t s);
+                    long long ldy, cudaStream_t s, int nbase = 1, long long bstride = 0);
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s);
