@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "linmarch.cuh"
 #include "mg.h"
 #include "pcg_ops.cuh"
@@ -214,6 +215,59 @@ struct HmLinOp {
   __device__ void finish() {}
 };
 
+// Double-float coefficients from the FP64 chunks staged in shared memory.
+template <>
+__device__ __forceinline__ void lin_lds_c8<dfl>(const uint4* p, dfl* c) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const double2 a = *reinterpret_cast<const double2*>(p + 32 * h);
+    c[2 * h] = dfl_from_bits(a.x);
+    c[2 * h + 1] = dfl_from_bits(a.y);
+  }
+}
+
+// H and M of FP64 vectors in double-float arithmetic: the z-march stages the FP64 inputs and
+// coefficients as raw 8-byte values, which are split into double-float pairs where they are read;
+// outputs are rounded to FP64.
+struct HmDfOp {
+  static constexpr int NIN = 1;
+  static constexpr bool SEPM = true;
+  struct Pre {};
+  const double* x;
+  double* hx;
+  double* mx;
+  const double* cV;
+  long long ld;
+  dfl mscale;
+  const double* xv;
+  double* hv;
+  double* mv;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int vec) {
+    const long long o = (long long)vec * ld;
+    xv = x + o;
+    hv = hx ? hx + o : nullptr;
+    mv = mx ? mx + o : nullptr;
+  }
+  __device__ const dfl* coeffs() const { return reinterpret_cast<const dfl*>(cV); }
+  __device__ const dfl* lin_src(int) const { return reinterpret_cast<const dfl*>(xv); }
+  // a staged value holds the bytes of an FP64 input
+  __device__ dfl lin_mix(dfl raw, dfl) const {
+    return dfl_from_bits(__longlong_as_double((long long)(((unsigned long long)__float_as_uint(raw.l) << 32) |
+                                                          __float_as_uint(raw.h))));
+  }
+  __device__ dfl lin_in(int n) const { return dfl_from_bits(xv[n]); }
+  __device__ Pre lin_pre(int) const { return Pre{}; }
+  __device__ bool lin_dir() const { return true; }
+  __device__ dfl m_scale() const { return mscale; }
+  __device__ void lin_out(int, const Pre&, dfl, dfl) {}
+  __device__ void lin_out2(int n, dfl yh, dfl ym) {
+    if (hv) hv[n] = dfl_to_double(yh);
+    if (mv) mv[n] = dfl_to_double(ym);
+  }
+  __device__ void finish() {}
+};
+
 template <class T, int BY, int R, class Op>
 static void lin_launch_vec(const Grid<T>& g, const Op& op, int kchunk, int nvec, cudaStream_t s) {
   using S = LinShape<T, BY, R>;
@@ -243,6 +297,17 @@ void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg,
 }
 template void launch_hm_apply_lin<float>(const Grid<float>&, const HmArgs<float>&, LaunchCfg, cudaStream_t);
 template void launch_hm_apply_lin<double>(const Grid<double>&, const HmArgs<double>&, LaunchCfg, cudaStream_t);
+
+void launch_hm_apply_df(const Grid<dfl>& g, const HmArgs<double>& args, cudaStream_t s) {
+  HmDfOp op = {};
+  op.x = args.x;
+  op.hx = args.hx;
+  op.mx = args.mx;
+  op.cV = args.cV;
+  op.ld = args.ld;
+  op.mscale = dfl(args.mscale);
+  lin_launch_vec<dfl, 8, 2>(g, op, 16, args.nvec, s);
+}
 
 // Batched PCG apply: a work table maps each block to (instance, tile) of instances of different
 // sizes; plane-factorized march with 8 warps and two rows per thread.

@@ -3,6 +3,8 @@
 // Schrodinger3D) with the potential energy of Eq. SchrodPotEnergy (no V_xc).
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 #include <cstdlib>
 #include <cstring>
 #include <type_traits>
@@ -176,45 +178,15 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sl += e + pl;
 }
 
-// The conversions between FP64 and FP32 run on the FP64 pipe of this part (2 lanes per SM per
-// clock), so splitting and joining in float arithmetic would cost more than the products
-// themselves. These do it with integer operations on the bit patterns instead.
-//
-// a = h + l for 2^-80 <= |a| < 2^127: h keeps the sign, exponent and top 23 mantissa bits of a
-// (truncation, exact), l the next 23 mantissa bits (bits 28..6), so |a - h - l| <= 2^-46 |a|.
-// Below 2^-80 l is dropped (|a - h| < 2^-23 |a|), below 2^-100 a is taken as zero; these
-// magnitudes do not occur in the eigensolver's blocks, whose entries are of order 1e-6 and above.
+// Splits and joins of FP64 values go through the bit patterns (dfloat.cuh): the FP32<->FP64
+// conversion instructions run on the FP64 pipe of this part (2 lanes per SM per clock), so
+// converting in float arithmetic would cost more than the products themselves.
 __device__ __forceinline__ void df_split_i(double a, float& h, float& l) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(a);
-  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
-  const int e = (int)((hi32 >> 20) & 0x7FF);
-  const unsigned sgn = hi32 & 0x80000000u;
-  if (e < 923 || e > 1150) {  // tiny, zero, huge, inf or nan: the FP64 conversion
-    h = __double2float_rn(a);
-    l = 0.0f;
-    return;
-  }
-  h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
-  if (e < 943) {
-    l = 0.0f;
-    return;
-  }
-  const float m = __uint_as_float(0x4B000000u | ((lo32 >> 6) & 0x7FFFFFu)) - 8388608.0f;  // bits 28..6 exactly
-  l = __uint_as_float(__float_as_uint(m * __uint_as_float((unsigned)(e - 942) << 23)) | sgn);
+  const dfl d = dfl_from_bits(a);
+  h = d.h;
+  l = d.l;
 }
-
-// The FP64 value of a float, by its bit pattern (exact for normal floats and zero).
-__device__ __forceinline__ double f2d_i(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (double)x;  // zero, subnormal, inf, nan
-  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
-                                          ((unsigned long long)(e + 896u) << 52) |
-                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-
-// h + l rounded to FP64 with one FP64 addition.
-__device__ __forceinline__ double df_join(float h, float l) { return f2d_i(h) + f2d_i(l); }
+__device__ __forceinline__ double df_join(float h, float l) { return dfl_to_double(dfl(h, l)); }
 
 // (ah, al) += (bh, bl) in double-float (Knuth's two-sum on the high words, low words summed).
 __device__ __forceinline__ void df_acc(float& ah, float& al, float bh, float bl) {

@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "mesh.h"
 
 namespace qcad {
@@ -52,6 +53,7 @@ struct SubSetup {
   long long ndof;   // interior nodes
   GridDev<double> g64;
   GridDev<float> g32;
+  GridDev<dfl> gdf;  // double-float tables: the FP64 phase's H and M applies
   DevBuf cV64, cV32, dinv, interior;
   double vmin;
   double inv_kx;    // 1 / kappa_x = 2 m_x / hbar^2 (scale of the separable mass stencil)
@@ -99,6 +101,10 @@ static void setup_sub(qcad_mesh_s* m, const qcad_bias* b, const double* phi, con
     S.g32.g.dir_boundary = 1;
     S.g32.g.dir_bottom = 0;
     S.g32.g.dir_top = nullptr;
+    build_grid<dfl>(S.gdf, t, hx, hy, hz, s);
+    S.gdf.g.dir_boundary = 1;
+    S.gdf.g.dir_bottom = 0;
+    S.gdf.g.dir_top = nullptr;
   }
   // potential energy at the qp: V = q phi_ref - chi - q phi (Eq. SchrodPotEnergy, no V_xc)
   const Phys P = make_phys(m, b);
@@ -361,9 +367,22 @@ struct LobpcgRun {
     a.mscale = S->inv_kx;
     Profiler::Pair pp;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
-    launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
+    if constexpr (sizeof(T) == 8) {
+      // FP64 vectors: H and M in double-float arithmetic on the FP32 pipes (2^-46 relative, far
+      // below the 1e-8 residuals this phase iterates to); QCAD_LOBPCG_NATIVE64 selects FP64 ones
+      if (use_df_apply())
+        launch_hm_apply_df(S->gdf.g, a, s);
+      else
+        launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
+    } else {
+      launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
+    }
     if (m->prof.on) m->prof.end(pp, s);
     applies += nb;
+  }
+  static bool use_df_apply() {
+    static const bool df = std::getenv("QCAD_LOBPCG_NATIVE64") == nullptr;
+    return df;
   }
   const T* cv();
   const Grid<T>& grid();

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 
+#include "dfloat.cuh"
 #include "mesh.h"
 
 namespace qcad {
@@ -287,6 +288,8 @@ template void build_grid<float>(GridDev<float>&, const GridTables&, const std::v
                                 const std::vector<double>&, const std::vector<double>&, cudaStream_t);
 template void build_grid<double>(GridDev<double>&, const GridTables&, const std::vector<double>&,
                                  const std::vector<double>&, const std::vector<double>&, cudaStream_t);
+template void build_grid<dfl>(GridDev<dfl>&, const GridTables&, const std::vector<double>&,
+                              const std::vector<double>&, const std::vector<double>&, cudaStream_t);
 
 // Faces (fi, fj) of a node plane whose four corners lie in the closed rectangle: fi in [i0, i1),
 // fj in [j0, j1) (empty ranges when none).

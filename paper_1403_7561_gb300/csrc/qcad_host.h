@@ -170,6 +170,10 @@ template <class T>
 void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
 template <class T>
 void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+struct dfl;
+// The H and M applies of FP64 vectors in double-float arithmetic on the FP32 pipes (g: the
+// subdomain grid's tables as double-float pairs; a.cV the FP64 coefficients).
+void launch_hm_apply_df(const Grid<dfl>& g, const HmArgs<double>& a, cudaStream_t s);
 
 }  // namespace qcad
 
