@@ -231,7 +231,7 @@ __device__ __forceinline__ void gram_cp(T* smem, const T* gmem, bool valid) {
 
 template <class T>
 __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, const T* A, long long lda,
-                                                   const T* B1, const T* B2, long long ldb, double* part) {
+                                                   const T* B1, const T* B2, long long ldb, double* part, int G) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   T* sh = reinterpret_cast<T*>(sh_raw);      // two stages of GR x W
   const int q = p;
@@ -243,8 +243,12 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
   // padding columns stay zero (the copies write only the real columns)
   for (int t = tid; t < 2 * GR * W; t += nth) sh[t] = T(0);
   __syncthreads();
-  const bool active = tid < ta_n * tb_n;
-  const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
+  // G row groups of nt = ta_n * tb_n output tiles: group g takes the rows g, g + G, ... of each
+  // shared tile, so that small products still occupy the block
+  const int nt = ta_n * tb_n;
+  const bool active = tid < G * nt;
+  const int grp = active ? tid / nt : 0, tt = active ? tid % nt : 0;
+  const int ta = tt / tb_n, tb = tt % tb_n;
   // across tiles: FP64 (double storage) or double-float on the FP32 pipes (float storage, where
   // an FP64 add per output and tile would cost more than the tile's products)
   double acc[16];
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
 #pragma unroll
       for (int s = 0; s < 16; ++s) s16[s] = T(0);
 #pragma unroll 4
-      for (int rr = 0; rr < GR; ++rr) {
+      for (int rr = grp; rr < GR; rr += G) {
         const T* row = st + rr * W;
         T av[4], bv[4];
         gram_ld4(row + 4 * ta, av);
@@ -313,11 +317,21 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
     stage ^= 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  if (!active) return;
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
     for (int s = 0; s < 16; ++s) acc[s] = df_join(acch[s], accl[s]);
   }
+  // the groups' sums in a fixed order (the staging area is free now)
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(sh_raw);  // [G][nt][16]
+  if (active)
+#pragma unroll
+    for (int s = 0; s < 16; ++s) red[((size_t)grp * nt + tt) * 16 + s] = acc[s];
+  __syncthreads();
+  if (!active || grp != 0) return;
+  for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc[s] += red[((size_t)g2 * nt + tt) * 16 + s];
   // slot layout: product 0 (p*q) then product 1
   double* out = part + (size_t)blockIdx.x * p * qt;
 #pragma unroll
@@ -362,7 +376,7 @@ size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 
 // double-float before it is added to the FP64 accumulators.
 __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb2, const double* A, long long lda,
                                                       const double* B1, const double* B2, long long ldb,
-                                                      double* part) {
+                                                      double* part, int G) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   const int q = p;
   const int qt = q * nb2;
@@ -375,8 +389,11 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int t = tid; t < 2 * GR * W; t += nth) sh[t] = 0.0;
   __syncthreads();
-  const bool active = tid < ta_n * tb_n;
-  const int ta = active ? tid / tb_n : 0, tb = active ? tid % tb_n : 0;
+  // G row groups of nt output tiles, as in gram_kernel
+  const int nt = ta_n * tb_n;
+  const bool active = tid < G * nt;
+  const int grp = active ? tid / nt : 0, tt = active ? tid % nt : 0;
+  const int ta = tt / tb_n, tb = tt % tb_n;
   float acch[16], accl[16];  // double-float accumulation across tiles
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
@@ -426,7 +443,7 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
         sl16[s] = 0.0f;
       }
 #pragma unroll 2
-      for (int rr = 0; rr < GR; ++rr) {
+      for (int rr = grp; rr < GR; rr += G) {
         float ah[4], al[4], bh[4], bl[4];
         gram_ld4(fh + rr * W + 4 * ta, ah);
         gram_ld4(fl + rr * W + 4 * ta, al);
@@ -444,10 +461,19 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
     stage ^= 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  if (!active) return;
   double acc[16];
 #pragma unroll
   for (int s = 0; s < 16; ++s) acc[s] = df_join(acch[s], accl[s]);
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(sh_raw);  // [G][nt][16]
+  if (active)
+#pragma unroll
+    for (int s = 0; s < 16; ++s) red[((size_t)grp * nt + tt) * 16 + s] = acc[s];
+  __syncthreads();
+  if (!active || grp != 0) return;
+  for (int g2 = 1; g2 < G; ++g2)
+#pragma unroll
+    for (int s = 0; s < 16; ++s) acc[s] += red[((size_t)g2 * nt + tt) * 16 + s];
   double* out = part + (size_t)blockIdx.x * p * qt;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -478,28 +504,34 @@ void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* 
   (void)q;  // the products of LOBPCG are square: q == p
   const int nb2 = B2 ? 2 : 1;
   const int ta_n = (p + 3) / 4, tb_n = (p * nb2 + 3) / 4;
-  const int nth = std::min(512, std::max(256, ((ta_n * tb_n + 31) / 32) * 32));
+  // row groups (double storage): as many copies of the output tiles as fit 512 threads (at most
+  // 8), so that the double-float products of small blocks occupy the block; with float storage a
+  // tile's products are cheap next to the per-tile accumulation, so one group
+  const int nt = ta_n * tb_n;
+  const int G = sizeof(T) == 8 ? std::max(1, std::min(8, 512 / nt)) : 1;
+  const int nth = std::min(512, std::max(256, ((G * nt + 31) / 32) * 32));
   const long long ntiles = (n + GR - 1) / GR;
   const int nblk = (int)std::max<long long>(1, std::min<long long>(GRAM_MAX_BLOCKS, ntiles));
-  const size_t shm = (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T);
+  const size_t red = (size_t)G * nt * 16 * sizeof(double);  // the groups' sums, after the tiles
+  const size_t shm = std::max(red, (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T));
   static bool attr = false;
   if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
                     cudaSuccess;
   if constexpr (std::is_same<T, double>::value) {
     if (dense_df()) {
       // two double stages plus the hi and lo float tiles
-      const size_t shm_df = shm + (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(float);
+      const size_t shm_df = std::max(red, (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * (sizeof(double) + sizeof(float)));
       static bool attr_df = false;
       if (!attr_df)
         attr_df = cudaFuncSetAttribute(gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
                   cudaSuccess;
-      note_launch(), gram_df_kernel<<<nblk, nth, shm_df, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part);
+      note_launch(), gram_df_kernel<<<nblk, nth, shm_df, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
       const int tot = p * p * nb2;
       note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
       return;
     }
   }
-  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part);
+  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
   const int tot = p * p * nb2;
   note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
 }

@@ -368,9 +368,9 @@ struct LobpcgRun {
     Profiler::Pair pp;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
     if constexpr (sizeof(T) == 8) {
-      // FP64 vectors: H and M in double-float arithmetic on the FP32 pipes (2^-46 relative, far
-      // below the 1e-8 residuals this phase iterates to); QCAD_LOBPCG_NATIVE64 selects FP64 ones
-      if (use_df_apply())
+      // FP64 vectors: H and M in double-float arithmetic on the FP32 pipes while the residuals are
+      // above DF_FLOOR, FP64 applies below it; QCAD_LOBPCG_NATIVE64 selects FP64 ones throughout
+      if (df_ok && use_df_apply())
         launch_hm_apply_df(S->gdf.g, a, s);
       else
         launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
@@ -384,6 +384,16 @@ struct LobpcgRun {
     static const bool df = std::getenv("QCAD_LOBPCG_NATIVE64") == nullptr;
     return df;
   }
+  // The double-float apply carries a 2^-46 relative error per term; the stiffness part of H w
+  // cancels to about (h/L)^2 of its terms for smooth w, so its result is good to about 1e-10
+  // relative. Below DF_FLOOR the phase refreshes H X, M X with FP64 applies and continues with
+  // them, and the final Rayleigh-Ritz step always uses FP64 applies.
+  T* xbest = nullptr;     // copy of X at the best iteration (stall mode), or null
+  bool restored = false;  // run() returned that copy: H X, M X and lam no longer match X
+  int rr_restarts = 0;
+  static constexpr double DF_FLOOR = 1e-9;
+  bool df_ok = true;
+  bool fresh64 = false;  // the run ended right after an FP64 refresh and Rayleigh-Ritz step
   const T* cv();
   const Grid<T>& grid();
 
@@ -491,14 +501,41 @@ struct LobpcgRun {
       if (debug_level() >= 2)
         std::fprintf(stderr, "[qcad] lobpcg %s it %d worst %.3e\n", sizeof(T) == 4 ? "fp32" : "fp64", it,
                      *std::max_element(rel.begin(), rel.begin() + nev));
+      if constexpr (sizeof(T) == 8) {
+        if (df_ok && use_df_apply() &&
+            (conv || *std::max_element(rel.begin(), rel.begin() + nev) < DF_FLOOR)) {
+          // switch to FP64 applies: fresh H X, M X, Rayleigh-Ritz on X, and the residuals again
+          df_ok = false;
+          apply(0);
+          rr_x();
+          haveP = false;
+          residual(lam_d, norms_d);
+          sync();
+          if (converged(tol)) {
+            fresh64 = true;  // X, H X, M X and the eigenvalues are FP64 Rayleigh-Ritz results
+            return true;
+          }
+          continue;
+        }
+      }
       if (conv) return true;
       if (it > maxit) break;
       if (stall > 0) {
+        // the storage precision's floor: stop once the largest residual has not dropped below 0.9
+        // of its best for `stall` iterations, or has grown tenfold past a best below 1e-4 (LOBPCG
+        // started at or near that floor, e.g. from the previous eigenvectors, can drift away from
+        // it); the X of the best iteration is kept and restored
         const double worst = *std::max_element(rel.begin(), rel.begin() + nev);
         if (worst < 0.9 * best) {
           best = worst;
           since = 0;
-        } else if (++since >= stall) {
+          if (xbest != nullptr)
+            CK(cudaMemcpyAsync(xbest, blk(Sx, 0), (size_t)ns * nb * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        } else if (++since >= stall || (worst > 10.0 * best && best < 1e-4)) {
+          if (xbest != nullptr && worst > best) {
+            CK(cudaMemcpyAsync(blk(Sx, 0), xbest, (size_t)ns * nb * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            restored = true;
+          }
           return false;
         }
       }
@@ -573,7 +610,21 @@ struct LobpcgRun {
         Ct.assign((size_t)nuse * nuse, 0.0);
         ok = dense_gen_eig(nuse, GHt.data(), GMt.data(), w.data(), Ct.data());
       }
-      if (!ok) throw Error(QCAD_ERR_NONFINITE, "LOBPCG Rayleigh-Ritz failed");
+      if (!ok && debug_level() >= 2) {
+        std::fprintf(stderr, "[qcad] lobpcg %s Rayleigh-Ritz failed at it %d (basis %d); M-Gram diagonal:",
+                     sizeof(T) == 4 ? "fp32" : "fp64", it, nuse);
+        for (int i = 0; i < nuse; ++i) std::fprintf(stderr, " %.3e", GMt[(size_t)i * nuse + i]);
+        std::fprintf(stderr, "\n");
+      }
+      if (!ok) {
+        // the projected M-Gram matrix lost definiteness (the basis became nearly dependent in the
+        // storage precision): restart the search space from the current X
+        if (++rr_restarts > 10) throw Error(QCAD_ERR_NONFINITE, "LOBPCG Rayleigh-Ritz failed");
+        apply(0);
+        rr_x();
+        haveP = false;
+        continue;
+      }
       // the Ritz vectors in the stored basis: C = T C'
       std::vector<double> C((size_t)nuse * nuse, 0.0);
       for (int j = 0; j < nb; ++j)
@@ -681,6 +732,9 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   // the FP32 phase stops at 3e-6 relative residual, above where single-precision LOBPCG loses
   // the P block's conditioning (near 2e-6 on these devices), or when it stops improving
   const double tol32 = std::max(tol, 3e-6);
+  DevBuf xbest32;
+  xbest32.ensure((size_t)nb * ns * sizeof(float) + 64);
+  A.xbest = xbest32.as<float>();
   A.run(tol32, 3000, lam_d, norms_d, 15);
   const double t_a = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 
@@ -693,9 +747,12 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   B.apply(0);
   B.rr_x();
   bool converged = B.run(tol, 500, lam_d, norms_d);
-  // final Rayleigh-Ritz with fresh FP64 applies
-  B.apply(0);
-  B.rr_x();
+  // final Rayleigh-Ritz with fresh FP64 applies (unless the run just did one)
+  B.df_ok = false;
+  if (!B.fresh64) {
+    B.apply(0);
+    B.rr_x();
+  }
   for (int j = 0; j < nev; ++j) evals[j] = B.lam[j] - S.shift;
   if (evecs) launch_pack(S.sm, nev, B.Sx, ns, evecs, S.ndof, 0, s);
   CK(cudaGetLastError());
