@@ -216,7 +216,8 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
   // sum to 1) and its Jacobian coefficients vanish. A warp whose elements are all flat (or not
   // semiconductor) skips the interpolation and the transposed interpolation.
   if (a.counts == nullptr && a.qd.w == nullptr) {
-    const int zone = semi ? charge_zone(a.P, v) : -2;  // -2: no charge term at all (oxide, padding)
+    // -2: no charge term at all (oxide, padding)
+    const int zone = semi ? charge_zone_key(a.P, double_key((unsigned long long)__double_as_longlong(v))) : -2;
     int zmin = zone, zmax = zone;
 #pragma unroll
     for (int sft = 1; sft < 8; sft <<= 1) {
@@ -226,10 +227,12 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
     const bool eflat = zmin == zmax && zmin != -1;
     if (__all_sync(FULL_MASK, eflat)) {
       if (valid) {
-        const double wdet = g.hx[i] * g.hy[j] * g.hz[k] * 0.125;
         const double th = a.theta ? a.theta[e] : 0.0;
         const double rho = zone >= 0 ? zone_charge(a.P, zone) : 0.0;
-        elR[t] = -a.P.qe * wdet * (rho + th);
+        if (a.wq != nullptr)
+          elR[t] = a.wq[k] * (rho + th);
+        else
+          elR[t] = -a.P.qe * (g.hx[i] * g.hy[j] * g.hz[k] * 0.125) * (rho + th);
         elD[t] = 0.0;
         if (a.c64) a.c64[t] = 0.0;
         if (a.c32) a.c32[t] = 0.0f;

@@ -152,6 +152,17 @@ Phys make_phys_material(const qcad_material& s, const qcad_bias* b) {
   P.phi_a_hi = ca + 45.0 * kT + w;
   P.phi_d_lo = cd - 45.0 * kT - w;
   P.phi_d_hi = cd + P.z_max_d * kT + w;
+  auto key = [](double v) {
+    unsigned long long b;
+    std::memcpy(&b, &v, sizeof(b));
+    return double_key(b);
+  };
+  P.key_n_on = key(P.phi_n_on);
+  P.key_p_on = key(P.phi_p_on);
+  P.key_a_lo = key(P.phi_a_lo);
+  P.key_a_hi = key(P.phi_a_hi);
+  P.key_d_lo = key(P.phi_d_lo);
+  P.key_d_hi = key(P.phi_d_hi);
   return P;
 }
 
@@ -537,6 +548,17 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
     upload<double>(m->d_zn, m->zc, s);
     m->d_layer_semi.ensure(m->nz + 16);
     CK(cudaMemcpyAsync(m->d_layer_semi.p, m->layer_semi.data(), m->nz, cudaMemcpyHostToDevice, s));
+    // -(q/eps0) w|J| of one Gauss point of a layer-k element (uniform x and y spacing, the
+    // tensor-product grid of every device): the load factor of the residual's constant-charge
+    // elements
+    {
+      std::vector<double> wq(m->nz);
+      const double hxy = (dev->Lx / m->nx) * (dev->Ly / m->ny);
+      for (int k = 0; k < m->nz; ++k) wq[k] = -host_qe() * hxy * m->hzv[k] * 0.125;
+      m->d_wq.ensure(m->nz * sizeof(double) + 16);
+      CK(cudaMemcpyAsync(m->d_wq.p, wq.data(), m->nz * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
     m->d_gate_top.ensure(m->gate_top.size() + 16);
     CK(cudaMemcpyAsync(m->d_gate_top.p, m->gate_top.data(), m->gate_top.size(), cudaMemcpyHostToDevice, s));
     m->d_dir_top.ensure(dir_top.size() + 16);

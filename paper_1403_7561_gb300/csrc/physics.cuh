@@ -144,6 +144,27 @@ __device__ __forceinline__ int charge_zone(const Phys& P, double phi) {
   return z;
 }
 
+// charge_zone of a potential given as its double_key (integer comparisons only).
+__device__ __forceinline__ int charge_zone_key(const Phys& P, unsigned long long key) {
+  if (!(key < P.key_n_on && key > P.key_p_on)) return -1;
+  int z = 0;
+  if (P.incomplete) {
+    if (P.NA != 0.0) {
+      if (key > P.key_a_hi)
+        z += 1;
+      else if (!(key < P.key_a_lo))
+        return -1;
+    }
+    if (P.ND != 0.0) {
+      if (key < P.key_d_lo)
+        z += 2;
+      else if (!(key > P.key_d_hi))
+        return -1;
+    }
+  }
+  return z;
+}
+
 // The charge of a constant-charge zone (the value charge_resid returns there).
 __device__ __forceinline__ double zone_charge(const Phys& P, int zone) {
   if (!P.incomplete) return P.ND - P.NA;

@@ -122,7 +122,16 @@ struct Phys {
   // phi <= phi_p_on; the acceptor (donor) ionization is a constant (0 or 1) outside
   // [phi_a_lo, phi_a_hi] ([phi_d_lo, phi_d_hi]), where its argument is beyond the cutoff or below -45
   double phi_n_on, phi_p_on, phi_a_lo, phi_a_hi, phi_d_lo, phi_d_hi;
+  // the same potentials as order-preserving integer keys (double_key), compared on the integer
+  // pipes instead of the 2-lane FP64 pipe
+  unsigned long long key_n_on, key_p_on, key_a_lo, key_a_hi, key_d_lo, key_d_hi;
 };
+
+// An unsigned integer key of a double that orders like the doubles (non-NaN): the sign bit set
+// for non-negative values, all bits flipped for negative ones.
+__host__ __device__ __forceinline__ unsigned long long double_key(unsigned long long bits) {
+  return (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull);
+}
 
 struct DotBoxes {
   int n;
