@@ -227,12 +227,14 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
     const bool eflat = zmin == zmax && zmin != -1;
     if (__all_sync(FULL_MASK, eflat)) {
       if (valid) {
-        const double th = a.theta ? a.theta[e] : 0.0;
-        const double rho = zone >= 0 ? zone_charge(a.P, zone) : 0.0;
-        if (a.wq != nullptr)
-          elR[t] = a.wq[k] * (rho + th);
-        else
-          elR[t] = -a.P.qe * (g.hx[i] * g.hy[j] * g.hz[k] * 0.125) * (rho + th);
+        if (a.wq != nullptr && a.theta == nullptr) {
+          elR[t] = zone >= 0 ? a.wq[8 * k + (a.P.incomplete ? zone : WQ_ZONE_COMPLETE)] : 0.0;
+        } else {
+          const double th = a.theta ? a.theta[e] : 0.0;
+          const double rho = zone >= 0 ? zone_charge(a.P, zone) : 0.0;
+          const double w = a.wq != nullptr ? a.wq[8 * k + WQ_WEIGHT] : -a.P.qe * (g.hx[i] * g.hy[j] * g.hz[k] * 0.125);
+          elR[t] = w * (rho + th);
+        }
         elD[t] = 0.0;
         if (a.c64) a.c64[t] = 0.0;
         if (a.c32) a.c32[t] = 0.0f;
@@ -344,7 +346,9 @@ struct ResidualGatherOp {
     R[n] = Rn;
     if (diag) diag[n] = dg;
     if (dinv64) dinv64[n] = 1.0 / dg;
-    if (dinv32) dinv32[n] = (float)(1.0 / dg);
+    // the FP32 Jacobi scale as an FP32 reciprocal (an FP64 division is a long sequence on the
+    // FP64 pipe; the rounded diagonal's reciprocal is within an FP32 ulp of the rounded inverse)
+    if (dinv32) dinv32[n] = __frcp_rn(__double2float_rn(dg));
     if (b64) b64[n] = -Rn;
     if (b32) b32[n] = (float)(-Rn);
     acc_r2 += Rn * Rn;
@@ -376,7 +380,9 @@ struct SurfaceGatherOp : ResidualGatherOp {
     R[n] = Rn;
     if (diag) diag[n] = dg;
     if (dinv64) dinv64[n] = 1.0 / dg;
-    if (dinv32) dinv32[n] = (float)(1.0 / dg);
+    // the FP32 Jacobi scale as an FP32 reciprocal (an FP64 division is a long sequence on the
+    // FP64 pipe; the rounded diagonal's reciprocal is within an FP32 ulp of the rounded inverse)
+    if (dinv32) dinv32[n] = __frcp_rn(__double2float_rn(dg));
     if (b64) b64[n] = -Rn;
     if (b32) b32[n] = (float)(-Rn);
     acc_r2 += Rn * Rn;

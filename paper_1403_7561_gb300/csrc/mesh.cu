@@ -8,6 +8,7 @@
 
 #include "dfloat.cuh"
 #include "mesh.h"
+#include "physics.cuh"
 
 namespace qcad {
 
@@ -132,6 +133,8 @@ Phys make_phys_material(const qcad_material& s, const qcad_bias* b) {
   P.qe = host_qe();
   P.statistics = b->statistics;
   P.incomplete = b->incomplete_ionization;
+  P.na_on = s.N_A != 0.0;
+  P.nd_on = s.N_D != 0.0;
   // below-resolution cutoffs (physics.cuh): N F(eta) < floor for eta < ln(floor / N) (F <= e^eta),
   // N s < floor for s ~ e^-z / g below floor / N; never tighter than the count cutoffs (eta -150,
   // z 746)
@@ -548,15 +551,29 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
     upload<double>(m->d_zn, m->zc, s);
     m->d_layer_semi.ensure(m->nz + 16);
     CK(cudaMemcpyAsync(m->d_layer_semi.p, m->layer_semi.data(), m->nz, cudaMemcpyHostToDevice, s));
-    // -(q/eps0) w|J| of one Gauss point of a layer-k element (uniform x and y spacing, the
-    // tensor-product grid of every device): the load factor of the residual's constant-charge
-    // elements
+    // the residual's per-layer load table: -(q/eps0) w|J| of one Gauss point of a layer-k element
+    // (uniform x and y spacing, the tensor-product grid of every device) and its products with
+    // the semiconductor's constant charges (slots in physics.cuh)
     {
-      std::vector<double> wq(m->nz);
+      Phys Pz{};
+      if (m->semi >= 0) {
+        Pz.NA = m->mats[m->semi].N_A;
+        Pz.ND = m->mats[m->semi].N_D;
+        Pz.na_on = Pz.NA != 0.0;
+        Pz.nd_on = Pz.ND != 0.0;
+      }
+      std::vector<double> wq(8 * (size_t)m->nz, 0.0);
       const double hxy = (dev->Lx / m->nx) * (dev->Ly / m->ny);
-      for (int k = 0; k < m->nz; ++k) wq[k] = -host_qe() * hxy * m->hzv[k] * 0.125;
-      m->d_wq.ensure(m->nz * sizeof(double) + 16);
-      CK(cudaMemcpyAsync(m->d_wq.p, wq.data(), m->nz * sizeof(double), cudaMemcpyHostToDevice, s));
+      for (int k = 0; k < m->nz; ++k) {
+        const double w = -host_qe() * hxy * m->hzv[k] * 0.125;
+        Pz.incomplete = 1;
+        for (int z = 0; z < 4; ++z) wq[8 * k + z] = w * zone_charge(Pz, z);
+        Pz.incomplete = 0;
+        wq[8 * k + WQ_ZONE_COMPLETE] = w * zone_charge(Pz, 0);
+        wq[8 * k + WQ_WEIGHT] = w;
+      }
+      m->d_wq.ensure(wq.size() * sizeof(double) + 16);
+      CK(cudaMemcpyAsync(m->d_wq.p, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice, s));
       CK(cudaStreamSynchronize(s));
     }
     m->d_gate_top.ensure(m->gate_top.size() + 16);

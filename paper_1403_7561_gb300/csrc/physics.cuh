@@ -102,13 +102,13 @@ __device__ __forceinline__ Charge charge_at(const Phys& P, double phi, bool resi
   }
   double NDp = P.ND, dND = 0.0, NAm = P.NA, dNA = 0.0;
   if (P.incomplete) {
-    if (P.ND != 0.0) {
+    if (P.nd_on) {
       double s, oms;
       sigmoid_pair((P.EF + P.Ed - P.phi_ref + P.chi + phi) * ik, P.gD, s, oms, resid ? P.z_max_d : 746.0);
       NDp = P.ND * s;
       dND = -P.ND * s * oms * ik;
     }
-    if (P.NA != 0.0) {
+    if (P.na_on) {
       double s, oms;
       sigmoid_pair((-P.EF + P.Ea + P.phi_ref - P.chi - P.Eg - phi) * ik, P.gA, s, oms, resid ? P.z_max_a : 746.0);
       NAm = P.NA * s;
@@ -128,13 +128,13 @@ __device__ __forceinline__ int charge_zone(const Phys& P, double phi) {
   if (!(phi < P.phi_n_on && phi > P.phi_p_on)) return -1;
   int z = 0;
   if (P.incomplete) {
-    if (P.NA != 0.0) {
+    if (P.na_on) {
       if (phi > P.phi_a_hi)
         z += 1;
       else if (!(phi < P.phi_a_lo))
         return -1;
     }
-    if (P.ND != 0.0) {
+    if (P.nd_on) {
       if (phi < P.phi_d_lo)
         z += 2;
       else if (!(phi > P.phi_d_hi))
@@ -149,13 +149,13 @@ __device__ __forceinline__ int charge_zone_key(const Phys& P, unsigned long long
   if (!(key < P.key_n_on && key > P.key_p_on)) return -1;
   int z = 0;
   if (P.incomplete) {
-    if (P.NA != 0.0) {
+    if (P.na_on) {
       if (key > P.key_a_hi)
         z += 1;
       else if (!(key < P.key_a_lo))
         return -1;
     }
-    if (P.ND != 0.0) {
+    if (P.nd_on) {
       if (key < P.key_d_lo)
         z += 2;
       else if (!(key > P.key_d_hi))
@@ -165,14 +165,22 @@ __device__ __forceinline__ int charge_zone_key(const Phys& P, unsigned long long
   return z;
 }
 
-// The charge of a constant-charge zone (the value charge_resid returns there).
-__device__ __forceinline__ double zone_charge(const Phys& P, int zone) {
+// The charge of a constant-charge zone (the value charge_resid returns there); host and device
+// evaluate it in the same order.
+__host__ __device__ __forceinline__ double zone_charge(const Phys& P, int zone) {
   if (!P.incomplete) return P.ND - P.NA;
   double rho = 0.0;
-  if (P.NA != 0.0) rho -= (zone & 1) ? P.NA : 0.0;
-  if (P.ND != 0.0) rho += (zone & 2) ? P.ND : 0.0;
+  if (P.na_on) rho -= (zone & 1) ? P.NA : 0.0;
+  if (P.nd_on) rho += (zone & 2) ? P.ND : 0.0;
   return rho;
 }
+
+// Slots of the residual's per-layer load table ([nz][8], ResidualArgs::wq): w_k = -(q/eps0) w|J|
+// of one Gauss point of a layer-k element, and w_k times each constant charge, so that an element
+// in a constant-charge zone takes its load from the table without FP64 arithmetic.
+constexpr int WQ_ZONE_COMPLETE = 4;  // w_k (N_D - N_A): complete ionization
+constexpr int WQ_WEIGHT = 5;         // w_k
+// zones 0..3 (incomplete ionization): w_k zone_charge(zone)
 
 // The residual's charge outside the dots: where phi lies outside every cutoff band (n and p below
 // resolution, each dopant fully ionized or below resolution) the charge is a constant and its
@@ -183,11 +191,11 @@ __device__ __forceinline__ Charge charge_resid(const Phys& P, double phi) {
   bool flat = no_n && no_p;
   double rho = 0.0;
   if (P.incomplete) {
-    if (P.NA != 0.0) {
+    if (P.na_on) {
       flat = flat && (phi < P.phi_a_lo || phi > P.phi_a_hi);
       rho -= phi > P.phi_a_hi ? P.NA : 0.0;  // z_a < -45: fully ionized; above the cutoff: none
     }
-    if (P.ND != 0.0) {
+    if (P.nd_on) {
       flat = flat && (phi < P.phi_d_lo || phi > P.phi_d_hi);
       rho += phi < P.phi_d_lo ? P.ND : 0.0;
     }

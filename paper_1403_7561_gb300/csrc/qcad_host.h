@@ -69,7 +69,7 @@ struct ResidualArgs {
   int linear;
   QuantumDensity qd;         // quantum density in the quantum region (inactive: qd.w null)
   const double* bsurf;       // [n_nodes] constant surface load b (R -= b; two-pass residual) or null
-  const double* wq;          // [nz] -(q/eps0) w|J| per Gauss point of each element layer, or null
+  const double* wq;          // [nz][8] per-layer load table of constant-charge elements (physics.cuh) or null
 };
 
 template <class T>

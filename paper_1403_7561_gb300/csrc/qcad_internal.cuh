@@ -114,6 +114,7 @@ struct Phys {
   double qe;              // q/eps0, V*nm
   int statistics;         // 0 MB, 1 FD
   int incomplete;         // 1: Eq. FinalIonization
+  int na_on, nd_on;       // NA != 0, ND != 0 (tested on the integer pipes)
   // Below-resolution cutoffs of the residual outside the dots (densities under RHO_RESID_FLOOR,
   // physics.cuh): n and p are not evaluated for eta below eta_min_n / eta_min_p, and the ionized
   // acceptor (donor) density is taken as zero for an ionization argument above z_max_a (z_max_d).
