@@ -491,21 +491,22 @@ void launch_dot_count(const Grid<double>& g, const double* phi, const unsigned c
 }
 
 // ---------------------------------------------------------------------------
-// dN_d/dphi nodal vector of one dot, in two passes.
+// dN_d/dphi nodal vector of one dot, in two passes over the dot's element box only (every other
+// element has no count, and its nodes get zero).
 
-// Pass 1 of the count gradient: wdet dn/dphi at the quadrature points of dot d's elements,
-// mapped to the element corners by the transposed interpolation (lane butterflies as in
-// residual_qp_kernel); [8 e + corner].
+// Pass 1: wdet dn/dphi at the quadrature points of the box's elements that belong to dot d (the
+// first dot holding the element's centroid), mapped to the element corners by the transposed
+// interpolation (lane butterflies as in residual_qp_kernel); [8 be + corner], be the element's
+// index inside the box (x fastest).
 __global__ void __launch_bounds__(256) count_grad_qp_kernel(const __grid_constant__ Grid<double> g,
-                                                            const __grid_constant__ ResidualArgs a, int d,
-                                                            double* el) {
-  const long long ne = (long long)g.nx * g.ny * g.nz;
+                                                            const __grid_constant__ ResidualArgs a, int d, int i0,
+                                                            int j0, int k0, int bx, int by, int bz, double* el) {
+  const long long ne = (long long)bx * by * bz;
   const long long t = blockIdx.x * 256LL + threadIdx.x;
   const bool valid = t < 8 * ne;
-  const int e = valid ? (int)(t >> 3) : 0;
+  const long long be = valid ? (t >> 3) : 0;
   const int l = threadIdx.x & 7;
-  const int i = e % g.nx, r = e / g.nx;
-  const int j = r % g.ny, k = r / g.ny;
+  const int i = i0 + (int)(be % bx), j = j0 + (int)((be / bx) % by), k = k0 + (int)(be / ((long long)bx * by));
   const bool in = valid && a.layer_semi[k] && dot_of_element(a, i, j, k) == d;
   const double A = GaussConst<double>::a(), B = GaussConst<double>::b();
   double v = 0.0;
@@ -522,29 +523,33 @@ __global__ void __launch_bounds__(256) count_grad_qp_kernel(const __grid_constan
   if (valid) el[t] = f;
 }
 
-// Pass 2: each node sums its elements' corner values.
-struct CornerGatherOp {
-  static constexpr int NF = 1;
-  static constexpr bool STIFF = false;
-  using ED = char;
-  const double* el;
-  double* out;
-  __device__ bool skip() const { return false; }
-  __device__ void set_vec(int) {}
-  __device__ double load(const Grid<double>&, int, bool, int, int, int) const { return 0.0; }
-  __device__ char edata(const Grid<double>&, int, int, int) const { return 0; }
-  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double*, char, double (*o)[8], bool) const {
-    load_c8<double>(el, elem_index(g, i, j, k), o[0]);
+// Pass 2: each node of the box's node range sums the corner values of its (up to eight) box
+// elements: element (li - cx, lj - cy, lk - cz) holds the node as its corner cx + 2 cy + 4 cz.
+__global__ void __launch_bounds__(256) count_grad_gather_kernel(const __grid_constant__ Grid<double> g,
+                                                                const double* el, int i0, int j0, int k0, int bx,
+                                                                int by, int bz, double* out) {
+  const long long nn = (long long)(bx + 1) * (by + 1) * (bz + 1);
+  const long long t = blockIdx.x * 256LL + threadIdx.x;
+  if (t >= nn) return;
+  const int li = (int)(t % (bx + 1)), lj = (int)((t / (bx + 1)) % (by + 1));
+  const int lk = (int)(t / ((long long)(bx + 1) * (by + 1)));
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ei = li - (c & 1), ej = lj - ((c >> 1) & 1), ek = lk - (c >> 2);
+    if (ei >= 0 && ei < bx && ej >= 0 && ej < by && ek >= 0 && ek < bz)
+      s += el[8 * (ei + (long long)bx * (ej + (long long)by * ek)) + c];
   }
-  __device__ void node(const Grid<double>&, int n, int, int, int, double, double, const double* mass) {
-    out[n] = mass[0];
-  }
-  __device__ void finish() {}
-};
+  out[(i0 + li) + (long long)g.nxn * ((j0 + lj) + (long long)g.nyn * (k0 + lk))] = s;
+}
 
 void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
                            const double* xn, const double* yn, const double* zn, const Phys& P,
-                           const DotBoxes& dots, int d, double* out, double* el, LaunchCfg cfg, cudaStream_t s) {
+                           const DotBoxes& dots, int d, const int* box, double* out, double* el, cudaStream_t s) {
+  if (box == nullptr) return;
+  const int bx = box[1] - box[0], by = box[3] - box[2], bz = box[5] - box[4];
+  const long long ne = (long long)bx * by * bz;
+  if (ne <= 0) return;
   ResidualArgs a{};
   a.phi = phi;
   a.layer_semi = layer_semi;
@@ -553,14 +558,11 @@ void launch_count_gradient(const Grid<double>& g, const double* phi, const unsig
   a.zn = zn;
   a.P = P;
   a.dots = dots;
-  const long long ne = (long long)g.nx * g.ny * g.nz;
-  note_launch(), count_grad_qp_kernel<<<(int)((8 * ne + 255) / 256), 256, 0, s>>>(g, a, d, el);
-  CornerGatherOp op = {};
-  op.el = el;
-  op.out = out;
-  LaunchCfg c = cfg;
-  if (c.by == 32) c.by = 16;
-  run_march<double>(g, op, c, s);
+  note_launch(), count_grad_qp_kernel<<<(int)((8 * ne + 255) / 256), 256, 0, s>>>(g, a, d, box[0], box[2], box[4],
+                                                                                  bx, by, bz, el);
+  const long long nn = (long long)(bx + 1) * (by + 1) * (bz + 1);
+  note_launch(), count_grad_gather_kernel<<<(int)((nn + 255) / 256), 256, 0, s>>>(g, el, box[0], box[2], box[4], bx,
+                                                                                  by, bz, out);
 }
 
 

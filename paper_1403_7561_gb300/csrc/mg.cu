@@ -42,6 +42,13 @@ struct MgHier {
   bool ok = false;
   bool alloc[2] = {false, false};  // the precision's operators and vectors exist
   long long lin_ver[2] = {-1, -1}; // linearization the operators were built for
+  // The stiffness-only parts, built once per precision (the stiffness and the Dirichlet masks do
+  // not change between linearizations): level-1 element matrices P^T K P (64 per coarse element)
+  // and the level-0 Gershgorin row sums sum_j |K_ij| (per node). Where every coefficient c of the
+  // elements involved is zero (no charge response) the operator is the stiffness alone, and the
+  // setup copies these instead of rebuilding them.
+  DevBuf S1[2], ra0[2];
+  bool stiff_ok[2] = {false, false};
 };
 
 MgHier* hier(qcad_mesh_s* m) { return static_cast<MgHier*>(m->mg.get()); }
@@ -255,20 +262,49 @@ __device__ __forceinline__ void mg_fine_row(const Grid<T>& g, int i, int j, int 
   }
 }
 
-// Level-1 element matrices from the mesh operator (coefficients c, 8 per element).
+// All eight coefficients of element e zero (no charge response).
 template <class T>
+__device__ __forceinline__ bool mg_coef_zero(const T* __restrict__ coef, long long e) {
+  T c[8];
+  load_c8<T>(coef, e, c);
+  bool z = true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) z = z && c[q] == T(0);
+  return z;
+}
+
+// Level-1 element matrices from the mesh operator (coefficients c, 8 per element). STIFF: the
+// stiffness-only matrices (c taken as zero, coef unused), stored once as S1. Otherwise a coarse
+// element whose children all have zero coefficients copies its S1 matrix (the same values the
+// rebuild would give), and the others are rebuilt.
+template <class T, bool STIFF>
 __global__ void __launch_bounds__(128) mg_galerkin0_kernel(const Grid<T> g, const T* __restrict__ coef,
-                                                           const MgLevelDev<T> F, const MgLevelDev<T> Cl, T* Aout) {
+                                                           const T* __restrict__ S1, const MgLevelDev<T> F,
+                                                           const MgLevelDev<T> Cl, T* Aout) {
   const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long ne = (long long)Cl.nx * Cl.ny * Cl.nz;
   if (E >= ne) return;
   const int I = (int)(E % Cl.nx);
   const long long r = E / Cl.nx;
   const int J = (int)(r % Cl.ny), K = (int)(r / Cl.ny);
+  const MgChild cx = F.ch[0][I], cy = F.ch[1][J], cz = F.ch[2][K];
+  if (!STIFF) {
+    bool zero = true;
+    for (int k = cz.first; k < cz.first + cz.count; ++k)
+      for (int j = cy.first; j < cy.first + cy.count; ++j)
+        for (int i = cx.first; i < cx.first + cx.count; ++i)
+          zero = zero && mg_coef_zero<T>(coef, i + (long long)g.nx * (j + (long long)g.ny * k));
+    if (zero) {
+      const uint4* src = reinterpret_cast<const uint4*>(S1 + 64 * E);
+      uint4* dst = reinterpret_cast<uint4*>(Aout + 64 * E);
+#pragma unroll
+      for (int q = 0; q < (int)(64 * sizeof(T) / 16); ++q) dst[q] = __ldg(src + q);
+      return;
+    }
+  }
   T AE[64];
 #pragma unroll
   for (int q = 0; q < 64; ++q) AE[q] = T(0);
-  const MgChild cx = F.ch[0][I], cy = F.ch[1][J], cz = F.ch[2][K];
   for (int k = cz.first; k < cz.first + cz.count; ++k)
     for (int j = cy.first; j < cy.first + cy.count; ++j)
       for (int i = cx.first; i < cx.first + cx.count; ++i) {
@@ -277,7 +313,12 @@ __global__ void __launch_bounds__(128) mg_galerkin0_kernel(const Grid<T> g, cons
         const T py[4] = {(T)ey.p00, (T)ey.p01, (T)ey.p10, (T)ey.p11};
         const T pz[4] = {(T)ez.p00, (T)ez.p01, (T)ez.p10, (T)ez.p11};
         T c[8];
-        load_c8<T>(coef, i + (long long)g.nx * (j + (long long)g.ny * k), c);
+        if (STIFF) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) c[q] = T(0);
+        } else {
+          load_c8<T>(coef, i + (long long)g.nx * (j + (long long)g.ny * k), c);
+        }
         bool dm[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -404,10 +445,12 @@ __global__ void mg_diag_kernel(const MgLevelDev<T> L, T* dinv, T* par_l) {
 }
 
 // Gershgorin bound of D^-1 J on the mesh (rows of the element matrices rebuilt from the
-// coefficients; Dirichlet rows are identity rows there, ratio 1).
-template <class T>
+// coefficients; Dirichlet rows are identity rows there, ratio 1). STIFF: the stiffness-only row
+// sums sum_j |K_ij| into ra0 (c taken as zero). Otherwise a node whose adjacent elements all have
+// zero coefficients takes its row sum from ra0 (the value the rebuild would give).
+template <class T, bool STIFF>
 __global__ void mg_gersh0_kernel(const Grid<T> g, const T* __restrict__ coef, const MgLevelDev<T> F,
-                                 const T* dinv0, T* par0) {
+                                 const T* dinv0, T* ra0, T* par0) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nn = (long long)F.nxn * F.nyn * F.nzn;
   T ratio = T(0);
@@ -416,28 +459,49 @@ __global__ void mg_gersh0_kernel(const Grid<T> g, const T* __restrict__ coef, co
     node_ijk(F, n, i, j, k);
     if (F.mask[n]) {
       ratio = T(1);
+      if (STIFF) ra0[n] = T(0);
     } else {
-      T ra = T(0);
-      for (int e = 0; e < 8; ++e) {
-        const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
-        const int I = i - 1 + ex, J = j - 1 + ey, K = k - 1 + ez;
-        if (I < 0 || J < 0 || K < 0 || I >= F.nx || J >= F.ny || K >= F.nz) continue;
-        const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-        T c[8];
-        load_c8<T>(coef, I + (long long)g.nx * (J + (long long)g.ny * K), c);
-        bool dm[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          dm[q] = F.mask[(I + (q & 1)) + (long long)F.nxn * ((J + ((q >> 1) & 1)) + (long long)F.nyn * (K + (q >> 2)))] != 0;
-        T row[8];
-        mg_fine_row<T>(g, I, J, K, c, dm, a, row);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) ra += fabs(row[q]);
+      bool zero = true;
+      if (!STIFF) {
+        for (int e = 0; e < 8; ++e) {
+          const int I = i - 1 + (e & 1), J = j - 1 + ((e >> 1) & 1), K = k - 1 + (e >> 2);
+          if (I < 0 || J < 0 || K < 0 || I >= F.nx || J >= F.ny || K >= F.nz) continue;
+          zero = zero && mg_coef_zero<T>(coef, I + (long long)g.nx * (J + (long long)g.ny * K));
+        }
       }
-      ratio = ra * dinv0[n];
+      T ra = T(0);
+      if (!STIFF && zero) {
+        ra = ra0[n];
+      } else {
+        for (int e = 0; e < 8; ++e) {
+          const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+          const int I = i - 1 + ex, J = j - 1 + ey, K = k - 1 + ez;
+          if (I < 0 || J < 0 || K < 0 || I >= F.nx || J >= F.ny || K >= F.nz) continue;
+          const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+          T c[8];
+          if (STIFF) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = T(0);
+          } else {
+            load_c8<T>(coef, I + (long long)g.nx * (J + (long long)g.ny * K), c);
+          }
+          bool dm[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            dm[q] = F.mask[(I + (q & 1)) + (long long)F.nxn * ((J + ((q >> 1) & 1)) + (long long)F.nyn * (K + (q >> 2)))] != 0;
+          T row[8];
+          mg_fine_row<T>(g, I, J, K, c, dm, a, row);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) ra += fabs(row[q]);
+        }
+      }
+      if (STIFF)
+        ra0[n] = ra;
+      else
+        ratio = ra * dinv0[n];
     }
   }
-  mg_block_max<T>(ratio, par0);
+  if (!STIFF) mg_block_max<T>(ratio, par0);
 }
 
 // ---------------------------------------------------------------------------
@@ -798,12 +862,24 @@ void mg_setup(qcad_mesh_s* m, cudaStream_t s, bool force) {
   std::deque<MgLevel>& L = H->L;
   const PcgBufs<T>& k = mesh_bufs<T>(m);
   T* par = H->par[p].template as<T>();
+  if (!H->stiff_ok[p]) {
+    H->S1[p].ensure((size_t)64 * L[1].ne * sizeof(T) + 64);
+    H->ra0[p].ensure((size_t)L[0].n * sizeof(T) + 64);
+    mg_gersh0_kernel<T, true><<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(
+        mesh_grid<T>(m), nullptr, level_dev<T>(L[0]), k.dinv.template as<T>(), H->ra0[p].template as<T>(), nullptr);
+    mg_galerkin0_kernel<T, true><<<blocks_for(L[1].ne, 128), 128, 0, s>>>(
+        mesh_grid<T>(m), nullptr, nullptr, level_dev<T>(L[0]), level_dev<T>(L[1]), H->S1[p].template as<T>());
+    note_launch(2);
+    CK(cudaGetLastError());
+    H->stiff_ok[p] = true;
+  }
   CK(cudaMemsetAsync(par, 0, MG_MAX_LEVELS * sizeof(T), s));
-  mg_gersh0_kernel<T><<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(mesh_grid<T>(m), k.c.template as<T>(),
-                                                                level_dev<T>(L[0]), k.dinv.template as<T>(), par);
-  mg_galerkin0_kernel<T><<<blocks_for(L[1].ne, 128), 128, 0, s>>>(mesh_grid<T>(m), k.c.template as<T>(),
-                                                                  level_dev<T>(L[0]), level_dev<T>(L[1]),
-                                                                  L[1].A[p].template as<T>());
+  mg_gersh0_kernel<T, false><<<blocks_for(L[0].n), MG_THREADS, 0, s>>>(
+      mesh_grid<T>(m), k.c.template as<T>(), level_dev<T>(L[0]), k.dinv.template as<T>(), H->ra0[p].template as<T>(),
+      par);
+  mg_galerkin0_kernel<T, false><<<blocks_for(L[1].ne, 128), 128, 0, s>>>(
+      mesh_grid<T>(m), k.c.template as<T>(), H->S1[p].template as<T>(), level_dev<T>(L[0]), level_dev<T>(L[1]),
+      L[1].A[p].template as<T>());
   for (size_t l = 1; l < L.size(); ++l) {
     if (l > 1)
       mg_galerkin_kernel<T><<<blocks_for(L[l].ne, 128), 128, 0, s>>>(level_dev<T>(L[l - 1]), level_dev<T>(L[l]),

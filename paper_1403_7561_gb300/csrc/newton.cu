@@ -1161,10 +1161,14 @@ static void adjoint_prepare(AdjWork& A, qcad_mesh_s* m, const qcad_bias* b, cons
   A.zero_v = acc + 2 * nd * ng;               // one zero per gate, for masking Dirichlet rows
   CK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), s));
   m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
-  for (int d = 0; d < nd; ++d)
+  for (int d = 0; d < nd; ++d) {
+    int box[6];
+    const bool have = dot_element_box(m, d, box);
+    CK(cudaMemsetAsync(G + (size_t)d * n, 0, n * sizeof(double), s));
     launch_count_gradient(m->g64.g, phi, m->d_layer_semi.as<unsigned char>(), m->d_xn.as<double>(),
-                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, G + (size_t)d * n,
-                          m->el_res.as<double>(), m->cfg_res, s);
+                          m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, have ? box : nullptr,
+                          G + (size_t)d * n, m->el_res.as<double>(), s);
+  }
   // gate lifts e_g: their raw J e_g (shared by every dot) and dN_d/dphi . e_g before masking
   for (int gi = 0; gi < ng; ++gi) {
     CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));

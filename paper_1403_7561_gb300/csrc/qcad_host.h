@@ -143,11 +143,13 @@ void launch_set_dirichlet(long long nxn, long long nyn, long long nzn, int botto
 void launch_d2f(long long n, const double* a, float* b, cudaStream_t s);
 void launch_f2d(long long n, const float* a, double* b, cudaStream_t s);
 
-// dN_d/dphi as a nodal vector for dot d: sum over dot elements of w|J| n'(phi_q) N_a(q).
+// dN_d/dphi as a nodal vector for dot d: sum over dot elements of w|J| n'(phi_q) N_a(q), written
+// at the nodes of the dot's element box (the caller zeroes out beforehand). box: the
+// dot's element box {i0, i1, j0, j1, k0, k1} (elements i0 <= i < i1, ...) or null when it is empty;
+// el: scratch of 8 doubles per box element.
 void launch_count_gradient(const Grid<double>& g, const double* phi, const unsigned char* layer_semi,
                            const double* xn, const double* yn, const double* zn, const Phys& P,
-                           const DotBoxes& dots, int d, double* out, double* el /* 8 per element */,
-                           LaunchCfg cfg, cudaStream_t s);
+                           const DotBoxes& dots, int d, const int* box, double* out, double* el, cudaStream_t s);
 
 // theta-gradient of N_d: out[e] = qe * (|e|/8) * sum of lam over the 8 corners of e (lam is
 // zero on Dirichlet nodes); |e|/8 = int_e N_a exactly on a box.
