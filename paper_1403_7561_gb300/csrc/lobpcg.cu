@@ -694,7 +694,15 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   const double t_setup = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (S.ndof < 3 * (nev + 4)) throw Error(QCAD_ERR_INVALID_ARG, "subdomain too small for nev");
   cudaStream_t s = io.s;
-  const int nb = (int)std::min<long long>(nev + std::max(2, nev / 4), S.ndof / 3);
+  // block size: nev plus guard vectors (QCAD_LOBPCG_GUARD overrides the count). The lowest levels
+  // of a double dot cluster within a few meV, so convergence is set by the gap to the first level
+  // outside the block: with a multigrid V-cycle of K + M_{V - min V} as the preconditioner the
+  // worst residual fell by the same factor per iteration (about 0.7) as with this polynomial, and
+  // more guard vectors cost more per iteration than they save
+  const char* ge = std::getenv("QCAD_LOBPCG_GUARD");
+  const int guard = ge ? std::max(1, std::atoi(ge)) : std::max(2, nev / 4);
+  // (at most 20 columns: the [X W P] kernels take up to 64 columns and the host eigensolver 60)
+  const int nb = (int)std::min<long long>(std::min(nev + guard, 20), S.ndof / 3);
   const long long ns = S.ns;
   DevBuf lam_d, norms_d, dinv32;
   lam_d.ensure(nb * sizeof(double) + 64);
