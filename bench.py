@@ -26,6 +26,8 @@ line reports:
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Profiling workloads (ncu launch lists and single-kernel captures):
   python bench.py --profile step|solve|apply|eigs|batch [--workload NAME] [--launch v,r,z]
+Recording an ncu metrics capture (CSV) of a kernel class as the line's traffic and flop counters:
+  python bench.py --ncu-counters CSV --kernel-class residual|apply32 --workload NAME --launch v,r,z --per N
 Multi-GPU: launched by torch.distributed.run; ranks solve independent
 replicas of the device (weak scaling, no collective on the data path).
 """
@@ -80,6 +82,12 @@ def parse(argv=None):
                     help="run a profiling workload instead of the benchmark")
     ap.add_argument("--precision", type=int, default=1, help="precision of --profile apply")
     ap.add_argument("--reps", type=int, default=3, help="repetitions of --profile apply")
+    ap.add_argument("--ncu-counters", default=None,
+                    help="ncu --csv metrics capture of one kernel class to record in profiles/ncu_counters.json "
+                         "(with --kernel-class, --workload, --launch, --per, --profile-md)")
+    ap.add_argument("--kernel-class", default="residual")
+    ap.add_argument("--per", type=int, default=1, help="launches per unit of --ncu-counters (residual: 2 passes)")
+    ap.add_argument("--profile-md", default=None, help="the profiles/ summary that records the capture command")
     return ap.parse_args(argv)
 
 
@@ -177,16 +185,50 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# ncu counters (DRAM bytes per launch, FP64 flops) of the kernel classes, from the capture
-# commands recorded beside them in profiles/. Each entry carries the hash of the kernel sources it
-# was captured from; an entry whose hash differs from the current sources is stale and not used.
-def kernel_source_hash():
+# ncu counters (DRAM bytes per launch, FP64 flops) of the kernel classes, written by
+# `bench.py --ncu-counters` from the capture commands recorded beside them in profiles/. Each entry
+# carries the hash of the sources of its kernel class (the translation units that hold the
+# kernels and the local headers they include); an entry whose hash differs from the current
+# sources is stale and not used.
+CSRC = os.path.join(ROOT, "paper_1403_7561_gb300", "csrc")
+CLASS_UNITS = {
+    "residual": ["kernels_poisson.cu"],
+    "apply32": ["kernels_poisson.cu", "kernels_lin.cu"],
+    "apply64": ["kernels_poisson.cu", "kernels_lin.cu"],
+    "update32": ["kernels_poisson.cu"],
+    "update64": ["kernels_poisson.cu"],
+}
+
+
+def _with_includes(units):
+    seen, todo = [], list(units)
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(CSRC, f)):
+            continue
+        seen.append(f)
+        with open(os.path.join(CSRC, f)) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith('#include "'):
+                    inc = line.split('"')[1]
+                    if "/" not in inc:
+                        todo.append(inc)
+    return sorted(seen)
+
+
+def kernel_source_hash(cls=None):
+    """Hash of the sources of one kernel class (all of csrc/ when cls is None)."""
+    if cls in CLASS_UNITS:
+        files = _with_includes(CLASS_UNITS[cls])
+    else:
+        files = sorted(os.path.basename(p) for p in glob.glob(os.path.join(CSRC, "*"))
+                       if p.endswith((".cu", ".cuh", ".h", ".cpp")))
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1403_7561_gb300", "csrc", "*"))):
-        if p.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(os.path.basename(p).encode())
-            with open(p, "rb") as f:
-                h.update(f.read())
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -201,10 +243,52 @@ def counter(counters, cur_hash, kernel, workload, launch, key):
     """(value, note): the counter of this kernel class, workload and launch shape if current."""
     for e in counters.get("entries", []):
         if e["kernel"] == kernel and e["workload"] == workload and tuple(e.get("launch") or ()) == tuple(launch):
-            if e.get("source_hash") != cur_hash:
+            if e.get("source_hash") != kernel_source_hash(kernel):
                 return None, "stale: kernel sources changed since the capture (%s)" % e.get("source_hash")
             return e.get(key), "ncu capture %s" % e.get("profile", "")
     return None, "no capture for this kernel, workload and launch shape"
+
+
+def ingest_ncu(args):
+    """Average an ncu CSV capture (--metrics ... --csv) of one kernel class over its units (a unit is
+    `--per` consecutive launches: 2 for the two-pass residual) and record DRAM bytes and FP64 flops
+    per unit in the counters file, with the class's current source hash."""
+    import csv
+    rows = list(csv.reader(open(args.ncu_counters)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    h = rows[hi]
+    ii, mi, vi, ui = h.index("ID"), h.index("Metric Name"), h.index("Metric Value"), h.index("Metric Unit")
+    per_launch = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= vi:
+            continue
+        v = float(r[vi].replace(",", ""))
+        unit = r[ui]
+        scale = {"Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}.get(unit, 1.0)
+        per_launch.setdefault(r[ii], {})[r[mi]] = v * scale
+    launches = list(per_launch.values())
+    units = len(launches) / float(args.per)
+
+    def total(name):
+        return sum(l.get(name, 0.0) for l in launches) / units
+
+    dram = total("dram__bytes_read.sum") + total("dram__bytes_write.sum")
+    flops = (2 * total("sm__sass_thread_inst_executed_op_dfma_pred_on.sum") +
+             total("sm__sass_thread_inst_executed_op_dadd_pred_on.sum") +
+             total("sm__sass_thread_inst_executed_op_dmul_pred_on.sum"))
+    d = json.load(open(COUNTERS)) if os.path.exists(COUNTERS) else {"entries": []}
+    launch = [int(x) for x in args.launch.split(",")] if args.launch else []
+    d["entries"] = [e for e in d.get("entries", []) if not (e["kernel"] == args.kernel_class and
+                                                             e["workload"] == args.workload and
+                                                             e.get("launch") == launch)]
+    d["entries"].append({"kernel": args.kernel_class, "workload": args.workload, "launch": launch,
+                         "source_hash": kernel_source_hash(args.kernel_class), "dram_bytes": dram,
+                         "fp64_flops": flops or None, "launches_per_unit": args.per,
+                         "units_captured": units, "profile": args.profile_md or ""})
+    os.makedirs(os.path.dirname(COUNTERS), exist_ok=True)
+    with open(COUNTERS, "w") as f:
+        json.dump(d, f, indent=1)
+    print(json.dumps(d["entries"][-1]))
 
 
 # FP64 peak of this part: 2 DFMA lanes per SM per clock (ncu
@@ -697,7 +781,7 @@ def native_arm(args):
             "alu_peaks": dict(alu, kind="microbenchmarks on this GPU: FMA chains (2 flops per FMA), FP64 exp()"),
             "op_apply_roofline": op_apply,
             "kernel_profile_ms": {c: round(v[1], 3) for c, v in prof.items()},
-            "kernel_source_hash": cur_hash,
+            "kernel_source_hash": {c: kernel_source_hash(c) for c in ("residual", "apply32")},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -791,7 +875,9 @@ def profile_arm(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.ncu_counters:
+        ingest_ncu(args)
+    elif args.impl == "reference":
         reference_arm(args)
     elif args.profile:
         profile_arm(args)

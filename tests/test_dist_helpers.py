@@ -136,14 +136,43 @@ def test_power_law_extrapolation():
 
 
 def test_kernel_source_hash_tracks_the_sources():
-    # the ncu counters are keyed by this hash: it is stable and covers every kernel source
+    # the ncu counters are keyed by the hash of their kernel class's sources: it is stable, covers
+    # the translation units and the local headers they include, and differs between classes whose
+    # sources differ
     import bench
-    h = bench.kernel_source_hash()
-    assert h == bench.kernel_source_hash() and len(h) == 16
+    h = bench.kernel_source_hash("apply32")
+    assert h == bench.kernel_source_hash("apply32") and len(h) == 16
+    assert bench.kernel_source_hash("residual") != h
+    assert "linmarch.cuh" in bench._with_includes(bench.CLASS_UNITS["apply32"])
+    assert "physics.cuh" in bench._with_includes(bench.CLASS_UNITS["residual"])
+    assert "lobpcg.cu" not in bench._with_includes(bench.CLASS_UNITS["residual"])
     counters = {"entries": [{"kernel": "apply32", "workload": "w", "launch": [3, 8, 16], "dram_bytes": 5.0,
                              "source_hash": "0" * 16}]}
-    v, note = bench.counter(counters, h, "apply32", "w", (3, 8, 16), "dram_bytes")
+    v, note = bench.counter(counters, None, "apply32", "w", (3, 8, 16), "dram_bytes")
     assert v is None and note.startswith("stale")
     counters["entries"][0]["source_hash"] = h
-    assert bench.counter(counters, h, "apply32", "w", (3, 8, 16), "dram_bytes")[0] == 5.0
-    assert bench.counter(counters, h, "apply32", "w", (3, 8, 19), "dram_bytes")[0] is None
+    assert bench.counter(counters, None, "apply32", "w", (3, 8, 16), "dram_bytes")[0] == 5.0
+    assert bench.counter(counters, None, "apply32", "w", (3, 8, 19), "dram_bytes")[0] is None
+
+
+def test_ingest_ncu_averages_units(tmp_path, monkeypatch):
+    # two captured evaluations of the two-pass residual (four launches) become one entry per unit
+    import argparse
+    import json as _json
+    import bench
+    monkeypatch.setattr(bench, "COUNTERS", str(tmp_path / "c.json"))
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for i in range(4):
+        rows.append('"%d","k%d","dram__bytes_read.sum","byte","%d"' % (i, i % 2, 100 * (i % 2 + 1)))
+        rows.append('"%d","k%d","dram__bytes_write.sum","Kbyte","1"' % (i, i % 2))
+        rows.append('"%d","k%d","sm__sass_thread_inst_executed_op_dfma_pred_on.sum","inst","10"' % (i, i % 2))
+        rows.append('"%d","k%d","sm__sass_thread_inst_executed_op_dadd_pred_on.sum","inst","3"' % (i, i % 2))
+    csv_path = tmp_path / "cap.csv"
+    csv_path.write_text("==PROF== header line\n" + "\n".join(rows) + "\n")
+    args = argparse.Namespace(ncu_counters=str(csv_path), kernel_class="residual", workload="w", launch="3,8,19",
+                              per=2, profile_md="profiles/x.md")
+    bench.ingest_ncu(args)
+    e = _json.loads((tmp_path / "c.json").read_text())["entries"][0]
+    assert e["dram_bytes"] == 100 + 200 + 2 * 1000
+    assert e["fp64_flops"] == 2 * (2 * 10 + 3)
+    assert e["launch"] == [3, 8, 19] and e["source_hash"] == bench.kernel_source_hash("residual")
