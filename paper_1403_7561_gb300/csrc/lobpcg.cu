@@ -368,27 +368,6 @@ struct LobpcgRun {
     Profiler::Pair pp;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
     if constexpr (sizeof(T) == 8) {
-      if (b != 0 && w32_ok()) {
-        // the W block (an FP32 preconditioner output, exact in FP32) through the FP32 apply: its
-        // H W and M W enter the Rayleigh-Ritz step only through blocks that gram_sym takes from
-        // the FP64 side (W^T H X) or that carry the small W and P coefficients twice
-        const long long tot = ns * nb;
-        launch_d2f(tot, blk(Sx, b), pre->R32, s);
-        HmArgs<float> a32{};
-        a32.x = pre->R32;
-        a32.hx = pre->W;
-        a32.mx = pre->D;
-        a32.cV = S->cV32.as<float>();
-        a32.ld = ns;
-        a32.nvec = nb;
-        a32.mscale = S->inv_kx;
-        launch_hm_apply<float>(S->g32.g, a32, LaunchCfg{8, 16}, s);
-        launch_f2d(tot, pre->W, blk(HS, b), s);
-        launch_f2d(tot, pre->D, blk(MS, b), s);
-        if (m->prof.on) m->prof.end(pp, s);
-        applies += nb;
-        return;
-      }
       // FP64 vectors: H and M in double-float arithmetic on the FP32 pipes while the residuals are
       // above DF_FLOOR, FP64 applies below it; QCAD_LOBPCG_NATIVE64 selects FP64 ones throughout
       if (df_ok && use_df_apply())
@@ -404,12 +383,6 @@ struct LobpcgRun {
   static bool use_df_apply() {
     static const bool df = std::getenv("QCAD_LOBPCG_NATIVE64") == nullptr;
     return df;
-  }
-  // FP32 applies for the W block of the FP64 phase (while the X block still takes double-float
-  // ones; QCAD_LOBPCG_W64 keeps W in the X block's precision)
-  bool w32_ok() const {
-    static const bool on = std::getenv("QCAD_LOBPCG_W64") == nullptr;
-    return on && df_ok && use_df_apply() && pre != nullptr && pre->R32 != nullptr;
   }
   // The double-float apply carries a 2^-46 relative error per term; the stiffness part of H w
   // cancels to about (h/L)^2 of its terms for smooth w, so its result is good to about 1e-10
@@ -430,16 +403,12 @@ struct LobpcgRun {
     launch_gram<T>(ns, p, q, A, ns, B1, B2, ns, G, B2 ? G + (size_t)p * q : nullptr, part, s);
     CK(cudaMemcpyAsync(hG, G, (size_t)p * q * (B2 ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
-  // Symmetrized copy of the p x p Gram matrix at hG + off (entry a p + b: A_a^T B_b). With FP32
-  // applies for W, the entries between X (columns < nb) and W or P are taken as W^T (H X), with the
-  // FP64 H X, rather than averaged with X^T (H W).
+  // Symmetrized copy of the p x p Gram matrix at hG + off.
   std::vector<double> gram_sym(int p, size_t off) const {
     std::vector<double> out(hG + off, hG + off + (size_t)p * p);
-    const bool onesided = sizeof(T) == 8 && w32_ok() && p > nb;
     for (int j = 0; j < p; ++j)
       for (int i = 0; i < j; ++i) {
-        const double v = (onesided && i < nb && j >= nb) ? out[(size_t)j * p + i]
-                                                         : 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
+        const double v = 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
         out[(size_t)j * p + i] = out[(size_t)i * p + j] = v;
       }
     return out;
