@@ -669,6 +669,169 @@ template void launch_combine<float>(long long, int, int, int, const float*, long
 template void launch_combine<double>(long long, int, int, int, const double*, long long, const double*, double*,
                                      double*, long long, cudaStream_t, int, long long);
 
+// LOBPCG update of the block sets [X | W | P] (nb columns each, columns at stride ld; blockIdx.y
+// selects S, H S or M S, bstride elements apart): with Z = [W P] (the nz = nuse - nb columns after
+// X) and the first nb Ritz vectors' coefficients C (nuse x nb, column-major) split into the X rows
+// Cx and the Z rows Cz,
+//   P' = Z Cz   and   X' = X Cx + P'
+// written in place over P (block 2) and X (block 0). This is X' = [X W P] C with the P' products
+// shared, about half the products of forming X' and P' separately. Each row is read completely
+// into registers before any output of the row is written; four outputs are formed together.
+template <class T, int NBX, int NZX>
+__global__ void __launch_bounds__(256) lobpcg_update_kernel(long long n, int nb, int nz, T* S, long long ld,
+                                                            const T* C, long long bstride) {
+  extern __shared__ __align__(16) unsigned char su_raw[];
+  S += blockIdx.y * bstride;
+  const int px = (nb + 3) & ~3, pz = (nz + 3) & ~3, nq = (nb + 3) & ~3, nuse = nb + nz;
+  T* sCx = reinterpret_cast<T*>(su_raw);  // [nq][px], zero beyond nb
+  T* sCz = sCx + (size_t)nq * px;         // [nq][pz], zero beyond nz
+  for (int t = threadIdx.x; t < nq * px; t += blockDim.x) {
+    const int j = t / px, i = t % px;
+    sCx[t] = (i < nb && j < nb) ? C[j * nuse + i] : T(0);
+  }
+  for (int t = threadIdx.x; t < nq * pz; t += blockDim.x) {
+    const int j = t / pz, i = t % pz;
+    sCz[t] = (i < nz && j < nb) ? C[j * nuse + nb + i] : T(0);
+  }
+  __syncthreads();
+  T* X = S;
+  T* P = S + 2 * (long long)nb * ld;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    T ax[NBX], az[NZX];
+#pragma unroll
+    for (int i = 0; i < NBX; ++i) ax[i] = i < nb ? X[i * ld + r] : T(0);
+#pragma unroll
+    for (int i = 0; i < NZX; ++i) az[i] = i < nz ? S[(nb + i) * ld + r] : T(0);
+    for (int j0 = 0; j0 < nb; j0 += 4) {
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int i = 0; i < NZX; i += 4) {
+        if (i < pz) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            T c4[4];
+            gram_ld4(sCz + (j0 + u) * pz + i, c4);  // 16-byte aligned: pz is a multiple of 4
+            acc[u] += az[i] * c4[0] + az[i + 1] * c4[1];
+            acc[u] += az[i + 2] * c4[2] + az[i + 3] * c4[3];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < nb) P[(j0 + u) * ld + r] = acc[u];
+#pragma unroll
+      for (int i = 0; i < NBX; i += 4) {
+        if (i < px) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            T c4[4];
+            gram_ld4(sCx + (j0 + u) * px + i, c4);
+            acc[u] += ax[i] * c4[0] + ax[i + 1] * c4[1];
+            acc[u] += ax[i + 2] * c4[2] + ax[i + 3] * c4[3];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < nb) X[(j0 + u) * ld + r] = acc[u];
+    }
+  }
+}
+
+// lobpcg_update_kernel for FP64 blocks in double-float arithmetic (C split into hi and lo float
+// tables, each row split once; X' continues P's unrounded double-float sums).
+template <int NBX, int NZX>
+__global__ void __launch_bounds__(256, (NBX <= 12 ? 2 : 1)) lobpcg_update_df_kernel(long long n, int nb, int nz, double* S,
+                                                                long long ld, const double* C, long long bstride) {
+  extern __shared__ __align__(16) unsigned char su_raw[];
+  S += blockIdx.y * bstride;
+  const int px = (nb + 3) & ~3, pz = (nz + 3) & ~3, nq = (nb + 3) & ~3, nuse = nb + nz;
+  float* sCxh = reinterpret_cast<float*>(su_raw);  // [nq][px]
+  float* sCxl = sCxh + (size_t)nq * px;
+  float* sCzh = sCxl + (size_t)nq * px;            // [nq][pz]
+  float* sCzl = sCzh + (size_t)nq * pz;
+  for (int t = threadIdx.x; t < nq * px; t += blockDim.x) {
+    const int j = t / px, i = t % px;
+    df_split((i < nb && j < nb) ? C[j * nuse + i] : 0.0, sCxh[t], sCxl[t]);
+  }
+  for (int t = threadIdx.x; t < nq * pz; t += blockDim.x) {
+    const int j = t / pz, i = t % pz;
+    df_split((i < nz && j < nb) ? C[j * nuse + nb + i] : 0.0, sCzh[t], sCzl[t]);
+  }
+  __syncthreads();
+  double* X = S;
+  double* P = S + 2 * (long long)nb * ld;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    float axh[NBX], axl[NBX], azh[NZX], azl[NZX];
+#pragma unroll
+    for (int i = 0; i < NBX; ++i) df_split_i(i < nb ? X[i * ld + r] : 0.0, axh[i], axl[i]);
+#pragma unroll
+    for (int i = 0; i < NZX; ++i) df_split_i(i < nz ? S[(nb + i) * ld + r] : 0.0, azh[i], azl[i]);
+    for (int j0 = 0; j0 < nb; j0 += 4) {
+      float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int i = 0; i < NZX; i += 4) {
+        if (i < pz) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float ch[4], cl[4];
+            gram_ld4(sCzh + (j0 + u) * pz + i, ch);
+            gram_ld4(sCzl + (j0 + u) * pz + i, cl);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) df_mac(sh[u], sl[u], azh[i + w], azl[i + w], ch[w], cl[w]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < nb) P[(j0 + u) * ld + r] = df_join(sh[u], sl[u]);
+#pragma unroll
+      for (int i = 0; i < NBX; i += 4) {
+        if (i < px) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float ch[4], cl[4];
+            gram_ld4(sCxh + (j0 + u) * px + i, ch);
+            gram_ld4(sCxl + (j0 + u) * px + i, cl);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) df_mac(sh[u], sl[u], axh[i + w], axl[i + w], ch[w], cl[w]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < nb) X[(j0 + u) * ld + r] = df_join(sh[u], sl[u]);
+    }
+  }
+}
+
+template <class T>
+void launch_lobpcg_update(long long n, int nb, int nz, T* S, long long ld, const T* C, cudaStream_t s, int nbase,
+                          long long bstride) {
+  const int px = (nb + 3) & ~3, pz = (nz + 3) & ~3, nq = (nb + 3) & ~3;
+  const dim3 grid(dblocks(n), std::max(1, nbase));
+  const bool small = nb <= 12 && nz <= 24;
+  if constexpr (std::is_same<T, double>::value) {
+    if (dense_df()) {
+      const size_t shm = (size_t)nq * (px + pz) * 2 * sizeof(float);
+      if (small)
+        note_launch(), lobpcg_update_df_kernel<12, 24><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+      else
+        note_launch(), lobpcg_update_df_kernel<20, 40><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+      return;
+    }
+  }
+  const size_t shm = (size_t)nq * (px + pz) * sizeof(T);
+  if (small)
+    note_launch(), lobpcg_update_kernel<T, 12, 24><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+  else
+    note_launch(), lobpcg_update_kernel<T, 20, 40><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+}
+template void launch_lobpcg_update<float>(long long, int, int, float*, long long, const float*, cudaStream_t, int,
+                                          long long);
+template void launch_lobpcg_update<double>(long long, int, int, double*, long long, const double*, cudaStream_t, int,
+                                           long long);
+
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms[2j] += |R_j|^2,
 // norms[2j+1] += |MX_j|^2 (FP64 sums per thread, reduced per block, one atomic per block).
 template <class T>

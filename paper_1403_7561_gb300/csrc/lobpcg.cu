@@ -633,15 +633,11 @@ struct LobpcgRun {
           if (c == 0.0) continue;
           for (int i = 0; i < nuse; ++i) C[(size_t)j * nuse + i] += Tm[(size_t)k * nuse + i] * c;
         }
-      // new X = [X W P] C[:, :nb];  new P = [W P] C[nb:, :nb] = [X W P] (C[:, :nb] with the X rows zeroed)
-      std::vector<double> Cxp((size_t)nuse * 2 * nb, 0.0);
-      for (int j = 0; j < nb; ++j)
-        for (int i = 0; i < nuse; ++i) {
-          Cxp[(size_t)j * nuse + i] = C[(size_t)j * nuse + i];
-          Cxp[(size_t)(nb + j) * nuse + i] = i < nb ? 0.0 : C[(size_t)j * nuse + i];
-        }
+      // new P = [W P] C[nb:, :nb] and new X = X C[:nb, :nb] + new P, in one pass over the rows
       t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - th).count();
-      combine(0, nuse, Cxp, 2 * nb, nb, 0, 2);
+      for (size_t t = 0; t < (size_t)nuse * nb; ++t) hC[t] = (T)C[t];
+      CK(cudaMemcpyAsync(Cd, hC, (size_t)nuse * nb * sizeof(T), cudaMemcpyHostToDevice, s));
+      launch_lobpcg_update<T>(ns, nb, nuse - nb, Sx, ns, Cd, s, 3, (long long)3 * nb * ns);
       haveP = true;
       lam.assign(w.begin(), w.begin() + nb);
       if (iters % 25 == 0) apply(0);  // refresh H X, M X against recurrence drift

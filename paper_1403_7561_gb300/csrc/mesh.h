@@ -170,7 +170,9 @@ struct qcad_mesh_s {
   qcad::DevBuf stats2;
   double* h_small2 = nullptr;
   qcad::PcgGraph graph64, graph32;
-  qcad::LaunchCfg cfg_res, cfg64, cfg32;
+  // residual passes (16-row tiles: the FP64 node pass is pipe-bound, so its halo rows cost the most),
+  // FP64 and FP32 operators
+  qcad::LaunchCfg cfg_res{16, 16, 3}, cfg64, cfg32;
   int cheb_auto[2] = {0, 0};               // autotuned Chebyshev degree per precision (0 = not yet)
   int batch_kchunk = 0;                    // z chunk of this mesh in batched launches (0 = not tuned)
   // largest eigenvalue of D^-1 J of the stored linearization per precision, valid while
