@@ -228,14 +228,23 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
     if (__all_sync(FULL_MASK, eflat)) {
       if (valid) {
         if (a.wq != nullptr && a.theta == nullptr) {
-          elR[t] = zone >= 0 ? a.wq[8 * k + (a.P.incomplete ? zone : WQ_ZONE_COMPLETE)] : 0.0;
+          const int slot = zone >= 0 ? (a.P.incomplete ? zone : WQ_ZONE_COMPLETE) : WQ_ZERO;
+          if (a.ecode != nullptr) {
+            // the element's corner loads are one table entry and its diagonal contributions zero:
+            // pass 2 reads the code (1 + the slot) instead of 128 bytes of corner values
+            if (l == 0) a.ecode[e] = (unsigned char)(1 + slot);
+          } else {
+            elR[t] = a.wq[8 * k + slot];
+            elD[t] = 0.0;
+          }
         } else {
           const double th = a.theta ? a.theta[e] : 0.0;
           const double rho = zone >= 0 ? zone_charge(a.P, zone) : 0.0;
           const double w = a.wq != nullptr ? a.wq[8 * k + WQ_WEIGHT] : -a.P.qe * (g.hx[i] * g.hy[j] * g.hz[k] * 0.125);
           elR[t] = w * (rho + th);
+          elD[t] = 0.0;
+          if (a.ecode != nullptr && l == 0) a.ecode[e] = 0;
         }
-        elD[t] = 0.0;
         if (a.c64) a.c64[t] = 0.0;
         if (a.c32) a.c32[t] = 0.0f;
       }
@@ -293,6 +302,7 @@ __device__ __forceinline__ void residual_qp_body(const Grid<double>& g, const Re
   if (valid) {
     elR[t] = f;
     elD[t] = c;
+    if (a.ecode != nullptr && l == 0) a.ecode[e] = 0;
   }
   if (a.counts != nullptr) {
     double s[2] = {0.0, 0.0};
@@ -320,18 +330,33 @@ __global__ void __launch_bounds__(256) residual_qp_kernel(const __grid_constant_
 struct ResidualGatherOp {
   static constexpr int NF = 2;
   static constexpr bool STIFF = true;
-  using ED = char;
+  using ED = unsigned char;  // the element's load code from pass 1 (0: corner values in elR, elD)
   const double* phi;
   const double* elR;
   const double* elD;
+  const unsigned char* ecode;
+  const double* wq;
   double *R, *diag, *dinv64, *b64, *stats;
   float *dinv32, *b32;
   double acc_r2, acc_rmax;
   __device__ bool skip() const { return false; }
   __device__ void set_vec(int) {}
   __device__ double load(const Grid<double>&, int n, bool in, int, int, int) const { return in ? phi[n] : 0.0; }
-  __device__ char edata(const Grid<double>&, int, int, int) const { return 0; }
-  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double*, char, double (*out)[8], bool) const {
+  __device__ unsigned char edata(const Grid<double>& g, int i, int j, int k) const {
+    return ecode != nullptr ? ecode[elem_index(g, i, j, k)] : (unsigned char)0;
+  }
+  __device__ void elem(const Grid<double>& g, int i, int j, int k, const double*, unsigned char code,
+                       double (*out)[8], bool) const {
+    if (code != 0) {
+      // a constant-charge element: every corner load is the layer's table entry, no diagonal term
+      const double v = wq[8 * k + code - 1];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        out[0][q] = v;
+        out[1][q] = 0.0;
+      }
+      return;
+    }
     const long long e = elem_index(g, i, j, k);
     load_c8<double>(elR, e, out[0]);
     load_c8<double>(elD, e, out[1]);
@@ -395,6 +420,8 @@ __host__ __device__ inline ResidualGatherOp make_gather_op(const ResidualArgs& a
   op.phi = args.phi;
   op.elR = elR;
   op.elD = elD;
+  op.ecode = args.ecode;
+  op.wq = args.wq;
   op.R = args.R;
   op.diag = args.diag;
   op.dinv64 = args.dinv64;

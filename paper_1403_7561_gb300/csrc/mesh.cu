@@ -574,6 +574,7 @@ void mesh_create(const qcad_device* dev, void* stream, qcad_mesh_t* out) {
       }
       m->d_wq.ensure(wq.size() * sizeof(double) + 16);
       CK(cudaMemcpyAsync(m->d_wq.p, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      m->d_ecode.ensure((size_t)m->nx * m->ny * m->nz + 16);
       CK(cudaStreamSynchronize(s));
     }
     m->d_gate_top.ensure(m->gate_top.size() + 16);

@@ -138,6 +138,7 @@ struct qcad_mesh_s {
   qcad::GridDev<float> g32;
   qcad::DevBuf d_xn, d_yn, d_zn, d_layer_semi, d_gate_top, d_dir_top, d_vgate;
   qcad::DevBuf d_wq;  // [nz][8] the residual's per-layer load table (slots in physics.cuh)
+  qcad::DevBuf d_ecode;  // [n_elems] the residual's per-element load codes (kernels_poisson.cu)
   // surface terms (charged gates under the Robin condition, surface charges): the face
   // coefficients eps_r/d of the top plane (FP64 and FP32, in the grids' face_alpha), the
   // constant load b = sum_sheets (q/eps0) sigma int N + sum_charged ((eps_r/d) phi_0 + (q/eps0)

@@ -389,6 +389,7 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   a.stats = m->stats.as<double>();
   if (m->qd_active) a.qd = m->qd;  // predictor density in the quantum region (Sec. II.C)
   a.wq = m->d_wq.as<double>();
+  a.ecode = m->d_ecode.as<unsigned char>();
   if (m->has_surface) a.bsurf = m->d_bsurf.as<double>();  // charged gates, surface charges
   CK(cudaMemsetAsync(a.stats, 0, 2 * sizeof(double), s));
   if (counts_out) {
@@ -841,6 +842,7 @@ static void batch_residual(BatchCtx& B, const std::vector<int>& idx, const std::
     a.linear = linear;
     a.stats = m->stats.as<double>();
     a.wq = m->d_wq.as<double>();
+    a.ecode = m->d_ecode.as<unsigned char>();
     e.kchunk = std::max(2, m->cfg_res.kchunk);
     e.tiles_x = (e.g.nxn + QCAD_BX - 3) / (QCAD_BX - 2);
     e.tiles_y = (e.g.nyn + 8 - 3) / (8 - 2);

@@ -180,6 +180,7 @@ __host__ __device__ __forceinline__ double zone_charge(const Phys& P, int zone) 
 // in a constant-charge zone takes its load from the table without FP64 arithmetic.
 constexpr int WQ_ZONE_COMPLETE = 4;  // w_k (N_D - N_A): complete ionization
 constexpr int WQ_WEIGHT = 5;         // w_k
+constexpr int WQ_ZERO = 6;           // 0: no charge (oxide, padding)
 // zones 0..3 (incomplete ionization): w_k zone_charge(zone)
 
 // The residual's charge outside the dots: where phi lies outside every cutoff band (n and p below

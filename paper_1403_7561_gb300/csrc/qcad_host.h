@@ -70,6 +70,7 @@ struct ResidualArgs {
   QuantumDensity qd;         // quantum density in the quantum region (inactive: qd.w null)
   const double* bsurf;       // [n_nodes] constant surface load b (R -= b; two-pass residual) or null
   const double* wq;          // [nz][8] per-layer load table of constant-charge elements (physics.cuh) or null
+  unsigned char* ecode;      // [n_elems] per-element load code between the two residual passes, or null
 };
 
 template <class T>
