@@ -229,9 +229,12 @@ __device__ __forceinline__ void gram_cp(T* smem, const T* gmem, bool valid) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
 }
 
-template <class T>
+// GC > 0: the row-group count G at compile time (FP32 storage takes one group), so that the row loop
+// over a shared tile unrolls completely.
+template <class T, int GC = 0>
 __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, const T* A, long long lda,
-                                                   const T* B1, const T* B2, long long ldb, double* part, int G) {
+                                                   const T* B1, const T* B2, long long ldb, double* part, int G_) {
+  const int G = GC > 0 ? GC : G_;
   extern __shared__ __align__(16) unsigned char sh_raw[];
   T* sh = reinterpret_cast<T*>(sh_raw);      // two stages of GR x W
   const int q = p;
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(512) gram_kernel(long long n, int p, int nb2, 
       T s16[16];
 #pragma unroll
       for (int s = 0; s < 16; ++s) s16[s] = T(0);
-#pragma unroll 4
+#pragma unroll(GC > 0 ? GR / (GC > 0 ? GC : 1) : 4)
       for (int rr = grp; rr < GR; rr += G) {
         const T* row = st + rr * W;
         T av[4], bv[4];
@@ -374,9 +377,11 @@ size_t gram_part_doubles(int p, int q) { return (size_t)GRAM_MAX_BLOCKS * p * 2 
 // gram_kernel for FP64 blocks in double-float arithmetic: the double tile lands in shared
 // memory as before, is split once into hi and lo float tiles, and each 32-row tile is summed in
 // double-float before it is added to the FP64 accumulators.
+// upper: only the output tiles on or above the diagonal of each product (p == q, q a multiple of
+// 4); the entries below are left unwritten.
 __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb2, const double* A, long long lda,
                                                       const double* B1, const double* B2, long long ldb,
-                                                      double* part, int G) {
+                                                      double* part, int G, int upper) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   const int q = p;
   const int qt = q * nb2;
@@ -390,10 +395,24 @@ __global__ void __launch_bounds__(512) gram_df_kernel(long long n, int p, int nb
   for (int t = tid; t < 2 * GR * W; t += nth) sh[t] = 0.0;
   __syncthreads();
   // G row groups of nt output tiles, as in gram_kernel
-  const int nt = ta_n * tb_n;
+  const int tq = ta_n, tri = tq * (tq + 1) / 2;  // upper: tiles per product on or above its diagonal
+  const int nt = upper ? nb2 * tri : ta_n * tb_n;
   const bool active = tid < G * nt;
   const int grp = active ? tid / nt : 0, tt = active ? tid % nt : 0;
-  const int ta = tt / tb_n, tb = tt % tb_n;
+  int ta, tb;
+  if (upper) {
+    const int k = tt / tri;
+    int r = tt % tri, row = 0;
+    while (r >= tq - row) {
+      r -= tq - row;
+      ++row;
+    }
+    ta = row;
+    tb = k * tq + row + r;
+  } else {
+    ta = tt / tb_n;
+    tb = tt % tb_n;
+  }
   float acch[16], accl[16];  // double-float accumulation across tiles
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
@@ -500,7 +519,7 @@ static bool dense_df() {
 
 template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
-                 double* G1, double* G2, double* part, cudaStream_t s) {
+                 double* G1, double* G2, double* part, cudaStream_t s, bool upper) {
   (void)q;  // the products of LOBPCG are square: q == p
   const int nb2 = B2 ? 2 : 1;
   const int ta_n = (p + 3) / 4, tb_n = (p * nb2 + 3) / 4;
@@ -515,30 +534,42 @@ void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* 
   const size_t red = (size_t)G * nt * 16 * sizeof(double);  // the groups' sums, after the tiles
   const size_t shm = std::max(red, (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * sizeof(T));
   static bool attr = false;
-  if (!attr) attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
-                    cudaSuccess;
+  if (!attr)
+    attr = cudaFuncSetAttribute(gram_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess &&
+           cudaFuncSetAttribute(gram_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) ==
+               cudaSuccess;
   if constexpr (std::is_same<T, double>::value) {
     if (dense_df()) {
+      // the upper triangles only (the caller mirrors them), where the tiles align with the products
+      const int up = (upper && p == q && p % 4 == 0) ? 1 : 0;
+      const int nt_df = up ? nb2 * (ta_n * (ta_n + 1) / 2) : nt;
+      const int G_df = std::max(1, std::min(8, 512 / nt_df));
+      const int nth_df = std::min(512, std::max(256, ((G_df * nt_df + 31) / 32) * 32));
+      const size_t red_df = (size_t)G_df * nt_df * 16 * sizeof(double);
       // two double stages plus the hi and lo float tiles
-      const size_t shm_df = std::max(red, (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * (sizeof(double) + sizeof(float)));
+      const size_t shm_df =
+          std::max(red_df, (size_t)2 * GR * (4 * ta_n + 4 * tb_n + 4) * (sizeof(double) + sizeof(float)));
       static bool attr_df = false;
       if (!attr_df)
         attr_df = cudaFuncSetAttribute(gram_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
                   cudaSuccess;
-      note_launch(), gram_df_kernel<<<nblk, nth, shm_df, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
+      note_launch(), gram_df_kernel<<<nblk, nth_df, shm_df, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G_df, up);
       const int tot = p * p * nb2;
       note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
       return;
     }
   }
-  note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
+  if (G == 1)
+    note_launch(), gram_kernel<T, 1><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
+  else
+    note_launch(), gram_kernel<T><<<nblk, nth, shm, s>>>(n, p, nb2, A, lda, B1, B2, ldb, part, G);
   const int tot = p * p * nb2;
   note_launch(), gram_reduce_kernel<<<(tot + 31) / 32, dim3(32, 8), 0, s>>>(nblk, tot, p * p, part, G1, G2);
 }
 template void launch_gram<float>(long long, int, int, const float*, long long, const float*, const float*, long long,
-                                 double*, double*, double*, cudaStream_t);
+                                 double*, double*, double*, cudaStream_t, bool);
 template void launch_gram<double>(long long, int, int, const double*, long long, const double*, const double*,
-                                  long long, double*, double*, double*, cudaStream_t);
+                                  long long, double*, double*, double*, cudaStream_t, bool);
 
 // Row-wise block combination, safe in place: each row of A is read completely into
 // registers by one thread before any output of the row is written. Y = A C with A n x p

@@ -399,19 +399,30 @@ struct LobpcgRun {
 
   // Enqueues G1 = A^T B1 (and G2 = A^T B2) for p columns of A and q of B, with the copy of
   // both to hG (G1 at hG, G2 at hG + p*q); the caller synchronizes.
-  void gram_async(int p, int q, const T* A, const T* B1, const T* B2) {
-    launch_gram<T>(ns, p, q, A, ns, B1, B2, ns, G, B2 ? G + (size_t)p * q : nullptr, part, s);
+  void gram_async(int p, int q, const T* A, const T* B1, const T* B2, bool upper = false) {
+    launch_gram<T>(ns, p, q, A, ns, B1, B2, ns, G, B2 ? G + (size_t)p * q : nullptr, part, s, upper);
     CK(cudaMemcpyAsync(hG, G, (size_t)p * q * (B2 ? 2 : 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   // Symmetrized copy of the p x p Gram matrix at hG + off.
-  std::vector<double> gram_sym(int p, size_t off) const {
+  // upper: only the entries a p + b with a <= b were formed; they are mirrored.
+  std::vector<double> gram_sym(int p, size_t off, bool upper = false) const {
     std::vector<double> out(hG + off, hG + off + (size_t)p * p);
     for (int j = 0; j < p; ++j)
       for (int i = 0; i < j; ++i) {
-        const double v = 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
+        const double v = upper ? out[(size_t)i * p + j] : 0.5 * (out[(size_t)j * p + i] + out[(size_t)i * p + j]);
         out[(size_t)j * p + i] = out[(size_t)i * p + j] = v;
       }
     return out;
+  }
+  // The FP64 phase's Rayleigh-Ritz Gram matrices from their upper triangles (H S and M S come from
+  // the double-float applies, accurate to about 1e-10, so the two triangles agree far below the
+  // tolerance; QCAD_LOBPCG_GRAM=full forms and averages both)
+  static bool gram_upper() {
+    static const bool up = [] {
+      const char* e = std::getenv("QCAD_LOBPCG_GRAM");
+      return sizeof(T) == 8 && !(e && std::string(e) == "full");
+    }();
+    return up;
   }
   void sync() {
     const auto t0 = std::chrono::steady_clock::now();
@@ -495,7 +506,8 @@ struct LobpcgRun {
       // of P is applied to the small matrices on the host (G -> T^T G T), which gives the
       // Rayleigh-Ritz problem of the orthonormalized blocks without forming them
       int nuse = haveP ? 3 * nb : 2 * nb;
-      gram_async(nuse, nuse, Sx, HS, MS);
+      const bool up = gram_upper() && nuse % 4 == 0;
+      gram_async(nuse, nuse, Sx, HS, MS, up);
       sync();
       const bool conv = converged(tol);
       if (debug_level() >= 2)
@@ -541,7 +553,7 @@ struct LobpcgRun {
       }
       ++iters;
       const auto th = std::chrono::steady_clock::now();
-      std::vector<double> GH = gram_sym(nuse, 0), GM = gram_sym(nuse, (size_t)nuse * nuse), RW, RP;
+      std::vector<double> GH = gram_sym(nuse, 0, up), GM = gram_sym(nuse, (size_t)nuse * nuse, up), RW, RP;
       if (!chol_inv(GM, nuse, nb, nb, RW)) {
         // W lost rank: restart it from a random block (and drop P)
         haveP = false;

@@ -24,10 +24,11 @@ void launch_potential(const SubdomainMap& sm, const double* phi, double V0, cons
 void launch_pack(const SubdomainMap& sm, int nvec, double* full, long long ldf, double* dof, long long ldd,
                  int unpack, cudaStream_t s);
 // G1 = A^T B1 and, if B2 is not null, G2 = A^T B2 (p x p each, row-major, FP64, overwritten;
-// q must equal p). part: device scratch of gram_part_doubles(p, p) doubles. p <= 64.
+// q must equal p). part: device scratch of gram_part_doubles(p, p) doubles. p <= 64. upper: the
+// double-float kernel may form only the entries a <= b (the others are then unspecified).
 template <class T>
 void launch_gram(long long n, int p, int q, const T* A, long long lda, const T* B1, const T* B2, long long ldb,
-                 double* G1, double* G2, double* part, cudaStream_t s);
+                 double* G1, double* G2, double* part, cudaStream_t s, bool upper = false);
 size_t gram_part_doubles(int p, int q);
 // p <= 64. nbase > 1: the same C applied to nbase block sets, set b at A, Y1, Y2 + b * bstride.
 // LOBPCG update of [X | W | P] (nb columns each at stride ld; nbase block sets bstride elements
