@@ -752,7 +752,25 @@ struct BatchCtx {
   double* h_rstats = nullptr;
   PcgScalars* h_sc = nullptr;         // pinned host staging of the entries' scalars
   cudaGraphExec_t exec = nullptr;
+  // streams the entries' multigrid PCG graphs are spread over (instances run concurrently), with
+  // the events that fork them from s and join them back
+  static constexpr int NPOOL = 8;
+  cudaStream_t pool[NPOOL] = {};
+  cudaEvent_t fork = nullptr, join[NPOOL] = {};
+  void ensure_pool() {
+    if (fork) return;
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int k = 0; k < NPOOL; ++k) {
+      CK(cudaStreamCreateWithFlags(&pool[k], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    }
+  }
   ~BatchCtx() {
+    for (int k = 0; k < NPOOL; ++k) {
+      if (pool[k]) cudaStreamDestroy(pool[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
     if (exec) cudaGraphExecDestroy(exec);
     if (h_status) cudaFreeHost(h_status);
     if (h_rstats) cudaFreeHost(h_rstats);
@@ -940,11 +958,21 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
   std::vector<char> active(B.n);
   for (int i = 0; i < B.n; ++i) active[i] = rtol[i] > 0;
   int guard = 0;
+  B.ensure_pool();
   for (;;) {
+    // each active entry's chunk of PCG iterations (its captured graph), the entries spread over
+    // the stream pool so that the small instances' kernels overlap
+    CK(cudaEventRecord(B.fork, B.s));
+    for (int k = 0; k < BatchCtx::NPOOL; ++k) CK(cudaStreamWaitEvent(B.pool[k], B.fork, 0));
+    int slot = 0;
     for (int i = 0; i < B.n; ++i) {
       if (!active[i]) continue;
-      CK(cudaGraphLaunch(B.ms[i]->graph32.exec, B.s));
+      CK(cudaGraphLaunch(B.ms[i]->graph32.exec, B.pool[slot++ % BatchCtx::NPOOL]));
       note_launch(mg_launches_per_iteration(B.ms[i]) * B.ms[i]->graph32.chunk);
+    }
+    for (int k = 0; k < BatchCtx::NPOOL; ++k) {
+      CK(cudaEventRecord(B.join[k], B.pool[k]));
+      CK(cudaStreamWaitEvent(B.s, B.join[k], 0));
     }
     launch_batch_status(B.tab_v.as<BatchVecEntry>(), B.n, B.status.as<int>(), B.s);
     CK(cudaMemcpyAsync(B.h_status, B.status.p, (size_t)4 * B.n * sizeof(int), cudaMemcpyDeviceToHost, B.s));
