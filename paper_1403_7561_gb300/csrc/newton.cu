@@ -940,6 +940,15 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
       build_graph<float>(m, B.vecs[i], DEG_MG);
       G.key = (const void*)B.vecs[i].x;
     }
+  }
+  // each entry's scalars, multigrid setup and PCG start on the stream pool (entries are distinct
+  // meshes), joined back into s
+  B.ensure_pool();
+  CK(cudaEventRecord(B.fork, B.s));
+  for (int k = 0; k < BatchCtx::NPOOL; ++k) CK(cudaStreamWaitEvent(B.pool[k], B.fork, 0));
+  for (int i = 0; i < B.n; ++i) {
+    qcad_mesh_s* m = B.ms[i];
+    cudaStream_t ps = B.pool[i % BatchCtx::NPOOL];
     PcgScalars* h = B.h_sc + i;
     std::memset(h, 0, sizeof(PcgScalars));
     h->tol2 = rtol[i] * rtol[i];
@@ -948,17 +957,20 @@ static void batch_pcg_mg(BatchCtx& B, const std::vector<double>& rtol, int maxit
     h->theta = 1.0;
     h->delta = 0.5;
     if (!(rtol[i] > 0)) h->done = 1;
-    CK(cudaMemcpyAsync(B.scd[i], h, sizeof(PcgScalars), cudaMemcpyHostToDevice, B.s));
+    CK(cudaMemcpyAsync(B.scd[i], h, sizeof(PcgScalars), cudaMemcpyHostToDevice, ps));
     if (rtol[i] > 0) {
-      mg_setup<float>(m, B.s);
-      mg_enqueue_init<float>(m, B.vecs[i], B.scd[i], B.s);
+      mg_setup<float>(m, ps);
+      mg_enqueue_init<float>(m, B.vecs[i], B.scd[i], ps);
     }
+  }
+  for (int k = 0; k < BatchCtx::NPOOL; ++k) {
+    CK(cudaEventRecord(B.join[k], B.pool[k]));
+    CK(cudaStreamWaitEvent(B.s, B.join[k], 0));
   }
   CK(cudaGetLastError());
   std::vector<char> active(B.n);
   for (int i = 0; i < B.n; ++i) active[i] = rtol[i] > 0;
   int guard = 0;
-  B.ensure_pool();
   for (;;) {
     // each active entry's chunk of PCG iterations (its captured graph), the entries spread over
     // the stream pool so that the small instances' kernels overlap
