@@ -298,6 +298,52 @@ void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& args, LaunchCfg cfg,
 template void launch_hm_apply_lin<float>(const Grid<float>&, const HmArgs<float>&, LaunchCfg, cudaStream_t);
 template void launch_hm_apply_lin<double>(const Grid<double>&, const HmArgs<double>&, LaunchCfg, cudaStream_t);
 
+// One step of the eigensolver's Chebyshev-Jacobi block preconditioner fused into the H apply of its
+// direction block: with h = (H D_in)_n at every node (Dirichlet rows: h = D_in = 0 there),
+//   W <- W - h,  D_out <- c1 D_in + c2 D^-1 W,  Z <- Z + D_out
+// (the recurrence of cheb_block_step_kernel). D is double-buffered: other tiles still read D_in.
+struct ChebHmOp {
+  static constexpr int NIN = 1;
+  static constexpr bool SEPM = false;
+  struct Pre {
+    float w, z;
+  };
+  ChebHmArgs a;
+  const float *din, *dinv;
+  float *dout, *w, *z;
+  __device__ bool skip() const { return false; }
+  __device__ void set_vec(int vec) {
+    const long long o = (long long)vec * a.ld;
+    din = a.din + o;
+    dout = a.dout + o;
+    w = a.w + o;
+    z = a.z + o;
+    dinv = a.dinv;
+  }
+  __device__ const float* coeffs() const { return a.cV; }
+  __device__ const float* lin_src(int) const { return din; }
+  __device__ float lin_mix(float x0, float) const { return x0; }
+  __device__ float lin_in(int n) const { return din[n]; }
+  __device__ Pre lin_pre(int n) const { return Pre{w[n], z[n]}; }
+  __device__ bool lin_dir() const { return true; }
+  __device__ float m_scale() const { return 0.0f; }
+  __device__ void lin_out(int n, const Pre& pre, float vin, float h) {
+    const float wn = pre.w - h;
+    const float d = a.c1 * vin + a.c2 * dinv[n] * wn;
+    w[n] = wn;
+    dout[n] = d;
+    z[n] = pre.z + d;
+  }
+  __device__ void lin_out2(int, float, float) {}
+  __device__ void finish() {}
+};
+
+void launch_cheb_hm_step(const Grid<float>& g, const ChebHmArgs& args, cudaStream_t s) {
+  ChebHmOp op = {};
+  op.a = args;
+  lin_launch_vec<float, 8, 2>(g, op, 16, args.nvec, s);
+}
+
 void launch_hm_apply_df(const Grid<dfl>& g, const HmArgs<double>& args, cudaStream_t s) {
   HmDfOp op = {};
   op.x = args.x;

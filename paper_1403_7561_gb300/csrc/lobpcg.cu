@@ -293,17 +293,30 @@ struct ChebPre {
     theta = 0.5 * (a + b);
     delta = 0.5 * (b - a);
   }
-  // Z = p_k(D^-1 H) D^-1 R for nb columns (Z may alias R).
+  // Z = p_k(D^-1 H) D^-1 R for nb columns (Z may alias R). Each step's H apply carries the
+  // recurrence in its epilogue, the direction block alternating between D and HD.
   void apply(const float* R, float* Z) {
     cudaStream_t s = io.s;
     launch_cheb_block_init<float>(ns, nb, ns, R, dinv, 1.0 / theta, W, D, Z, s);
     const double sigma = theta / delta;
     double rho_prev = 1.0 / sigma, rho = rho_prev;
+    float *dcur = D, *dnext = HD;
     for (int j = 1; j < k; ++j) {
       rho_prev = rho;
       rho = 1.0 / (2.0 * sigma - rho_prev);
-      hmul(D, HD, nb);
-      launch_cheb_block_step<float>(ns, nb, ns, HD, dinv, rho * rho_prev, 2.0 * rho / delta, W, D, Z, s);
+      ChebHmArgs a{};
+      a.din = dcur;
+      a.dout = dnext;
+      a.w = W;
+      a.z = Z;
+      a.dinv = dinv;
+      a.cV = S->cV32.as<float>();
+      a.ld = ns;
+      a.nvec = nb;
+      a.c1 = (float)(rho * rho_prev);
+      a.c2 = (float)(2.0 * rho / delta);
+      launch_cheb_hm_step(S->g32.g, a, s);
+      std::swap(dcur, dnext);
     }
   }
 };

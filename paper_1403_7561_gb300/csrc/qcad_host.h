@@ -174,6 +174,21 @@ template <class T>
 void launch_hm_apply(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
 template <class T>
 void launch_hm_apply_lin(const Grid<T>& g, const HmArgs<T>& a, LaunchCfg cfg, cudaStream_t s);
+// One fused step of the LOBPCG Chebyshev-Jacobi block preconditioner (kernels_lin.cu): the H apply
+// of D_in (nvec columns at stride ld, coefficients cV) with the recurrence W -= H D_in,
+// D_out = c1 D_in + c2 D^-1 W, Z += D_out in its epilogue.
+struct ChebHmArgs {
+  const float* din;
+  float* dout;
+  float* w;
+  float* z;
+  const float* dinv;
+  const float* cV;
+  long long ld;
+  int nvec;
+  float c1, c2;
+};
+void launch_cheb_hm_step(const Grid<float>& g, const ChebHmArgs& args, cudaStream_t s);
 struct dfl;
 // The H and M applies of FP64 vectors in double-float arithmetic on the FP32 pipes (g: the
 // subdomain grid's tables as double-float pairs; a.cV the FP64 coefficients).
