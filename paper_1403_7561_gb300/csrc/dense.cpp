@@ -13,18 +13,21 @@ namespace qcad {
 #define A_(i, j) A[(size_t)(j) * n + (i)]
 
 bool dense_cholesky(int n, double* A) {
+  // left-looking by columns: column j less its earlier columns scaled by row j (the same
+  // subtractions, in the same order, as the row-wise dot products), then scaled by 1 / L(j, j)
   for (int j = 0; j < n; ++j) {
-    double d = A_(j, j);
-    for (int k = 0; k < j; ++k) d -= A_(j, k) * A_(j, k);
+    double* cj = A + (size_t)j * n;
+    for (int k = 0; k < j; ++k) {
+      const double* ck = A + (size_t)k * n;
+      const double f = ck[j];
+      for (int i = j; i < n; ++i) cj[i] -= ck[i] * f;
+    }
+    const double d = cj[j];
     if (!(d > 0.0) || !std::isfinite(d)) return false;
     const double l = std::sqrt(d);
-    A_(j, j) = l;
-    for (int i = j + 1; i < n; ++i) {
-      double s = A_(i, j);
-      for (int k = 0; k < j; ++k) s -= A_(i, k) * A_(j, k);
-      A_(i, j) = s / l;
-    }
-    for (int i = 0; i < j; ++i) A_(i, j) = 0.0;
+    cj[j] = l;
+    for (int i = j + 1; i < n; ++i) cj[i] /= l;
+    for (int i = 0; i < j; ++i) cj[i] = 0.0;
   }
   return true;
 }
@@ -36,7 +39,7 @@ bool dense_cholesky(int n, double* A) {
 void dense_sym_eig(int n, double* A, double* w, double* V) {
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) V[(size_t)j * n + i] = (i == j) ? 1.0 : 0.0;
-  std::vector<double> v(n), p(n), wv(n);
+  std::vector<double> v(n), p(n), wv(n), t(n);
   // Householder: column k below the subdiagonal is annihilated by H = I - 2 u u^T acting on
   // rows/columns k+1..n-1 (A22 <- A22 - 2 u w^T - 2 w u^T, w = A22 u - (u^T A22 u) u).
   for (int k = 0; k + 2 < n; ++k) {
@@ -55,10 +58,12 @@ void dense_sym_eig(int n, double* A, double* w, double* V) {
     if (vn2 == 0.0) continue;
     const double inv = 1.0 / std::sqrt(vn2);
     for (int i = 0; i < m; ++i) v[i] *= inv;
+    // p = A22 v, row i taken as column i (A22 is symmetric), so that the inner loops run down columns
     double up = 0.0;
     for (int i = 0; i < m; ++i) {
+      const double* col = A + (size_t)(k + 1 + i) * n + (k + 1);
       double s = 0.0;
-      for (int j = 0; j < m; ++j) s += A_(k + 1 + i, k + 1 + j) * v[j];
+      for (int j = 0; j < m; ++j) s += col[j] * v[j];
       p[i] = s;
       up += v[i] * s;
     }
@@ -71,11 +76,17 @@ void dense_sym_eig(int n, double* A, double* w, double* V) {
       A_(k + 1 + i, k) = 0.0;
       A_(k, k + 1 + i) = 0.0;
     }
-    // V <- V H on columns k+1..n-1
-    for (int r = 0; r < n; ++r) {
-      double s = 0.0;
-      for (int i = 0; i < m; ++i) s += V[(size_t)(k + 1 + i) * n + r] * v[i];
-      for (int i = 0; i < m; ++i) V[(size_t)(k + 1 + i) * n + r] -= 2.0 * s * v[i];
+    // V <- V H on columns k+1..n-1: t = V[:, k+1:] v, then V[:, k+1+i] -= 2 v_i t (column sweeps)
+    std::fill(t.begin(), t.end(), 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double* col = V + (size_t)(k + 1 + i) * n;
+      const double vi = v[i];
+      for (int r = 0; r < n; ++r) t[r] += col[r] * vi;
+    }
+    for (int i = 0; i < m; ++i) {
+      double* col = V + (size_t)(k + 1 + i) * n;
+      const double f = 2.0 * v[i];
+      for (int r = 0; r < n; ++r) col[r] -= f * t[r];
     }
   }
   std::vector<double> d(n), e(n, 0.0);
@@ -104,7 +115,8 @@ void dense_sym_eig(int n, double* A, double* w, double* V) {
         x = e[k - 1];
         y = bulge;
       }
-      const double r = std::hypot(x, y);
+      // the projected matrices' entries are far from the overflow and underflow thresholds
+      const double r = std::sqrt(x * x + y * y);
       const double c = r != 0.0 ? x / r : 1.0, s = r != 0.0 ? y / r : 0.0;
       if (k > l) e[k - 1] = r;
       const double a = d[k], b = e[k], cc = d[k + 1];
@@ -115,10 +127,12 @@ void dense_sym_eig(int n, double* A, double* w, double* V) {
         bulge = s * e[k + 1];
         e[k + 1] *= c;
       }
+      double* vk = V + (size_t)k * n;
+      double* vk1 = V + (size_t)(k + 1) * n;
       for (int r2 = 0; r2 < n; ++r2) {
-        const double vk = V[(size_t)k * n + r2], vk1 = V[(size_t)(k + 1) * n + r2];
-        V[(size_t)k * n + r2] = c * vk + s * vk1;
-        V[(size_t)(k + 1) * n + r2] = -s * vk + c * vk1;
+        const double a0 = vk[r2], a1 = vk1[r2];
+        vk[r2] = c * a0 + s * a1;
+        vk1[r2] = -s * a0 + c * a1;
       }
     }
   }
@@ -135,12 +149,15 @@ void dense_sym_eig(int n, double* A, double* w, double* V) {
 }
 
 void dense_inv_lt(int n, const double* L, double* R) {
-  // Solve L^T R = I column by column (R upper triangular).
+  // Solve L^T R = I column by column (R upper triangular: rows below j of column j are zero).
   for (int j = 0; j < n; ++j) {
-    for (int i = n - 1; i >= 0; --i) {
+    double* rj = R + (size_t)j * n;
+    for (int i = j + 1; i < n; ++i) rj[i] = 0.0;
+    for (int i = j; i >= 0; --i) {
+      const double* li = L + (size_t)i * n;  // column i of L: L(k, i) for k > i
       double s = (i == j) ? 1.0 : 0.0;
-      for (int k = i + 1; k < n; ++k) s -= L[(size_t)i * n + k] * R[(size_t)j * n + k];
-      R[(size_t)j * n + i] = s / L[(size_t)i * n + i];
+      for (int k = i + 1; k <= j; ++k) s -= li[k] * rj[k];
+      rj[i] = s / li[i];
     }
   }
 }
@@ -161,7 +178,7 @@ bool dense_gen_eig(int n, const double* A, const double* B, double* w, double* X
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
       double s = 0.0;
-      for (int k = 0; k < n; ++k) s += R[(size_t)i * n + k] * AR[(size_t)j * n + k];
+      for (int k = 0; k <= i; ++k) s += R[(size_t)i * n + k] * AR[(size_t)j * n + k];  // R upper triangular
       C[(size_t)j * n + i] = s;
     }
   // symmetrize against rounding
@@ -173,13 +190,16 @@ bool dense_gen_eig(int n, const double* A, const double* B, double* w, double* X
     }
   std::vector<double> V((size_t)n * n);
   dense_sym_eig(n, C.data(), w, V.data());
-  // X = R V
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int k = 0; k < n; ++k) s += R[(size_t)k * n + i] * V[(size_t)j * n + k];
-      X[(size_t)j * n + i] = s;
+  // X = R V (column j of X as a sum of columns of R)
+  for (int j = 0; j < n; ++j) {
+    double* xj = X + (size_t)j * n;
+    std::fill(xj, xj + n, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const double f = V[(size_t)j * n + k];
+      const double* rk = R.data() + (size_t)k * n;
+      for (int i = 0; i < n; ++i) xj[i] += rk[i] * f;
     }
+  }
   return true;
 }
 

@@ -614,10 +614,12 @@ struct LobpcgRun {
             if (t == 0.0) continue;
             for (int i = 0; i < n; ++i) GT[(size_t)j * n + i] += Gm[(size_t)k * n + i] * t;
           }
+        // T is block diagonal (blocks of nb): column i of T is nonzero only in i's block
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
+            const int kb = (i / nb) * nb, ke = std::min(n, kb + nb);
             double acc = 0.0;
-            for (int k = 0; k < n; ++k) acc += Tm[(size_t)i * n + k] * GT[(size_t)j * n + k];
+            for (int k = kb; k < ke; ++k) acc += Tm[(size_t)i * n + k] * GT[(size_t)j * n + k];
             out[(size_t)j * n + i] = acc;
           }
         return out;

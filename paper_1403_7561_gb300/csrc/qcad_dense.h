@@ -58,7 +58,7 @@ void launch_random_block(long long n, int m, long long ld, const unsigned char* 
 // Host dense routines on column-major n x n matrices (n <= QCAD_DENSE_MAXP).
 // Cholesky A = L L^T in place (lower); returns false if A is not numerically SPD.
 bool dense_cholesky(int n, double* A);
-// Symmetric eigen-decomposition by cyclic Jacobi rotations: A is destroyed,
+// Symmetric eigen-decomposition (Householder tridiagonalization, implicit QR): A is destroyed,
 // w ascending eigenvalues, V column eigenvectors.
 void dense_sym_eig(int n, double* A, double* w, double* V);
 // Generalized symmetric-definite problem A x = lam B x via Cholesky of B:
