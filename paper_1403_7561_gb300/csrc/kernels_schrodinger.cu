@@ -1008,6 +1008,37 @@ __global__ void random_block_kernel(long long n, int m, long long ld, const unsi
   }
 }
 
+// Smooth starting block: column j is the box mode sin(pi a x) sin(pi b y) sin(pi c z) (a, b, c =
+// modes[j], x, y, z the node's fractional position in the nx x ny x nz-element box) plus eps times
+// the random entries of random_block_kernel, on interior nodes.
+template <class T>
+__global__ void box_mode_block_kernel(long long n, int m, long long ld, int nx, int ny, int nz, BoxModes modes,
+                                      double eps, const unsigned char* interior, uint64_t seed, T* X) {
+  const long long total = n * (long long)m;
+  const double pi = 3.14159265358979323846;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t % n;
+    const int j = (int)(t / n);
+    const int i = (int)(r % (nx + 1)), jy = (int)((r / (nx + 1)) % (ny + 1)), k = (int)(r / ((long long)(nx + 1) * (ny + 1)));
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    const double v = sin(pi * modes.a[j] * i / nx) * sin(pi * modes.b[j] * jy / ny) * sin(pi * modes.c[j] * k / nz);
+    X[j * ld + r] = interior[r] ? (T)(v + eps * u) : T(0);
+  }
+}
+
+template <class T>
+void launch_box_mode_block(long long n, int m, long long ld, int nx, int ny, int nz, const BoxModes& modes, double eps,
+                           const unsigned char* interior, uint64_t seed, T* X, cudaStream_t s) {
+  note_launch(), box_mode_block_kernel<T><<<dblocks(n * m), DT, 0, s>>>(n, m, ld, nx, ny, nz, modes, eps, interior,
+                                                                          seed, X);
+}
+template void launch_box_mode_block<float>(long long, int, long long, int, int, int, const BoxModes&, double,
+                                           const unsigned char*, uint64_t, float*, cudaStream_t);
+
 template <class T>
 void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, T* X,
                          cudaStream_t s) {

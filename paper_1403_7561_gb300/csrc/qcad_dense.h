@@ -51,6 +51,13 @@ void launch_cheb_block_step(long long n, int m, long long ld, const T* HD, const
                             T* W, T* D, T* Z, cudaStream_t s);
 template <class T>
 void launch_power_sub(long long n, const T* v, const T* Hv, const T* dinv, T* vn, double* acc, cudaStream_t s);
+// Box modes (a, b, c) >= 1 of the columns of a smooth starting block (at most 32 columns).
+struct BoxModes {
+  int a[32], b[32], c[32];
+};
+template <class T>
+void launch_box_mode_block(long long n, int m, long long ld, int nx, int ny, int nz, const BoxModes& modes, double eps,
+                           const unsigned char* interior, uint64_t seed, T* X, cudaStream_t s);
 template <class T>
 void launch_random_block(long long n, int m, long long ld, const unsigned char* interior, uint64_t seed, T* X,
                          cudaStream_t s);
