@@ -1015,7 +1015,6 @@ template <class T>
 __global__ void box_mode_block_kernel(long long n, int m, long long ld, int nx, int ny, int nz, BoxModes modes,
                                       double eps, const unsigned char* interior, uint64_t seed, T* X) {
   const long long total = n * (long long)m;
-  const double pi = 3.14159265358979323846;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const long long r = t % n;
     const int j = (int)(t / n);
@@ -1025,7 +1024,9 @@ __global__ void box_mode_block_kernel(long long n, int m, long long ld, int nx, 
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-    const double v = sin(pi * modes.a[j] * i / nx) * sin(pi * modes.b[j] * jy / ny) * sin(pi * modes.c[j] * k / nz);
+    // a starting guess: FP32 (the FP64 sine runs on the FP64 pipe)
+    const float v = sinpif((float)(modes.a[j] * i) / nx) * sinpif((float)(modes.b[j] * jy) / ny) *
+                    sinpif((float)(modes.c[j] * k) / nz);
     X[j * ld + r] = interior[r] ? (T)(v + eps * u) : T(0);
   }
 }
