@@ -246,7 +246,8 @@ qcad_status qcad_schrodinger_apply(qcad_mesh_t m, const qcad_bias* b, const doub
 
 /* Lowest nev eigenpairs of H psi = E M psi on the subdomain by LOBPCG with a
  * degree-5 Chebyshev-Jacobi preconditioner and FP64 Rayleigh-Ritz (the paper uses an Anasazi
- * eigensolver, Sec. II.B). phi: device [n_nodes]. evals: host [nev], eV,
+ * eigensolver, Sec. II.B), started from the subdomain box's lowest sine modes; an FP32 phase,
+ * then FP64 vectors with double-float H/M applies, Gram products and block updates. phi: device [n_nodes]. evals: host [nev], eV,
  * ascending. evecs: device [n_sub_dof x nev] column-major, M-orthonormal, or
  * NULL. tol: relative residual ||H x - E M x|| / (|E| ||M x||) per pair.
  * Errors: NOT_CONVERGED (best pairs returned), INVALID_ARG (no subdomain,
@@ -329,8 +330,8 @@ qcad_status qcad_adjoint_eigs(qcad_mesh_t m, const qcad_bias* b, const qcad_solv
  * apply launch and one update launch (o->cheb_degree 1; chunks of 8 iterations
  * replayed from a captured CUDA graph), or (o->cheb_degree 0 or -1, every mesh
  * large enough for a coarse level) as each instance's multigrid-preconditioned
- * PCG, its captured 4-iteration graph replayed back to back with the others'
- * and one status read per round. Instances drop out on their own
+ * PCG, its captured 4-iteration graph replayed together with the others' on a
+ * pool of streams (instances run side by side) and one status read per round. Instances drop out on their own
  * device-resident convergence flags. ms, bs, phis: host arrays of n entries
  * (phis[i] device [n_nodes of ms[i]], FP64, also the warm start). reps: host
  * [n] or NULL. o->precision must be 1 (mixed). All meshes must be distinct and
