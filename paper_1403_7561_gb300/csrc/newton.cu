@@ -1211,20 +1211,39 @@ static void adjoint_prepare(AdjWork& A, qcad_mesh_s* m, const qcad_bias* b, cons
                           m->d_yn.as<double>(), m->d_zn.as<double>(), P, m->dots, d, have ? box : nullptr,
                           G + (size_t)d * n, m->el_res.as<double>(), s);
   }
-  // gate lifts e_g: their raw J e_g (shared by every dot) and dN_d/dphi . e_g before masking
+  // gate lifts e_g: their raw J e_g (shared by every dot) and dN_d/dphi . e_g before masking. e_g
+  // lives on the top node plane, so J e_g vanishes below plane nz-1: it is applied on the view of
+  // the top element layer (the same products as the whole mesh's apply there), and the dots run
+  // over the top plane
+  const Grid<double>& g64 = m->g64.g;
+  const int kl = m->nz - 1;
+  Grid<double> gtop = g64;
+  gtop.nz = 1;
+  gtop.nzn = 2;
+  gtop.mzx = g64.mzx + 3 * kl;
+  gtop.mzy = g64.mzy + 3 * kl;
+  gtop.kzz = g64.kzz + 3 * kl;
+  gtop.zt = g64.zt ? g64.zt + 12 * kl : nullptr;
+  gtop.hz = g64.hz + kl;
+  gtop.dir_bottom = 0;
+  const long long plane = g64.plane, off = (long long)kl * plane, top = (long long)m->nz * plane;
+  const size_t coff = (size_t)8 * kl * m->nx * m->ny;
+  CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));
   for (int gi = 0; gi < ng; ++gi) {
-    CK(cudaMemsetAsync(eg, 0, n * sizeof(double), s));
+    CK(cudaMemsetAsync(eg + top, 0, plane * sizeof(double), s));
     for (int q = 0; q < ng; ++q) m->h_small[16 + q] = q == gi ? 1.0 : 0.0;
     CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * ng, cudaMemcpyHostToDevice, s));
     launch_set_dirichlet(m->nxn, m->nyn, m->nzn, 0, 0.0, m->d_gate_top.as<signed char>(), m->d_vgate.as<double>(),
                          eg, s);
+    double* je = JE + (size_t)gi * n;
+    CK(cudaMemsetAsync(je, 0, n * sizeof(double), s));
     ApplyArgs<double> a{};
-    a.v = eg;
-    a.y = JE + (size_t)gi * n;
-    a.c = ensure_pcg<double>(m).c;
+    a.v = eg + off;
+    a.y = je + off;
+    a.c = ensure_pcg<double>(m).c + coff;
     a.raw = 1;
-    launch_apply<double>(m->g64.g, a, m->cfg64, s, Prec<double>::face(m));
-    for (int d = 0; d < nd; ++d) launch_dot<double>(n, G + (size_t)d * n, eg, acc + d * ng + gi, s);
+    launch_apply<double>(gtop, a, m->cfg64, s, Prec<double>::face(m));
+    for (int d = 0; d < nd; ++d) launch_dot<double>(plane, G + (size_t)d * n + top, eg + top, acc + d * ng + gi, s);
     CK(cudaStreamSynchronize(s));  // h_small is reused by the next gate's upload
   }
   // zero the Dirichlet rows of the right-hand sides
