@@ -367,12 +367,14 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   a.phi = phi;
   a.theta = theta;
   a.R = m->R.as<double>();
-  if (prec == 0) {
+  // prec 0: the FP64 linearization, 1: the FP32 one, 2: both from the one evaluation
+  if (prec == 0 || prec == 2) {
     PcgVecs<double> v = ensure_pcg<double>(m);
     a.c64 = const_cast<double*>(v.c);
     a.dinv64 = const_cast<double*>(v.dinv);
     a.b64 = const_cast<double*>(v.b);
-  } else {
+  }
+  if (prec == 1 || prec == 2) {
     PcgVecs<float> v = ensure_pcg<float>(m);
     a.c32 = const_cast<float*>(v.c);
     a.dinv32 = const_cast<float*>(v.dinv);
@@ -400,7 +402,8 @@ static ResStats eval_residual(qcad_mesh_s* m, const Phys& P, const double* phi, 
   if (m->prof.on) m->prof.begin(PROF_RESIDUAL, s, pp);
   m->el_res.ensure((size_t)16 * m->n_elems * sizeof(double) + 64);
   launch_residual_2pass(m->g64.g, a, m->el_res.as<double>(), m->cfg_res, s, Prec<double>::face(m));
-  m->lin_ver[prec == 0 ? 0 : 1] += 1;  // the stored linearization changed
+  if (prec != 1) m->lin_ver[0] += 1;  // the stored linearizations changed
+  if (prec != 0) m->lin_ver[1] += 1;
   if (m->prof.on) m->prof.end(pp, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(m->h_small, a.stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1190,13 +1193,13 @@ static void adjoint_prepare(AdjWork& A, qcad_mesh_s* m, const qcad_bias* b, cons
   A.P = make_phys(m, b);
   const Phys& P = A.P;
   // linearization at phi in FP64 (and FP32 for the mixed refinement)
-  eval_residual(m, P, phi, theta, 0, 0, nullptr);
-  if (o->precision == 1) eval_residual(m, P, phi, theta, 0, 1, nullptr);
-  A.work.ensure((size_t)(2 * nd + std::max(ng, 1) + 1) * n * sizeof(double) + 64);
+  eval_residual(m, P, phi, theta, 0, o->precision == 1 ? 2 : 0, nullptr);
+  const long long plane2 = 2LL * m->nxn * m->nyn;  // the top two node planes
+  A.work.ensure(((size_t)(2 * nd + 1) * n + (size_t)std::max(ng, 1) * plane2) * sizeof(double) + 64);
   double* G = A.G = A.work.as<double>();    // nd right-hand sides dN_d/dphi
   A.LAM = G + (size_t)nd * n;               // nd adjoint solutions
-  double* JE = A.JE = A.LAM + (size_t)nd * n;  // ng raw J e_g
-  double* eg = A.eg = JE + (size_t)std::max(ng, 1) * n;
+  double* eg = A.eg = A.LAM + (size_t)nd * n;
+  double* JE = A.JE = eg + n;  // ng raw J e_g on planes nz-1, nz (zero below)
   const size_t nacc = (size_t)2 * nd * ng + QCAD_MAX_GATES + 1;
   A.accs.ensure(nacc * sizeof(double) + 64);
   double* acc = A.acc = A.accs.as<double>();  // [0, nd*ng): dN/dphi_D . e_g; then lam_d . J e_g
@@ -1235,11 +1238,11 @@ static void adjoint_prepare(AdjWork& A, qcad_mesh_s* m, const qcad_bias* b, cons
     CK(cudaMemcpyAsync(m->d_vgate.p, m->h_small + 16, sizeof(double) * ng, cudaMemcpyHostToDevice, s));
     launch_set_dirichlet(m->nxn, m->nyn, m->nzn, 0, 0.0, m->d_gate_top.as<signed char>(), m->d_vgate.as<double>(),
                          eg, s);
-    double* je = JE + (size_t)gi * n;
-    CK(cudaMemsetAsync(je, 0, n * sizeof(double), s));
+    double* je = JE + (size_t)gi * plane2;
+    CK(cudaMemsetAsync(je, 0, plane2 * sizeof(double), s));
     ApplyArgs<double> a{};
     a.v = eg + off;
-    a.y = je + off;
+    a.y = je;
     a.c = ensure_pcg<double>(m).c + coff;
     a.raw = 1;
     launch_apply<double>(gtop, a, m->cfg64, s, Prec<double>::face(m));
@@ -1259,16 +1262,18 @@ static void adjoint_finish(AdjWork& A, double* dN_dV, double* dN_dq) {
   const long long n = m->n_nodes;
   const int nd = A.nd, ng = A.ng;
   double* acc = A.acc;
+  // J e_g vanishes below plane nz-1
+  const long long plane = (long long)m->nxn * m->nyn, off = (long long)(m->nz - 1) * plane;
   for (int d = 0; d < nd; ++d)
     for (int gi = 0; gi < ng; ++gi)
-      launch_dot<double>(n, A.LAM + (size_t)d * n, A.JE + (size_t)gi * n, acc + nd * ng + d * ng + gi, s);
+      launch_dot<double>(2 * plane, A.LAM + (size_t)d * n + off, A.JE + (size_t)gi * 2 * plane,
+                         acc + nd * ng + d * ng + gi, s);
   // charged gates (Robin condition): V_g enters through the load, d b / d V_g = (eps_r/d) int_f N_a
   // on the gate's faces (top plane), so dN_d/dV_g gains lam_d . d b / d V_g (lam is 0 on Dirichlet rows)
   const int nc = (int)m->charged_gate.size();
   DevBuf racc;
   std::vector<double> hr((size_t)std::max(1, nd * nc), 0.0);
   if (nc > 0) {
-    const long long plane = (long long)m->nxn * m->nyn;
     racc.ensure((size_t)nd * nc * sizeof(double) + 64);
     CK(cudaMemsetAsync(racc.p, 0, (size_t)nd * nc * sizeof(double), s));
     for (int d = 0; d < nd; ++d)
