@@ -863,6 +863,30 @@ template void launch_lobpcg_update<float>(long long, int, int, float*, long long
 template void launch_lobpcg_update<double>(long long, int, int, double*, long long, const double*, cudaStream_t, int,
                                            long long);
 
+template <class T>
+__global__ void __launch_bounds__(256) move_cols_kernel(long long n, T* S, long long ld, const ColMoves mv,
+                                                        long long bstride) {
+  S += blockIdx.y * bstride;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    T v[40];
+#pragma unroll
+    for (int t = 0; t < 40; ++t)
+      if (t < mv.n) v[t] = S[mv.src[t] * ld + r];
+#pragma unroll
+    for (int t = 0; t < 40; ++t)
+      if (t < mv.n) S[mv.dst[t] * ld + r] = v[t];
+  }
+}
+
+template <class T>
+void launch_move_cols(long long n, T* S, long long ld, const ColMoves& mv, cudaStream_t s, int nbase,
+                      long long bstride) {
+  if (mv.n <= 0 || mv.n > 40) return;  // the caller checks n <= 40
+  note_launch(), move_cols_kernel<T><<<dim3(dblocks(n), std::max(1, nbase)), 256, 0, s>>>(n, S, ld, mv, bstride);
+}
+template void launch_move_cols<float>(long long, float*, long long, const ColMoves&, cudaStream_t, int, long long);
+template void launch_move_cols<double>(long long, double*, long long, const ColMoves&, cudaStream_t, int, long long);
+
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms[2j] += |R_j|^2,
 // norms[2j+1] += |MX_j|^2 (FP64 sums per thread, reduced per block, one atomic per block).
 template <class T>

@@ -293,11 +293,11 @@ struct ChebPre {
     theta = 0.5 * (a + b);
     delta = 0.5 * (b - a);
   }
-  // Z = p_k(D^-1 H) D^-1 R for nb columns (Z may alias R). Each step's H apply carries the
-  // recurrence in its epilogue, the direction block alternating between D and HD.
-  void apply(const float* R, float* Z) {
+  // Z = p_k(D^-1 H) D^-1 R for nvec <= nb columns (Z may alias R). Each step's H apply carries
+  // the recurrence in its epilogue, the direction block alternating between D and HD.
+  void apply(const float* R, float* Z, int nvec) {
     cudaStream_t s = io.s;
-    launch_cheb_block_init<float>(ns, nb, ns, R, dinv, 1.0 / theta, W, D, Z, s);
+    launch_cheb_block_init<float>(ns, nvec, ns, R, dinv, 1.0 / theta, W, D, Z, s);
     const double sigma = theta / delta;
     double rho_prev = 1.0 / sigma, rho = rho_prev;
     float *dcur = D, *dnext = HD;
@@ -312,7 +312,7 @@ struct ChebPre {
       a.dinv = dinv;
       a.cV = S->cV32.as<float>();
       a.ld = ns;
-      a.nvec = nb;
+      a.nvec = nvec;
       a.c1 = (float)(rho * rho_prev);
       a.c2 = (float)(2.0 * rho / delta);
       launch_cheb_hm_step(S->g32.g, a, s);
@@ -321,11 +321,12 @@ struct ChebPre {
   }
 };
 
-// FP32 preconditioning of a residual block stored in precision T.
-static void precondition_block(ChebPre& P, float* Rb, long long) { P.apply(Rb, Rb); }
-static void precondition_block(ChebPre& P, double* Rb, long long tot) {
+// FP32 preconditioning of nvec residual columns (ns rows each) stored in precision T.
+static void precondition_block(ChebPre& P, float* Rb, int nvec) { P.apply(Rb, Rb, nvec); }
+static void precondition_block(ChebPre& P, double* Rb, int nvec) {
+  const long long tot = P.ns * nvec;
   launch_d2f(tot, Rb, P.R32, P.io.s);
-  P.apply(P.R32, P.R32);
+  P.apply(P.R32, P.R32, nvec);
   launch_f2d(tot, P.R32, Rb, P.io.s);
 }
 
@@ -333,10 +334,10 @@ static void precondition_block(ChebPre& P, double* Rb, long long tot) {
 // FP64 to polish). The blocks S = [X | W | P], HS = H S, MS = M S are kept
 // together (column-major, ns x 3nb each) so that the Rayleigh-Ritz Gram
 // matrices of H and M are one kernel launch; all block updates are row-wise
-// in place. An iteration synchronizes with the host twice: after the Gram
-// matrix of [W P] (the residual norms of the previous Ritz pairs come back
-// with it) and after the Rayleigh-Ritz Gram matrices. Small matrices travel
-// through pinned host buffers, so the block combinations need no wait.
+// in place. An iteration synchronizes with the host twice: after the residual
+// norms of the Ritz pairs (which decide convergence and the active columns)
+// and after the Rayleigh-Ritz Gram matrices. Small matrices travel through
+// pinned host buffers, so the block combinations need no wait.
 template <class T>
 struct LobpcgRun {
   qcad_mesh_s* m = nullptr;
@@ -369,14 +370,16 @@ struct LobpcgRun {
 
   T* blk(T* base, int b) { return base + (long long)b * ns * nb; }
 
-  void apply(int b) {
+  // H and M of the first nvec columns of block b (all nb by default).
+  void apply(int b, int nvec = 0) {
+    if (nvec <= 0) nvec = nb;
     HmArgs<T> a{};
     a.x = blk(Sx, b);
     a.hx = blk(HS, b);
     a.mx = blk(MS, b);
     a.cV = cv();
     a.ld = ns;
-    a.nvec = nb;
+    a.nvec = nvec;
     a.mscale = S->inv_kx;
     Profiler::Pair pp;
     if (m->prof.on) m->prof.begin(PROF_HM, s, pp);
@@ -391,7 +394,7 @@ struct LobpcgRun {
       launch_hm_apply<T>(grid(), a, LaunchCfg{8, 16}, s);
     }
     if (m->prof.on) m->prof.end(pp, s);
-    applies += nb;
+    applies += nvec;
   }
   static bool use_df_apply() {
     static const bool df = std::getenv("QCAD_LOBPCG_NATIVE64") == nullptr;
@@ -407,6 +410,11 @@ struct LobpcgRun {
   static constexpr double DF_FLOOR = 1e-9;
   bool df_ok = true;
   bool fresh64 = false;  // the run ended right after an FP64 refresh and Rayleigh-Ritz step
+  // Soft locking (the FP64 phase): columns whose residual is at or below the tolerance get no W
+  // and P directions. In the FP32 phase the tolerance sits near the single-precision floor, where
+  // locked columns are pulled back up by the rotations of the others and the iteration loses
+  // stability, so that phase keeps every column active.
+  bool soft_lock = false;
   const T* cv();
   const Grid<T>& grid();
 
@@ -464,18 +472,41 @@ struct LobpcgRun {
     lam.assign(w.begin(), w.end());
   }
 
-  // W = D^-1 (H X - M X diag(lam)) (or its Chebyshev-Jacobi preconditioning) into block 1 and
-  // the residual norms of the Ritz pairs,
-  // copied to the pinned buffer (read after the next synchronization).
+  // The residuals H X - M X diag(lam) of all nb Ritz pairs into block 1 (times D^-1 when the
+  // preconditioner is plain Jacobi) and their norms, copied to the pinned buffer (read after the
+  // next synchronization).
+  bool cheb() const { return pre && pre->k >= 2; }
   void residual(DevBuf& lam_d, DevBuf& norms_d) {
     std::copy(lam.begin(), lam.end(), h_lam());
     CK(cudaMemcpyAsync(lam_d.p, h_lam(), nb * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(norms_d.p, 0, 2 * nb * sizeof(double), s));
-    const bool cheb = pre && pre->k >= 2;
-    launch_residual_block<T>(ns, nb, blk(HS, 0), blk(MS, 0), ns, lam_d.as<double>(), cheb ? nullptr : dinv,
+    launch_residual_block<T>(ns, nb, blk(HS, 0), blk(MS, 0), ns, lam_d.as<double>(), cheb() ? nullptr : dinv,
                              blk(Sx, 1), norms_d.as<double>(), s);
     CK(cudaMemcpyAsync(h_norms(), norms_d.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (cheb) precondition_block(*pre, blk(Sx, 1), ns * nb);
+  }
+  // Soft locking: the W and P directions of the active columns `act` (residual above the phase's
+  // tolerance) only, packed after X: W to columns [nb, nb + na), P (if present, from block 2) to
+  // [nb + na, nb + 2 na), in S and (P) in H S and M S. The Ritz vectors of locked columns stay in X
+  // and in every Rayleigh-Ritz step.
+  void pack_active(const std::vector<int>& act, bool haveP) {
+    const int na = (int)act.size();
+    ColMoves ms{}, mp{};
+    for (int t = 0; t < na; ++t)
+      if (act[t] != t) {
+        ms.src[ms.n] = (short)(nb + act[t]);
+        ms.dst[ms.n++] = (short)(nb + t);
+      }
+    if (haveP)
+      for (int t = 0; t < na; ++t) {
+        const int src = 2 * nb + act[t], dst = nb + na + t;
+        if (src == dst) continue;
+        ms.src[ms.n] = mp.src[mp.n] = (short)src;
+        ms.dst[ms.n++] = mp.dst[mp.n++] = (short)dst;
+      }
+    if (ms.n > 40) throw Error(QCAD_ERR_INVALID_ARG, "LOBPCG: more than 40 column moves");
+    launch_move_cols<T>(ns, Sx, ns, ms, s, 1, 0);
+    launch_move_cols<T>(ns, HS, ns, mp, s, 2, (long long)3 * nb * ns);
+    if (cheb()) precondition_block(*pre, blk(Sx, 1), na);
   }
   // Relative residuals ||H x - lam M x|| / (|lam| ||M x||) from the copied norms; true when the
   // first nev are <= tol.
@@ -514,18 +545,16 @@ struct LobpcgRun {
     int since = 0;
     for (int it = 1; it <= maxit + 1; ++it) {
       residual(lam_d, norms_d);
-      apply(1);
-      // Rayleigh-Ritz Gram matrices of [X W P] with W and P as they are: the Cholesky QR of W and
-      // of P is applied to the small matrices on the host (G -> T^T G T), which gives the
-      // Rayleigh-Ritz problem of the orthonormalized blocks without forming them
-      int nuse = haveP ? 3 * nb : 2 * nb;
-      const bool up = gram_upper() && nuse % 4 == 0;
-      gram_async(nuse, nuse, Sx, HS, MS, up);
       sync();
-      const bool conv = converged(tol);
+      bool conv = converged(tol);
       if (debug_level() >= 2)
         std::fprintf(stderr, "[qcad] lobpcg %s it %d worst %.3e\n", sizeof(T) == 4 ? "fp32" : "fp64", it,
                      *std::max_element(rel.begin(), rel.begin() + nev));
+      if (debug_level() >= 3) {
+        std::fprintf(stderr, "[qcad]   rel");
+        for (int i = 0; i < nb; ++i) std::fprintf(stderr, " %.1e", rel[i]);
+        std::fprintf(stderr, "\n");
+      }
       if constexpr (sizeof(T) == 8) {
         if (df_ok && use_df_apply() &&
             (conv || *std::max_element(rel.begin(), rel.begin() + nev) < DF_FLOOR)) {
@@ -540,7 +569,7 @@ struct LobpcgRun {
             fresh64 = true;  // X, H X, M X and the eigenvalues are FP64 Rayleigh-Ritz results
             return true;
           }
-          continue;
+          conv = false;
         }
       }
       if (conv) return true;
@@ -564,22 +593,38 @@ struct LobpcgRun {
           return false;
         }
       }
+      // the active columns (with soft locking those with a residual above tol, at least one; else
+      // all): the basis is [X, W, P] with na columns each of W and P
+      std::vector<int> act;
+      for (int j = 0; j < nb; ++j)
+        if (!soft_lock || !(rel[j] <= tol)) act.push_back(j);
+      if (act.empty()) act.push_back(nb - 1);
+      const int na = (int)act.size();
+      pack_active(act, haveP);
+      apply(1, na);
+      // Rayleigh-Ritz Gram matrices of [X W P] with W and P as they are: the Cholesky QR of W and
+      // of P is applied to the small matrices on the host (G -> T^T G T), which gives the
+      // Rayleigh-Ritz problem of the orthonormalized blocks without forming them
+      int nuse = haveP ? nb + 2 * na : nb + na;
+      const bool up = gram_upper() && nuse % 4 == 0;
+      gram_async(nuse, nuse, Sx, HS, MS, up);
+      sync();
       ++iters;
       const auto th = std::chrono::steady_clock::now();
       std::vector<double> GH = gram_sym(nuse, 0, up), GM = gram_sym(nuse, (size_t)nuse * nuse, up), RW, RP;
-      if (!chol_inv(GM, nuse, nb, nb, RW)) {
+      if (!chol_inv(GM, nuse, nb, na, RW)) {
         // W lost rank: restart it from a random block (and drop P)
         haveP = false;
-        nuse = 2 * nb;
-        launch_random_block<T>(ns, nb, ns, S->interior.as<unsigned char>(), 0xABCDEF00ull + iters, blk(Sx, 1), s);
-        apply(1);
+        nuse = nb + na;
+        launch_random_block<T>(ns, na, ns, S->interior.as<unsigned char>(), 0xABCDEF00ull + iters, blk(Sx, 1), s);
+        apply(1, na);
         gram_async(nuse, nuse, Sx, HS, MS);
         sync();
         GH = gram_sym(nuse, 0);
         GM = gram_sym(nuse, (size_t)nuse * nuse);
-        if (!chol_inv(GM, nuse, nb, nb, RW)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
+        if (!chol_inv(GM, nuse, nb, na, RW)) throw Error(QCAD_ERR_NONFINITE, "LOBPCG: W block lost rank");
       }
-      if (haveP && !chol_inv(GM, nuse, 2 * nb, nb, RP)) haveP = false;
+      if (haveP && !chol_inv(GM, nuse, nb + na, na, RP)) haveP = false;
       // T = diag(I, RW, RP): the basis [X, W RW, P RP] has unit M-Gram blocks on its diagonal
       auto reduce_to = [&](int n2) {
         if (n2 == nuse) return;
@@ -593,17 +638,20 @@ struct LobpcgRun {
         GM.swap(gm2);
         nuse = n2;
       };
-      if (!haveP) reduce_to(2 * nb);
+      if (!haveP) reduce_to(nb + na);
       auto make_T = [&]() {
         std::vector<double> Tq((size_t)nuse * nuse, 0.0);
         for (int i = 0; i < nb; ++i) Tq[(size_t)i * nuse + i] = 1.0;
-        for (int j = 0; j < nb; ++j)
-          for (int i = 0; i < nb; ++i) {
-            Tq[(size_t)(nb + j) * nuse + nb + i] = RW[(size_t)j * nb + i];
-            if (nuse == 3 * nb) Tq[(size_t)(2 * nb + j) * nuse + 2 * nb + i] = RP[(size_t)j * nb + i];
+        for (int j = 0; j < na; ++j)
+          for (int i = 0; i < na; ++i) {
+            Tq[(size_t)(nb + j) * nuse + nb + i] = RW[(size_t)j * na + i];
+            if (nuse == nb + 2 * na) Tq[(size_t)(nb + na + j) * nuse + nb + na + i] = RP[(size_t)j * na + i];
           }
         return Tq;
       };
+      // the diagonal block of T holding row/column i: [0, nb), [nb, nb + na) or [nb + na, nuse)
+      auto blk_lo = [&](int i) { return i < nb ? 0 : (i < nb + na ? nb : nb + na); };
+      auto blk_hi = [&](int i) { return i < nb ? nb : (i < nb + na ? nb + na : nuse); };
       // G' = T^T G T (column-major n x n)
       auto congruence = [&](const std::vector<double>& Tm, const std::vector<double>& Gm) {
         const int n = nuse;
@@ -614,10 +662,10 @@ struct LobpcgRun {
             if (t == 0.0) continue;
             for (int i = 0; i < n; ++i) GT[(size_t)j * n + i] += Gm[(size_t)k * n + i] * t;
           }
-        // T is block diagonal (blocks of nb): column i of T is nonzero only in i's block
+        // T is block diagonal: column i of T is nonzero only in i's block
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
-            const int kb = (i / nb) * nb, ke = std::min(n, kb + nb);
+            const int kb = blk_lo(i), ke = blk_hi(i);
             double acc = 0.0;
             for (int k = kb; k < ke; ++k) acc += Tm[(size_t)i * n + k] * GT[(size_t)j * n + k];
             out[(size_t)j * n + i] = acc;
@@ -629,7 +677,7 @@ struct LobpcgRun {
       bool ok = dense_gen_eig(nuse, GHt.data(), GMt.data(), w.data(), Ct.data());
       if (!ok && haveP) {
         haveP = false;
-        reduce_to(2 * nb);
+        reduce_to(nb + na);
         Tm = make_T();
         GHt = congruence(Tm, GH);
         GMt = congruence(Tm, GM);
@@ -660,7 +708,8 @@ struct LobpcgRun {
           if (c == 0.0) continue;
           for (int i = 0; i < nuse; ++i) C[(size_t)j * nuse + i] += Tm[(size_t)k * nuse + i] * c;
         }
-      // new P = [W P] C[nb:, :nb] and new X = X C[:nb, :nb] + new P, in one pass over the rows
+      // new P = [W P] C[nb:, :nb] (all nb columns, into block 2) and new X = X C[:nb, :nb] + new P,
+      // in one pass over the rows
       t_host += std::chrono::duration<double>(std::chrono::steady_clock::now() - th).count();
       for (size_t t = 0; t < (size_t)nuse * nb; ++t) hC[t] = (T)C[t];
       CK(cudaMemcpyAsync(Cd, hC, (size_t)nuse * nb * sizeof(T), cudaMemcpyHostToDevice, s));
@@ -810,6 +859,7 @@ qcad_status schrodinger_eigs_io(qcad_mesh_s* m, const EigIo& io, const qcad_bias
   LobpcgRun<double> B;
   init_run<double>(B, m, io, &S, nb, nev, w64, S.dinv.as<double>());
   B.pre = &pre;
+  B.soft_lock = !(std::getenv("QCAD_LOBPCG_LOCK") && std::string(std::getenv("QCAD_LOBPCG_LOCK")) == "0");
   pre.set_degree(deg64);
   launch_f2d(ns * nb, A.Sx, B.Sx, s);
   B.apply(0);

@@ -33,10 +33,20 @@ size_t gram_part_doubles(int p, int q);
 // p <= 64. nbase > 1: the same C applied to nbase block sets, set b at A, Y1, Y2 + b * bstride.
 // LOBPCG update of [X | W | P] (nb columns each at stride ld; nbase block sets bstride elements
 // apart): P' = [W P] Cz, X' = X Cx + P' in place, with C = [Cx; Cz] the (nb + nz) x nb coefficients
-// of the first nb Ritz vectors (column-major); nz = nb (no P block) or 2 nb; nb <= 20.
+// of the first nb Ritz vectors (column-major); nz <= 2 nb (the W and P columns in use); nb <= 20.
 template <class T>
 void launch_lobpcg_update(long long n, int nb, int nz, T* S, long long ld, const T* C, cudaStream_t s, int nbase,
                           long long bstride);
+// Column moves within column-major blocks: column src[t] to column dst[t] for t < n (n <= 40),
+// each row's sources read before any of its destinations is written, so sources and
+// destinations may overlap; nbase block sets bstride elements apart, as launch_lobpcg_update.
+struct ColMoves {
+  int n;
+  short src[40], dst[40];
+};
+template <class T>
+void launch_move_cols(long long n, T* S, long long ld, const ColMoves& mv, cudaStream_t s, int nbase,
+                      long long bstride);
 template <class T>
 void launch_combine(long long n, int p, int q, int q1, const T* A, long long lda, const T* C, T* Y1, T* Y2,
                     long long ldy, cudaStream_t s, int nbase = 1, long long bstride = 0);
