@@ -781,6 +781,9 @@ __global__ void __launch_bounds__(256, (NBX <= 12 ? 2 : 1)) lobpcg_update_df_ker
   float* sCxl = sCxh + (size_t)nq * px;
   float* sCzh = sCxl + (size_t)nq * px;            // [nq][pz]
   float* sCzl = sCzh + (size_t)nq * pz;
+  // the next row of each thread, staged by cp.async while the current one is combined:
+  // [NBX + NZX][blockDim.x] doubles (column-major over the threads: conflict-free accesses)
+  double* stg = reinterpret_cast<double*>(su_raw + (((size_t)nq * (px + pz) * 2 * sizeof(float) + 15) & ~(size_t)15));
   for (int t = threadIdx.x; t < nq * px; t += blockDim.x) {
     const int j = t / px, i = t % px;
     df_split((i < nb && j < nb) ? C[j * nuse + i] : 0.0, sCxh[t], sCxl[t]);
@@ -792,12 +795,34 @@ __global__ void __launch_bounds__(256, (NBX <= 12 ? 2 : 1)) lobpcg_update_df_ker
   __syncthreads();
   double* X = S;
   double* P = S + 2 * (long long)nb * ld;
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const long long stride = (long long)gridDim.x * bd;
+  auto prefetch = [&](long long row) {
+    if (row < n) {
+      for (int i = 0; i < nb; ++i) gram_cp<double>(stg + (size_t)i * bd + tid, X + i * ld + row, true);
+      for (int i = 0; i < nz; ++i) gram_cp<double>(stg + (size_t)(NBX + i) * bd + tid, S + (nb + i) * ld + row, true);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  long long r = blockIdx.x * (long long)bd + tid;
+  prefetch(r);
+  for (; r < n; r += stride) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // this thread's staged row into registers (padding columns are zeros without a split: a zero
+    // would take the FP64 conversion), then the next row's copies into the freed stage (issue is
+    // in order, so they start after these reads have completed)
     float axh[NBX], axl[NBX], azh[NZX], azl[NZX];
 #pragma unroll
-    for (int i = 0; i < NBX; ++i) df_split_i(i < nb ? X[i * ld + r] : 0.0, axh[i], axl[i]);
+    for (int i = 0; i < NBX; ++i) {
+      axh[i] = axl[i] = 0.0f;
+      if (i < nb) df_split_i(stg[(size_t)i * bd + tid], axh[i], axl[i]);
+    }
 #pragma unroll
-    for (int i = 0; i < NZX; ++i) df_split_i(i < nz ? S[(nb + i) * ld + r] : 0.0, azh[i], azl[i]);
+    for (int i = 0; i < NZX; ++i) {
+      azh[i] = azl[i] = 0.0f;
+      if (i < nz) df_split_i(stg[(size_t)(NBX + i) * bd + tid], azh[i], azl[i]);
+    }
+    prefetch(r + stride);
     for (int j0 = 0; j0 < nb; j0 += 4) {
       float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -834,6 +859,7 @@ __global__ void __launch_bounds__(256, (NBX <= 12 ? 2 : 1)) lobpcg_update_df_ker
         if (j0 + u < nb) X[(j0 + u) * ld + r] = df_join(sh[u], sl[u]);
     }
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <class T>
@@ -844,11 +870,24 @@ void launch_lobpcg_update(long long n, int nb, int nz, T* S, long long ld, const
   const bool small = nb <= 12 && nz <= 24;
   if constexpr (std::is_same<T, double>::value) {
     if (dense_df()) {
-      const size_t shm = (size_t)nq * (px + pz) * 2 * sizeof(float);
+      // persistent: one wave of resident blocks over the nbase block sets, each thread walking
+      // rows with the next one staged in shared memory
+      const size_t tab = (((size_t)nq * (px + pz) * 2 * sizeof(float) + 15) & ~(size_t)15);
+      const size_t shm = tab + (size_t)(small ? 36 : 60) * 256 * sizeof(double);
+      static bool attr = false;
+      if (!attr)  // a failure shows as the launch's error, which the callers check
+        attr = cudaFuncSetAttribute(lobpcg_update_df_kernel<12, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    100 * 1024) == cudaSuccess &&
+               cudaFuncSetAttribute(lobpcg_update_df_kernel<20, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    150 * 1024) == cudaSuccess;
+      const long long rows = (n + 255) / 256;
+      const int per_sm = small ? 2 : 1;
+      const int gx = (int)std::max<long long>(1, std::min<long long>(rows, (long long)152 * per_sm / std::max(1, nbase)));
+      const dim3 pgrid(gx, std::max(1, nbase));
       if (small)
-        note_launch(), lobpcg_update_df_kernel<12, 24><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+        note_launch(), lobpcg_update_df_kernel<12, 24><<<pgrid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
       else
-        note_launch(), lobpcg_update_df_kernel<20, 40><<<grid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
+        note_launch(), lobpcg_update_df_kernel<20, 40><<<pgrid, 256, shm, s>>>(n, nb, nz, S, ld, C, bstride);
       return;
     }
   }
@@ -889,48 +928,63 @@ template void launch_move_cols<double>(long long, double*, long long, const ColM
 
 // R[:, j] = HX[:, j] - lam_j MX[:, j]; W[:, j] = dinv o R[:, j]; norms[2j] += |R_j|^2,
 // norms[2j+1] += |MX_j|^2 (FP64 sums per thread, reduced per block, one atomic per block).
-template <class T>
-__global__ void __launch_bounds__(256) residual_block_kernel(long long n, int m, const T* HX, const T* MX,
+template <class T, int MB>
+__global__ void __launch_bounds__(256, 2) residual_block_kernel(long long n, int m, const T* HX, const T* MX,
                                                              long long ld, const double* lam, const T* dinv, T* W,
                                                              double* norms) {
-  __shared__ double red[2][8];
+  // one pass over the rows for all m <= MB columns: each thread's sums for every column stay in
+  // registers, then one block reduction (FP64) and 2m atomics per block. A thread's sums cover a
+  // handful of rows and are kept in the storage precision: FP32 to FP64 conversions run on the
+  // FP64 pipe, which would bind this kernel with two of them per element.
+  __shared__ double red[2 * MB][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = 0; j < m; ++j) {
-    double r2 = 0.0, m2 = 0.0;
-    const T l = (T)lam[j];
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
-         r += (long long)gridDim.x * blockDim.x) {
-      const T mx = MX[j * ld + r];
-      const T res = HX[j * ld + r] - l * mx;
-      W[j * ld + r] = dinv ? dinv[r] * res : res;
-      r2 += (double)res * (double)res;
-      m2 += (double)mx * (double)mx;
-    }
-    r2 = warp_sum(r2);
-    m2 = warp_sum(m2);
-    if (lane == 0) {
-      red[0][warp] = r2;
-      red[1][warp] = m2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        a += red[0][w];
-        b += red[1][w];
+  T r2[MB], m2[MB];
+  T l[MB];
+#pragma unroll
+  for (int j = 0; j < MB; ++j) {
+    r2[j] = T(0);
+    m2[j] = T(0);
+    l[j] = j < m ? (T)lam[j] : T(0);
+  }
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    const T dr = dinv ? dinv[r] : T(1);
+#pragma unroll
+    for (int j = 0; j < MB; ++j) {
+      if (j < m) {
+        const T mx = MX[j * ld + r];
+        const T res = HX[j * ld + r] - l[j] * mx;
+        W[j * ld + r] = dinv ? dr * res : res;
+        r2[j] += res * res;
+        m2[j] += mx * mx;
       }
-      atomicAdd(norms + 2 * j, a);
-      atomicAdd(norms + 2 * j + 1, b);
     }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < MB; ++j) {
+    if (j < m) {
+      const double a = warp_sum((double)r2[j]), b = warp_sum((double)m2[j]);
+      if (lane == 0) {
+        red[2 * j][warp] = a;
+        red[2 * j + 1][warp] = b;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * m) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[threadIdx.x][w];
+    atomicAdd(norms + threadIdx.x, a);
   }
 }
 
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s) {
-  const int nb = (int)std::min<long long>(2 * 152, (n + 255) / 256);
-  note_launch(), residual_block_kernel<T><<<std::max(nb, 1), 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
+  const int nb = std::max(1, (int)std::min<long long>(2 * 152, (n + 255) / 256));
+  if (m <= 12)
+    note_launch(), residual_block_kernel<T, 12><<<nb, 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
+  else
+    note_launch(), residual_block_kernel<T, 20><<<nb, 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
 }
 template void launch_residual_block<float>(long long, int, const float*, const float*, long long, const double*,
                                            const float*, float*, double*, cudaStream_t);

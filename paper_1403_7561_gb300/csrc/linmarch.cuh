@@ -412,10 +412,10 @@ __device__ __forceinline__ void lin_body(const Grid<T>& g, const Op& op_in, int 
 }
 
 // Resident blocks per SM the register allocation is held to: 32 warps per SM for FP32 with one
-// row per thread, 16 with two, 16 (FP64, one row) and at least one block otherwise.
+// row per thread, 20 with two, 16 (FP64, one row) and at least one block otherwise.
 template <class T, int BY, int R>
 constexpr int lin_min_blocks() {
-  return sizeof(T) == 4 ? ((R == 1 ? 1024 : 512) / (32 * BY) > 0 ? (R == 1 ? 1024 : 512) / (32 * BY) : 1)
+  return sizeof(T) == 4 ? ((R == 1 ? 1024 : 640) / (32 * BY) > 0 ? (R == 1 ? 1024 : 640) / (32 * BY) : 1)
                         : (R == 1 && 512 / (32 * BY) > 0 ? 512 / (32 * BY) : 1);
 }
 
