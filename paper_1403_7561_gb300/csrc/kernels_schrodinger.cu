@@ -933,9 +933,10 @@ __global__ void __launch_bounds__(256, 2) residual_block_kernel(long long n, int
                                                              long long ld, const double* lam, const T* dinv, T* W,
                                                              double* norms) {
   // one pass over the rows for all m <= MB columns: each thread's sums for every column stay in
-  // registers, then one block reduction (FP64) and 2m atomics per block. A thread's sums cover a
-  // handful of rows and are kept in the storage precision: FP32 to FP64 conversions run on the
-  // FP64 pipe, which would bind this kernel with two of them per element.
+  // registers, then one block reduction and 2m atomics per block. A thread's sums (a few rows) and
+  // the warp's reduction stay in the storage precision, the warps' partials are added in FP64: on
+  // this part FP64 arithmetic and the FP32 to FP64 conversions run on the narrow FP64 pipe, which
+  // per-element or per-lane FP64 work would make the bound of this kernel.
   __shared__ double red[2 * MB][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T r2[MB], m2[MB];
@@ -962,10 +963,15 @@ __global__ void __launch_bounds__(256, 2) residual_block_kernel(long long n, int
 #pragma unroll
   for (int j = 0; j < MB; ++j) {
     if (j < m) {
-      const double a = warp_sum((double)r2[j]), b = warp_sum((double)m2[j]);
+      T a = r2[j], b = m2[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL_MASK, a, o);
+        b += __shfl_xor_sync(FULL_MASK, b, o);
+      }
       if (lane == 0) {
-        red[2 * j][warp] = a;
-        red[2 * j + 1][warp] = b;
+        red[2 * j][warp] = (double)a;
+        red[2 * j + 1][warp] = (double)b;
       }
     }
   }
@@ -980,7 +986,9 @@ __global__ void __launch_bounds__(256, 2) residual_block_kernel(long long n, int
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s) {
-  const int nb = std::max(1, (int)std::min<long long>(2 * 152, (n + 255) / 256));
+  // at least eight rows per thread (the reductions cost as much as a few rows), at most two
+  // resident blocks per SM
+  const int nb = std::max(1, (int)std::min<long long>(2 * 152, (n + 2047) / 2048));
   if (m <= 12)
     note_launch(), residual_block_kernel<T, 12><<<nb, 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
   else
