@@ -986,9 +986,11 @@ __global__ void __launch_bounds__(256, 2) residual_block_kernel(long long n, int
 template <class T>
 void launch_residual_block(long long n, int m, const T* HX, const T* MX, long long ld, const double* lam,
                            const T* dinv, T* W, double* norms, cudaStream_t s) {
-  // at least eight rows per thread (the reductions cost as much as a few rows), at most two
-  // resident blocks per SM
-  const int nb = std::max(1, (int)std::min<long long>(2 * 152, (n + 2047) / 2048));
+  // one block per SM at least (the loads of a thread's rows are its only latency cover), up to
+  // two resident blocks per SM with eight rows per thread or more (the reductions cost as much as
+  // a few rows)
+  const int nb = (int)std::max<long long>(std::min<long long>(152, (n + 255) / 256),
+                                          std::min<long long>(2 * 152, (n + 2047) / 2048));
   if (m <= 12)
     note_launch(), residual_block_kernel<T, 12><<<nb, 256, 0, s>>>(n, m, HX, MX, ld, lam, dinv, W, norms);
   else
