@@ -247,7 +247,9 @@ qcad_status qcad_schrodinger_apply(qcad_mesh_t m, const qcad_bias* b, const doub
 /* Lowest nev eigenpairs of H psi = E M psi on the subdomain by LOBPCG with a
  * degree-5 Chebyshev-Jacobi preconditioner and FP64 Rayleigh-Ritz (the paper uses an Anasazi
  * eigensolver, Sec. II.B), started from the subdomain box's lowest sine modes; an FP32 phase,
- * then FP64 vectors with double-float H/M applies, Gram products and block updates. phi: device [n_nodes]. evals: host [nev], eV,
+ * then FP64 vectors with double-float H/M applies, Gram products and block updates, where
+ * columns already at tol get no new search directions (soft locking; QCAD_LOBPCG_LOCK=0 turns
+ * it off). phi: device [n_nodes]. evals: host [nev], eV,
  * ascending. evecs: device [n_sub_dof x nev] column-major, M-orthonormal, or
  * NULL. tol: relative residual ||H x - E M x|| / (|E| ||M x||) per pair.
  * Errors: NOT_CONVERGED (best pairs returned), INVALID_ARG (no subdomain,
