@@ -92,6 +92,24 @@ def test_lobpcg_matches_oracle_eigenpairs(q, dqd):
         start = end
 
 
+def test_lobpcg_soft_locking_leaves_the_eigenpairs(q, dqd, monkeypatch):
+    # soft locking (columns of the FP64 phase already at the tolerance get no new search
+    # directions) changes the work per iteration, not the answer: with and without it the
+    # eigenvalues match the oracle's and each other
+    dev, P, phi = dqd
+    nev = 6
+    Eo = OS.solve_device(P, phi, nev=nev)[0]
+    m = q.qcad_mesh_create(dev)
+    got = {}
+    for lock in ("1", "0"):
+        monkeypatch.setenv("QCAD_LOBPCG_LOCK", lock)
+        E, rep = q.qcad_schrodinger_eigs(m, dev["bias"], dt(phi), nev=nev, tol=1e-8)
+        assert rep["status"] == "OK", (lock, rep)
+        got[lock] = np.array(E)
+        assert np.max(np.abs(got[lock] - Eo) / np.abs(Eo)) < 1e-9, lock
+    assert np.max(np.abs(got["1"] - got["0"]) / np.abs(Eo)) < 1e-9
+
+
 def test_particle_in_box_closed_form(q):
     # vacuum-flat potential: a linear solve with equal gate voltages and no charge gives V ~ const near the top;
     # use an all-Si slab with grounded contacts so phi = phi_ohm everywhere and V is constant
